@@ -1,0 +1,221 @@
+"""Plain FP64 CPU oracle for the voxel bidomain/monodomain time step.
+
+TEST INFRASTRUCTURE ONLY: imported by ``tests/``, by ``__graft_entry__.smoke``
+and by the CPU-baseline leg of ``bench.py``.  The product (the CUDA library and
+its binding) never imports, links or runs anything from this package.
+
+The arithmetic lives in ``ep_oracle.c`` (plain C, FP64, written from the
+thesis' definitions; see its header for every equation it follows).  This
+module only builds it with gcc and marshals numpy arrays through ctypes.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+from typing import Optional, Tuple
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "ep_oracle.c")
+_LIB_PATH = os.path.join(_HERE, "libep_oracle.so")
+_lib = None
+
+OG_MONO = 0
+OG_BI = 1
+
+
+def build(force: bool = False) -> str:
+    """Compile ep_oracle.c into libep_oracle.so (gcc, OpenMP, no FP contraction)."""
+    if not force and os.path.exists(_LIB_PATH) and \
+            os.path.getmtime(_LIB_PATH) >= max(os.path.getmtime(_SRC),
+                                               os.path.getmtime(os.path.join(_HERE, "ep_oracle.h"))):
+        return _LIB_PATH
+    tmp = _LIB_PATH + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-std=c99", "-fopenmp", "-ffp-contract=off", "-fPIC", "-shared",
+           "-o", tmp, _SRC, "-lm"]
+    subprocess.run(cmd, check=True, cwd=_HERE)
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+class _Grid(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+                ("dx", ctypes.c_double), ("mask", ctypes.c_void_p), ("fib", ctypes.c_void_p)]
+
+
+class _Params(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_double) for n in
+                ("tau_in", "tau_out", "tau_open", "tau_close", "v_gate",
+                 "sig_iL", "sig_iT", "sig_eL", "sig_eT", "lam", "K", "dt", "omega", "rel_tol")] + \
+               [("check_every", ctypes.c_int), ("max_iter", ctypes.c_int), ("model", ctypes.c_int)]
+
+
+class _Stim(ctypes.Structure):
+    _fields_ = [("lo", ctypes.c_int * 3), ("hi", ctypes.c_int * 3),
+                ("t_start", ctypes.c_double), ("dur", ctypes.c_double), ("amp", ctypes.c_double)]
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        build()
+        L = ctypes.CDLL(_LIB_PATH)
+        vp, dp, ip = ctypes.c_void_p, ctypes.c_double, ctypes.c_int
+        L.og_apply_L.argtypes = [ctypes.POINTER(_Grid), dp, dp, vp, vp]
+        L.og_diag_L.argtypes = [ctypes.POINTER(_Grid), dp, dp, vp]
+        L.og_components.argtypes = [ctypes.POINTER(_Grid), vp]
+        L.og_components.restype = ip
+        L.og_jacobi.argtypes = [ctypes.POINTER(_Grid), dp, dp, vp, vp, dp, dp, ip, ip,
+                                ctypes.POINTER(ip), ctypes.POINTER(dp)]
+        L.og_jacobi.restype = ip
+        L.og_default_omega.argtypes = [dp, dp]
+        L.og_default_omega.restype = dp
+        L.og_create.argtypes = [ip, ip, ip, dp, vp, vp, ctypes.POINTER(_Params),
+                                ctypes.POINTER(_Stim), ip]
+        L.og_create.restype = vp
+        L.og_destroy.argtypes = [vp]
+        L.og_set_state.argtypes = [vp, vp, vp, vp, ctypes.c_long]
+        L.og_get_state.argtypes = [vp, vp, vp, vp, vp, ctypes.POINTER(ctypes.c_long)]
+        L.og_step.argtypes = [vp, ctypes.POINTER(ip), ctypes.POINTER(dp)]
+        L.og_step.restype = ip
+        L.og_run.argtypes = [vp, ip, ctypes.POINTER(ip), ctypes.POINTER(dp)]
+        L.og_run.restype = ip
+        L.og_ncomp.argtypes = [vp]
+        L.og_ncomp.restype = ip
+        L.og_total_iters.argtypes = [vp]
+        L.og_total_iters.restype = ctypes.c_long
+        L.og_num_threads.restype = ip
+        _lib = L
+    return _lib
+
+
+def _ptr(a: np.ndarray) -> int:
+    return a.ctypes.data
+
+
+class Grid:
+    """Holds contiguous FP64 copies of a mask and fibre field."""
+
+    def __init__(self, nx: int, ny: int, nz: int, dx: float, mask, fib):
+        self.nx, self.ny, self.nz, self.dx = nx, ny, nz, float(dx)
+        self.mask = np.ascontiguousarray(np.asarray(mask).reshape(-1), dtype=np.uint8)
+        self.fib = np.ascontiguousarray(np.asarray(fib, dtype=np.float64).reshape(-1))
+        assert self.mask.size == nx * ny * nz and self.fib.size == 3 * nx * ny * nz
+        self._g = _Grid(nx, ny, nz, self.dx, _ptr(self.mask), _ptr(self.fib))
+
+    @classmethod
+    def from_case(cls, case) -> "Grid":
+        return cls(case.nx, case.ny, case.nz, case.dx, case.mask, case.fib)
+
+    @property
+    def n(self) -> int:
+        return self.nx * self.ny * self.nz
+
+    def apply_L(self, sL: float, sT: float, u) -> np.ndarray:
+        u = np.ascontiguousarray(np.asarray(u, dtype=np.float64).reshape(-1))
+        out = np.zeros(self.n)
+        lib().og_apply_L(ctypes.byref(self._g), sL, sT, _ptr(u), _ptr(out))
+        return out
+
+    def diag_L(self, sL: float, sT: float) -> np.ndarray:
+        out = np.zeros(self.n)
+        lib().og_diag_L(ctypes.byref(self._g), sL, sT, _ptr(out))
+        return out
+
+    def components(self) -> Tuple[int, np.ndarray]:
+        comp = np.zeros(self.n, np.int32)
+        nc = lib().og_components(ctypes.byref(self._g), _ptr(comp))
+        return nc, comp
+
+    def jacobi(self, sL, sT, b, x0, omega=0.0, tol=1e-6, m=10, max_iter=100000):
+        b = np.ascontiguousarray(np.asarray(b, dtype=np.float64).reshape(-1))
+        x = np.ascontiguousarray(np.array(x0, dtype=np.float64).reshape(-1))
+        it = ctypes.c_int(0)
+        rr = ctypes.c_double(0.0)
+        st = lib().og_jacobi(ctypes.byref(self._g), sL, sT, _ptr(b), _ptr(x), omega, tol, m,
+                             max_iter, ctypes.byref(it), ctypes.byref(rr))
+        return x, it.value, rr.value, st
+
+
+def _params_struct(p, model: int) -> _Params:
+    return _Params(p.tau_in, p.tau_out, p.tau_open, p.tau_close, p.v_gate,
+                   p.sig_iL, p.sig_iT, p.sig_eL, p.sig_eT, p.lam, p.K, p.dt, p.omega,
+                   p.rel_tol, int(p.check_every), int(p.max_iter), int(model))
+
+
+class Sim:
+    """FP64 oracle simulation of one case (see workloads.Case)."""
+
+    def __init__(self, case, params=None, model: Optional[int] = None):
+        self.case = case
+        self.grid = Grid.from_case(case)
+        p = params if params is not None else case.params
+        self.model = case.model if model is None else model
+        self._p = _params_struct(p, self.model)
+        st = (_Stim * max(1, len(case.stimuli)))()
+        for i, s in enumerate(case.stimuli):
+            st[i].lo[:] = list(s.lo)
+            st[i].hi[:] = list(s.hi)
+            st[i].t_start, st[i].dur, st[i].amp = s.t_start, s.dur, s.amp
+        self._st = st
+        self._h = lib().og_create(case.nx, case.ny, case.nz, float(case.dx),
+                                  _ptr(self.grid.mask), _ptr(self.grid.fib),
+                                  ctypes.byref(self._p), st, len(case.stimuli))
+        self.last_iters = 0
+        self.last_relres = 0.0
+
+    def close(self):
+        if self._h:
+            lib().og_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def ncomp(self) -> int:
+        return lib().og_ncomp(self._h)
+
+    @property
+    def total_iters(self) -> int:
+        return lib().og_total_iters(self._h)
+
+    def set_state(self, v=None, w=None, ve=None, step: int = 0):
+        arrs = [None if a is None else np.ascontiguousarray(np.asarray(a, np.float64).reshape(-1))
+                for a in (v, w, ve)]
+        lib().og_set_state(self._h, *[None if a is None else _ptr(a) for a in arrs], int(step))
+
+    def state(self):
+        n = self.grid.n
+        v, w, ve, ta = (np.zeros(n) for _ in range(4))
+        step = ctypes.c_long(0)
+        lib().og_get_state(self._h, _ptr(v), _ptr(w), _ptr(ve), _ptr(ta), ctypes.byref(step))
+        return {"v": v, "w": w, "ve": ve, "tact": ta, "step": step.value}
+
+    def step(self) -> int:
+        it = ctypes.c_int(0)
+        rr = ctypes.c_double(0.0)
+        st = lib().og_step(self._h, ctypes.byref(it), ctypes.byref(rr))
+        self.last_iters, self.last_relres = it.value, rr.value
+        return st
+
+    def run(self, nsteps: int) -> int:
+        it = ctypes.c_int(0)
+        rr = ctypes.c_double(0.0)
+        st = lib().og_run(self._h, int(nsteps), ctypes.byref(it), ctypes.byref(rr))
+        self.last_iters, self.last_relres = it.value, rr.value
+        return st
+
+
+def num_threads() -> int:
+    return lib().og_num_threads()
+
+
+def vm_mV(v):
+    """Transmembrane potential in mV from dimensionless v (V_m = 100 v - 80)."""
+    return 100.0 * np.asarray(v) - 80.0

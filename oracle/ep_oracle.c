@@ -1,0 +1,564 @@
+/*
+ * ep_oracle.c -- plain FP64 CPU oracle for the voxel bidomain/monodomain step.
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the independent reference that the
+ * CUDA path is checked against.  Only tests, the smoke check and the CPU
+ * baseline leg of the benchmark load it.  It shares no code, header, table or
+ * helper with the CUDA library.
+ *
+ * Everything is written directly from the thesis' definitions, in FP64, with
+ * no blocking, fusion or reordering beyond what the definitions state:
+ *
+ *  - Mitchell-Schaeffer ionic model, Eqs. ms1/ms2 (Sec. "Mitchell-Schaeffer
+ *    Model"), integrated with one explicit Euler step (Sec. "Algorithm
+ *    Details / Electrophysiology / Reaction").  Reading: the closing branch of
+ *    Eq. ms2 is -w/tau_close (the printed (1-w)/tau_close can never
+ *    repolarise), and the printed w-update "w = v + dt dw/dt" is read as
+ *    w + dt dw/dt.
+ *  - Conductivity tensor Sigma = sT I + (sL - sT) f f^T, Eq. sigma1; sT I
+ *    where the fibre is zero (Sec. "Fibre Directions").
+ *  - Self-dual Laplacian (Sec. "Operators / Laplacian", Eqs. refgrad2,
+ *    refdiv2/3, refintp2): the gradient of the voxel field at every grid vertex
+ *    is the average of the edge differences of the 2x2x2 voxel block around the
+ *    vertex; the conductivity tensor at the vertex is the average over the
+ *    block (non-tissue voxels contribute zero conductivity); the divergence
+ *    at a voxel sums the face-averaged fluxes.  Written as L = G'^T S G'
+ *    (matrix-free assembly of Sec. "Matrix-Free Assembly", Eq. ass3, with
+ *    F = dx I so the scale is 1/dx^2).  No-flux at the tissue mask: a voxel pair
+ *    contributes to a vertex gradient only if both voxels are tissue, and the
+ *    average is over the contributing pairs.  L u approximates -div(Sigma grad u).
+ *  - Operator splitting (Sec. "Algorithm Details / Electrophysiology"):
+ *    reaction, then diffusion, then (bidomain) the elliptic equation of
+ *    Eq. bidomain1 (second line).  Diffusion is explicit Euler.
+ *      monodomain  v+ = v* - dt/K * lambda/(1+lambda) * L_i v*     (Eq. monodomain1)
+ *      bidomain    v+ = v* - dt/K * L_i (v* + ve^n)                (Eq. bidomain1, line 1)
+ *                  (L_i + L_e) ve^{n+1} = -L_i v+                   (Eq. bidomain1, line 2)
+ *  - Elliptic solve by damped Jacobi, Eq. dampjac1, from the previous ve,
+ *    stopping when ||b - A x||_2 <= tol ||b||_2 (checked every m sweeps), then
+ *    the reference potential is fixed by subtracting the mean over every
+ *    face-connected tissue component (the pure-Neumann null space).
+ *
+ * Units: mm, ms, mS/mm; v dimensionless (0 rest, 1 peak).
+ * Index: q = i + nx*(j + ny*k).
+ */
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#include "ep_oracle.h"
+
+/* ------------------------------------------------------------------------ */
+/* grid helpers                                                              */
+/* ------------------------------------------------------------------------ */
+
+static long og_idx(const og_grid *g, int i, int j, int k)
+{
+    return (long)i + (long)g->nx * ((long)j + (long)g->ny * (long)k);
+}
+
+static int og_tissue(const og_grid *g, int i, int j, int k)
+{
+    if (i < 0 || j < 0 || k < 0 || i >= g->nx || j >= g->ny || k >= g->nz)
+        return 0;
+    return g->mask[og_idx(g, i, j, k)] != 0;
+}
+
+/* Offsets of the two voxels of pair number p (0..3) along axis a, inside the
+ * 2x2x2 block of vertex (I,J,K).  The block voxels are (I-1+s, J-1+t, K-1+u)
+ * with s,t,u in {0,1}; along axis a the pair is (lo: offset 0, hi: offset 1)
+ * and p enumerates the offsets of the two other axes. */
+static void og_pair(int I, int J, int K, int a, int p, int lo[3], int hi[3])
+{
+    int o1 = p & 1, o2 = (p >> 1) & 1;
+    int base[3] = {I - 1, J - 1, K - 1};
+    int b1 = (a + 1) % 3, b2 = (a + 2) % 3;
+    lo[0] = base[0]; lo[1] = base[1]; lo[2] = base[2];
+    lo[b1] += o1;
+    lo[b2] += o2;
+    hi[0] = lo[0]; hi[1] = lo[1]; hi[2] = lo[2];
+    hi[a] += 1;
+}
+
+/* Vertex data: per axis the number of valid pairs, and the block tensor
+ * S_p = (1/8) sum_{tissue j in block} Sigma_j. */
+static void og_vertex_tensor(const og_grid *g, int I, int J, int K, double sL, double sT,
+                             double S[3][3])
+{
+    int a, b, s, t, u;
+    for (a = 0; a < 3; a++)
+        for (b = 0; b < 3; b++)
+            S[a][b] = 0.0;
+    for (u = 0; u < 2; u++)
+        for (t = 0; t < 2; t++)
+            for (s = 0; s < 2; s++) {
+                int i = I - 1 + s, j = J - 1 + t, k = K - 1 + u;
+                if (!og_tissue(g, i, j, k))
+                    continue;
+                const double *f = g->fib + 3 * og_idx(g, i, j, k);
+                for (a = 0; a < 3; a++)
+                    for (b = 0; b < 3; b++)
+                        S[a][b] += (a == b ? sT : 0.0) + (sL - sT) * f[a] * f[b];
+            }
+    for (a = 0; a < 3; a++)
+        for (b = 0; b < 3; b++)
+            S[a][b] *= 0.125;
+}
+
+static int og_count_pairs(const og_grid *g, int I, int J, int K, int a)
+{
+    int p, n = 0, lo[3], hi[3];
+    for (p = 0; p < 4; p++) {
+        og_pair(I, J, K, a, p, lo, hi);
+        if (og_tissue(g, lo[0], lo[1], lo[2]) && og_tissue(g, hi[0], hi[1], hi[2]))
+            n++;
+    }
+    return n;
+}
+
+/* Contribution of vertex (I,J,K) to out = L u:  g = G'_p u, F = S_p g,
+ * out += G'_p^T F. */
+static void og_vertex_apply(const og_grid *g, int I, int J, int K, double sL, double sT,
+                            const double *u, double *out)
+{
+    double S[3][3], grad[3], F[3];
+    int np[3], a, b, p, lo[3], hi[3];
+    for (a = 0; a < 3; a++) {
+        double sum = 0.0;
+        np[a] = 0;
+        for (p = 0; p < 4; p++) {
+            og_pair(I, J, K, a, p, lo, hi);
+            if (og_tissue(g, lo[0], lo[1], lo[2]) && og_tissue(g, hi[0], hi[1], hi[2])) {
+                sum += u[og_idx(g, hi[0], hi[1], hi[2])] - u[og_idx(g, lo[0], lo[1], lo[2])];
+                np[a]++;
+            }
+        }
+        grad[a] = np[a] ? sum / (np[a] * g->dx) : 0.0;
+    }
+    if (!np[0] && !np[1] && !np[2])
+        return;
+    og_vertex_tensor(g, I, J, K, sL, sT, S);
+    for (a = 0; a < 3; a++) {
+        F[a] = 0.0;
+        for (b = 0; b < 3; b++)
+            F[a] += S[a][b] * grad[b];
+    }
+    for (a = 0; a < 3; a++) {
+        if (!np[a])
+            continue;
+        double wgt = F[a] / (np[a] * g->dx);
+        for (p = 0; p < 4; p++) {
+            og_pair(I, J, K, a, p, lo, hi);
+            if (og_tissue(g, lo[0], lo[1], lo[2]) && og_tissue(g, hi[0], hi[1], hi[2])) {
+                out[og_idx(g, hi[0], hi[1], hi[2])] += wgt;
+                out[og_idx(g, lo[0], lo[1], lo[2])] -= wgt;
+            }
+        }
+    }
+}
+
+/* Contribution of vertex (I,J,K) to the diagonal of L: for every tissue voxel q
+ * of the block, c = d g_p / d u_q and diag_q += c^T S_p c. */
+static void og_vertex_diag(const og_grid *g, int I, int J, int K, double sL, double sT,
+                           double *diag)
+{
+    double S[3][3];
+    int np[3], a, b, s, t, u;
+    for (a = 0; a < 3; a++)
+        np[a] = og_count_pairs(g, I, J, K, a);
+    if (!np[0] && !np[1] && !np[2])
+        return;
+    og_vertex_tensor(g, I, J, K, sL, sT, S);
+    for (u = 0; u < 2; u++)
+        for (t = 0; t < 2; t++)
+            for (s = 0; s < 2; s++) {
+                int q[3] = {I - 1 + s, J - 1 + t, K - 1 + u};
+                int off[3] = {s, t, u};
+                double c[3], acc = 0.0;
+                if (!og_tissue(g, q[0], q[1], q[2]))
+                    continue;
+                for (a = 0; a < 3; a++) {
+                    /* partner of q along a inside the block */
+                    int r[3] = {q[0], q[1], q[2]};
+                    r[a] += off[a] ? -1 : 1;
+                    c[a] = 0.0;
+                    if (np[a] && og_tissue(g, r[0], r[1], r[2]))
+                        c[a] = (off[a] ? 1.0 : -1.0) / (np[a] * g->dx);
+                }
+                for (a = 0; a < 3; a++)
+                    for (b = 0; b < 3; b++)
+                        acc += c[a] * S[a][b] * c[b];
+                diag[og_idx(g, q[0], q[1], q[2])] += acc;
+            }
+}
+
+/* Vertex planes K and K+2 touch disjoint voxel planes, so the scatter runs
+ * over even planes, then odd planes; every voxel gets its two contributions
+ * in the same order whatever the thread count. */
+void og_apply_L(const og_grid *g, double sL, double sT, const double *u, double *out)
+{
+    long n = (long)g->nx * g->ny * g->nz;
+    int color;
+    memset(out, 0, sizeof(double) * (size_t)n);
+    for (color = 0; color < 2; color++) {
+        int K;
+#pragma omp parallel for schedule(static)
+        for (K = color; K <= g->nz; K += 2) {
+            int I, J;
+            for (J = 0; J <= g->ny; J++)
+                for (I = 0; I <= g->nx; I++)
+                    og_vertex_apply(g, I, J, K, sL, sT, u, out);
+        }
+    }
+}
+
+void og_diag_L(const og_grid *g, double sL, double sT, double *diag)
+{
+    long n = (long)g->nx * g->ny * g->nz;
+    int color;
+    memset(diag, 0, sizeof(double) * (size_t)n);
+    for (color = 0; color < 2; color++) {
+        int K;
+#pragma omp parallel for schedule(static)
+        for (K = color; K <= g->nz; K += 2) {
+            int I, J;
+            for (J = 0; J <= g->ny; J++)
+                for (I = 0; I <= g->nx; I++)
+                    og_vertex_diag(g, I, J, K, sL, sT, diag);
+        }
+    }
+}
+
+/* Face-connected (6-neighbour) components of the tissue; comp[q] = -1 off tissue. */
+int og_components(const og_grid *g, int *comp)
+{
+    long n = (long)g->nx * g->ny * g->nz, q, head, tail;
+    long *queue = (long *)malloc(sizeof(long) * (size_t)(n > 0 ? n : 1));
+    int ncomp = 0;
+    for (q = 0; q < n; q++)
+        comp[q] = -1;
+    for (q = 0; q < n; q++) {
+        if (!g->mask[q] || comp[q] >= 0)
+            continue;
+        head = tail = 0;
+        queue[tail++] = q;
+        comp[q] = ncomp;
+        while (head < tail) {
+            long c = queue[head++];
+            int i = (int)(c % g->nx), j = (int)((c / g->nx) % g->ny), k = (int)(c / ((long)g->nx * g->ny));
+            int d;
+            for (d = 0; d < 6; d++) {
+                int ii = i + (d == 0) - (d == 1), jj = j + (d == 2) - (d == 3), kk = k + (d == 4) - (d == 5);
+                if (og_tissue(g, ii, jj, kk)) {
+                    long r = og_idx(g, ii, jj, kk);
+                    if (comp[r] < 0) {
+                        comp[r] = ncomp;
+                        queue[tail++] = r;
+                    }
+                }
+            }
+        }
+        ncomp++;
+    }
+    free(queue);
+    return ncomp;
+}
+
+/* x <- x - mean_c(x) on every component c (FP64, plain loop order). */
+static void og_project(long n, int ncomp, const int *comp, double *x)
+{
+    double *sum = (double *)calloc((size_t)(ncomp > 0 ? ncomp : 1), sizeof(double));
+    long *cnt = (long *)calloc((size_t)(ncomp > 0 ? ncomp : 1), sizeof(long));
+    long q;
+    for (q = 0; q < n; q++)
+        if (comp[q] >= 0) {
+            sum[comp[q]] += x[q];
+            cnt[comp[q]]++;
+        }
+    for (q = 0; q < n; q++)
+        if (comp[q] >= 0)
+            x[q] -= sum[comp[q]] / (double)cnt[comp[q]];
+    free(sum);
+    free(cnt);
+}
+
+/* Default damping when the caller passes omega <= 0.  The thesis requires
+ * damping but gives no value.  For a constant tensor with eigenvalues
+ * (sL, sT, sT) the Fourier symbol of L on the infinite grid gives
+ * rho(D^-1 L) <= 4 lambda_max(S) / (tr(S) / 2) = 8 sL / (sL + 2 sT); omega is
+ * chosen so that omega * rho = 1.8 (capped at 1). */
+double og_default_omega(double sL, double sT)
+{
+    double w = 1.8 * (sL + 2.0 * sT) / (8.0 * sL);
+    return w > 1.0 ? 1.0 : w;
+}
+
+/* Damped Jacobi (Eq. dampjac1) for A x = b on the tissue, A = L_{sL,sT}:
+ *   r^k = b - A x^k ;  x^{k+1} = x^k + omega D^{-1} r^k   (x_q kept where D_q = 0).
+ * At k = 0, m, 2m, ... the relative residual ||r^k|| / ||b|| is formed; when it
+ * is <= tol the sweep that used r^k is the last one.  Stops with status 1
+ * after max_iter sweeps.  If ||b|| = 0, x is left unchanged (0 sweeps). */
+int og_jacobi(const og_grid *g, double sL, double sT, const double *b, double *x,
+              double omega, double tol, int m, int max_iter, int *iters, double *relres)
+{
+    long n = (long)g->nx * g->ny * g->nz, q;
+    double *diag = (double *)malloc(sizeof(double) * (size_t)n);
+    double *Ax = (double *)malloc(sizeof(double) * (size_t)n);
+    double nb = 0.0, nr = 0.0;
+    int k = 0, status = 1;
+    for (q = 0; q < n; q++)
+        if (g->mask[q])
+            nb += b[q] * b[q];
+    nb = sqrt(nb);
+    *relres = 0.0;
+    if (nb == 0.0) {
+        *iters = 0;
+        free(diag);
+        free(Ax);
+        return 0;
+    }
+    if (m < 1)
+        m = 1;
+    if (omega <= 0.0)
+        omega = og_default_omega(sL, sT);
+    og_diag_L(g, sL, sT, diag);
+    for (k = 0; k < max_iter; k++) {
+        og_apply_L(g, sL, sT, x, Ax);
+        int check = (k % m) == 0;
+        if (check)
+            nr = 0.0;
+        for (q = 0; q < n; q++) {
+            if (!g->mask[q])
+                continue;
+            double r = b[q] - Ax[q];
+            if (check)
+                nr += r * r;
+            if (diag[q] > 0.0)      /* an isolated voxel has an empty row */
+                x[q] += omega * r / diag[q];
+        }
+        if (check) {
+            *relres = sqrt(nr) / nb;
+            if (*relres <= tol) {
+                status = 0;
+                k++;
+                break;
+            }
+        }
+    }
+    *iters = k;
+    free(diag);
+    free(Ax);
+    return status;
+}
+
+/* ------------------------------------------------------------------------ */
+/* time stepping                                                            */
+/* ------------------------------------------------------------------------ */
+
+struct og_sim {
+    og_grid g;
+    unsigned char *mask;
+    double *fib;
+    og_params p;
+    og_stim *stim;
+    int nstim;
+    long n;
+    int ncomp;
+    int *comp;
+    double *v, *w, *ve, *tact;
+    double *vs, *tmp, *b, *u;
+    long step;
+    long total_iters;
+};
+
+og_sim *og_create(int nx, int ny, int nz, double dx, const unsigned char *mask,
+                  const double *fib, const og_params *p, const og_stim *stim, int nstim)
+{
+    og_sim *s = (og_sim *)calloc(1, sizeof(og_sim));
+    long n = (long)nx * ny * nz, q;
+    s->n = n;
+    s->mask = (unsigned char *)malloc((size_t)n);
+    memcpy(s->mask, mask, (size_t)n);
+    s->fib = (double *)malloc(sizeof(double) * 3 * (size_t)n);
+    memcpy(s->fib, fib, sizeof(double) * 3 * (size_t)n);
+    s->g.nx = nx;
+    s->g.ny = ny;
+    s->g.nz = nz;
+    s->g.dx = dx;
+    s->g.mask = s->mask;
+    s->g.fib = s->fib;
+    s->p = *p;
+    s->nstim = nstim;
+    s->stim = (og_stim *)malloc(sizeof(og_stim) * (size_t)(nstim > 0 ? nstim : 1));
+    if (nstim > 0)
+        memcpy(s->stim, stim, sizeof(og_stim) * (size_t)nstim);
+    s->comp = (int *)malloc(sizeof(int) * (size_t)n);
+    s->ncomp = og_components(&s->g, s->comp);
+    s->v = (double *)calloc((size_t)n, sizeof(double));
+    s->w = (double *)malloc(sizeof(double) * (size_t)n);
+    s->ve = (double *)calloc((size_t)n, sizeof(double));
+    s->tact = (double *)malloc(sizeof(double) * (size_t)n);
+    s->vs = (double *)calloc((size_t)n, sizeof(double));
+    s->tmp = (double *)calloc((size_t)n, sizeof(double));
+    s->b = (double *)calloc((size_t)n, sizeof(double));
+    s->u = (double *)calloc((size_t)n, sizeof(double));
+    for (q = 0; q < n; q++) {
+        s->w[q] = 1.0;
+        s->tact[q] = -1.0;
+    }
+    return s;
+}
+
+void og_destroy(og_sim *s)
+{
+    if (!s)
+        return;
+    free(s->mask);
+    free(s->fib);
+    free(s->stim);
+    free(s->comp);
+    free(s->v);
+    free(s->w);
+    free(s->ve);
+    free(s->tact);
+    free(s->vs);
+    free(s->tmp);
+    free(s->b);
+    free(s->u);
+    free(s);
+}
+
+void og_set_state(og_sim *s, const double *v, const double *w, const double *ve, long step)
+{
+    long q;
+    for (q = 0; q < s->n; q++) {
+        if (!s->mask[q])
+            continue;
+        if (v)
+            s->v[q] = v[q];
+        if (w)
+            s->w[q] = w[q];
+        if (ve)
+            s->ve[q] = ve[q];
+    }
+    s->step = step;
+}
+
+void og_get_state(const og_sim *s, double *v, double *w, double *ve, double *tact, long *step)
+{
+    size_t bytes = sizeof(double) * (size_t)s->n;
+    if (v)
+        memcpy(v, s->v, bytes);
+    if (w)
+        memcpy(w, s->w, bytes);
+    if (ve)
+        memcpy(ve, s->ve, bytes);
+    if (tact)
+        memcpy(tact, s->tact, bytes);
+    if (step)
+        *step = s->step;
+}
+
+int og_ncomp(const og_sim *s) { return s->ncomp; }
+long og_total_iters(const og_sim *s) { return s->total_iters; }
+
+/* One step n -> n+1 (t_n = n dt).  Returns 0, or 1 if the elliptic solve hit
+ * its sweep cap (the step is still completed with the last iterate). */
+int og_step(og_sim *s, int *iters, double *relres)
+{
+    const og_params *p = &s->p;
+    const og_grid *g = &s->g;
+    long q, n = s->n;
+    double tn = (double)s->step * p->dt;
+    int status = 0, si;
+    *iters = 0;
+    *relres = 0.0;
+
+    /* 1. reaction: explicit Euler on (v, w), both from the old state */
+    for (q = 0; q < n; q++) {
+        if (!s->mask[q]) {
+            s->vs[q] = s->v[q];
+            continue;
+        }
+        int i = (int)(q % g->nx), j = (int)((q / g->nx) % g->ny), k = (int)(q / ((long)g->nx * g->ny));
+        double v = s->v[q], w = s->w[q], jst = 0.0;
+        for (si = 0; si < s->nstim; si++) {
+            const og_stim *st = &s->stim[si];
+            if (tn >= st->t_start && tn < st->t_start + st->dur &&
+                i >= st->lo[0] && i < st->hi[0] && j >= st->lo[1] && j < st->hi[1] &&
+                k >= st->lo[2] && k < st->hi[2])
+                jst += st->amp;
+        }
+        double jin = v * v * (1.0 - v) * w / p->tau_in;
+        double jout = -v / p->tau_out;
+        double dw = (v < p->v_gate) ? (1.0 - w) / p->tau_open : -w / p->tau_close;
+        s->vs[q] = v + p->dt * (jin + jout + jst);
+        s->w[q] = w + p->dt * dw;
+    }
+
+    /* 2. parabolic diffusion, explicit Euler */
+    if (p->model == OG_MONO) {
+        og_apply_L(g, p->sig_iL, p->sig_iT, s->vs, s->tmp);
+        double c = p->dt / p->K * p->lam / (1.0 + p->lam);
+        for (q = 0; q < n; q++)
+            if (s->mask[q])
+                s->tmp[q] = s->vs[q] - c * s->tmp[q];
+    } else {
+        for (q = 0; q < n; q++)
+            s->u[q] = s->mask[q] ? s->vs[q] + s->ve[q] : 0.0;
+        og_apply_L(g, p->sig_iL, p->sig_iT, s->u, s->tmp);
+        double c = p->dt / p->K;
+        for (q = 0; q < n; q++)
+            if (s->mask[q])
+                s->tmp[q] = s->vs[q] - c * s->tmp[q];
+    }
+
+    /* activation time: first upward crossing of v = 0.5, linear in t */
+    for (q = 0; q < n; q++) {
+        if (!s->mask[q])
+            continue;
+        double v0 = s->v[q], v1 = s->tmp[q];
+        if (s->tact[q] < 0.0 && v0 < 0.5 && v1 >= 0.5)
+            s->tact[q] = tn + p->dt * (0.5 - v0) / (v1 - v0);
+        s->v[q] = v1;
+    }
+
+    /* 3. elliptic: (L_i + L_e) ve = -L_i v+, zero mean per component */
+    if (p->model == OG_BI) {
+        og_apply_L(g, p->sig_iL, p->sig_iT, s->v, s->b);
+        for (q = 0; q < n; q++)
+            s->b[q] = s->mask[q] ? -s->b[q] : 0.0;
+        og_project(n, s->ncomp, s->comp, s->b);
+        status = og_jacobi(g, p->sig_iL + p->sig_eL, p->sig_iT + p->sig_eT, s->b, s->ve,
+                           p->omega, p->rel_tol, p->check_every, p->max_iter, iters, relres);
+        og_project(n, s->ncomp, s->comp, s->ve);
+        s->total_iters += *iters;
+    }
+    s->step++;
+    return status;
+}
+
+int og_run(og_sim *s, int nsteps, int *last_iters, double *last_relres)
+{
+    int st = 0, k, it = 0;
+    double rr = 0.0;
+    for (k = 0; k < nsteps; k++)
+        st |= og_step(s, &it, &rr);
+    if (last_iters)
+        *last_iters = it;
+    if (last_relres)
+        *last_relres = rr;
+    return st;
+}
+
+int og_num_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}

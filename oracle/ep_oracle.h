@@ -1,0 +1,57 @@
+/*
+ * ep_oracle.h -- interface of the plain FP64 CPU oracle (test infrastructure
+ * only; see ep_oracle.c for the definitions and their sources in the thesis).
+ */
+#ifndef EP_ORACLE_H
+#define EP_ORACLE_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define OG_MONO 0
+#define OG_BI 1
+
+typedef struct {
+    int nx, ny, nz;
+    double dx;                  /* mm */
+    const unsigned char *mask;  /* n, 1 = tissue */
+    const double *fib;          /* 3n, (fx, fy, fz) per voxel; unit or zero */
+} og_grid;
+
+typedef struct {
+    double tau_in, tau_out, tau_open, tau_close, v_gate;
+    double sig_iL, sig_iT, sig_eL, sig_eT;
+    double lam, K, dt, omega, rel_tol;
+    int check_every, max_iter, model;
+} og_params;
+
+typedef struct {
+    int lo[3], hi[3];           /* voxel box [lo, hi) */
+    double t_start, dur, amp;   /* ms, ms, 1/ms */
+} og_stim;
+
+typedef struct og_sim og_sim;
+
+void og_apply_L(const og_grid *g, double sL, double sT, const double *u, double *out);
+void og_diag_L(const og_grid *g, double sL, double sT, double *diag);
+int og_components(const og_grid *g, int *comp);
+double og_default_omega(double sL, double sT);
+int og_jacobi(const og_grid *g, double sL, double sT, const double *b, double *x,
+              double omega, double tol, int m, int max_iter, int *iters, double *relres);
+
+og_sim *og_create(int nx, int ny, int nz, double dx, const unsigned char *mask,
+                  const double *fib, const og_params *p, const og_stim *stim, int nstim);
+void og_destroy(og_sim *s);
+void og_set_state(og_sim *s, const double *v, const double *w, const double *ve, long step);
+void og_get_state(const og_sim *s, double *v, double *w, double *ve, double *tact, long *step);
+int og_step(og_sim *s, int *iters, double *relres);
+int og_run(og_sim *s, int nsteps, int *last_iters, double *last_relres);
+int og_ncomp(const og_sim *s);
+long og_total_iters(const og_sim *s);
+int og_num_threads(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif
