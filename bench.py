@@ -1,0 +1,333 @@
+#!/usr/bin/env python
+"""Throughput of the bidomain voxel time step on one or more GB300 GPUs.
+
+A "step" is one full time step of the hot path (reaction + diffusion kernel,
+elliptic right-hand side, damped-Jacobi solve to rel-residual 1e-6 with FP64
+norms, reference-potential projection) on the whole-heart-scale workload:
+256^3 grid, two truncated ellipsoidal shells (20.3 % tissue), fibres with
+seeded +-5 deg noise, bidomain FP32.  The run starts from rest with the apex
+stimulus at t = 0; W untimed warm-up steps, then K timed steps.
+
+Output: one JSON line (rank 0).  --impl reference times the FP64 CPU oracle
+on a bounded sample of the same workload instead.
+Multi-GPU: one independent replica per rank (the path shards by instance; no
+data-path collective), value = all ranks' voxel-steps / max rank time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+BYTES_PER_SWEEP_VOXEL = 19      # x 4 + b 4 + x' 4 + fibre 6 + mask 1 (algorithmic, per tissue voxel)
+REF_SAMPLE_SWEEPS = (2, 6)      # oracle sweeps timed per sample step (two caps -> per-sweep cost)
+DEFAULT_REF_SWEEPS_PER_STEP = 4000  # elliptic sweeps per step assumed by the reference arm when no GPU figure exists
+
+
+def _args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=["config2", "config1"], default="config2")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--ref-sweeps-per-step", type=float, default=None)
+    return ap.parse_args()
+
+
+def _workload(name):
+    import workloads as W
+    if name == "config1":
+        c = W.config1()
+        desc = "config1: bidomain FP32, 128^3 ellipsoidal shell (55,40,40) wall 10, 9.5% tissue"
+    else:
+        c = W.config2()
+        desc = "config2: bidomain FP32, 256^3 biventricular truncated shells, 20.3% tissue, +-5deg fibre noise"
+    return c, desc
+
+
+def _peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return None
+
+
+def _kernel_hash():
+    h = hashlib.sha256()
+    for p in ("paper_2302_12519_gb300/csrc/ep_kernels.cuh",):
+        h.update(open(os.path.join(ROOT, p), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def _traffic_record(workload):
+    """Per-tissue-voxel DRAM traffic of one sweep launch from the committed ncu
+    summary, if it was taken on the current kernel source."""
+    path = os.path.join(ROOT, "profiles", f"jacobi_sweep_{workload}.md")
+    try:
+        rec = {}
+        for line in open(path):
+            if line.startswith("- ") and ":" in line:
+                k, v = line[2:].split(":", 1)
+                rec[k.strip()] = v.strip().strip("`")
+        if rec.get("kernel_source_sha256_16") != _kernel_hash():
+            return None
+        return float(rec["dram_bytes_per_tissue_voxel"])
+    except Exception:
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def _dist():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def oracle_sample(case, sweeps_per_step, n_samples=1):
+    """Time the FP64 oracle on a bounded sample of one step of the workload:
+    the reaction, diffusion, right-hand-side and projection passes plus two
+    capped Jacobi solves give the fixed and the per-sweep cost; the full step
+    is fixed + sweeps_per_step * per-sweep."""
+    import oracle
+    import workloads as W
+    oracle.build()
+    fixed, per = [], []
+    for _ in range(n_samples):
+        t = []
+        for cap in REF_SAMPLE_SWEEPS:
+            p = W.Params(**{**case.params.__dict__, "max_iter": cap, "check_every": 10 ** 9})
+            sim = oracle.Sim(case, params=p)
+            t0 = time.perf_counter()
+            sim.step()
+            t.append(time.perf_counter() - t0)
+            sim.close()
+        ps = (t[1] - t[0]) / (REF_SAMPLE_SWEEPS[1] - REF_SAMPLE_SWEEPS[0])
+        per.append(max(ps, 1e-9))
+        fixed.append(max(t[0] - REF_SAMPLE_SWEEPS[0] * ps, 0.0))
+    f, p = float(np.median(fixed)), float(np.median(per))
+    step_s = f + sweeps_per_step * p
+    return {"step_s": step_s, "fixed_s": f, "per_sweep_s": p, "cores": oracle.num_threads(),
+            "sample_s": float(sum(fixed) + sum(per) * sum(REF_SAMPLE_SWEEPS))}
+
+
+def run_reference(a):
+    world, rank, local = _dist()
+    if rank != 0:
+        return
+    case, desc = _workload(a.workload)
+    M = case.n_tissue
+    k_ref = a.ref_sweeps_per_step or DEFAULT_REF_SWEEPS_PER_STEP
+    times = []
+    info = None
+    for i in range(a.warmup + a.steps):
+        info = oracle_sample(case, k_ref)
+        if i >= a.warmup:
+            times.append(info["step_s"])
+    tot = sum(times)
+    value = M * a.steps / tot
+    sample = (f"per step: one oracle step of the workload with the Jacobi solve capped at "
+              f"{REF_SAMPLE_SWEEPS[0]} and {REF_SAMPLE_SWEEPS[1]} sweeps (fixed {info['fixed_s']:.2f} s, "
+              f"{info['per_sweep_s']:.3f} s/sweep), extrapolated to {k_ref:.0f} sweeps per step")
+    line = {"impl": "reference", "metric": "voxel-steps/sec", "value": value, "unit": "tissue voxel-steps/s",
+            "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1e3 * tot / a.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": desc, "tissue_voxels": M},
+            "cpu_baseline": {"value": value, "unit": "tissue voxel-steps/s", "cores": info["cores"],
+                             "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "tissue voxel-steps/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(a):
+    import torch
+    import paper_2302_12519_gb300 as ep
+    from paper_2302_12519_gb300 import build as epbuild
+
+    world, rank, local = _dist()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    epbuild.build()
+    case, desc = _workload(a.workload)
+    M = case.n_tissue
+    stream = torch.cuda.Stream()
+    # run on a torch stream so torch events bracket the library's kernels
+    sim = ep.Sim(case.nx, case.ny, case.nz, case.dx, case.model, case.precision, use_torch=True,
+                 stream=stream.cuda_stream)
+    sim.set_mask(case.mask_flat())
+    sim.set_fibres(case.fib_flat())
+    sim.set_params(case.params)
+    for s in case.stimuli:
+        sim.add_stimulus(s.lo, s.hi, s.t_start, s.dur, s.amp)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    for _ in range(a.warmup):
+        sim.step(1, allow_noconv=True)
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    sim.profile_enable(True)
+    clocks = ClockSampler(local)
+    clocks.start()
+    ms = []
+    iters = []
+    statuses = []
+    for _ in range(a.steps):
+        with torch.cuda.stream(stream):
+            flush.fill_(1.0)          # evict L2 (256 MB > 126 MB) between timed steps
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        st = sim.step(1, allow_noconv=True)
+        e1.record(stream)
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+        iters.append(st.iters)
+        statuses.append(sim.last_status)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    prof = sim.profile()
+    total_s = sum(ms) / 1e3
+    if dist is not None:
+        t = torch.tensor([total_s], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_s = float(t.item())
+        dist.barrier()
+    value = world * M * a.steps / total_s
+
+    # roofline of the dominant kernel (Jacobi sweep)
+    peaks = _peaks()
+    peak = float(peaks["hbm_gbs"]) if peaks else 6800.0
+    peak_src = "of measured" if peaks else "of fallback"
+    sweep_s = prof.sweep_ms / 1e3
+    per_sweep_s = sweep_s / max(prof.sweeps, 1)
+    alg_bytes = BYTES_PER_SWEEP_VOXEL * M
+    achieved = alg_bytes / per_sweep_s / 1e9 if prof.sweeps else 0.0
+    tpv = _traffic_record(a.workload)
+    roofline = {"bound": "hbm", "kernel": "k_stencil<float,M_JAC> (damped Jacobi sweep)",
+                "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": (tpv * M) if tpv is not None else None,
+                "algorithmic_bytes_per_launch": alg_bytes, "avg_launch_us": per_sweep_s * 1e6,
+                "sweep_share_of_step": sweep_s / total_s if world == 1 else None, "peak_source": peak_src}
+
+    # end to end through the C ABI with host buffers: state in from pinned memory, V_m out
+    e2e = None
+    if not a.no_e2e:
+        nb = sim.state_bytes()
+        blob = torch.empty(nb, dtype=torch.uint8, pin_memory=True).numpy()
+        sim.read_state(blob)
+        out = np.empty(sim.n, np.float64)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(a.steps):
+            sim.write_state(blob)
+            sim.step(1, allow_noconv=True)
+            out[:] = sim.read(ep.EP_VM_MV)
+        torch.cuda.synchronize()
+        e2e_s = time.perf_counter() - t0
+        rb = 8 if case.precision == ep.EP_FP64 else 4
+        e2e = {"value": M * a.steps / e2e_s, "unit": "tissue voxel-steps/s", "h2d_bytes_per_step": int(nb),
+               "d2h_bytes_per_step": int(sim.n * rb)}
+
+    cpu = None
+    if rank == 0 and world == 1 and not a.no_cpu_baseline:
+        k = float(np.mean(iters)) if iters else DEFAULT_REF_SWEEPS_PER_STEP
+        info = oracle_sample(case, k)
+        cpu = {"value": M / info["step_s"], "unit": "tissue voxel-steps/s", "cores": info["cores"], "kind": "oracle",
+               "sample": (f"one oracle step of this workload with the Jacobi solve capped at {REF_SAMPLE_SWEEPS[0]} "
+                          f"and {REF_SAMPLE_SWEEPS[1]} sweeps (fixed {info['fixed_s']:.2f} s + "
+                          f"{info['per_sweep_s']:.3f} s/sweep, {info['sample_s']:.1f} s of CPU work), extrapolated "
+                          f"to the {k:.0f} sweeps per step of the timed GPU steps")}
+
+    if rank == 0:
+        line = {"metric": "voxel-steps/sec", "value": value, "unit": "tissue voxel-steps/s", "n_gpus": world,
+                "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1e3 * total_s / a.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+                "data": "synthetic",
+                "config": {"workload": desc, "grid": [case.nx, case.ny, case.nz], "tissue_voxels": M,
+                           "dt_ms": case.params.dt, "rel_tol": case.params.rel_tol,
+                           "window": f"steps {a.warmup}..{a.warmup + a.steps - 1} from rest, apex stimulus at t=0",
+                           "sweeps_per_step": iters, "step_status": statuses,
+                           "l2": "flushed between timed steps (256 MB write)",
+                           "parallelism": f"replicas x{world}"},
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": int(prof.sweep_launches + prof.other_launches),
+                "clocks": clk}
+        print(json.dumps(line), flush=True)
+    sim.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def main():
+    a = _args()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_ours(a)
+
+
+if __name__ == "__main__":
+    main()

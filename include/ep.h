@@ -1,0 +1,190 @@
+/*
+ * ep.h -- C ABI of the GB300 voxel electrophysiology step.
+ *
+ * One time step of the operator-split, matrix-free finite-volume
+ * bidomain / monodomain model of cardiac tissue on a voxel grid
+ * (T. Simpson, "Computational Tools for Cardiac Simulation", thesis,
+ * arXiv 2302.12519):
+ *
+ *   1. Mitchell-Schaeffer reaction, explicit Euler
+ *      (Eqs. ms1/ms2, Sec. "Algorithm Details / Electrophysiology / Reaction");
+ *   2. anisotropic diffusion with the self-dual 27-point operator, fibre
+ *      conductivity tensors (Eq. sigma1) and no-flux faces at the tissue mask
+ *      (Sec. "Operators", Sec. "Matrix-Free Assembly", Sec. "Diffusion");
+ *   3. bidomain only: the extracellular elliptic equation (Eq. bidomain1,
+ *      second line) by damped Jacobi (Eq. dampjac1), FP64 residual norms,
+ *      and the zero-mean reference potential per tissue component.
+ *
+ * All compute runs in CUDA kernels on one GPU; the host only orchestrates.
+ *
+ * Conventions for every call
+ *  - Every function returns an ep_status; nothing throws across the ABI.
+ *    On failure ep_last_error() returns a message for that handle.
+ *  - Host buffers passed in are copied before the call returns; the library
+ *    keeps no pointer to caller memory.
+ *  - Device memory is owned by the handle.  It is allocated with
+ *    ep_grid_desc.dev_alloc / dev_free when both are set (e.g. a framework's
+ *    caching allocator), otherwise with cudaMalloc / cudaFree.
+ *  - All work is issued on ep_grid_desc.cuda_stream (NULL = the legacy
+ *    default stream).  Calls that return host data synchronise that stream.
+ *  - A handle is not thread safe: use it from one host thread at a time.
+ *  - Grid: nx * ny * nz voxels, linear index q = i + nx*(j + ny*k).
+ *    Units: mm, ms, mS/mm.  The state v is dimensionless (0 rest, 1 peak);
+ *    potentials read in mV use V_m = 100 v - 80 and V_e = 100 v_e.
+ */
+#ifndef EP_H
+#define EP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    EP_OK = 0,
+    EP_EINVAL = 1,      /* bad argument, size or parameter value */
+    EP_ENOMEM = 2,      /* device or host allocation failed */
+    EP_ECUDA = 3,       /* a CUDA call failed (message has the CUDA error) */
+    EP_ENOCONV = 4,     /* elliptic solve hit max_iter (or diverged); step completed with the last iterate */
+    EP_ENONFINITE = 5,  /* a NaN / Inf appeared in the state */
+    EP_ESTATE = 6,      /* call not valid in the handle's current state */
+    EP_EBUSY = 7,       /* batch slot table full */
+    EP_EREJECTED = 8    /* batch admission refused: over the HBM budget */
+} ep_status;
+
+enum { EP_MONO = 0, EP_BI = 1 };          /* ep_grid_desc.model */
+enum { EP_FP32 = 0, EP_FP64 = 1 };        /* ep_grid_desc.precision: state and stencil arithmetic */
+
+/* fields for ep_read (always returned as n doubles) */
+enum {
+    EP_VM_MV = 0,   /* transmembrane potential, mV */
+    EP_W = 1,       /* gating variable */
+    EP_VE_MV = 2,   /* extracellular potential (zero mean per component), mV */
+    EP_TACT = 3,    /* activation time, ms; -1 where not yet activated */
+    EP_V = 4,       /* dimensionless v */
+    EP_VE = 5       /* dimensionless v_e */
+};
+
+typedef struct {
+    int nx, ny, nz;                  /* voxels per axis, each >= 1 */
+    double dx_mm;                    /* voxel edge, > 0 */
+    int model;                       /* EP_MONO or EP_BI */
+    int precision;                   /* EP_FP32 or EP_FP64 */
+    void *cuda_stream;               /* cudaStream_t, may be NULL */
+    void *(*dev_alloc)(size_t bytes, void *ctx);   /* optional device allocator */
+    void (*dev_free)(void *ptr, void *ctx);        /* optional, paired with dev_alloc */
+    void *alloc_ctx;                 /* passed to dev_alloc / dev_free */
+} ep_grid_desc;
+
+typedef struct {
+    /* Mitchell-Schaeffer constants (Eqs. ms1/ms2): ms, ms, ms, ms, dimensionless */
+    double tau_in, tau_out, tau_open, tau_close, v_gate;
+    /* conductivities (Eq. sigma1), mS/mm: intracellular and extracellular,
+     * longitudinal and transverse */
+    double sig_iL, sig_iT, sig_eL, sig_eT;
+    double lambda;        /* monodomain ratio (Eq. monodomain1) */
+    double K;             /* chi_m * C_m, > 0 */
+    double dt_ms;         /* time step, > 0 */
+    double jacobi_omega;  /* damping of Eq. dampjac1; <= 0 selects 1.8 / (8 sL / (sL + 2 sT))
+                             for the elliptic operator's sL = sig_iL + sig_eL, sT = sig_iT + sig_eT */
+    double rel_tol;       /* stop when ||b - A x||_2 <= rel_tol ||b||_2 */
+    int check_every;      /* residual check interval in sweeps, >= 1 */
+    int max_iter;         /* sweep cap per elliptic solve, >= 1 */
+} ep_params;
+
+typedef struct {
+    int iters;               /* Jacobi sweeps of the last elliptic solve (0 for monodomain) */
+    double rel_res;          /* last checked relative residual */
+    int converged;           /* 1 if every solve in the call met rel_tol */
+    long long total_iters;   /* sweeps summed over the steps of the call */
+    long long step;          /* step counter after the call (t = step * dt) */
+} ep_step_stats;
+
+typedef struct {
+    long long n_voxels;      /* nx * ny * nz */
+    long long n_tissue;      /* tissue voxels */
+    int n_components;        /* face-connected tissue components */
+    int n_segments;          /* z-march work items of the stencil kernels */
+    double omega;            /* damping in use */
+    size_t device_bytes;     /* device memory held by the handle */
+} ep_info;
+
+typedef struct ep_sim ep_sim;
+
+/* Create a handle for one simulation.  Validates the descriptor (EP_EINVAL),
+ * creates no device state until the first ep_step / ep_read / ep_apply_operator. */
+ep_status ep_create(const ep_grid_desc *desc, ep_sim **out);
+
+/* Tissue mask, n = nx*ny*nz bytes, non-zero = myocardium.  Required. */
+ep_status ep_set_mask(ep_sim *s, const uint8_t *mask, size_t n);
+
+/* Fibre field, 3n floats (fx, fy, fz) per voxel, unit length or zero (zero
+ * gives Sigma = sigma_T I, Sec. "Fibre Directions").  Stored as IEEE half
+ * precision.  Optional (default zero fibres). */
+ep_status ep_set_fibres(ep_sim *s, const float *f, size_t n3);
+
+/* Model parameters.  Required.  Values are validated (EP_EINVAL). */
+ep_status ep_set_params(ep_sim *s, const ep_params *p);
+
+/* Add a stimulus box [lo, hi) in voxel indices: J_stim = amp_per_ms is added to
+ * dv/dt of tissue voxels in the box while t_start <= t_n < t_start + dur, with
+ * t_n = n * dt evaluated in double precision.  At most 8 boxes. */
+ep_status ep_add_stimulus(ep_sim *s, const int lo[3], const int hi[3],
+                          double t_start_ms, double dur_ms, double amp_per_ms);
+
+/* The ep_set_mask/fibres/params/stimulus calls are valid only before device
+ * setup (first ep_step / ep_read / ep_apply_operator / ep_set_state); after
+ * that they return EP_ESTATE. */
+
+/* Overwrite the state: v, w, ve as n doubles each (any may be NULL to keep the
+ * current field), step counter.  Values off the tissue are ignored.  The
+ * default initial state is rest: v = 0, w = 1, ve = 0, step 0. */
+ep_status ep_set_state(ep_sim *s, const double *v, const double *w, const double *ve,
+                       size_t n, long long step);
+
+/* Advance n_steps >= 0 time steps.  Returns EP_ENOCONV if an elliptic solve hit
+ * max_iter (the step is completed with the last iterate), EP_ENONFINITE if a
+ * NaN/Inf appeared.  stats may be NULL. */
+ep_status ep_step(ep_sim *s, int n_steps, ep_step_stats *stats);
+
+/* Copy one field to host: bytes must be n * sizeof(double). */
+ep_status ep_read(ep_sim *s, int field, void *host, size_t bytes);
+
+/* Snapshot / restore of the full dynamic state (v, w, ve, activation times,
+ * step) in the handle's precision.  ep_state_bytes gives the blob size. */
+ep_status ep_state_bytes(ep_sim *s, size_t *bytes);
+ep_status ep_read_state(ep_sim *s, void *host, size_t bytes);
+ep_status ep_write_state(ep_sim *s, const void *host, size_t bytes);
+
+/* Apply the diffusion operator L_{sL,sT} = G'^T S G' of the handle's mask and
+ * fibres to a host field u (n doubles), writing L u (n doubles; zero off the
+ * tissue).  L u approximates -div(Sigma grad u) (Sec. "Operators / Laplacian",
+ * Eq. ass3).  Uses the same stencil kernel as the time step. */
+ep_status ep_apply_operator(ep_sim *s, double sig_L, double sig_T,
+                            const double *u_host, double *out_host, size_t n);
+
+ep_status ep_get_info(ep_sim *s, ep_info *info);
+
+/* Device-time accounting of ep_step, measured with CUDA events on the
+ * handle's stream (for throughput and roofline reporting).  Enabling resets
+ * the counters; enabled accounting adds one event pair per kernel group. */
+typedef struct {
+    double sweep_ms;             /* Jacobi sweep launches (the elliptic solve) */
+    double other_ms;             /* reaction+diffusion, right-hand side, reductions, projection */
+    long long sweep_launches;    /* sweep kernels launched, including ones that found the solve finished */
+    long long sweeps;            /* sweeps that did work */
+    long long other_launches;    /* all other kernels launched by ep_step */
+    long long steps;             /* steps taken while enabled */
+} ep_profile;
+
+ep_status ep_profile_enable(ep_sim *s, int on);
+ep_status ep_get_profile(ep_sim *s, ep_profile *prof);
+const char *ep_last_error(const ep_sim *s);
+void ep_destroy(ep_sim *s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* EP_H */

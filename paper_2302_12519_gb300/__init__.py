@@ -1,0 +1,262 @@
+"""Python binding of the GB300 voxel electrophysiology library (libep.so).
+
+Argument marshalling only: every step of the time step runs in the CUDA
+kernels behind the C ABI declared in ``include/ep.h``.  There is no CPU
+fallback; importing fails if the library has not been built (run
+``python -m paper_2302_12519_gb300.build``).  PyTorch, when present, is used
+only to supply device memory (its caching allocator) and the CUDA stream.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libep.so")
+
+EP_OK, EP_EINVAL, EP_ENOMEM, EP_ECUDA, EP_ENOCONV, EP_ENONFINITE, EP_ESTATE, EP_EBUSY, EP_EREJECTED = range(9)
+STATUS_NAMES = ["EP_OK", "EP_EINVAL", "EP_ENOMEM", "EP_ECUDA", "EP_ENOCONV", "EP_ENONFINITE", "EP_ESTATE",
+                "EP_EBUSY", "EP_EREJECTED"]
+EP_MONO, EP_BI = 0, 1
+EP_FP32, EP_FP64 = 0, 1
+EP_VM_MV, EP_W, EP_VE_MV, EP_TACT, EP_V, EP_VE = range(6)
+
+# every symbol include/ep.h declares
+EXPORTS = ["ep_create", "ep_set_mask", "ep_set_fibres", "ep_set_params", "ep_add_stimulus", "ep_set_state",
+           "ep_step", "ep_read", "ep_state_bytes", "ep_read_state", "ep_write_state", "ep_apply_operator",
+           "ep_get_info", "ep_profile_enable", "ep_get_profile", "ep_last_error", "ep_destroy"]
+
+_ALLOC_T = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+_FREE_T = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
+
+
+class GridDesc(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int), ("dx_mm", ctypes.c_double),
+                ("model", ctypes.c_int), ("precision", ctypes.c_int), ("cuda_stream", ctypes.c_void_p),
+                ("dev_alloc", _ALLOC_T), ("dev_free", _FREE_T), ("alloc_ctx", ctypes.c_void_p)]
+
+
+class Params(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_double) for n in
+                ("tau_in", "tau_out", "tau_open", "tau_close", "v_gate", "sig_iL", "sig_iT", "sig_eL", "sig_eT",
+                 "lambda_", "K", "dt_ms", "jacobi_omega", "rel_tol")] + \
+               [("check_every", ctypes.c_int), ("max_iter", ctypes.c_int)]
+
+
+class StepStats(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int), ("rel_res", ctypes.c_double), ("converged", ctypes.c_int),
+                ("total_iters", ctypes.c_longlong), ("step", ctypes.c_longlong)]
+
+
+class Info(ctypes.Structure):
+    _fields_ = [("n_voxels", ctypes.c_longlong), ("n_tissue", ctypes.c_longlong), ("n_components", ctypes.c_int),
+                ("n_segments", ctypes.c_int), ("omega", ctypes.c_double), ("device_bytes", ctypes.c_size_t)]
+
+
+class Profile(ctypes.Structure):
+    _fields_ = [("sweep_ms", ctypes.c_double), ("other_ms", ctypes.c_double),
+                ("sweep_launches", ctypes.c_longlong), ("sweeps", ctypes.c_longlong),
+                ("other_launches", ctypes.c_longlong), ("steps", ctypes.c_longlong)]
+
+
+class EPError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES[status] if 0 <= status < len(STATUS_NAMES) else status}: {msg}")
+        self.status = status
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libep.so (raises if it is missing: there is no fallback)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"{path} is missing; build it with `python -m paper_2302_12519_gb300.build`")
+    L = ctypes.CDLL(path)
+    vp, ip, dp, sz = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_size_t
+    sigs = {
+        "ep_create": ([ctypes.POINTER(GridDesc), ctypes.POINTER(vp)], ip),
+        "ep_set_mask": ([vp, vp, sz], ip),
+        "ep_set_fibres": ([vp, vp, sz], ip),
+        "ep_set_params": ([vp, ctypes.POINTER(Params)], ip),
+        "ep_add_stimulus": ([vp, ctypes.POINTER(ctypes.c_int * 3), ctypes.POINTER(ctypes.c_int * 3), dp, dp, dp], ip),
+        "ep_set_state": ([vp, vp, vp, vp, sz, ctypes.c_longlong], ip),
+        "ep_step": ([vp, ip, ctypes.POINTER(StepStats)], ip),
+        "ep_read": ([vp, ip, vp, sz], ip),
+        "ep_state_bytes": ([vp, ctypes.POINTER(sz)], ip),
+        "ep_read_state": ([vp, vp, sz], ip),
+        "ep_write_state": ([vp, vp, sz], ip),
+        "ep_apply_operator": ([vp, dp, dp, vp, vp, sz], ip),
+        "ep_get_info": ([vp, ctypes.POINTER(Info)], ip),
+        "ep_profile_enable": ([vp, ip], ip),
+        "ep_get_profile": ([vp, ctypes.POINTER(Profile)], ip),
+        "ep_last_error": ([vp], ctypes.c_char_p),
+        "ep_destroy": ([vp], None),
+    }
+    for name, (args, res) in sigs.items():
+        fn = getattr(L, name)
+        fn.argtypes = args
+        fn.restype = res
+    _lib = L
+    return L
+
+
+def _torch_hooks():
+    """Device allocator callbacks backed by torch's caching allocator, and the
+    current torch stream.  Returns (alloc, free, stream) or None."""
+    try:
+        import torch
+    except Exception:
+        return None
+    if not torch.cuda.is_available():
+        return None
+    dev = torch.cuda.current_device()
+    stream = torch.cuda.current_stream(dev)
+
+    def _alloc(nbytes, ctx):
+        return int(torch.cuda.caching_allocator_alloc(int(nbytes), dev, stream))
+
+    def _free(ptr, ctx):
+        torch.cuda.caching_allocator_delete(int(ptr))
+
+    return _ALLOC_T(_alloc), _FREE_T(_free), int(stream.cuda_stream)
+
+
+def _f64(a, n: int) -> np.ndarray:
+    a = np.ascontiguousarray(np.asarray(a, dtype=np.float64).reshape(-1))
+    if a.size != n:
+        raise ValueError(f"expected {n} values, got {a.size}")
+    return a
+
+
+class Sim:
+    """One simulation handle (ep_sim).  Mirrors the C ABI one call per method."""
+
+    def __init__(self, nx: int, ny: int, nz: int, dx_mm: float, model: int = EP_BI, precision: int = EP_FP32,
+                 use_torch: bool = True, stream: Optional[int] = None):
+        L = load()
+        self._L = L
+        self.nx, self.ny, self.nz = int(nx), int(ny), int(nz)
+        self.n = self.nx * self.ny * self.nz
+        d = GridDesc()
+        d.nx, d.ny, d.nz, d.dx_mm, d.model, d.precision = self.nx, self.ny, self.nz, float(dx_mm), int(model), int(precision)
+        self._hooks = _torch_hooks() if use_torch else None
+        if self._hooks is not None:
+            d.dev_alloc, d.dev_free = self._hooks[0], self._hooks[1]
+            d.cuda_stream = self._hooks[2] if stream is None else stream
+        elif stream is not None:
+            d.cuda_stream = stream
+        self._desc = d
+        h = ctypes.c_void_p()
+        st = L.ep_create(ctypes.byref(d), ctypes.byref(h))
+        if st != EP_OK:
+            raise EPError(st, "ep_create")
+        self._h = h
+
+    # -- helpers -------------------------------------------------------------
+    def _check(self, st: int, what: str):
+        if st != EP_OK:
+            raise EPError(st, f"{what}: {self._L.ep_last_error(self._h).decode()}")
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._L.ep_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- set-up --------------------------------------------------------------
+    def set_mask(self, mask):
+        m = np.ascontiguousarray(np.asarray(mask, dtype=np.uint8).reshape(-1))
+        self._check(self._L.ep_set_mask(self._h, m.ctypes.data, m.size), "ep_set_mask")
+
+    def set_fibres(self, fib):
+        f = np.ascontiguousarray(np.asarray(fib, dtype=np.float32).reshape(-1))
+        self._check(self._L.ep_set_fibres(self._h, f.ctypes.data, f.size), "ep_set_fibres")
+
+    def set_params(self, p):
+        P = Params(p.tau_in, p.tau_out, p.tau_open, p.tau_close, p.v_gate, p.sig_iL, p.sig_iT, p.sig_eL, p.sig_eT,
+                   p.lam, p.K, p.dt, p.omega, p.rel_tol, int(p.check_every), int(p.max_iter))
+        self._check(self._L.ep_set_params(self._h, ctypes.byref(P)), "ep_set_params")
+
+    def add_stimulus(self, lo: Sequence[int], hi: Sequence[int], t_start: float, dur: float, amp: float):
+        a, b = (ctypes.c_int * 3)(*lo), (ctypes.c_int * 3)(*hi)
+        self._check(self._L.ep_add_stimulus(self._h, ctypes.byref(a), ctypes.byref(b), float(t_start), float(dur),
+                                            float(amp)), "ep_add_stimulus")
+
+    def set_state(self, v=None, w=None, ve=None, step: int = 0):
+        arrs = [None if a is None else _f64(a, self.n) for a in (v, w, ve)]
+        ptrs = [None if a is None else a.ctypes.data for a in arrs]
+        self._check(self._L.ep_set_state(self._h, *ptrs, self.n, int(step)), "ep_set_state")
+
+    # -- stepping and reads --------------------------------------------------
+    def step(self, n_steps: int = 1, allow_noconv: bool = False) -> StepStats:
+        s = StepStats()
+        st = self._L.ep_step(self._h, int(n_steps), ctypes.byref(s))
+        if not (allow_noconv and st == EP_ENOCONV):
+            self._check(st, "ep_step")
+        self.last_status = st
+        return s
+
+    def read(self, field: int) -> np.ndarray:
+        out = np.empty(self.n, np.float64)
+        self._check(self._L.ep_read(self._h, int(field), out.ctypes.data, out.nbytes), "ep_read")
+        return out
+
+    def state_bytes(self) -> int:
+        b = ctypes.c_size_t(0)
+        self._check(self._L.ep_state_bytes(self._h, ctypes.byref(b)), "ep_state_bytes")
+        return b.value
+
+    def read_state(self, out: Optional[np.ndarray] = None) -> np.ndarray:
+        nb = self.state_bytes()
+        if out is None:
+            out = np.empty(nb, np.uint8)
+        self._check(self._L.ep_read_state(self._h, out.ctypes.data, nb), "ep_read_state")
+        return out
+
+    def write_state(self, blob: np.ndarray):
+        blob = np.ascontiguousarray(blob, dtype=np.uint8)
+        self._check(self._L.ep_write_state(self._h, blob.ctypes.data, blob.nbytes), "ep_write_state")
+
+    def apply_operator(self, sig_L: float, sig_T: float, u) -> np.ndarray:
+        u = _f64(u, self.n)
+        out = np.empty(self.n, np.float64)
+        self._check(self._L.ep_apply_operator(self._h, float(sig_L), float(sig_T), u.ctypes.data, out.ctypes.data,
+                                              self.n), "ep_apply_operator")
+        return out
+
+    def profile_enable(self, on: bool = True):
+        self._check(self._L.ep_profile_enable(self._h, int(bool(on))), "ep_profile_enable")
+
+    def profile(self) -> Profile:
+        p = Profile()
+        self._check(self._L.ep_get_profile(self._h, ctypes.byref(p)), "ep_get_profile")
+        return p
+
+    def info(self) -> Info:
+        i = Info()
+        self._check(self._L.ep_get_info(self._h, ctypes.byref(i)), "ep_get_info")
+        return i
+
+
+def sim_from_case(case, use_torch: bool = True, model: Optional[int] = None, precision: Optional[int] = None) -> Sim:
+    """Create a handle from a ``workloads.Case`` (mask, fibres, parameters, stimuli)."""
+    s = Sim(case.nx, case.ny, case.nz, case.dx, case.model if model is None else model,
+            case.precision if precision is None else precision, use_torch=use_torch)
+    s.set_mask(case.mask_flat())
+    s.set_fibres(case.fib_flat())
+    s.set_params(case.params)
+    for st in case.stimuli:
+        s.add_stimulus(st.lo, st.hi, st.t_start, st.dur, st.amp)
+    return s

@@ -1,0 +1,838 @@
+// ep_api.cu -- C ABI of the GB300 voxel electrophysiology step (see include/ep.h).
+//
+// Host side: validation, set-up of the data layout (fp16 fibre records,
+// z-march segment list, component-sorted tissue index list), and the step
+// orchestration.  Every arithmetic step of the time step runs in the kernels
+// of ep_kernels.cuh.
+//
+// Elliptic solve control: the sweep count, residual checks and the stop
+// decision live in a device control block.  Sweeps are queued in CUDA-graph
+// chunks; a sweep that finds the solve finished returns at once, so the host
+// only needs to look at the flag once per chunk (one chunk of look-ahead) and
+// never stalls the GPU between sweeps.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/ep.h"
+#include "ep_kernels.cuh"
+
+using namespace gbep;
+
+namespace {
+
+constexpr int kZSeg = 16;          // output planes per segment
+constexpr int kSweepChunk = 64;    // sweeps per queued graph chunk
+constexpr double kDivFactor = 1e16;
+
+struct StimDef {
+    int lo[3], hi[3];
+    double t0, dur, amp;
+};
+
+}  // namespace
+
+struct ep_sim {
+    ep_grid_desc d{};
+    long long n = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    std::string err;
+    std::vector<uint8_t> mask;
+    std::vector<float> fib;
+    bool have_mask = false, have_params = false;
+    ep_params p{};
+    std::vector<StimDef> stims;
+    bool ready = false;
+    // derived layout
+    long long n_tissue = 0;
+    int ncomp = 0, nseg = 0, nchunk = 0;
+    double omega = 0.0;
+    size_t rsz = 4;
+    // device memory
+    std::vector<void *> allocs;
+    size_t dev_bytes = 0;
+    ushort4 *rec = nullptr;
+    void *v[2] = {nullptr, nullptr}, *w[2] = {nullptr, nullptr}, *x[2] = {nullptr, nullptr};
+    void *b = nullptr, *tact = nullptr;
+    Seg *segs = nullptr;
+    int *idx = nullptr;
+    Chunk *chunks = nullptr;
+    int *comp_chunk0 = nullptr;
+    long long *comp_count = nullptr;
+    double *means = nullptr, *partials = nullptr;
+    Ctl *ctl = nullptr;
+    Ctl *ctl_host = nullptr;   // pinned, 2 slots
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+    cudaGraphExec_t sweep_graph = nullptr;
+    int cur = 0;
+    long long step = 0;
+    // device-time accounting (ep_profile_enable)
+    bool prof_on = false;
+    cudaEvent_t pev[4] = {nullptr, nullptr, nullptr, nullptr};
+    ep_profile prof{};
+};
+
+namespace {
+
+ep_status fail(ep_sim *s, ep_status st, const std::string &msg)
+{
+    if (s) s->err = msg;
+    return st;
+}
+
+#define CK(call)                                                                                    \
+    do {                                                                                            \
+        cudaError_t e_ = (call);                                                                    \
+        if (e_ != cudaSuccess)                                                                      \
+            return fail(s, EP_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_));          \
+    } while (0)
+
+void *dalloc(ep_sim *s, size_t bytes)
+{
+    if (bytes == 0) bytes = 16;
+    void *p = nullptr;
+    if (s->d.dev_alloc && s->d.dev_free) {
+        p = s->d.dev_alloc(bytes, s->d.alloc_ctx);
+    } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        p = nullptr;
+    }
+    if (p) {
+        s->allocs.push_back(p);
+        s->dev_bytes += bytes;
+    }
+    return p;
+}
+
+void dfree_all(ep_sim *s)
+{
+    for (void *p : s->allocs) {
+        if (s->d.dev_alloc && s->d.dev_free) s->d.dev_free(p, s->d.alloc_ctx);
+        else cudaFree(p);
+    }
+    s->allocs.clear();
+    s->dev_bytes = 0;
+}
+
+int grid_for(long long n, int threads)
+{
+    long long g = (n + threads - 1) / threads;
+    return (int)std::max<long long>(1, std::min<long long>(g, 152LL * 32));
+}
+
+bool params_ok(const ep_params &p, std::string &why)
+{
+    auto pos = [](double v) { return std::isfinite(v) && v > 0.0; };
+    if (!pos(p.tau_in) || !pos(p.tau_out) || !pos(p.tau_open) || !pos(p.tau_close)) { why = "time constants must be > 0"; return false; }
+    if (!std::isfinite(p.v_gate)) { why = "v_gate must be finite"; return false; }
+    if (!pos(p.sig_iL) || !pos(p.sig_iT) || !pos(p.sig_eL) || !pos(p.sig_eT)) { why = "conductivities must be > 0"; return false; }
+    if (!std::isfinite(p.lambda) || p.lambda <= 0.0) { why = "lambda must be > 0"; return false; }
+    if (!pos(p.K) || !pos(p.dt_ms)) { why = "K and dt_ms must be > 0"; return false; }
+    if (!std::isfinite(p.jacobi_omega) || p.jacobi_omega >= 2.0) { why = "jacobi_omega must be < 2 (<= 0 selects the default)"; return false; }
+    if (!std::isfinite(p.rel_tol) || p.rel_tol < 0.0) { why = "rel_tol must be >= 0"; return false; }
+    if (p.check_every < 1 || p.max_iter < 1) { why = "check_every and max_iter must be >= 1"; return false; }
+    return true;
+}
+
+// ---------------------------------------------------------------------------
+// set-up: layout built on the host from the mask, records on the device
+// ---------------------------------------------------------------------------
+template <typename real>
+ep_status setup_typed(ep_sim *s)
+{
+    const int nx = s->d.nx, ny = s->d.ny, nz = s->d.nz;
+    const long long n = s->n;
+    const uint8_t *m = s->mask.data();
+    // face-connected components (breadth-first), tissue index list sorted by component
+    std::vector<int> comp(n, -1);
+    std::vector<int> order;
+    order.reserve((size_t)std::count_if(s->mask.begin(), s->mask.end(), [](uint8_t c) { return c != 0; }));
+    std::vector<long long> comp_count;
+    std::vector<long long> queue;
+    int nc = 0;
+    for (long long q = 0; q < n; ++q) {
+        if (!m[q] || comp[q] >= 0) continue;
+        queue.clear();
+        queue.push_back(q);
+        comp[q] = nc;
+        size_t head = 0;
+        while (head < queue.size()) {
+            const long long c = queue[head++];
+            const int i = (int)(c % nx), j = (int)((c / nx) % ny), k = (int)(c / ((long long)nx * ny));
+            const int nb[6][3] = {{i - 1, j, k}, {i + 1, j, k}, {i, j - 1, k}, {i, j + 1, k}, {i, j, k - 1}, {i, j, k + 1}};
+            for (auto &t : nb) {
+                if (t[0] < 0 || t[1] < 0 || t[2] < 0 || t[0] >= nx || t[1] >= ny || t[2] >= nz) continue;
+                const long long r = t[0] + (long long)nx * (t[1] + (long long)ny * t[2]);
+                if (m[r] && comp[r] < 0) {
+                    comp[r] = nc;
+                    queue.push_back(r);
+                }
+            }
+        }
+        std::sort(queue.begin(), queue.end());
+        for (long long r : queue) order.push_back((int)r);
+        comp_count.push_back((long long)queue.size());
+        ++nc;
+    }
+    s->n_tissue = (long long)order.size();
+    s->ncomp = nc;
+    if (s->n_tissue == 0) return fail(s, EP_EINVAL, "mask has no tissue voxel");
+    if (n > 2147483647LL) return fail(s, EP_EINVAL, "grid too large for 32-bit voxel indices");
+    std::vector<Chunk> chunks;
+    std::vector<int> comp_chunk0(nc + 1, 0);
+    {
+        long long pos = 0;
+        for (int c = 0; c < nc; ++c) {
+            comp_chunk0[c] = (int)chunks.size();
+            const long long end = pos + comp_count[c];
+            for (long long st = pos; st < end; st += kChunk)
+                chunks.push_back(Chunk{(int)st, (int)std::min<long long>(st + kChunk, end), c});
+            pos = end;
+        }
+        comp_chunk0[nc] = (int)chunks.size();
+    }
+    s->nchunk = (int)chunks.size();
+    // z-march segments over tile columns with tissue
+    std::vector<Seg> segs;
+    const int nbx = (nx + kTileX - 1) / kTileX, nby = (ny + kTileY - 1) / kTileY;
+    std::vector<char> has(nz);
+    for (int by = 0; by < nby; ++by)
+        for (int bx = 0; bx < nbx; ++bx) {
+            const int xa = bx * kTileX, xb = std::min(xa + kTileX, nx);
+            const int ya = by * kTileY, yb = std::min(ya + kTileY, ny);
+            for (int k = 0; k < nz; ++k) {
+                char h = 0;
+                for (int j = ya; j < yb && !h; ++j) {
+                    const uint8_t *row = m + (long long)nx * (j + (long long)ny * k);
+                    for (int i = xa; i < xb; ++i)
+                        if (row[i]) { h = 1; break; }
+                }
+                has[k] = h;
+            }
+            int k = 0;
+            while (k < nz) {
+                if (!has[k]) { ++k; continue; }
+                const int k0 = k;
+                int k1 = std::min(k0 + kZSeg, nz);
+                while (!has[k1 - 1]) --k1;
+                segs.push_back(Seg{bx, by, k0, k1});
+                k = k1;
+            }
+        }
+    std::stable_sort(segs.begin(), segs.end(), [](const Seg &a, const Seg &b) {
+        if (a.k0 / kZSeg != b.k0 / kZSeg) return a.k0 / kZSeg < b.k0 / kZSeg;
+        if (a.by != b.by) return a.by < b.by;
+        return a.bx < b.bx;
+    });
+    s->nseg = (int)segs.size();
+
+    // device buffers
+    const size_t rb = sizeof(real);
+    s->rsz = rb;
+    s->rec = (ushort4 *)dalloc(s, sizeof(ushort4) * n);
+    for (int i = 0; i < 2; ++i) {
+        s->v[i] = dalloc(s, rb * n);
+        s->w[i] = dalloc(s, rb * n);
+        s->x[i] = dalloc(s, rb * n);
+    }
+    s->b = dalloc(s, rb * n);
+    s->tact = dalloc(s, rb * n);
+    s->segs = (Seg *)dalloc(s, sizeof(Seg) * segs.size());
+    s->idx = (int *)dalloc(s, sizeof(int) * order.size());
+    s->chunks = (Chunk *)dalloc(s, sizeof(Chunk) * chunks.size());
+    s->comp_chunk0 = (int *)dalloc(s, sizeof(int) * comp_chunk0.size());
+    s->comp_count = (long long *)dalloc(s, sizeof(long long) * comp_count.size());
+    s->means = (double *)dalloc(s, sizeof(double) * nc);
+    s->partials = (double *)dalloc(s, sizeof(double) * std::max(s->nseg, s->nchunk));
+    s->ctl = (Ctl *)dalloc(s, sizeof(Ctl));
+    void *tmp_fib = dalloc(s, sizeof(float) * 3 * n);
+    void *tmp_mask = dalloc(s, n);
+    void *tmp_rec = dalloc(s, sizeof(ushort4) * n);
+    const void *all[] = {s->rec, s->v[0], s->v[1], s->w[0], s->w[1], s->x[0], s->x[1], s->b, s->tact, s->segs,
+                         s->idx, s->chunks, s->comp_chunk0, s->comp_count, s->means, s->partials, s->ctl,
+                         tmp_fib, tmp_mask, tmp_rec};
+    for (const void *p : all)
+        if (!p) return fail(s, EP_ENOMEM, "device allocation failed");
+    cudaStream_t st = s->stream;
+    CK(cudaMemcpyAsync(s->segs, segs.data(), sizeof(Seg) * segs.size(), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(s->idx, order.data(), sizeof(int) * order.size(), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(s->chunks, chunks.data(), sizeof(Chunk) * chunks.size(), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(s->comp_chunk0, comp_chunk0.data(), sizeof(int) * comp_chunk0.size(), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(s->comp_count, comp_count.data(), sizeof(long long) * comp_count.size(), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(tmp_mask, m, n, cudaMemcpyHostToDevice, st));
+    if (s->fib.empty()) CK(cudaMemsetAsync(tmp_fib, 0, sizeof(float) * 3 * n, st));
+    else CK(cudaMemcpyAsync(tmp_fib, s->fib.data(), sizeof(float) * 3 * n, cudaMemcpyHostToDevice, st));
+    k_build_records<<<grid_for(n, 256), 256, 0, st>>>(nx, ny, nz, (const float *)tmp_fib, (const uint8_t *)tmp_mask,
+                                                      (ushort4 *)tmp_rec);
+    // Jacobi diagonal of the elliptic operator L_i + L_e (conductivities add)
+    const double sL = s->p.sig_iL + s->p.sig_eL, sT = s->p.sig_iT + s->p.sig_eT;
+    k_build_diag<<<grid_for(n, 128), 128, 0, st>>>(nx, ny, nz, sT, sL - sT, (const ushort4 *)tmp_rec, s->rec);
+    CK(cudaGetLastError());
+    // rest state
+    for (int i = 0; i < 2; ++i) {
+        k_fill<real><<<grid_for(n, 256), 256, 0, st>>>((real *)s->v[i], n, real(0));
+        k_fill<real><<<grid_for(n, 256), 256, 0, st>>>((real *)s->w[i], n, real(1));
+        k_fill<real><<<grid_for(n, 256), 256, 0, st>>>((real *)s->x[i], n, real(0));
+    }
+    k_fill<real><<<grid_for(n, 256), 256, 0, st>>>((real *)s->b, n, real(0));
+    k_fill<real><<<grid_for(n, 256), 256, 0, st>>>((real *)s->tact, n, real(-1));
+    CK(cudaGetLastError());
+    CK(cudaMemsetAsync(s->ctl, 0, sizeof(Ctl), st));
+    CK(cudaStreamSynchronize(st));
+    // free the set-up temporaries
+    for (void *t : {tmp_fib, tmp_mask, tmp_rec}) {
+        auto it = std::find(s->allocs.begin(), s->allocs.end(), t);
+        if (it != s->allocs.end()) {
+            if (s->d.dev_alloc && s->d.dev_free) s->d.dev_free(t, s->d.alloc_ctx);
+            else cudaFree(t);
+            s->allocs.erase(it);
+        }
+    }
+    s->dev_bytes -= sizeof(float) * 3 * n + n + sizeof(ushort4) * n;
+    CK(cudaMallocHost((void **)&s->ctl_host, 2 * sizeof(Ctl)));
+    std::memset(s->ctl_host, 0, 2 * sizeof(Ctl));
+    CK(cudaEventCreateWithFlags(&s->ev[0], cudaEventDisableTiming));
+    CK(cudaEventCreateWithFlags(&s->ev[1], cudaEventDisableTiming));
+    s->cur = 0;
+    return EP_OK;
+}
+
+template <typename real>
+StencilArgs<real> base_args(ep_sim *s)
+{
+    StencilArgs<real> a;
+    std::memset(&a, 0, sizeof(a));
+    a.nx = s->d.nx;
+    a.ny = s->d.ny;
+    a.nz = s->d.nz;
+    a.segs = s->segs;
+    a.rec = s->rec;
+    a.C = (real)(1.0 / (8.0 * s->d.dx_mm * s->d.dx_mm));
+    a.ctl = s->ctl;
+    a.partials = s->partials;
+    return a;
+}
+
+template <typename real>
+StencilArgs<real> jac_args(ep_sim *s)
+{
+    StencilArgs<real> a = base_args<real>(s);
+    const double sL = s->p.sig_iL + s->p.sig_eL, sT = s->p.sig_iT + s->p.sig_eT;
+    a.sT = (real)sT;
+    a.dS = (real)(sL - sT);
+    a.coef = (real)(s->omega / (1.0 / (8.0 * s->d.dx_mm * s->d.dx_mm)));
+    a.x0 = (real *)s->x[0];
+    a.x1 = (real *)s->x[1];
+    a.b = (const real *)s->b;
+    a.check_every = s->p.check_every;
+    a.max_iter = s->p.max_iter;
+    a.div_factor = kDivFactor;
+    return a;
+}
+
+template <typename real>
+ep_status build_sweep_graph(ep_sim *s)
+{
+    if (s->sweep_graph) return EP_OK;
+    const StencilArgs<real> a = jac_args<real>(s);
+    cudaGraph_t g = nullptr;
+    CK(cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeThreadLocal));
+    for (int i = 0; i < kSweepChunk; ++i)
+        k_stencil<real, M_JAC><<<s->nseg, kThreads, 0, s->stream>>>(a);
+    cudaError_t e = cudaStreamEndCapture(s->stream, &g);
+    if (e != cudaSuccess) return fail(s, EP_ECUDA, std::string("sweep graph capture: ") + cudaGetErrorString(e));
+    e = cudaGraphInstantiate(&s->sweep_graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        s->sweep_graph = nullptr;
+        return fail(s, EP_ECUDA, std::string("sweep graph instantiate: ") + cudaGetErrorString(e));
+    }
+    return EP_OK;
+}
+
+ep_status ensure_ready(ep_sim *s)
+{
+    if (s->ready) return EP_OK;
+    if (!s->have_mask) return fail(s, EP_ESTATE, "ep_set_mask must be called before stepping");
+    if (!s->have_params) return fail(s, EP_ESTATE, "ep_set_params must be called before stepping");
+    if (!s->stream) {
+        // a non-blocking private stream: CUDA-graph capture needs a stream other than the legacy one
+        cudaError_t e = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            s->stream = nullptr;
+            return fail(s, EP_ECUDA, std::string("cudaStreamCreate: ") + cudaGetErrorString(e));
+        }
+        s->own_stream = true;
+    }
+    const double sL = s->p.sig_iL + s->p.sig_eL, sT = s->p.sig_iT + s->p.sig_eT;
+    s->omega = s->p.jacobi_omega > 0.0 ? s->p.jacobi_omega : std::min(1.0, 1.8 * (sL + 2.0 * sT) / (8.0 * sL));
+    ep_status st = s->d.precision == EP_FP64 ? setup_typed<double>(s) : setup_typed<float>(s);
+    if (st != EP_OK) {
+        dfree_all(s);
+        return st;
+    }
+    s->ready = true;
+    return EP_OK;
+}
+
+void active_stims(const ep_sim *s, double tn, StimSet &set)
+{
+    set.n = 0;
+    for (const StimDef &d : s->stims) {
+        if (tn >= d.t0 && tn < d.t0 + d.dur && set.n < kMaxStim) {
+            StimBox &b = set.box[set.n++];
+            for (int i = 0; i < 3; ++i) {
+                b.lo[i] = d.lo[i];
+                b.hi[i] = d.hi[i];
+            }
+            b.amp = d.amp;
+        }
+    }
+}
+
+template <typename real>
+ep_status solve_elliptic(ep_sim *s, int &iters, double &relres, int &conv, int &flags)
+{
+    cudaStream_t st = s->stream;
+    // b = -L_i v, zero mean per component, ||b|| and a fresh solve in ctl
+    StencilArgs<real> r = base_args<real>(s);
+    r.sT = (real)s->p.sig_iT;
+    r.dS = (real)(s->p.sig_iL - s->p.sig_iT);
+    r.u = (const real *)s->v[s->cur];
+    r.out = (real *)s->b;
+    k_stencil<real, M_RHS><<<s->nseg, kThreads, 0, st>>>(r);
+    k_comp_mean<real><<<s->nchunk, kRedThreads, 0, st>>>((const real *)s->b, (const real *)s->b, 0, s->idx, s->chunks,
+                                                         s->comp_chunk0, s->comp_count, s->ncomp, s->partials,
+                                                         s->means, s->ctl);
+    const double tol2 = s->p.rel_tol * s->p.rel_tol;
+    k_comp_subtract<real><<<s->nchunk, kRedThreads, 0, st>>>((real *)s->b, s->idx, s->chunks, s->means, 1, tol2,
+                                                             s->partials, s->ctl);
+    CK(cudaGetLastError());
+    // sweeps, queued in graph chunks, one chunk of look-ahead
+    ep_status gs = build_sweep_graph<real>(s);
+    if (gs != EP_OK) return gs;
+    if (s->prof_on) CK(cudaEventRecord(s->pev[2], st));
+    const long long maxit = s->p.max_iter;
+    long long queued = 0;
+    for (int c = 0;; ++c) {
+        if (queued + kSweepChunk <= maxit) {
+            CK(cudaGraphLaunch(s->sweep_graph, st));
+            queued += kSweepChunk;
+        } else {
+            const StencilArgs<real> a = jac_args<real>(s);
+            for (; queued < maxit; ++queued) k_stencil<real, M_JAC><<<s->nseg, kThreads, 0, st>>>(a);
+            CK(cudaGetLastError());
+        }
+        CK(cudaMemcpyAsync(&s->ctl_host[c & 1], s->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
+        CK(cudaEventRecord(s->ev[c & 1], st));
+        if (queued >= maxit) {   // everything up to the cap is queued; the last sweep marks done
+            CK(cudaEventSynchronize(s->ev[c & 1]));
+            break;
+        }
+        if (c >= 1) {            // one chunk of look-ahead keeps the GPU busy while the host checks
+            CK(cudaEventSynchronize(s->ev[(c - 1) & 1]));
+            if (s->ctl_host[(c - 1) & 1].done) break;
+        }
+    }
+    if (s->prof_on) {
+        CK(cudaEventRecord(s->pev[3], st));
+        s->prof.sweep_launches += queued;
+        s->prof.other_launches += 5;   // RHS, 2 reductions + subtract, projection
+    }
+    // reference potential: subtract each component's mean of the final iterate
+    k_comp_mean<real><<<s->nchunk, kRedThreads, 0, st>>>((const real *)s->x[0], (const real *)s->x[1], 1, s->idx,
+                                                         s->chunks, s->comp_chunk0, s->comp_count, s->ncomp,
+                                                         s->partials, s->means, s->ctl);
+    k_project<real><<<s->nchunk, kRedThreads, 0, st>>>((real *)s->x[0], (const real *)s->x[1], s->idx, s->chunks,
+                                                       s->means, s->ctl);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(&s->ctl_host[0], s->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    const Ctl &h = s->ctl_host[0];
+    if (s->prof_on) {
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, s->pev[2], s->pev[3]));
+        s->prof.sweep_ms += ms;
+        s->prof.sweeps += h.iters;
+    }
+    iters = h.iters;
+    relres = h.bnorm2 > 0.0 ? std::sqrt(h.rnorm2 / h.bnorm2) : 0.0;
+    conv = h.converged;
+    flags = (h.nonfinite ? 1 : 0) | (h.diverged ? 2 : 0);
+    return EP_OK;
+}
+
+template <typename real>
+ep_status step_typed(ep_sim *s, int n_steps, ep_step_stats *stats)
+{
+    cudaStream_t st = s->stream;
+    ep_status ret = EP_OK;
+    int last_iters = 0, all_conv = 1;
+    double last_rr = 0.0;
+    long long total = 0;
+    const double fac = s->d.model == EP_MONO ? s->p.lambda / (1.0 + s->p.lambda) : 1.0;
+    for (int it = 0; it < n_steps; ++it) {
+        const double sweep_ms0 = s->prof.sweep_ms;
+        if (s->prof_on) CK(cudaEventRecord(s->pev[0], st));
+        StencilArgs<real> a = base_args<real>(s);
+        a.sT = (real)s->p.sig_iT;
+        a.dS = (real)(s->p.sig_iL - s->p.sig_iT);
+        a.coef = (real)(s->p.dt_ms / s->p.K * fac);
+        a.dt = (real)s->p.dt_ms;
+        a.inv_tin = (real)(1.0 / s->p.tau_in);
+        a.inv_tout = (real)(1.0 / s->p.tau_out);
+        a.inv_topen = (real)(1.0 / s->p.tau_open);
+        a.inv_tclose = (real)(1.0 / s->p.tau_close);
+        a.vgate = (real)s->p.v_gate;
+        a.tn = (double)s->step * s->p.dt_ms;
+        a.dt_d = s->p.dt_ms;
+        active_stims(s, a.tn, a.stim);
+        a.u = (const real *)s->v[s->cur];
+        a.w = (const real *)s->w[s->cur];
+        a.ve = (const real *)s->x[0];
+        a.out = (real *)s->v[1 - s->cur];
+        a.wout = (real *)s->w[1 - s->cur];
+        a.tact = (real *)s->tact;
+        // off-tissue values of the new buffers must equal the old ones (rest):
+        // they are never written, and both buffers were initialised alike.
+        if (s->d.model == EP_MONO) k_stencil<real, M_PAR_MONO><<<s->nseg, kThreads, 0, st>>>(a);
+        else k_stencil<real, M_PAR_BI><<<s->nseg, kThreads, 0, st>>>(a);
+        CK(cudaGetLastError());
+        s->cur = 1 - s->cur;
+        if (s->d.model == EP_BI) {
+            int iters = 0, conv = 0, flags = 0;
+            double rr = 0.0;
+            ep_status e = solve_elliptic<real>(s, iters, rr, conv, flags);
+            if (e != EP_OK) return e;
+            last_iters = iters;
+            last_rr = rr;
+            total += iters;
+            if (!conv) all_conv = 0;
+            if (flags & 1) ret = EP_ENONFINITE;
+            else if (!conv && ret == EP_OK) ret = EP_ENOCONV;
+        }
+        if (s->prof_on) {
+            CK(cudaEventRecord(s->pev[1], st));
+            CK(cudaEventSynchronize(s->pev[1]));
+            float ms = 0.f;
+            CK(cudaEventElapsedTime(&ms, s->pev[0], s->pev[1]));
+            s->prof.other_ms += ms - (s->prof.sweep_ms - sweep_ms0);
+            s->prof.other_launches += 1;
+            s->prof.steps += 1;
+        }
+        s->step++;
+    }
+    CK(cudaMemcpyAsync(&s->ctl_host[1], s->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (s->ctl_host[1].nonfinite) ret = EP_ENONFINITE;
+    if (stats) {
+        stats->iters = last_iters;
+        stats->rel_res = last_rr;
+        stats->converged = all_conv;
+        stats->total_iters = total;
+        stats->step = s->step;
+    }
+    if (ret == EP_ENOCONV) s->err = "elliptic solve reached max_iter or diverged";
+    if (ret == EP_ENONFINITE) s->err = "non-finite value in the state";
+    return ret;
+}
+
+template <typename real>
+ep_status read_typed(ep_sim *s, int field, double *out)
+{
+    const void *src = nullptr;
+    switch (field) {
+    case EP_VM_MV: case EP_V: src = s->v[s->cur]; break;
+    case EP_W: src = s->w[s->cur]; break;
+    case EP_VE_MV: case EP_VE: src = s->x[0]; break;
+    case EP_TACT: src = s->tact; break;
+    default: return fail(s, EP_EINVAL, "unknown field");
+    }
+    std::vector<real> h(s->n);
+    CK(cudaMemcpyAsync(h.data(), src, sizeof(real) * s->n, cudaMemcpyDeviceToHost, s->stream));
+    CK(cudaStreamSynchronize(s->stream));
+    for (long long q = 0; q < s->n; ++q) {
+        const double v = (double)h[q];
+        out[q] = field == EP_VM_MV ? 100.0 * v - 80.0 : field == EP_VE_MV ? 100.0 * v : v;
+    }
+    return EP_OK;
+}
+
+template <typename real>
+ep_status set_state_typed(ep_sim *s, const double *v, const double *w, const double *ve)
+{
+    const double *src[3] = {v, w, ve};
+    void *dst[3] = {s->v[s->cur], s->w[s->cur], s->x[0]};
+    const double rest[3] = {0.0, 1.0, 0.0};
+    std::vector<real> h(s->n);
+    for (int f = 0; f < 3; ++f) {
+        if (!src[f]) continue;
+        for (long long q = 0; q < s->n; ++q) h[q] = (real)(s->mask[q] ? src[f][q] : rest[f]);
+        CK(cudaMemcpyAsync(dst[f], h.data(), sizeof(real) * s->n, cudaMemcpyHostToDevice, s->stream));
+        CK(cudaStreamSynchronize(s->stream));
+    }
+    return EP_OK;
+}
+
+struct StateHeader {
+    char magic[8];
+    long long n;
+    long long step;
+    int precision;
+    int pad;
+};
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+extern "C" {
+
+ep_status ep_create(const ep_grid_desc *desc, ep_sim **out)
+{
+    if (!out) return EP_EINVAL;
+    *out = nullptr;
+    if (!desc) return EP_EINVAL;
+    if (desc->nx < 1 || desc->ny < 1 || desc->nz < 1 || !(desc->dx_mm > 0.0) || !std::isfinite(desc->dx_mm))
+        return EP_EINVAL;
+    if ((desc->model != EP_MONO && desc->model != EP_BI) || (desc->precision != EP_FP32 && desc->precision != EP_FP64))
+        return EP_EINVAL;
+    if ((desc->dev_alloc == nullptr) != (desc->dev_free == nullptr)) return EP_EINVAL;
+    const long long n = (long long)desc->nx * desc->ny * desc->nz;
+    if (n > 2147483647LL) return EP_EINVAL;
+    ep_sim *s = new (std::nothrow) ep_sim();
+    if (!s) return EP_ENOMEM;
+    s->d = *desc;
+    s->n = n;
+    s->stream = (cudaStream_t)desc->cuda_stream;   // NULL: a private stream is created at set-up
+    *out = s;
+    return EP_OK;
+}
+
+ep_status ep_set_mask(ep_sim *s, const uint8_t *mask, size_t n)
+{
+    if (!s) return EP_EINVAL;
+    if (s->ready) return fail(s, EP_ESTATE, "mask can only be set before the first step");
+    if (!mask || (long long)n != s->n) return fail(s, EP_EINVAL, "mask must hold nx*ny*nz bytes");
+    s->mask.assign(mask, mask + n);
+    for (auto &c : s->mask) c = c ? 1 : 0;
+    s->have_mask = true;
+    return EP_OK;
+}
+
+ep_status ep_set_fibres(ep_sim *s, const float *f, size_t n3)
+{
+    if (!s) return EP_EINVAL;
+    if (s->ready) return fail(s, EP_ESTATE, "fibres can only be set before the first step");
+    if (!f || (long long)n3 != 3 * s->n) return fail(s, EP_EINVAL, "fibres must hold 3*nx*ny*nz floats");
+    for (size_t i = 0; i < n3; ++i)
+        if (!std::isfinite(f[i]) || std::fabs(f[i]) > 1.0001f) return fail(s, EP_EINVAL, "fibre components must be finite and unit or zero");
+    s->fib.assign(f, f + n3);
+    return EP_OK;
+}
+
+ep_status ep_set_params(ep_sim *s, const ep_params *p)
+{
+    if (!s) return EP_EINVAL;
+    if (s->ready) return fail(s, EP_ESTATE, "parameters can only be set before the first step");
+    if (!p) return fail(s, EP_EINVAL, "null parameters");
+    std::string why;
+    if (!params_ok(*p, why)) return fail(s, EP_EINVAL, why);
+    s->p = *p;
+    s->have_params = true;
+    return EP_OK;
+}
+
+ep_status ep_add_stimulus(ep_sim *s, const int lo[3], const int hi[3], double t_start_ms, double dur_ms,
+                          double amp_per_ms)
+{
+    if (!s) return EP_EINVAL;
+    if (s->ready) return fail(s, EP_ESTATE, "stimuli can only be added before the first step");
+    if (!lo || !hi) return fail(s, EP_EINVAL, "null box");
+    if ((int)s->stims.size() >= kMaxStim) return fail(s, EP_EINVAL, "at most 8 stimulus boxes");
+    if (!std::isfinite(t_start_ms) || !std::isfinite(dur_ms) || dur_ms < 0.0 || !std::isfinite(amp_per_ms))
+        return fail(s, EP_EINVAL, "stimulus times and amplitude must be finite, dur >= 0");
+    StimDef d;
+    for (int i = 0; i < 3; ++i) {
+        d.lo[i] = lo[i];
+        d.hi[i] = hi[i];
+    }
+    d.t0 = t_start_ms;
+    d.dur = dur_ms;
+    d.amp = amp_per_ms;
+    s->stims.push_back(d);
+    return EP_OK;
+}
+
+ep_status ep_set_state(ep_sim *s, const double *v, const double *w, const double *ve, size_t n, long long step)
+{
+    if (!s) return EP_EINVAL;
+    if ((long long)n != s->n) return fail(s, EP_EINVAL, "state fields must hold nx*ny*nz doubles");
+    if (step < 0) return fail(s, EP_EINVAL, "step must be >= 0");
+    ep_status st = ensure_ready(s);
+    if (st != EP_OK) return st;
+    st = s->d.precision == EP_FP64 ? set_state_typed<double>(s, v, w, ve) : set_state_typed<float>(s, v, w, ve);
+    if (st == EP_OK) s->step = step;
+    return st;
+}
+
+ep_status ep_step(ep_sim *s, int n_steps, ep_step_stats *stats)
+{
+    if (!s) return EP_EINVAL;
+    if (n_steps < 0) return fail(s, EP_EINVAL, "n_steps must be >= 0");
+    ep_status st = ensure_ready(s);
+    if (st != EP_OK) return st;
+    return s->d.precision == EP_FP64 ? step_typed<double>(s, n_steps, stats) : step_typed<float>(s, n_steps, stats);
+}
+
+ep_status ep_read(ep_sim *s, int field, void *host, size_t bytes)
+{
+    if (!s) return EP_EINVAL;
+    if (!host || (long long)bytes != s->n * (long long)sizeof(double)) return fail(s, EP_EINVAL, "bytes must be n * 8");
+    ep_status st = ensure_ready(s);
+    if (st != EP_OK) return st;
+    return s->d.precision == EP_FP64 ? read_typed<double>(s, field, (double *)host) : read_typed<float>(s, field, (double *)host);
+}
+
+ep_status ep_state_bytes(ep_sim *s, size_t *bytes)
+{
+    if (!s || !bytes) return EP_EINVAL;
+    const size_t rb = s->d.precision == EP_FP64 ? 8 : 4;
+    *bytes = sizeof(StateHeader) + 4 * rb * (size_t)s->n;
+    return EP_OK;
+}
+
+ep_status ep_read_state(ep_sim *s, void *host, size_t bytes)
+{
+    size_t need = 0;
+    if (ep_state_bytes(s, &need) != EP_OK) return EP_EINVAL;
+    if (!host || bytes != need) return fail(s, EP_EINVAL, "state buffer size mismatch (see ep_state_bytes)");
+    ep_status st = ensure_ready(s);
+    if (st != EP_OK) return st;
+    StateHeader h{};
+    std::memcpy(h.magic, "EPSTATE1", 8);
+    h.n = s->n;
+    h.step = s->step;
+    h.precision = s->d.precision;
+    char *p = (char *)host;
+    std::memcpy(p, &h, sizeof(h));
+    p += sizeof(h);
+    const size_t fb = s->rsz * (size_t)s->n;
+    const void *src[4] = {s->v[s->cur], s->w[s->cur], s->x[0], s->tact};
+    for (int f = 0; f < 4; ++f) CK(cudaMemcpyAsync(p + f * fb, src[f], fb, cudaMemcpyDeviceToHost, s->stream));
+    CK(cudaStreamSynchronize(s->stream));
+    return EP_OK;
+}
+
+ep_status ep_write_state(ep_sim *s, const void *host, size_t bytes)
+{
+    size_t need = 0;
+    if (ep_state_bytes(s, &need) != EP_OK) return EP_EINVAL;
+    if (!host || bytes != need) return fail(s, EP_EINVAL, "state buffer size mismatch (see ep_state_bytes)");
+    StateHeader h;
+    std::memcpy(&h, host, sizeof(h));
+    if (std::memcmp(h.magic, "EPSTATE1", 8) != 0 || h.n != s->n || h.precision != s->d.precision || h.step < 0)
+        return fail(s, EP_EINVAL, "state blob does not match this handle");
+    ep_status st = ensure_ready(s);
+    if (st != EP_OK) return st;
+    const char *p = (const char *)host + sizeof(h);
+    const size_t fb = s->rsz * (size_t)s->n;
+    void *dst[4] = {s->v[s->cur], s->w[s->cur], s->x[0], s->tact};
+    for (int f = 0; f < 4; ++f) CK(cudaMemcpyAsync(dst[f], p + f * fb, fb, cudaMemcpyHostToDevice, s->stream));
+    CK(cudaStreamSynchronize(s->stream));
+    s->step = h.step;
+    return EP_OK;
+}
+
+ep_status ep_apply_operator(ep_sim *s, double sig_L, double sig_T, const double *u_host, double *out_host, size_t n)
+{
+    if (!s) return EP_EINVAL;
+    if (!u_host || !out_host || (long long)n != s->n) return fail(s, EP_EINVAL, "fields must hold nx*ny*nz doubles");
+    if (!(sig_T > 0.0) || !(sig_L > 0.0) || !std::isfinite(sig_L) || !std::isfinite(sig_T))
+        return fail(s, EP_EINVAL, "conductivities must be > 0");
+    ep_status st = ensure_ready(s);
+    if (st != EP_OK) return st;
+    // b and x[1] are scratch between steps
+    auto run = [&](auto tag) -> ep_status {
+        using real = decltype(tag);
+        std::vector<real> h(s->n);
+        for (long long q = 0; q < s->n; ++q) h[q] = (real)u_host[q];
+        CK(cudaMemcpyAsync(s->b, h.data(), sizeof(real) * s->n, cudaMemcpyHostToDevice, s->stream));
+        k_fill<real><<<grid_for(s->n, 256), 256, 0, s->stream>>>((real *)s->x[1], s->n, real(0));
+        StencilArgs<real> a = base_args<real>(s);
+        a.sT = (real)sig_T;
+        a.dS = (real)(sig_L - sig_T);
+        a.u = (const real *)s->b;
+        a.out = (real *)s->x[1];
+        k_stencil<real, M_APPLY><<<s->nseg, kThreads, 0, s->stream>>>(a);
+        CK(cudaGetLastError());
+        CK(cudaMemcpyAsync(h.data(), s->x[1], sizeof(real) * s->n, cudaMemcpyDeviceToHost, s->stream));
+        CK(cudaStreamSynchronize(s->stream));
+        for (long long q = 0; q < s->n; ++q) out_host[q] = (double)h[q];
+        return EP_OK;
+    };
+    return s->d.precision == EP_FP64 ? run(double(0)) : run(float(0));
+}
+
+ep_status ep_get_info(ep_sim *s, ep_info *info)
+{
+    if (!s || !info) return EP_EINVAL;
+    ep_status st = ensure_ready(s);
+    if (st != EP_OK) return st;
+    info->n_voxels = s->n;
+    info->n_tissue = s->n_tissue;
+    info->n_components = s->ncomp;
+    info->n_segments = s->nseg;
+    info->omega = s->omega;
+    info->device_bytes = s->dev_bytes;
+    return EP_OK;
+}
+
+ep_status ep_profile_enable(ep_sim *s, int on)
+{
+    if (!s) return EP_EINVAL;
+    ep_status st = ensure_ready(s);
+    if (st != EP_OK) return st;
+    for (auto &e : s->pev)
+        if (!e) CK(cudaEventCreate(&e));
+    s->prof = ep_profile{};
+    s->prof_on = on != 0;
+    return EP_OK;
+}
+
+ep_status ep_get_profile(ep_sim *s, ep_profile *prof)
+{
+    if (!s || !prof) return EP_EINVAL;
+    *prof = s->prof;
+    return EP_OK;
+}
+
+const char *ep_last_error(const ep_sim *s)
+{
+    if (!s) return "null handle";
+    return s->err.c_str();
+}
+
+void ep_destroy(ep_sim *s)
+{
+    if (!s) return;
+    if (s->ready && s->stream) cudaStreamSynchronize(s->stream);
+    if (s->sweep_graph) cudaGraphExecDestroy(s->sweep_graph);
+    for (auto &e : s->ev)
+        if (e) cudaEventDestroy(e);
+    for (auto &e : s->pev)
+        if (e) cudaEventDestroy(e);
+    if (s->ctl_host) cudaFreeHost(s->ctl_host);
+    dfree_all(s);
+    if (s->own_stream) cudaStreamDestroy(s->stream);
+    delete s;
+}
+
+}  // extern "C"
