@@ -13,7 +13,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libep.so")
 SOURCES = [os.path.join(CSRC, "ep_api.cu")]
-DEPS = SOURCES + [os.path.join(CSRC, "ep_kernels.cuh"), os.path.join(ROOT, "include", "ep.h")]
+HEADERS = [os.path.join(CSRC, h) for h in ("ep_kernels.cuh", "ep_common.cuh", "ep_stencil.cuh", "ep_aux.cuh")]
+DEPS = SOURCES + HEADERS + [os.path.join(ROOT, "include", "ep.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -31,12 +32,17 @@ def needs_build() -> bool:
     return any(os.path.getmtime(p) > t for p in DEPS)
 
 
-def build(force: bool = False, ptxas_verbose: bool = False) -> str:
-    if not force and not needs_build():
+def build(force: bool = False, ptxas_verbose: bool = False, defines=None, out: str = None) -> str:
+    """Compile libep.so.  ``defines`` (e.g. {"EP_WARPS": 8}) override the tile
+    constants; ``out`` writes the library elsewhere (used for tuning builds)."""
+    target = out or LIB
+    if out is None and not defines and not force and not needs_build():
         return LIB
-    tmp = LIB + f".tmp{os.getpid()}"
+    tmp = target + f".tmp{os.getpid()}"
     cmd = [nvcc(), *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-shared",
            "-I", os.path.join(ROOT, "include"), "-o", tmp, *SOURCES]
+    for k, v in (defines or {}).items():
+        cmd.insert(1, f"-D{k}={v}")
     if ptxas_verbose:
         cmd.insert(1, "-Xptxas=-v")
     r = subprocess.run(cmd, cwd=HERE, capture_output=True, text=True)
@@ -45,8 +51,8 @@ def build(force: bool = False, ptxas_verbose: bool = False) -> str:
         raise RuntimeError("nvcc failed building libep.so")
     if ptxas_verbose:
         sys.stderr.write(r.stderr)
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, target)
+    return target
 
 
 if __name__ == "__main__":

@@ -25,7 +25,10 @@ using namespace gbep;
 
 namespace {
 
-constexpr int kZSeg = 16;          // output planes per segment
+#ifndef EP_ZSEG
+#define EP_ZSEG 16
+#endif
+constexpr int kZSeg = EP_ZSEG;     // output planes per z-march segment
 constexpr int kSweepChunk = 64;    // sweeps per queued graph chunk
 constexpr double kDivFactor = 1e16;
 
@@ -118,6 +121,9 @@ void dfree_all(ep_sim *s)
     s->allocs.clear();
     s->dev_bytes = 0;
 }
+
+// CTAs of a stencil launch: one per work item (segment)
+int stencil_blocks(const ep_sim *s) { return std::max(1, s->nseg); }
 
 int grid_for(long long n, int threads)
 {
@@ -225,9 +231,10 @@ ep_status setup_typed(ep_sim *s)
             }
         }
     std::stable_sort(segs.begin(), segs.end(), [](const Seg &a, const Seg &b) {
+        // warps of one CTA take consecutive row tiles of one column (shared halo rows hit L1)
         if (a.k0 / kZSeg != b.k0 / kZSeg) return a.k0 / kZSeg < b.k0 / kZSeg;
-        if (a.by != b.by) return a.by < b.by;
-        return a.bx < b.bx;
+        if (a.bx != b.bx) return a.bx < b.bx;
+        return a.by < b.by;
     });
     s->nseg = (int)segs.size();
 
@@ -248,7 +255,7 @@ ep_status setup_typed(ep_sim *s)
     s->comp_chunk0 = (int *)dalloc(s, sizeof(int) * comp_chunk0.size());
     s->comp_count = (long long *)dalloc(s, sizeof(long long) * comp_count.size());
     s->means = (double *)dalloc(s, sizeof(double) * nc);
-    s->partials = (double *)dalloc(s, sizeof(double) * std::max(s->nseg, s->nchunk));
+    s->partials = (double *)dalloc(s, sizeof(double) * std::max(stencil_blocks(s), s->nchunk));
     s->ctl = (Ctl *)dalloc(s, sizeof(Ctl));
     void *tmp_fib = dalloc(s, sizeof(float) * 3 * n);
     void *tmp_mask = dalloc(s, n);
@@ -311,6 +318,7 @@ StencilArgs<real> base_args(ep_sim *s)
     a.ny = s->d.ny;
     a.nz = s->d.nz;
     a.segs = s->segs;
+    a.nseg = s->nseg;
     a.rec = s->rec;
     a.C = (real)(1.0 / (8.0 * s->d.dx_mm * s->d.dx_mm));
     a.ctl = s->ctl;
@@ -343,7 +351,7 @@ ep_status build_sweep_graph(ep_sim *s)
     cudaGraph_t g = nullptr;
     CK(cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeThreadLocal));
     for (int i = 0; i < kSweepChunk; ++i)
-        k_stencil<real, M_JAC><<<s->nseg, kThreads, 0, s->stream>>>(a);
+        k_stencil<real, M_JAC><<<stencil_blocks(s), kThreads,0, s->stream>>>(a);
     cudaError_t e = cudaStreamEndCapture(s->stream, &g);
     if (e != cudaSuccess) return fail(s, EP_ECUDA, std::string("sweep graph capture: ") + cudaGetErrorString(e));
     e = cudaGraphInstantiate(&s->sweep_graph, g, 0);
@@ -406,7 +414,7 @@ ep_status solve_elliptic(ep_sim *s, int &iters, double &relres, int &conv, int &
     r.dS = (real)(s->p.sig_iL - s->p.sig_iT);
     r.u = (const real *)s->v[s->cur];
     r.out = (real *)s->b;
-    k_stencil<real, M_RHS><<<s->nseg, kThreads, 0, st>>>(r);
+    k_stencil<real, M_RHS><<<stencil_blocks(s), kThreads,0, st>>>(r);
     k_comp_mean<real><<<s->nchunk, kRedThreads, 0, st>>>((const real *)s->b, (const real *)s->b, 0, s->idx, s->chunks,
                                                          s->comp_chunk0, s->comp_count, s->ncomp, s->partials,
                                                          s->means, s->ctl);
@@ -426,7 +434,7 @@ ep_status solve_elliptic(ep_sim *s, int &iters, double &relres, int &conv, int &
             queued += kSweepChunk;
         } else {
             const StencilArgs<real> a = jac_args<real>(s);
-            for (; queued < maxit; ++queued) k_stencil<real, M_JAC><<<s->nseg, kThreads, 0, st>>>(a);
+            for (; queued < maxit; ++queued) k_stencil<real, M_JAC><<<stencil_blocks(s), kThreads,0, st>>>(a);
             CK(cudaGetLastError());
         }
         CK(cudaMemcpyAsync(&s->ctl_host[c & 1], s->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
@@ -501,8 +509,8 @@ ep_status step_typed(ep_sim *s, int n_steps, ep_step_stats *stats)
         a.tact = (real *)s->tact;
         // off-tissue values of the new buffers must equal the old ones (rest):
         // they are never written, and both buffers were initialised alike.
-        if (s->d.model == EP_MONO) k_stencil<real, M_PAR_MONO><<<s->nseg, kThreads, 0, st>>>(a);
-        else k_stencil<real, M_PAR_BI><<<s->nseg, kThreads, 0, st>>>(a);
+        if (s->d.model == EP_MONO) k_stencil<real, M_PAR_MONO><<<stencil_blocks(s), kThreads,0, st>>>(a);
+        else k_stencil<real, M_PAR_BI><<<stencil_blocks(s), kThreads,0, st>>>(a);
         CK(cudaGetLastError());
         s->cur = 1 - s->cur;
         if (s->d.model == EP_BI) {
@@ -771,7 +779,7 @@ ep_status ep_apply_operator(ep_sim *s, double sig_L, double sig_T, const double 
         a.dS = (real)(sig_L - sig_T);
         a.u = (const real *)s->b;
         a.out = (real *)s->x[1];
-        k_stencil<real, M_APPLY><<<s->nseg, kThreads, 0, s->stream>>>(a);
+        k_stencil<real, M_APPLY><<<stencil_blocks(s), kThreads,0, s->stream>>>(a);
         CK(cudaGetLastError());
         CK(cudaMemcpyAsync(h.data(), s->x[1], sizeof(real) * s->n, cudaMemcpyDeviceToHost, s->stream));
         CK(cudaStreamSynchronize(s->stream));

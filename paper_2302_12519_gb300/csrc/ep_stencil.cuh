@@ -1,0 +1,334 @@
+// ep_stencil.cuh -- the z-marching stencil kernel of the voxel electrophysiology step.
+//
+// Operator (Sec. "Operators / Laplacian", Sec. "Matrix-Free Assembly",
+// Eq. ass3 with F = dx I, and the conductivity block S1 of Sec. "Diffusion"):
+//   at every grid vertex p (corner of a 2x2x2 voxel block)
+//     h_a   = mean over the valid a-pairs of the block of (u_hi - u_lo)
+//             (a pair is valid when both voxels are tissue: no-flux mask)
+//     S_p   = (1/8) sum over tissue voxels j of the block of Sigma_j,
+//             Sigma_j = sT I + (sL - sT) f_j f_j^T                (Eq. sigma1)
+//     Fh_a  = r_a (nT sT h + dS M h)_a,   r_a = 1 / (#valid a-pairs), 0 if none,
+//             nT = #tissue voxels, M = sum f f^T, dS = sL - sT
+//   at every tissue voxel q
+//     (L u)_q = C * sum_a [ T(q - e_a) Phi_a^- - T(q + e_a) Phi_a^+ ],
+//             Phi = sum of Fh_a over the 4 vertices of the face,
+//             C = 1 / (8 dx^2).
+//   L u approximates -div(Sigma grad u); L is symmetric PSD and conserves
+//   charge (L 1 = 0).
+//
+// Work decomposition (GB300 design; the paper runs one thread per matrix row):
+// a CTA owns 30 x kTileY output voxels of the x-y plane and marches through a
+// z-range.  Warp w holds voxel rows (y0 + w - 1, y0 + w); lane l holds voxel
+// column x0 - 1 + l, so x-neighbours come from warp shuffles.  Each warp forms
+// the vertex row between its two voxel rows; the vertex row below comes from
+// warp w - 1 through shared memory (one barrier per z-plane).  Tissue flags
+// are 0/1 multipliers, so masking costs one multiply; the fibre outer
+// products of a column are summed once and the left column's sum arrives by
+// shuffle.  The plane loop is unrolled by two with two state records that
+// swap roles, so nothing is copied between planes, and the loads of plane
+// k + 1 are issued before plane k is processed.  The conductivity sums are
+// rebuilt from the fp16 fibres on every pass: on this GPU recomputing them
+// costs less than streaming precomputed FP32 coefficients.
+#pragma once
+
+#include "ep_common.cuh"
+
+namespace gbep {
+
+template <typename real>
+__device__ __forceinline__ real rcp_count(real n)
+{
+    return n > real(0.5) ? real(1) / n : real(0);
+}
+template <>
+__device__ __forceinline__ float rcp_count<float>(float n)
+{
+    return n > 0.5f ? __fdividef(1.0f, n) : 0.0f;   // n in {1, 2, 3, 4}
+}
+
+// Loads of one plane for a lane's two voxel rows (lo = y0 + w - 1, hi = y0 + w).
+template <typename real, int MODE>
+struct Ld {
+    ushort4 rLo, rHi;
+    real uLo, uHi;
+    real wLo, wHi;     // PAR
+    real veLo, veHi;   // PAR_BI
+    real bLo;          // JAC
+};
+
+// What the next plane needs from this one.
+template <typename real>
+struct St {
+    real uLo, uHi, uLoL, uHiL;   // values of own / left column (0 off the tissue)
+    real tLo, tHi, tLoL, tHiL;   // tissue 0/1
+    real nT;                     // tissue count of the four voxels of this plane
+    real Y[6];                   // sum of f f^T over the four voxels of this plane
+    real sx, cx;                 // masked x-differences of this plane and their count
+    real sy, cy;                 // masked y-differences of this plane and their count
+    real FB[3], FA[3];           // vertex fluxes of the vertex plane below: own row, row below
+    real tYm;                    // tissue of voxel (x, lo - 1) in this plane
+    real tzm;                    // tissue of voxel (x, lo) in the plane below
+    real e0, e1, e2;             // output voxel (x, lo): JAC b, 1/Dhat ; PAR v*, w+, v
+};
+
+template <typename real, int MODE>
+__device__ __forceinline__ void load_plane(const StencilArgs<real> &a, const real *src, int k, bool lo_in, bool hi_in,
+                                           int qlo, int qhi, int plane, Ld<real, MODE> &L)
+{
+    const bool kin = (unsigned)k < (unsigned)a.nz;
+    L.rLo = L.rHi = make_ushort4(0, 0, 0, kNonTissue);
+    L.uLo = L.uHi = L.veLo = L.veHi = L.bLo = real(0);
+    L.wLo = L.wHi = real(1);
+    if (kin && lo_in) {
+        const int q = qlo + k * plane;
+        L.rLo = __ldg(a.rec + q);
+        L.uLo = __ldg(src + q);
+        if (MODE == M_PAR_MONO || MODE == M_PAR_BI) L.wLo = __ldg(a.w + q);
+        if (MODE == M_PAR_BI) L.veLo = __ldg(a.ve + q);
+        if (MODE == M_JAC) L.bLo = __ldg(a.b + q);
+    }
+    if (kin && hi_in) {
+        const int q = qhi + k * plane;
+        L.rHi = __ldg(a.rec + q);
+        L.uHi = __ldg(src + q);
+        if (MODE == M_PAR_MONO || MODE == M_PAR_BI) L.wHi = __ldg(a.w + q);
+        if (MODE == M_PAR_BI) L.veHi = __ldg(a.ve + q);
+    }
+}
+
+struct Lane {
+    int lane, wid, x, ylo;
+    int qlo, plane;
+    bool out_lane;
+};
+
+// Process plane k: P = state of plane k - 1, C receives the state of plane k.
+// Forms the vertex row between rows lo/hi at vertex plane k (k > kbeg) and
+// writes voxel (x, lo, k - 1) (k > kbeg + 1).
+template <typename real, int MODE>
+__device__ __forceinline__ void plane_step(const StencilArgs<real> &a, const Lane &g, int k, bool do_vertex,
+                                           bool do_output, const St<real> &P, St<real> &C, const Ld<real, MODE> &L,
+                                           real (*sF)[3][kWarps][32], real (*sT)[kWarps][32], real *dst, bool check,
+                                           float &acc)
+{
+    // ---- decode the two voxels of the lane ----
+    const bool tlo = rec_tissue(L.rLo), thi = rec_tissue(L.rHi);
+    const real flo0 = (real)h2f(L.rLo.x), flo1 = (real)h2f(L.rLo.y), flo2 = (real)h2f(L.rLo.z);
+    const real fhi0 = (real)h2f(L.rHi.x), fhi1 = (real)h2f(L.rHi.y), fhi2 = (real)h2f(L.rHi.z);
+    real ulo, uhi;
+    C.e0 = C.e1 = C.e2 = real(0);
+    if (MODE == M_PAR_MONO || MODE == M_PAR_BI) {
+        real vs, wn, vs2, wn2;
+        ms_step(a, L.uLo, L.wLo, g.x, g.ylo, k, vs, wn);
+        ms_step(a, L.uHi, L.wHi, g.x, g.ylo + 1, k, vs2, wn2);
+        ulo = tlo ? ((MODE == M_PAR_BI) ? vs + L.veLo : vs) : real(0);
+        uhi = thi ? ((MODE == M_PAR_BI) ? vs2 + L.veHi : vs2) : real(0);
+        C.e0 = vs; C.e1 = wn; C.e2 = L.uLo;
+    } else {
+        ulo = tlo ? L.uLo : real(0);
+        uhi = thi ? L.uHi : real(0);
+        if (MODE == M_JAC) { C.e0 = L.bLo; C.e1 = (real)h2f(L.rLo.w); }
+    }
+    C.uLo = ulo;
+    C.uHi = uhi;
+    C.tLo = tlo ? real(1) : real(0);
+    C.tHi = thi ? real(1) : real(0);
+    C.uLoL = __shfl_up_sync(kFull, ulo, 1);
+    C.uHiL = __shfl_up_sync(kFull, uhi, 1);
+    C.tLoL = __shfl_up_sync(kFull, C.tLo, 1);
+    C.tHiL = __shfl_up_sync(kFull, C.tHi, 1);
+    C.tzm = P.tLo;
+    // outer products of the lane's column (fibres are zero off the tissue), then add the left column
+    real Zo[6];
+    Zo[0] = flo0 * flo0 + fhi0 * fhi0;
+    Zo[1] = flo1 * flo1 + fhi1 * fhi1;
+    Zo[2] = flo2 * flo2 + fhi2 * fhi2;
+    Zo[3] = flo0 * flo1 + fhi0 * fhi1;
+    Zo[4] = flo0 * flo2 + fhi0 * fhi2;
+    Zo[5] = flo1 * flo2 + fhi1 * fhi2;
+#pragma unroll
+    for (int j = 0; j < 6; ++j) C.Y[j] = Zo[j] + __shfl_up_sync(kFull, Zo[j], 1);
+    C.nT = (C.tLo + C.tHi) + (C.tLoL + C.tHiL);
+    // pair differences of this plane: x (left -> own) in rows lo/hi, y (lo -> hi) in columns own/left
+    const real cxlo = C.tLo * C.tLoL, cxhi = C.tHi * C.tHiL;
+    C.sx = cxlo * (ulo - C.uLoL) + cxhi * (uhi - C.uHiL);
+    C.cx = cxlo + cxhi;
+    const real cyo = C.tLo * C.tHi, cyl = C.tLoL * C.tHiL;
+    C.sy = cyo * (uhi - ulo) + cyl * (C.uHiL - C.uLoL);
+    C.cy = cyo + cyl;
+
+    // ---- vertex (x - 1/2, lo + 1/2, k - 1/2) ----
+    real F0 = real(0), F1 = real(0), F2 = real(0);
+    if (do_vertex) {
+        const real czlo = P.tLo * C.tLo, czhi = P.tHi * C.tHi, czlol = P.tLoL * C.tLoL, czhil = P.tHiL * C.tHiL;
+        const real gz = czlo * (ulo - P.uLo) + czhi * (uhi - P.uHi) + czlol * (C.uLoL - P.uLoL) +
+                        czhil * (C.uHiL - P.uHiL);
+        const real nz = (czlo + czhi) + (czlol + czhil);
+        const real gx = P.sx + C.sx, nx = P.cx + C.cx;
+        const real gy = P.sy + C.sy, ny = P.cy + C.cy;
+        const real rx = rcp_count(nx), ry = rcp_count(ny), rz = rcp_count(nz);
+        const real hx = gx * rx, hy = gy * ry, hz = gz * rz;
+        const real iso = a.sT * (P.nT + C.nT);
+        const real M0 = P.Y[0] + C.Y[0], M1 = P.Y[1] + C.Y[1], M2 = P.Y[2] + C.Y[2];
+        const real M3 = P.Y[3] + C.Y[3], M4 = P.Y[4] + C.Y[4], M5 = P.Y[5] + C.Y[5];
+        F0 = rx * (iso * hx + a.dS * (M0 * hx + M3 * hy + M4 * hz));
+        F1 = ry * (iso * hy + a.dS * (M3 * hx + M1 * hy + M5 * hz));
+        F2 = rz * (iso * hz + a.dS * (M4 * hx + M5 * hy + M2 * hz));
+    }
+    // ---- exchange vertex rows between warps (buffer by plane parity) ----
+    const int par = k & 1;
+    sF[par][0][g.wid][g.lane] = F0;
+    sF[par][1][g.wid][g.lane] = F1;
+    sF[par][2][g.wid][g.lane] = F2;
+    sT[par][g.wid][g.lane] = C.tLo;
+    __syncthreads();
+    C.FB[0] = F0; C.FB[1] = F1; C.FB[2] = F2;
+    if (g.wid >= 1) {
+        C.FA[0] = sF[par][0][g.wid - 1][g.lane];
+        C.FA[1] = sF[par][1][g.wid - 1][g.lane];
+        C.FA[2] = sF[par][2][g.wid - 1][g.lane];
+        C.tYm = sT[par][g.wid - 1][g.lane];
+    } else {
+        C.FA[0] = C.FA[1] = C.FA[2] = C.tYm = real(0);
+    }
+
+    // ---- output voxel (x, lo, k - 1) ----
+    if (do_output) {
+        const real phxm = (P.FA[0] + C.FA[0]) + (P.FB[0] + C.FB[0]);
+        const real phxp = __shfl_down_sync(kFull, phxm, 1);
+        const real psyA = P.FA[1] + C.FA[1], psyB = P.FB[1] + C.FB[1];
+        const real phym = psyA + __shfl_down_sync(kFull, psyA, 1);
+        const real phyp = psyB + __shfl_down_sync(kFull, psyB, 1);
+        const real pszP = P.FA[2] + P.FB[2], pszC = C.FA[2] + C.FB[2];
+        const real phzm = pszP + __shfl_down_sync(kFull, pszP, 1);
+        const real phzp = pszC + __shfl_down_sync(kFull, pszC, 1);
+        const real tR = __shfl_down_sync(kFull, P.tLo, 1);
+        if (g.out_lane && P.tLo != real(0)) {
+            const real s = P.tLoL * phxm - tR * phxp + P.tYm * phym - P.tHi * phyp + P.tzm * phzm - C.tLo * phzp;
+            const real Lu = a.C * s;
+            const int q = g.qlo + (k - 1) * g.plane;
+            if (MODE == M_APPLY) {
+                a.out[q] = Lu;
+            } else if (MODE == M_RHS) {
+                a.out[q] = -Lu;
+            } else if (MODE == M_JAC) {
+                const real r = P.e0 - Lu;
+                dst[q] = P.uLo + a.coef * P.e1 * r;
+                if (check) acc += (float)r * (float)r;
+            } else {
+                const real vnew = P.e0 - a.coef * Lu;
+                a.out[q] = vnew;
+                a.wout[q] = P.e1;
+                const real vold = P.e2;
+                if (vold < real(0.5) && vnew >= real(0.5)) {
+                    const real t0 = a.tact[q];
+                    if (t0 < real(0))
+                        a.tact[q] = (real)(a.tn + a.dt_d * (0.5 - (double)vold) / ((double)vnew - (double)vold));
+                }
+                if (!isfinite((double)vnew)) atomicOr(&a.ctl->nonfinite, 1);
+            }
+        }
+    }
+}
+
+template <typename real>
+__device__ __forceinline__ void zero_state(St<real> &S)
+{
+    S.uLo = S.uHi = S.uLoL = S.uHiL = S.tLo = S.tHi = S.tLoL = S.tHiL = S.nT = real(0);
+#pragma unroll
+    for (int j = 0; j < 6; ++j) S.Y[j] = real(0);
+    S.sx = S.cx = S.sy = S.cy = S.tYm = S.tzm = S.e0 = S.e1 = S.e2 = real(0);
+#pragma unroll
+    for (int j = 0; j < 3; ++j) S.FB[j] = S.FA[j] = real(0);
+}
+
+template <typename real, int MODE>
+__global__ void __launch_bounds__(kThreads, kMinBlocks) k_stencil(StencilArgs<real> a)
+{
+    __shared__ real sF[2][3][kWarps][32];   // vertex fluxes, double-buffered by plane parity
+    __shared__ real sT[2][kWarps][32];      // tissue of each warp's lower row
+    __shared__ double sred[kWarps];
+    __shared__ int sLast;
+
+    int sweep = 0;
+    bool check = false;
+    const real *src = a.u;
+    real *dst = a.out;
+    if (MODE == M_JAC) {
+        if (a.ctl->done) return;            // converged earlier: queued sweeps are no-ops
+        sweep = a.ctl->sweep;
+        src = (sweep & 1) ? a.x1 : a.x0;
+        dst = (sweep & 1) ? a.x0 : a.x1;
+        check = (sweep % a.check_every) == 0;
+    }
+
+    Lane g;
+    g.lane = threadIdx.x & 31;
+    g.wid = threadIdx.x >> 5;
+    const Seg sg = a.segs[blockIdx.x];
+    g.x = sg.bx * kTileX - 1 + g.lane;
+    g.ylo = sg.by * kTileY + g.wid - 1;
+    const bool xin = g.x >= 0 && g.x < a.nx;
+    const bool lo_in = xin && g.ylo >= 0 && g.ylo < a.ny;
+    const bool hi_in = xin && g.ylo + 1 >= 0 && g.ylo + 1 < a.ny;
+    g.plane = a.nx * a.ny;
+    g.qlo = lo_in ? g.x + a.nx * g.ylo : 0;
+    const int qhi = hi_in ? g.x + a.nx * (g.ylo + 1) : 0;
+    g.out_lane = g.lane >= 1 && g.lane <= kTileX && g.wid >= 1 && lo_in;
+
+    float acc = 0.f;
+    St<real> S0, S1;
+    zero_state(S0);
+    zero_state(S1);
+    Ld<real, MODE> L0, L1;
+    const int kbeg = sg.k0 - 1, kend = sg.k1;
+    load_plane<real, MODE>(a, src, kbeg, lo_in, hi_in, g.qlo, qhi, g.plane, L0);
+    // two planes per iteration; the state records swap roles
+    for (int k = kbeg;;) {
+        if (k + 1 <= kend) load_plane<real, MODE>(a, src, k + 1, lo_in, hi_in, g.qlo, qhi, g.plane, L1);
+        plane_step<real, MODE>(a, g, k, k > kbeg, k > kbeg + 1, S1, S0, L0, sF, sT, dst, check, acc);
+        if (++k > kend) break;
+        if (k + 1 <= kend) load_plane<real, MODE>(a, src, k + 1, lo_in, hi_in, g.qlo, qhi, g.plane, L0);
+        plane_step<real, MODE>(a, g, k, k > kbeg, k > kbeg + 1, S0, S1, L1, sF, sT, dst, check, acc);
+        if (++k > kend) break;
+    }
+
+    if (MODE == M_JAC) {
+        // residual norm of this sweep's input: per-thread FP32 partial over its
+        // few voxels, FP64 above; deterministic fixed-order reduction
+        double tot = block_sum<kThreads>(check ? (double)acc : 0.0, sred);
+        if (threadIdx.x == 0) {
+            a.partials[blockIdx.x] = tot;
+            __threadfence();
+            sLast = (atomicAdd(&a.ctl->arrive, 1u) == gridDim.x - 1);
+        }
+        __syncthreads();
+        if (sLast) {
+            __threadfence();
+            double s = 0;
+            if (check)
+                for (int i = threadIdx.x; i < (int)gridDim.x; i += kThreads) s += ((volatile double *)a.partials)[i];
+            s = block_sum<kThreads>(s, sred);
+            if (threadIdx.x == 0) {
+                Ctl *c = a.ctl;
+                c->arrive = 0;
+                const int j = sweep + 1;
+                c->sweep = j;
+                if (check) {
+                    c->rnorm2 = s;
+                    if (!(s == s) || isinf(s)) {
+                        c->nonfinite = 1; c->done = 1; c->iters = j;
+                    } else if (s <= c->thresh2) {
+                        c->converged = 1; c->done = 1; c->iters = j;
+                    } else if (s > a.div_factor * c->bnorm2) {
+                        c->diverged = 1; c->done = 1; c->iters = j;
+                    }
+                }
+                if (!c->done && j >= a.max_iter) { c->done = 1; c->iters = j; }
+                __threadfence();
+            }
+        }
+    }
+}
+
+}  // namespace gbep
