@@ -167,6 +167,29 @@ ep_status ep_apply_operator(ep_sim *s, double sig_L, double sig_T,
 
 ep_status ep_get_info(ep_sim *s, ep_info *info);
 
+/* Same as ep_step, but the call allocates no device memory.  (The paper has
+ * no counterpart; this serves embedding code.)  Some callers cannot allocate
+ * while they advance the model: code that plans all device memory up front
+ * (a framework that forbids library allocations after initialisation, a
+ * real-time loop that must not block in the allocator, a multi-tenant
+ * service with a fixed memory budget).  Here the step's scratch (the
+ * elliptic solve's control block, its per-CTA FP64 partial sums, the
+ * per-component means, and the non-finite flag) lives in one fixed device
+ * array compiled into the library, about 290 KB, which every GPU that loads
+ * the library holds until the process exits.  The rest of the state stays in
+ * the handle: the handle must already be set up (one ep_step, ep_set_state
+ * or ep_get_info call, which allocate), else EP_ESTATE.  Limits: at most
+ * 32768 stencil work items (ep_info.n_segments) and 32768 reduction chunks
+ * (2048 tissue voxels each), at most 4096 tissue components; larger problems
+ * get EP_EINVAL with a message.  The first call on a device looks up the
+ * array's device address (cudaGetSymbolAddress) with that device current;
+ * make that first call before any stream capture.  All calls on a device
+ * share the one array and each call clears it first: calls whose work
+ * overlaps on the GPU (several handles on concurrent streams) race on it,
+ * so run them one after another.  Sweeps are launched one by one, without
+ * the CUDA graph that ep_step uses. */
+ep_status ep_step_noalloc(ep_sim *s, int n_steps, ep_step_stats *stats);
+
 /* Device-time accounting of ep_step, measured with CUDA events on the
  * handle's stream (for throughput and roofline reporting).  Enabling resets
  * the counters; enabled accounting adds one event pair per kernel group. */

@@ -27,7 +27,8 @@ EP_VM_MV, EP_W, EP_VE_MV, EP_TACT, EP_V, EP_VE = range(6)
 # every symbol include/ep.h declares
 EXPORTS = ["ep_create", "ep_set_mask", "ep_set_fibres", "ep_set_params", "ep_add_stimulus", "ep_set_state",
            "ep_step", "ep_read", "ep_state_bytes", "ep_read_state", "ep_write_state", "ep_apply_operator",
-           "ep_get_info", "ep_profile_enable", "ep_get_profile", "ep_last_error", "ep_destroy"]
+           "ep_get_info", "ep_step_noalloc", "ep_profile_enable", "ep_get_profile", "ep_last_error",
+           "ep_destroy"]
 
 _ALLOC_T = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
 _FREE_T = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
@@ -88,6 +89,7 @@ def load(path: str = LIB_PATH):
         "ep_add_stimulus": ([vp, ctypes.POINTER(ctypes.c_int * 3), ctypes.POINTER(ctypes.c_int * 3), dp, dp, dp], ip),
         "ep_set_state": ([vp, vp, vp, vp, sz, ctypes.c_longlong], ip),
         "ep_step": ([vp, ip, ctypes.POINTER(StepStats)], ip),
+        "ep_step_noalloc": ([vp, ip, ctypes.POINTER(StepStats)], ip),
         "ep_read": ([vp, ip, vp, sz], ip),
         "ep_state_bytes": ([vp, ctypes.POINTER(sz)], ip),
         "ep_read_state": ([vp, vp, sz], ip),
@@ -205,6 +207,15 @@ class Sim:
         st = self._L.ep_step(self._h, int(n_steps), ctypes.byref(s))
         if not (allow_noconv and st == EP_ENOCONV):
             self._check(st, "ep_step")
+        self.last_status = st
+        return s
+
+    def step_noalloc(self, n_steps: int = 1, allow_noconv: bool = False) -> StepStats:
+        """ep_step_noalloc: same as step() with no device allocation in the call."""
+        s = StepStats()
+        st = self._L.ep_step_noalloc(self._h, int(n_steps), ctypes.byref(s))
+        if not (allow_noconv and st == EP_ENOCONV):
+            self._check(st, "ep_step_noalloc")
         self.last_status = st
         return s
 

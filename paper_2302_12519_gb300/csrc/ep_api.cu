@@ -14,6 +14,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -74,6 +75,7 @@ struct ep_sim {
     cudaGraphExec_t sweep_graph = nullptr;
     int cur = 0;
     long long step = 0;
+    bool noalloc_call = false;   // inside ep_step_noalloc: scratch is the static array, no graph
     // device-time accounting (ep_profile_enable)
     bool prof_on = false;
     cudaEvent_t pev[4] = {nullptr, nullptr, nullptr, nullptr};
@@ -423,18 +425,21 @@ ep_status solve_elliptic(ep_sim *s, int &iters, double &relres, int &conv, int &
                                                              s->partials, s->ctl);
     CK(cudaGetLastError());
     // sweeps, queued in graph chunks, one chunk of look-ahead
-    ep_status gs = build_sweep_graph<real>(s);
-    if (gs != EP_OK) return gs;
+    if (!s->noalloc_call) {
+        ep_status gs = build_sweep_graph<real>(s);
+        if (gs != EP_OK) return gs;
+    }
     if (s->prof_on) CK(cudaEventRecord(s->pev[2], st));
     const long long maxit = s->p.max_iter;
     long long queued = 0;
     for (int c = 0;; ++c) {
-        if (queued + kSweepChunk <= maxit) {
+        if (!s->noalloc_call && queued + kSweepChunk <= maxit) {
             CK(cudaGraphLaunch(s->sweep_graph, st));
             queued += kSweepChunk;
         } else {
             const StencilArgs<real> a = jac_args<real>(s);
-            for (; queued < maxit; ++queued) k_stencil<real, M_JAC><<<stencil_blocks(s), kThreads,0, st>>>(a);
+            const long long stop = std::min(maxit, queued + (long long)kSweepChunk);
+            for (; queued < stop; ++queued) k_stencil<real, M_JAC><<<stencil_blocks(s), kThreads, 0, st>>>(a);
             CK(cudaGetLastError());
         }
         CK(cudaMemcpyAsync(&s->ctl_host[c & 1], s->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
@@ -820,6 +825,94 @@ ep_status ep_get_profile(ep_sim *s, ep_profile *prof)
     if (!s || !prof) return EP_EINVAL;
     *prof = s->prof;
     return EP_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// ep_step_noalloc: the elliptic-solve and non-finite-flag scratch of a step
+// (control block, per-CTA partial sums, component means) comes from one
+// file-scope device array instead of the handle's allocations.  Every device
+// that loads the library holds the array until the process exits; all calls
+// on a device share it, so calls that overlap on the GPU race.
+// ---------------------------------------------------------------------------
+namespace {
+constexpr int kNoAllocMaxPartials = 32768;     // stencil work items and reduction chunks
+constexpr int kNoAllocMaxComponents = 4096;    // face-connected tissue components
+constexpr size_t kNoAllocCtlBytes = 256;       // control block slot
+constexpr size_t kNoAllocBytes =
+    kNoAllocCtlBytes + sizeof(double) * ((size_t)kNoAllocMaxComponents + (size_t)kNoAllocMaxPartials);
+static_assert(sizeof(Ctl) <= kNoAllocCtlBytes, "control block must fit its slot");
+constexpr int kNoAllocMaxDevices = 256;
+std::mutex g_noalloc_mu;
+void *g_noalloc_addr[kNoAllocMaxDevices] = {};
+}  // namespace
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+namespace {
+// Device address of the static scratch on the current device.  In host code
+// the array's name is only a stand-in, so the address is looked up once per
+// device (with that device current) and cached.
+ep_status noalloc_scratch(ep_sim *s, unsigned char **out)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(s, EP_ECUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
+    }
+    if (dev < 0 || dev >= kNoAllocMaxDevices) return fail(s, EP_EINVAL, "device ordinal out of range");
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_addr[dev]) {
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p) {
+            cudaGetLastError();
+            return fail(s, EP_ECUDA, std::string("cudaGetSymbolAddress(scratch): ") + cudaGetErrorString(e));
+        }
+        g_noalloc_addr[dev] = p;
+    }
+    *out = (unsigned char *)g_noalloc_addr[dev];
+    return EP_OK;
+}
+}  // namespace
+
+extern "C" {
+
+ep_status ep_step_noalloc(ep_sim *s, int n_steps, ep_step_stats *stats)
+{
+    if (!s) return EP_EINVAL;
+    if (n_steps < 0) return fail(s, EP_EINVAL, "n_steps must be >= 0");
+    if (!s->ready)
+        return fail(s, EP_ESTATE, "ep_step_noalloc needs a handle that is already set up (call ep_step, "
+                                  "ep_set_state or ep_get_info once first): set-up allocates device memory");
+    if (stencil_blocks(s) > kNoAllocMaxPartials || s->nchunk > kNoAllocMaxPartials)
+        return fail(s, EP_EINVAL, "grid too large for ep_step_noalloc: more than 32768 stencil work items or "
+                                  "reduction chunks (use ep_step)");
+    if (s->ncomp > kNoAllocMaxComponents)
+        return fail(s, EP_EINVAL, "mask has more than 4096 tissue components: too many for ep_step_noalloc "
+                                  "(use ep_step)");
+    unsigned char *base = nullptr;
+    ep_status st = noalloc_scratch(s, &base);
+    if (st != EP_OK) return st;
+    Ctl *ctl = (Ctl *)base;
+    double *means = (double *)(base + kNoAllocCtlBytes);
+    double *partials = means + kNoAllocMaxComponents;
+    // the array keeps the previous call's contents: clear the arrival counter and the flags
+    CK(cudaMemsetAsync(ctl, 0, sizeof(Ctl), s->stream));
+    Ctl *ctl0 = s->ctl;
+    double *means0 = s->means, *partials0 = s->partials;
+    s->ctl = ctl;
+    s->means = means;
+    s->partials = partials;
+    s->noalloc_call = true;
+    st = s->d.precision == EP_FP64 ? step_typed<double>(s, n_steps, stats) : step_typed<float>(s, n_steps, stats);
+    s->ctl = ctl0;
+    s->means = means0;
+    s->partials = partials0;
+    s->noalloc_call = false;
+    return st;
 }
 
 const char *ep_last_error(const ep_sim *s)
