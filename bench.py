@@ -68,7 +68,7 @@ def _peaks():
 
 def _kernel_hash():
     h = hashlib.sha256()
-    for p in ("paper_2302_12519_gb300/csrc/ep_kernels.cuh",):
+    for p in ("paper_2302_12519_gb300/csrc/ep_common.cuh", "paper_2302_12519_gb300/csrc/ep_stencil.cuh"):
         h.update(open(os.path.join(ROOT, p), "rb").read())
     return h.hexdigest()[:16]
 
