@@ -204,6 +204,60 @@ typedef struct {
 
 ep_status ep_profile_enable(ep_sim *s, int on);
 ep_status ep_get_profile(ep_sim *s, ep_profile *prof);
+
+/* ------------------------------------------------------------------------ */
+/* Batched form: many instances advance together.                            */
+/* ------------------------------------------------------------------------ */
+/* The thesis proposes running many cardiac simulations in parallel on one
+ * GPU; this is that form.  Uneven FP32 instances (different grids,
+ * conductivities, stimuli) are advanced together.  Each kernel of a step is
+ * one persistent launch over the packed list of all instances' work items.
+ * Every instance keeps its own elliptic solve: its own sweep count, FP64
+ * residual and stop flag.  A whole chunk of steps, including every
+ * convergence loop, is one CUDA graph with device-side loop conditions, so
+ * the host is not involved between steps.  Results per instance are the same
+ * as ep_step on that instance alone, up to the order of the FP64 reductions
+ * (which does not change either). */
+typedef struct ep_batch ep_batch;
+
+typedef struct {
+    int instances;               /* instances in the batch */
+    long long stencil_items;     /* packed stencil work items per launch */
+    long long chunk_items;       /* packed reduction chunks per launch */
+    size_t device_bytes;         /* device memory of the member handles */
+    size_t budget_bytes;         /* admission budget */
+    int ctas_per_sm;             /* persistent grid: CTAs per SM (tuned) */
+    int sweeps_per_check;        /* sweep launches between device loop checks (tuned) */
+    int zseg;                    /* z-planes per stencil work item (tuned) */
+} ep_batch_info;
+
+/* Create a batch of at most max_instances handles whose device memory may
+ * total at most hbm_budget_bytes (0 = no budget).  cuda_stream may be NULL. */
+ep_status ep_batch_create(int max_instances, size_t hbm_budget_bytes, void *cuda_stream, ep_batch **out);
+
+/* Admit a handle (FP32, same model as the batch's other members; it is set up
+ * here if needed).  The batch does not own it: the caller keeps it alive until
+ * ep_batch_remove and reads results with ep_read on it.  EP_EREJECTED if its
+ * device memory would exceed the budget, EP_EBUSY if the batch is full.
+ * *slot receives the slot number. */
+ep_status ep_batch_add(ep_batch *b, ep_sim *sim, int *slot);
+ep_status ep_batch_remove(ep_batch *b, int slot);
+
+/* Advance every member n_steps time steps (one graph launch). */
+ep_status ep_batch_step(ep_batch *b, int n_steps);
+
+/* Per-member statistics of the last ep_batch_step (iters of its last solve,
+ * whether every solve converged, its step counter). */
+ep_status ep_batch_slot_stats(ep_batch *b, int slot, ep_step_stats *stats);
+
+/* Choose the persistent grid size, the sweeps per device loop check and the
+ * z-planes per work item by timing trial_sweeps sweeps of each candidate on
+ * the members' current states (states are restored afterwards). */
+ep_status ep_batch_autotune(ep_batch *b, int trial_sweeps);
+
+ep_status ep_batch_get_info(ep_batch *b, ep_batch_info *info);
+const char *ep_batch_last_error(const ep_batch *b);
+void ep_batch_destroy(ep_batch *b);
 const char *ep_last_error(const ep_sim *s);
 void ep_destroy(ep_sim *s);
 

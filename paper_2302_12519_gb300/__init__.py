@@ -28,7 +28,9 @@ EP_VM_MV, EP_W, EP_VE_MV, EP_TACT, EP_V, EP_VE = range(6)
 EXPORTS = ["ep_create", "ep_set_mask", "ep_set_fibres", "ep_set_params", "ep_add_stimulus", "ep_set_state",
            "ep_step", "ep_read", "ep_state_bytes", "ep_read_state", "ep_write_state", "ep_apply_operator",
            "ep_get_info", "ep_step_noalloc", "ep_profile_enable", "ep_get_profile", "ep_last_error",
-           "ep_destroy"]
+           "ep_destroy", "ep_batch_create", "ep_batch_add", "ep_batch_remove", "ep_batch_step",
+           "ep_batch_slot_stats", "ep_batch_autotune", "ep_batch_get_info", "ep_batch_last_error",
+           "ep_batch_destroy"]
 
 _ALLOC_T = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
 _FREE_T = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
@@ -61,6 +63,13 @@ class Profile(ctypes.Structure):
     _fields_ = [("sweep_ms", ctypes.c_double), ("other_ms", ctypes.c_double),
                 ("sweep_launches", ctypes.c_longlong), ("sweeps", ctypes.c_longlong),
                 ("other_launches", ctypes.c_longlong), ("steps", ctypes.c_longlong)]
+
+
+class BatchInfo(ctypes.Structure):
+    _fields_ = [("instances", ctypes.c_int), ("stencil_items", ctypes.c_longlong),
+                ("chunk_items", ctypes.c_longlong), ("device_bytes", ctypes.c_size_t),
+                ("budget_bytes", ctypes.c_size_t), ("ctas_per_sm", ctypes.c_int),
+                ("sweeps_per_check", ctypes.c_int), ("zseg", ctypes.c_int)]
 
 
 class EPError(RuntimeError):
@@ -99,6 +108,15 @@ def load(path: str = LIB_PATH):
         "ep_profile_enable": ([vp, ip], ip),
         "ep_get_profile": ([vp, ctypes.POINTER(Profile)], ip),
         "ep_last_error": ([vp], ctypes.c_char_p),
+        "ep_batch_create": ([ip, sz, vp, ctypes.POINTER(vp)], ip),
+        "ep_batch_add": ([vp, vp, ctypes.POINTER(ip)], ip),
+        "ep_batch_remove": ([vp, ip], ip),
+        "ep_batch_step": ([vp, ip], ip),
+        "ep_batch_slot_stats": ([vp, ip, ctypes.POINTER(StepStats)], ip),
+        "ep_batch_autotune": ([vp, ip], ip),
+        "ep_batch_get_info": ([vp, ctypes.POINTER(BatchInfo)], ip),
+        "ep_batch_last_error": ([vp], ctypes.c_char_p),
+        "ep_batch_destroy": ([vp], None),
         "ep_destroy": ([vp], None),
     }
     for name, (args, res) in sigs.items():
@@ -259,6 +277,65 @@ class Sim:
         i = Info()
         self._check(self._L.ep_get_info(self._h, ctypes.byref(i)), "ep_get_info")
         return i
+
+
+class Batch:
+    """A batch of handles advanced together (ep_batch).  Members stay owned by
+    the caller and must outlive their membership."""
+
+    def __init__(self, max_instances: int, hbm_budget_bytes: int = 0, stream: Optional[int] = None):
+        L = load()
+        self._L = L
+        h = ctypes.c_void_p()
+        st = L.ep_batch_create(int(max_instances), int(hbm_budget_bytes), stream, ctypes.byref(h))
+        if st != EP_OK:
+            raise EPError(st, "ep_batch_create")
+        self._h = h
+        self._members = {}
+
+    def _check(self, st: int, what: str):
+        if st != EP_OK:
+            raise EPError(st, f"{what}: {self._L.ep_batch_last_error(self._h).decode()}")
+
+    def add(self, sim: "Sim") -> int:
+        slot = ctypes.c_int(-1)
+        self._check(self._L.ep_batch_add(self._h, sim._h, ctypes.byref(slot)), "ep_batch_add")
+        self._members[slot.value] = sim
+        return slot.value
+
+    def remove(self, slot: int):
+        self._check(self._L.ep_batch_remove(self._h, int(slot)), "ep_batch_remove")
+        self._members.pop(slot, None)
+
+    def step(self, n_steps: int, allow_noconv: bool = False) -> int:
+        st = self._L.ep_batch_step(self._h, int(n_steps))
+        if not (allow_noconv and st == EP_ENOCONV):
+            self._check(st, "ep_batch_step")
+        return st
+
+    def slot_stats(self, slot: int) -> StepStats:
+        s = StepStats()
+        self._check(self._L.ep_batch_slot_stats(self._h, int(slot), ctypes.byref(s)), "ep_batch_slot_stats")
+        return s
+
+    def autotune(self, trial_sweeps: int = 20):
+        self._check(self._L.ep_batch_autotune(self._h, int(trial_sweeps)), "ep_batch_autotune")
+
+    def info(self) -> BatchInfo:
+        i = BatchInfo()
+        self._check(self._L.ep_batch_get_info(self._h, ctypes.byref(i)), "ep_batch_get_info")
+        return i
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._L.ep_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def sim_from_case(case, use_torch: bool = True, model: Optional[int] = None, precision: Optional[int] = None) -> Sim:

@@ -13,6 +13,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <new>
@@ -29,7 +30,8 @@ namespace {
 #ifndef EP_ZSEG
 #define EP_ZSEG 16
 #endif
-constexpr int kZSeg = EP_ZSEG;     // output planes per z-march segment
+constexpr int kZSeg = EP_ZSEG;     // default output planes per z-march segment
+constexpr int kZSegMin = 8;        // smallest segment length the batch autotuner tries
 constexpr int kSweepChunk = 64;    // sweeps per queued graph chunk
 constexpr double kDivFactor = 1e16;
 
@@ -55,6 +57,8 @@ struct ep_sim {
     // derived layout
     long long n_tissue = 0;
     int ncomp = 0, nseg = 0, nchunk = 0;
+    int zseg = kZSeg;            // z-planes per stencil work item
+    long long max_items = 0;     // segment capacity of the segs / partials buffers
     double omega = 0.0;
     size_t rsz = 4;
     // device memory
@@ -73,7 +77,6 @@ struct ep_sim {
     Ctl *ctl_host = nullptr;   // pinned, 2 slots
     cudaEvent_t ev[2] = {nullptr, nullptr};
     cudaGraphExec_t sweep_graph = nullptr;
-    int cur = 0;
     long long step = 0;
     bool noalloc_call = false;   // inside ep_step_noalloc: scratch is the static array, no graph
     // device-time accounting (ep_profile_enable)
@@ -147,6 +150,45 @@ bool params_ok(const ep_params &p, std::string &why)
     return true;
 }
 
+// Stencil work items: every 30 x kTileY tile column that holds tissue is cut
+// into z-ranges of at most zseg planes, skipping planes without tissue.
+std::vector<Seg> build_segments(const uint8_t *m, int nx, int ny, int nz, int zseg)
+{
+    std::vector<Seg> segs;
+    const int nbx = (nx + kTileX - 1) / kTileX, nby = (ny + kTileY - 1) / kTileY;
+    std::vector<char> has(nz);
+    for (int by = 0; by < nby; ++by)
+        for (int bx = 0; bx < nbx; ++bx) {
+            const int xa = bx * kTileX, xb = std::min(xa + kTileX, nx);
+            const int ya = by * kTileY, yb = std::min(ya + kTileY, ny);
+            for (int k = 0; k < nz; ++k) {
+                char h = 0;
+                for (int j = ya; j < yb && !h; ++j) {
+                    const uint8_t *row = m + (long long)nx * (j + (long long)ny * k);
+                    for (int i = xa; i < xb; ++i)
+                        if (row[i]) { h = 1; break; }
+                }
+                has[k] = h;
+            }
+            int k = 0;
+            while (k < nz) {
+                if (!has[k]) { ++k; continue; }
+                const int k0 = k;
+                int k1 = std::min(k0 + zseg, nz);
+                while (!has[k1 - 1]) --k1;
+                segs.push_back(Seg{bx, by, k0, k1});
+                k = k1;
+            }
+        }
+    // neighbouring tiles of one z-range run together (their shared halos hit L2)
+    std::stable_sort(segs.begin(), segs.end(), [zseg](const Seg &a, const Seg &b) {
+        if (a.k0 / zseg != b.k0 / zseg) return a.k0 / zseg < b.k0 / zseg;
+        if (a.bx != b.bx) return a.bx < b.bx;
+        return a.by < b.by;
+    });
+    return segs;
+}
+
 // ---------------------------------------------------------------------------
 // set-up: layout built on the host from the mask, records on the device
 // ---------------------------------------------------------------------------
@@ -206,39 +248,9 @@ ep_status setup_typed(ep_sim *s)
     }
     s->nchunk = (int)chunks.size();
     // z-march segments over tile columns with tissue
-    std::vector<Seg> segs;
-    const int nbx = (nx + kTileX - 1) / kTileX, nby = (ny + kTileY - 1) / kTileY;
-    std::vector<char> has(nz);
-    for (int by = 0; by < nby; ++by)
-        for (int bx = 0; bx < nbx; ++bx) {
-            const int xa = bx * kTileX, xb = std::min(xa + kTileX, nx);
-            const int ya = by * kTileY, yb = std::min(ya + kTileY, ny);
-            for (int k = 0; k < nz; ++k) {
-                char h = 0;
-                for (int j = ya; j < yb && !h; ++j) {
-                    const uint8_t *row = m + (long long)nx * (j + (long long)ny * k);
-                    for (int i = xa; i < xb; ++i)
-                        if (row[i]) { h = 1; break; }
-                }
-                has[k] = h;
-            }
-            int k = 0;
-            while (k < nz) {
-                if (!has[k]) { ++k; continue; }
-                const int k0 = k;
-                int k1 = std::min(k0 + kZSeg, nz);
-                while (!has[k1 - 1]) --k1;
-                segs.push_back(Seg{bx, by, k0, k1});
-                k = k1;
-            }
-        }
-    std::stable_sort(segs.begin(), segs.end(), [](const Seg &a, const Seg &b) {
-        // warps of one CTA take consecutive row tiles of one column (shared halo rows hit L1)
-        if (a.k0 / kZSeg != b.k0 / kZSeg) return a.k0 / kZSeg < b.k0 / kZSeg;
-        if (a.bx != b.bx) return a.bx < b.bx;
-        return a.by < b.by;
-    });
+    std::vector<Seg> segs = build_segments(m, nx, ny, nz, s->zseg);
     s->nseg = (int)segs.size();
+    s->max_items = std::max<long long>((long long)build_segments(m, nx, ny, nz, kZSegMin).size(), s->nseg);
 
     // device buffers
     const size_t rb = sizeof(real);
@@ -251,13 +263,13 @@ ep_status setup_typed(ep_sim *s)
     }
     s->b = dalloc(s, rb * n);
     s->tact = dalloc(s, rb * n);
-    s->segs = (Seg *)dalloc(s, sizeof(Seg) * segs.size());
+    s->segs = (Seg *)dalloc(s, sizeof(Seg) * (size_t)s->max_items);
     s->idx = (int *)dalloc(s, sizeof(int) * order.size());
     s->chunks = (Chunk *)dalloc(s, sizeof(Chunk) * chunks.size());
     s->comp_chunk0 = (int *)dalloc(s, sizeof(int) * comp_chunk0.size());
     s->comp_count = (long long *)dalloc(s, sizeof(long long) * comp_count.size());
     s->means = (double *)dalloc(s, sizeof(double) * nc);
-    s->partials = (double *)dalloc(s, sizeof(double) * std::max(stencil_blocks(s), s->nchunk));
+    s->partials = (double *)dalloc(s, sizeof(double) * std::max<long long>(s->max_items, s->nchunk));
     s->ctl = (Ctl *)dalloc(s, sizeof(Ctl));
     void *tmp_fib = dalloc(s, sizeof(float) * 3 * n);
     void *tmp_mask = dalloc(s, n);
@@ -307,53 +319,93 @@ ep_status setup_typed(ep_sim *s)
     std::memset(s->ctl_host, 0, 2 * sizeof(Ctl));
     CK(cudaEventCreateWithFlags(&s->ev[0], cudaEventDisableTiming));
     CK(cudaEventCreateWithFlags(&s->ev[1], cudaEventDisableTiming));
-    s->cur = 0;
+
     return EP_OK;
 }
 
+// Descriptor of this handle for the kernels.
 template <typename real>
-StencilArgs<real> base_args(ep_sim *s)
+Inst<real> make_inst(const ep_sim *s)
 {
-    StencilArgs<real> a;
-    std::memset(&a, 0, sizeof(a));
-    a.nx = s->d.nx;
-    a.ny = s->d.ny;
-    a.nz = s->d.nz;
-    a.segs = s->segs;
-    a.nseg = s->nseg;
-    a.rec = s->rec;
-    a.C = (real)(1.0 / (8.0 * s->d.dx_mm * s->d.dx_mm));
-    a.ctl = s->ctl;
-    a.partials = s->partials;
-    return a;
+    Inst<real> I;
+    std::memset(&I, 0, sizeof(I));
+    I.nx = s->d.nx;
+    I.ny = s->d.ny;
+    I.nz = s->d.nz;
+    I.model = s->d.model == EP_MONO ? MODEL_MONO : MODEL_BI;
+    I.nseg = s->nseg;
+    I.nchunk = s->nchunk;
+    I.ncomp = s->ncomp;
+    I.check_every = s->p.check_every;
+    I.max_iter = s->p.max_iter;
+    I.segs = s->segs;
+    I.rec = s->rec;
+    for (int i = 0; i < 2; ++i) {
+        I.v[i] = (real *)s->v[i];
+        I.w[i] = (real *)s->w[i];
+    }
+    I.x0 = (real *)s->x[0];
+    I.x1 = (real *)s->x[1];
+    I.b = (real *)s->b;
+    I.tact = (real *)s->tact;
+    I.idx = s->idx;
+    I.chunks = s->chunks;
+    I.comp_chunk0 = s->comp_chunk0;
+    I.comp_count = s->comp_count;
+    I.means = s->means;
+    I.partials = s->partials;
+    I.ctl = s->ctl;
+    const double C = 1.0 / (8.0 * s->d.dx_mm * s->d.dx_mm);
+    const double sLie = s->p.sig_iL + s->p.sig_eL, sTie = s->p.sig_iT + s->p.sig_eT;
+    const double fac = s->d.model == EP_MONO ? s->p.lambda / (1.0 + s->p.lambda) : 1.0;
+    I.sTi = (real)s->p.sig_iT;
+    I.dSi = (real)(s->p.sig_iL - s->p.sig_iT);
+    I.sTie = (real)sTie;
+    I.dSie = (real)(sLie - sTie);
+    I.C = (real)C;
+    I.coef_par = (real)(s->p.dt_ms / s->p.K * fac);
+    I.coef_jac = (real)(s->omega / C);
+    I.dt = (real)s->p.dt_ms;
+    I.inv_tin = (real)(1.0 / s->p.tau_in);
+    I.inv_tout = (real)(1.0 / s->p.tau_out);
+    I.inv_topen = (real)(1.0 / s->p.tau_open);
+    I.inv_tclose = (real)(1.0 / s->p.tau_close);
+    I.vgate = (real)s->p.v_gate;
+    I.dt_d = s->p.dt_ms;
+    I.rel_tol2 = s->p.rel_tol * s->p.rel_tol;
+    I.div_factor = kDivFactor;
+    I.stim.n = 0;
+    for (const StimDef &d : s->stims) {
+        StimBox &b = I.stim.box[I.stim.n++];
+        for (int i = 0; i < 3; ++i) {
+            b.lo[i] = d.lo[i];
+            b.hi[i] = d.hi[i];
+        }
+        b.t0 = d.t0;
+        b.t1 = d.t0 + d.dur;   // the same double expression as t_start + dur
+        b.amp = d.amp;
+    }
+    return I;
 }
 
 template <typename real>
-StencilArgs<real> jac_args(ep_sim *s)
+ApplyIO<real> no_io()
 {
-    StencilArgs<real> a = base_args<real>(s);
-    const double sL = s->p.sig_iL + s->p.sig_eL, sT = s->p.sig_iT + s->p.sig_eT;
-    a.sT = (real)sT;
-    a.dS = (real)(sL - sT);
-    a.coef = (real)(s->omega / (1.0 / (8.0 * s->d.dx_mm * s->d.dx_mm)));
-    a.x0 = (real *)s->x[0];
-    a.x1 = (real *)s->x[1];
-    a.b = (const real *)s->b;
-    a.check_every = s->p.check_every;
-    a.max_iter = s->p.max_iter;
-    a.div_factor = kDivFactor;
-    return a;
+    ApplyIO<real> io;
+    std::memset(&io, 0, sizeof(io));
+    return io;
 }
 
 template <typename real>
 ep_status build_sweep_graph(ep_sim *s)
 {
     if (s->sweep_graph) return EP_OK;
-    const StencilArgs<real> a = jac_args<real>(s);
+    const Inst<real> I = make_inst<real>(s);
+    const ApplyIO<real> io = no_io<real>();
     cudaGraph_t g = nullptr;
     CK(cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeThreadLocal));
     for (int i = 0; i < kSweepChunk; ++i)
-        k_stencil<real, M_JAC><<<stencil_blocks(s), kThreads,0, s->stream>>>(a);
+        k_stencil<real, M_JAC><<<stencil_blocks(s), kThreads, 0, s->stream>>>(I, io);
     cudaError_t e = cudaStreamEndCapture(s->stream, &g);
     if (e != cudaSuccess) return fail(s, EP_ECUDA, std::string("sweep graph capture: ") + cudaGetErrorString(e));
     e = cudaGraphInstantiate(&s->sweep_graph, g, 0);
@@ -364,6 +416,8 @@ ep_status build_sweep_graph(ep_sim *s)
     }
     return EP_OK;
 }
+
+}  // namespace
 
 ep_status ensure_ready(ep_sim *s)
 {
@@ -391,38 +445,26 @@ ep_status ensure_ready(ep_sim *s)
     return EP_OK;
 }
 
-void active_stims(const ep_sim *s, double tn, StimSet &set)
+namespace {
+
+// Writes the device step counter (the state of step n lives in buffers n & 1).
+ep_status set_device_step(ep_sim *s, long long step)
 {
-    set.n = 0;
-    for (const StimDef &d : s->stims) {
-        if (tn >= d.t0 && tn < d.t0 + d.dur && set.n < kMaxStim) {
-            StimBox &b = set.box[set.n++];
-            for (int i = 0; i < 3; ++i) {
-                b.lo[i] = d.lo[i];
-                b.hi[i] = d.hi[i];
-            }
-            b.amp = d.amp;
-        }
-    }
+    CK(cudaMemcpyAsync((char *)s->ctl + offsetof(Ctl, step), &step, sizeof(step), cudaMemcpyHostToDevice, s->stream));
+    CK(cudaStreamSynchronize(s->stream));
+    s->step = step;
+    return EP_OK;
 }
 
 template <typename real>
-ep_status solve_elliptic(ep_sim *s, int &iters, double &relres, int &conv, int &flags)
+ep_status solve_elliptic(ep_sim *s, const Inst<real> &I, int &iters, double &relres, int &conv, int &flags)
 {
     cudaStream_t st = s->stream;
+    const ApplyIO<real> io = no_io<real>();
     // b = -L_i v, zero mean per component, ||b|| and a fresh solve in ctl
-    StencilArgs<real> r = base_args<real>(s);
-    r.sT = (real)s->p.sig_iT;
-    r.dS = (real)(s->p.sig_iL - s->p.sig_iT);
-    r.u = (const real *)s->v[s->cur];
-    r.out = (real *)s->b;
-    k_stencil<real, M_RHS><<<stencil_blocks(s), kThreads,0, st>>>(r);
-    k_comp_mean<real><<<s->nchunk, kRedThreads, 0, st>>>((const real *)s->b, (const real *)s->b, 0, s->idx, s->chunks,
-                                                         s->comp_chunk0, s->comp_count, s->ncomp, s->partials,
-                                                         s->means, s->ctl);
-    const double tol2 = s->p.rel_tol * s->p.rel_tol;
-    k_comp_subtract<real><<<s->nchunk, kRedThreads, 0, st>>>((real *)s->b, s->idx, s->chunks, s->means, 1, tol2,
-                                                             s->partials, s->ctl);
+    k_stencil<real, M_RHS><<<stencil_blocks(s), kThreads, 0, st>>>(I, io);
+    k_comp_mean<real><<<s->nchunk, kRedThreads, 0, st>>>(I, (int)RED_B);
+    k_comp_subtract<real><<<s->nchunk, kRedThreads, 0, st>>>(I);
     CK(cudaGetLastError());
     // sweeps, queued in graph chunks, one chunk of look-ahead
     if (!s->noalloc_call) {
@@ -437,9 +479,8 @@ ep_status solve_elliptic(ep_sim *s, int &iters, double &relres, int &conv, int &
             CK(cudaGraphLaunch(s->sweep_graph, st));
             queued += kSweepChunk;
         } else {
-            const StencilArgs<real> a = jac_args<real>(s);
             const long long stop = std::min(maxit, queued + (long long)kSweepChunk);
-            for (; queued < stop; ++queued) k_stencil<real, M_JAC><<<stencil_blocks(s), kThreads, 0, st>>>(a);
+            for (; queued < stop; ++queued) k_stencil<real, M_JAC><<<stencil_blocks(s), kThreads, 0, st>>>(I, io);
             CK(cudaGetLastError());
         }
         CK(cudaMemcpyAsync(&s->ctl_host[c & 1], s->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
@@ -459,11 +500,8 @@ ep_status solve_elliptic(ep_sim *s, int &iters, double &relres, int &conv, int &
         s->prof.other_launches += 5;   // RHS, 2 reductions + subtract, projection
     }
     // reference potential: subtract each component's mean of the final iterate
-    k_comp_mean<real><<<s->nchunk, kRedThreads, 0, st>>>((const real *)s->x[0], (const real *)s->x[1], 1, s->idx,
-                                                         s->chunks, s->comp_chunk0, s->comp_count, s->ncomp,
-                                                         s->partials, s->means, s->ctl);
-    k_project<real><<<s->nchunk, kRedThreads, 0, st>>>((real *)s->x[0], (const real *)s->x[1], s->idx, s->chunks,
-                                                       s->means, s->ctl);
+    k_comp_mean<real><<<s->nchunk, kRedThreads, 0, st>>>(I, (int)RED_X_FINAL);
+    k_project<real><<<s->nchunk, kRedThreads, 0, st>>>(I);
     CK(cudaGetLastError());
     CK(cudaMemcpyAsync(&s->ctl_host[0], s->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
@@ -489,39 +527,19 @@ ep_status step_typed(ep_sim *s, int n_steps, ep_step_stats *stats)
     int last_iters = 0, all_conv = 1;
     double last_rr = 0.0;
     long long total = 0;
-    const double fac = s->d.model == EP_MONO ? s->p.lambda / (1.0 + s->p.lambda) : 1.0;
+    const Inst<real> I = make_inst<real>(s);
+    const ApplyIO<real> io = no_io<real>();
     for (int it = 0; it < n_steps; ++it) {
         const double sweep_ms0 = s->prof.sweep_ms;
         if (s->prof_on) CK(cudaEventRecord(s->pev[0], st));
-        StencilArgs<real> a = base_args<real>(s);
-        a.sT = (real)s->p.sig_iT;
-        a.dS = (real)(s->p.sig_iL - s->p.sig_iT);
-        a.coef = (real)(s->p.dt_ms / s->p.K * fac);
-        a.dt = (real)s->p.dt_ms;
-        a.inv_tin = (real)(1.0 / s->p.tau_in);
-        a.inv_tout = (real)(1.0 / s->p.tau_out);
-        a.inv_topen = (real)(1.0 / s->p.tau_open);
-        a.inv_tclose = (real)(1.0 / s->p.tau_close);
-        a.vgate = (real)s->p.v_gate;
-        a.tn = (double)s->step * s->p.dt_ms;
-        a.dt_d = s->p.dt_ms;
-        active_stims(s, a.tn, a.stim);
-        a.u = (const real *)s->v[s->cur];
-        a.w = (const real *)s->w[s->cur];
-        a.ve = (const real *)s->x[0];
-        a.out = (real *)s->v[1 - s->cur];
-        a.wout = (real *)s->w[1 - s->cur];
-        a.tact = (real *)s->tact;
-        // off-tissue values of the new buffers must equal the old ones (rest):
-        // they are never written, and both buffers were initialised alike.
-        if (s->d.model == EP_MONO) k_stencil<real, M_PAR_MONO><<<stencil_blocks(s), kThreads,0, st>>>(a);
-        else k_stencil<real, M_PAR_BI><<<stencil_blocks(s), kThreads,0, st>>>(a);
+        // reaction + diffusion: reads v, w of step n (buffer n & 1), writes buffer (n + 1) & 1
+        if (s->d.model == EP_MONO) k_stencil<real, M_PAR_MONO><<<stencil_blocks(s), kThreads, 0, st>>>(I, io);
+        else k_stencil<real, M_PAR_BI><<<stencil_blocks(s), kThreads, 0, st>>>(I, io);
         CK(cudaGetLastError());
-        s->cur = 1 - s->cur;
         if (s->d.model == EP_BI) {
             int iters = 0, conv = 0, flags = 0;
             double rr = 0.0;
-            ep_status e = solve_elliptic<real>(s, iters, rr, conv, flags);
+            ep_status e = solve_elliptic<real>(s, I, iters, rr, conv, flags);
             if (e != EP_OK) return e;
             last_iters = iters;
             last_rr = rr;
@@ -530,13 +548,15 @@ ep_status step_typed(ep_sim *s, int n_steps, ep_step_stats *stats)
             if (flags & 1) ret = EP_ENONFINITE;
             else if (!conv && ret == EP_OK) ret = EP_ENOCONV;
         }
+        k_end_step<real><<<1, 32, 0, st>>>(nullptr, 0, I);
+        CK(cudaGetLastError());
         if (s->prof_on) {
             CK(cudaEventRecord(s->pev[1], st));
             CK(cudaEventSynchronize(s->pev[1]));
             float ms = 0.f;
             CK(cudaEventElapsedTime(&ms, s->pev[0], s->pev[1]));
             s->prof.other_ms += ms - (s->prof.sweep_ms - sweep_ms0);
-            s->prof.other_launches += 1;
+            s->prof.other_launches += 2;
             s->prof.steps += 1;
         }
         s->step++;
@@ -561,8 +581,8 @@ ep_status read_typed(ep_sim *s, int field, double *out)
 {
     const void *src = nullptr;
     switch (field) {
-    case EP_VM_MV: case EP_V: src = s->v[s->cur]; break;
-    case EP_W: src = s->w[s->cur]; break;
+    case EP_VM_MV: case EP_V: src = s->v[s->step & 1]; break;
+    case EP_W: src = s->w[s->step & 1]; break;
     case EP_VE_MV: case EP_VE: src = s->x[0]; break;
     case EP_TACT: src = s->tact; break;
     default: return fail(s, EP_EINVAL, "unknown field");
@@ -581,7 +601,7 @@ template <typename real>
 ep_status set_state_typed(ep_sim *s, const double *v, const double *w, const double *ve)
 {
     const double *src[3] = {v, w, ve};
-    void *dst[3] = {s->v[s->cur], s->w[s->cur], s->x[0]};
+    void *dst[3] = {s->v[s->step & 1], s->w[s->step & 1], s->x[0]};
     const double rest[3] = {0.0, 1.0, 0.0};
     std::vector<real> h(s->n);
     for (int f = 0; f < 3; ++f) {
@@ -691,9 +711,10 @@ ep_status ep_set_state(ep_sim *s, const double *v, const double *w, const double
     if (step < 0) return fail(s, EP_EINVAL, "step must be >= 0");
     ep_status st = ensure_ready(s);
     if (st != EP_OK) return st;
-    st = s->d.precision == EP_FP64 ? set_state_typed<double>(s, v, w, ve) : set_state_typed<float>(s, v, w, ve);
-    if (st == EP_OK) s->step = step;
-    return st;
+    // the state of step n lives in buffers n & 1: move the counter first
+    st = set_device_step(s, step);
+    if (st != EP_OK) return st;
+    return s->d.precision == EP_FP64 ? set_state_typed<double>(s, v, w, ve) : set_state_typed<float>(s, v, w, ve);
 }
 
 ep_status ep_step(ep_sim *s, int n_steps, ep_step_stats *stats)
@@ -738,7 +759,7 @@ ep_status ep_read_state(ep_sim *s, void *host, size_t bytes)
     std::memcpy(p, &h, sizeof(h));
     p += sizeof(h);
     const size_t fb = s->rsz * (size_t)s->n;
-    const void *src[4] = {s->v[s->cur], s->w[s->cur], s->x[0], s->tact};
+    const void *src[4] = {s->v[s->step & 1], s->w[s->step & 1], s->x[0], s->tact};
     for (int f = 0; f < 4; ++f) CK(cudaMemcpyAsync(p + f * fb, src[f], fb, cudaMemcpyDeviceToHost, s->stream));
     CK(cudaStreamSynchronize(s->stream));
     return EP_OK;
@@ -755,12 +776,13 @@ ep_status ep_write_state(ep_sim *s, const void *host, size_t bytes)
         return fail(s, EP_EINVAL, "state blob does not match this handle");
     ep_status st = ensure_ready(s);
     if (st != EP_OK) return st;
+    st = set_device_step(s, h.step);
+    if (st != EP_OK) return st;
     const char *p = (const char *)host + sizeof(h);
     const size_t fb = s->rsz * (size_t)s->n;
-    void *dst[4] = {s->v[s->cur], s->w[s->cur], s->x[0], s->tact};
+    void *dst[4] = {s->v[s->step & 1], s->w[s->step & 1], s->x[0], s->tact};
     for (int f = 0; f < 4; ++f) CK(cudaMemcpyAsync(dst[f], p + f * fb, fb, cudaMemcpyHostToDevice, s->stream));
     CK(cudaStreamSynchronize(s->stream));
-    s->step = h.step;
     return EP_OK;
 }
 
@@ -779,12 +801,13 @@ ep_status ep_apply_operator(ep_sim *s, double sig_L, double sig_T, const double 
         for (long long q = 0; q < s->n; ++q) h[q] = (real)u_host[q];
         CK(cudaMemcpyAsync(s->b, h.data(), sizeof(real) * s->n, cudaMemcpyHostToDevice, s->stream));
         k_fill<real><<<grid_for(s->n, 256), 256, 0, s->stream>>>((real *)s->x[1], s->n, real(0));
-        StencilArgs<real> a = base_args<real>(s);
-        a.sT = (real)sig_T;
-        a.dS = (real)(sig_L - sig_T);
-        a.u = (const real *)s->b;
-        a.out = (real *)s->x[1];
-        k_stencil<real, M_APPLY><<<stencil_blocks(s), kThreads,0, s->stream>>>(a);
+        const Inst<real> I = make_inst<real>(s);
+        ApplyIO<real> io;
+        io.u = (const real *)s->b;
+        io.out = (real *)s->x[1];
+        io.sT = (real)sig_T;
+        io.dS = (real)(sig_L - sig_T);
+        k_stencil<real, M_APPLY><<<stencil_blocks(s), kThreads, 0, s->stream>>>(I, io);
         CK(cudaGetLastError());
         CK(cudaMemcpyAsync(h.data(), s->x[1], sizeof(real) * s->n, cudaMemcpyDeviceToHost, s->stream));
         CK(cudaStreamSynchronize(s->stream));
@@ -899,8 +922,11 @@ ep_status ep_step_noalloc(ep_sim *s, int n_steps, ep_step_stats *stats)
     Ctl *ctl = (Ctl *)base;
     double *means = (double *)(base + kNoAllocCtlBytes);
     double *partials = means + kNoAllocMaxComponents;
-    // the array keeps the previous call's contents: clear the arrival counter and the flags
+    // the array keeps the previous call's contents: clear the arrival counter and the
+    // flags, and carry the handle's step counter in
     CK(cudaMemsetAsync(ctl, 0, sizeof(Ctl), s->stream));
+    const long long step0 = s->step;
+    CK(cudaMemcpyAsync((char *)ctl + offsetof(Ctl, step), &step0, sizeof(step0), cudaMemcpyHostToDevice, s->stream));
     Ctl *ctl0 = s->ctl;
     double *means0 = s->means, *partials0 = s->partials;
     s->ctl = ctl;
@@ -912,6 +938,10 @@ ep_status ep_step_noalloc(ep_sim *s, int n_steps, ep_step_stats *stats)
     s->means = means0;
     s->partials = partials0;
     s->noalloc_call = false;
+    // the handle's own control block follows the step counter
+    const long long step1 = s->step;
+    CK(cudaMemcpyAsync((char *)s->ctl + offsetof(Ctl, step), &step1, sizeof(step1), cudaMemcpyHostToDevice, s->stream));
+    CK(cudaStreamSynchronize(s->stream));
     return st;
 }
 
@@ -934,6 +964,463 @@ void ep_destroy(ep_sim *s)
     dfree_all(s);
     if (s->own_stream) cudaStreamDestroy(s->stream);
     delete s;
+}
+
+}  // extern "C"
+
+// ===========================================================================
+// Batched form (config 3) and the basis of the serving loop.
+// ===========================================================================
+struct ep_batch {
+    int max_inst = 0;
+    size_t budget = 0;
+    cudaStream_t stream = nullptr, side = nullptr;
+    bool own_stream = false;
+    std::string err;
+    std::vector<ep_sim *> slot;   // nullptr = free
+    int model = -1;
+    // device tables: descriptors, packed stencil items, packed reduction chunks
+    Inst<float> *d_inst = nullptr;
+    BItem *d_seg = nullptr, *d_chunk = nullptr;
+    long long *d_steps_left = nullptr;
+    size_t cap_inst = 0, cap_seg = 0, cap_chunk = 0;
+    int ninst = 0;
+    long long nseg_items = 0, nchunk_items = 0;
+    std::vector<int> order;        // slot of each table row
+    cudaGraphExec_t graph = nullptr;
+    bool dirty = true;
+    int nsm = 152, ctas_per_sm = kMinBlocks, sweeps_per_check = 16, zseg = kZSeg;
+    std::vector<Ctl> last;         // per table row, after the last step
+    std::vector<ep_step_stats> stats;
+};
+
+namespace {
+
+ep_status bfail(ep_batch *b, ep_status st, const std::string &msg)
+{
+    if (b) b->err = msg;
+    return st;
+}
+
+#define CKB(call)                                                                                   \
+    do {                                                                                            \
+        cudaError_t e_ = (call);                                                                    \
+        if (e_ != cudaSuccess) {                                                                    \
+            cudaGetLastError();                                                                     \
+            return bfail(b, EP_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_));         \
+        }                                                                                           \
+    } while (0)
+
+// Rebuilds a handle's stencil work items with zseg planes per item (within
+// the capacity allocated at set-up).
+ep_status relayout_segments(ep_sim *s, int zseg)
+{
+    if (zseg == s->zseg) return EP_OK;
+    std::vector<Seg> segs = build_segments(s->mask.data(), s->d.nx, s->d.ny, s->d.nz, zseg);
+    if ((long long)segs.size() > s->max_items) return fail(s, EP_EINVAL, "segment capacity exceeded");
+    CK(cudaMemcpyAsync(s->segs, segs.data(), sizeof(Seg) * segs.size(), cudaMemcpyHostToDevice, s->stream));
+    CK(cudaStreamSynchronize(s->stream));
+    s->nseg = (int)segs.size();
+    s->zseg = zseg;
+    if (s->sweep_graph) {
+        cudaGraphExecDestroy(s->sweep_graph);
+        s->sweep_graph = nullptr;
+    }
+    return EP_OK;
+}
+
+template <typename T>
+ep_status grow(ep_batch *b, T **p, size_t *cap, size_t need)
+{
+    if (need <= *cap && *p) return EP_OK;
+    if (*p) cudaFree(*p);
+    *p = nullptr;
+    *cap = 0;
+    const size_t n = std::max<size_t>(need, 1);
+    CKB(cudaMalloc((void **)p, sizeof(T) * n));
+    *cap = n;
+    return EP_OK;
+}
+
+ep_status rebuild_tables(ep_batch *b)
+{
+    b->order.clear();
+    for (int i = 0; i < b->max_inst; ++i)
+        if (b->slot[i]) b->order.push_back(i);
+    b->ninst = (int)b->order.size();
+    std::vector<Inst<float>> insts;
+    std::vector<BItem> segs, chunks;
+    for (int r = 0; r < b->ninst; ++r) {
+        ep_sim *s = b->slot[b->order[r]];
+        insts.push_back(make_inst<float>(s));
+        for (int i = 0; i < s->nseg; ++i) segs.push_back(BItem{r, i, s->nseg, 0});
+        for (int i = 0; i < s->nchunk; ++i) chunks.push_back(BItem{r, i, s->nchunk, 0});
+    }
+    // interleave instances so that every part of the persistent grid sees work of several
+    // instances (long instances do not end up on a few CTAs)
+    std::stable_sort(segs.begin(), segs.end(), [](const BItem &x, const BItem &y) {
+        const double fx = (x.item + 0.5) / x.nitems, fy = (y.item + 0.5) / y.nitems;
+        return fx < fy;
+    });
+    b->nseg_items = (long long)segs.size();
+    b->nchunk_items = (long long)chunks.size();
+    ep_status st;
+    if ((st = grow(b, &b->d_inst, &b->cap_inst, insts.size())) != EP_OK) return st;
+    if ((st = grow(b, &b->d_seg, &b->cap_seg, segs.size())) != EP_OK) return st;
+    if ((st = grow(b, &b->d_chunk, &b->cap_chunk, chunks.size())) != EP_OK) return st;
+    if (!insts.empty()) {
+        CKB(cudaMemcpyAsync(b->d_inst, insts.data(), sizeof(Inst<float>) * insts.size(), cudaMemcpyHostToDevice,
+                            b->stream));
+        CKB(cudaMemcpyAsync(b->d_seg, segs.data(), sizeof(BItem) * segs.size(), cudaMemcpyHostToDevice, b->stream));
+        CKB(cudaMemcpyAsync(b->d_chunk, chunks.data(), sizeof(BItem) * chunks.size(), cudaMemcpyHostToDevice,
+                            b->stream));
+    }
+    CKB(cudaStreamSynchronize(b->stream));
+    if (b->graph) {
+        cudaGraphExecDestroy(b->graph);
+        b->graph = nullptr;
+    }
+    b->last.assign(b->ninst, Ctl{});
+    b->dirty = false;
+    return EP_OK;
+}
+
+int grid_of(long long items, int cap) { return (int)std::max<long long>(1, std::min<long long>(items, cap)); }
+
+// One graph runs a whole chunk of steps: an outer loop over the steps left
+// (device counter) whose body is one step; inside it, the sweeps of all
+// unfinished solves repeat until every member has converged (or hit its cap).
+ep_status build_batch_graph(ep_batch *b)
+{
+    if (b->graph) return EP_OK;
+    cudaStream_t st = b->stream;
+    const int gs = grid_of(b->nseg_items, b->nsm * b->ctas_per_sm);
+    const int gc = grid_of(b->nchunk_items, b->nsm * 4);
+    const int ns = (int)b->nseg_items, nc = (int)b->nchunk_items;
+    Inst<float> none;
+    std::memset(&none, 0, sizeof(none));
+    cudaGraph_t g = nullptr;
+    CKB(cudaGraphCreate(&g, 0));
+    cudaGraphConditionalHandle ho = 0, hi = 0;
+    CKB(cudaGraphConditionalHandleCreate(&ho, g, 1, cudaGraphCondAssignDefault));
+    alignas(cudaGraphNodeParams) unsigned char po_buf[sizeof(cudaGraphNodeParams)] = {};
+    cudaGraphNodeParams &po = *reinterpret_cast<cudaGraphNodeParams *>(po_buf);
+    po.type = cudaGraphNodeTypeConditional;
+    po.conditional.handle = ho;
+    po.conditional.type = cudaGraphCondTypeWhile;
+    po.conditional.size = 1;
+    cudaGraphNode_t no;
+    CKB(cudaGraphAddNode(&no, g, nullptr, nullptr, 0, &po));
+    cudaGraph_t body = po.conditional.phGraph_out[0];
+    // inner loop handle (bidomain only: a handle without its conditional node is invalid);
+    // the first kernel of every step sets it to 1
+    if (b->model == EP_BI) CKB(cudaGraphConditionalHandleCreate(&hi, body, 1, 0));
+
+    CKB(cudaStreamBeginCaptureToGraph(st, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    if (b->model == EP_BI) k_set_cond<<<1, 1, 0, st>>>(hi, 1u);
+    if (b->model == EP_MONO) k_stencil_batch<float, M_PAR_MONO><<<gs, kThreads, 0, st>>>(b->d_inst, b->d_seg, ns);
+    else k_stencil_batch<float, M_PAR_BI><<<gs, kThreads, 0, st>>>(b->d_inst, b->d_seg, ns);
+    if (b->model == EP_BI) {
+        k_stencil_batch<float, M_RHS><<<gs, kThreads, 0, st>>>(b->d_inst, b->d_seg, ns);
+        k_comp_mean_batch<float><<<gc, kRedThreads, 0, st>>>(b->d_inst, b->d_chunk, nc, (int)RED_B);
+        k_comp_subtract_batch<float><<<gc, kRedThreads, 0, st>>>(b->d_inst, b->d_chunk, nc);
+        // inner loop: sweeps until every member's solve is finished
+        cudaStreamCaptureStatus cs;
+        cudaGraph_t cg = nullptr;
+        const cudaGraphNode_t *deps = nullptr;
+        const cudaGraphEdgeData *ed = nullptr;
+        size_t nd = 0;
+        CKB(cudaStreamGetCaptureInfo(st, &cs, nullptr, &cg, &deps, &ed, &nd));
+        alignas(cudaGraphNodeParams) unsigned char pi_buf[sizeof(cudaGraphNodeParams)] = {};
+        cudaGraphNodeParams &pi = *reinterpret_cast<cudaGraphNodeParams *>(pi_buf);
+        pi.type = cudaGraphNodeTypeConditional;
+        pi.conditional.handle = hi;
+        pi.conditional.type = cudaGraphCondTypeWhile;
+        pi.conditional.size = 1;
+        cudaGraphNode_t ni;
+        CKB(cudaGraphAddNode(&ni, cg, deps, ed, nd, &pi));
+        cudaGraph_t ibody = pi.conditional.phGraph_out[0];
+        CKB(cudaStreamUpdateCaptureDependencies(st, &ni, nullptr, 1, cudaStreamSetCaptureDependencies));
+        CKB(cudaStreamBeginCaptureToGraph(b->side, ibody, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+        for (int i = 0; i < b->sweeps_per_check; ++i)
+            k_stencil_batch<float, M_JAC><<<gs, kThreads, 0, b->side>>>(b->d_inst, b->d_seg, ns);
+        k_solve_cond<float><<<1, 256, 0, b->side>>>(b->d_inst, b->ninst, hi);
+        CKB(cudaStreamEndCapture(b->side, nullptr));
+        k_comp_mean_batch<float><<<gc, kRedThreads, 0, st>>>(b->d_inst, b->d_chunk, nc, (int)RED_X_FINAL);
+        k_project_batch<float><<<gc, kRedThreads, 0, st>>>(b->d_inst, b->d_chunk, nc);
+    }
+    k_end_step<float><<<1, 256, 0, st>>>(b->d_inst, b->ninst, none);
+    k_steps_cond<<<1, 1, 0, st>>>(b->d_steps_left, ho);
+    CKB(cudaStreamEndCapture(st, nullptr));
+    cudaGraphInstantiateParams ip;
+    std::memset(&ip, 0, sizeof(ip));
+    cudaError_t e = cudaGraphInstantiateWithParams(&b->graph, g, &ip);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        b->graph = nullptr;
+        std::string why = std::string("batch graph instantiate: ") + cudaGetErrorString(e) +
+                          " (result " + std::to_string((int)ip.result_out);
+        if (ip.errNode_out) {
+            cudaGraphNodeType t;
+            if (cudaGraphNodeGetType(ip.errNode_out, &t) == cudaSuccess) why += ", node type " + std::to_string((int)t);
+        }
+        why += ")";
+        if (const char *dump = std::getenv("EP_GRAPH_DOT")) cudaGraphDebugDotPrint(g, dump, cudaGraphDebugDotFlagsVerbose);
+        cudaGetLastError();
+        cudaGraphDestroy(g);
+        return bfail(b, EP_ECUDA, why);
+    }
+    cudaGraphDestroy(g);
+    return EP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+ep_status ep_batch_create(int max_instances, size_t hbm_budget_bytes, void *cuda_stream, ep_batch **out)
+{
+    if (!out) return EP_EINVAL;
+    *out = nullptr;
+    if (max_instances < 1 || max_instances > 65536) return EP_EINVAL;
+    ep_batch *b = new (std::nothrow) ep_batch();
+    if (!b) return EP_ENOMEM;
+    b->max_inst = max_instances;
+    b->budget = hbm_budget_bytes;
+    b->slot.assign(max_instances, nullptr);
+    b->stats.assign(max_instances, ep_step_stats{});
+    auto bad = [&](cudaError_t e) {
+        cudaGetLastError();
+        (void)e;
+        if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
+        if (b->side) cudaStreamDestroy(b->side);
+        if (b->d_steps_left) cudaFree(b->d_steps_left);
+        delete b;
+        return EP_ECUDA;
+    };
+    cudaError_t e;
+    if (cuda_stream) {
+        b->stream = (cudaStream_t)cuda_stream;
+    } else {
+        if ((e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking)) != cudaSuccess) return bad(e);
+        b->own_stream = true;
+    }
+    if ((e = cudaStreamCreateWithFlags(&b->side, cudaStreamNonBlocking)) != cudaSuccess) return bad(e);
+    int dev = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return bad(e);
+    if ((e = cudaDeviceGetAttribute(&b->nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return bad(e);
+    if ((e = cudaMalloc((void **)&b->d_steps_left, sizeof(long long))) != cudaSuccess) return bad(e);
+    *out = b;
+    return EP_OK;
+}
+
+ep_status ep_batch_add(ep_batch *b, ep_sim *s, int *slot)
+{
+    if (!b || !s || !slot) return EP_EINVAL;
+    if (s->d.precision != EP_FP32) return bfail(b, EP_EINVAL, "batched members must be FP32 handles");
+    if (b->model >= 0 && s->d.model != b->model)
+        return bfail(b, EP_EINVAL, "batched members must share the model (monodomain or bidomain)");
+    for (ep_sim *t : b->slot)
+        if (t == s) return bfail(b, EP_EINVAL, "handle is already in the batch");
+    int free_slot = -1;
+    size_t used = 0;
+    for (int i = 0; i < b->max_inst; ++i) {
+        if (b->slot[i]) used += b->slot[i]->dev_bytes;
+        else if (free_slot < 0) free_slot = i;
+    }
+    if (free_slot < 0) return bfail(b, EP_EBUSY, "batch is full");
+    ep_status st = ensure_ready(s);
+    if (st != EP_OK) return bfail(b, st, std::string("set-up of the handle failed: ") + s->err);
+    if (b->budget && used + s->dev_bytes > b->budget)
+        return bfail(b, EP_EREJECTED, "admission refused: device memory budget exceeded");
+    if (s->stream) {
+        cudaError_t e = cudaStreamSynchronize(s->stream);
+        if (e != cudaSuccess) return bfail(b, EP_ECUDA, std::string("cudaStreamSynchronize: ") + cudaGetErrorString(e));
+    }
+    st = relayout_segments(s, b->zseg);
+    if (st != EP_OK) return bfail(b, st, s->err);
+    b->slot[free_slot] = s;
+    b->model = s->d.model;
+    b->dirty = true;
+    *slot = free_slot;
+    return EP_OK;
+}
+
+ep_status ep_batch_remove(ep_batch *b, int slot)
+{
+    if (!b || slot < 0 || slot >= b->max_inst || !b->slot[slot]) return EP_EINVAL;
+    b->slot[slot] = nullptr;
+    b->dirty = true;
+    bool any = false;
+    for (ep_sim *t : b->slot) any = any || t;
+    if (!any) b->model = -1;
+    return EP_OK;
+}
+
+ep_status ep_batch_step(ep_batch *b, int n_steps)
+{
+    if (!b) return EP_EINVAL;
+    if (n_steps < 0) return bfail(b, EP_EINVAL, "n_steps must be >= 0");
+    ep_status st;
+    if (b->dirty && (st = rebuild_tables(b)) != EP_OK) return st;
+    if (b->ninst == 0 || n_steps == 0) return EP_OK;
+    if ((st = build_batch_graph(b)) != EP_OK) return st;
+    cudaStream_t s0 = b->stream;
+    // members may have been stepped on their own streams before
+    for (int r = 0; r < b->ninst; ++r) {
+        ep_sim *s = b->slot[b->order[r]];
+        CKB(cudaStreamSynchronize(s->stream));
+        // flags of this call start clear
+        const int zero = 0;
+        CKB(cudaMemcpyAsync((char *)s->ctl + offsetof(Ctl, noconv), &zero, sizeof(int), cudaMemcpyHostToDevice, s0));
+    }
+    const long long n = n_steps;
+    CKB(cudaMemcpyAsync(b->d_steps_left, &n, sizeof(n), cudaMemcpyHostToDevice, s0));
+    CKB(cudaGraphLaunch(b->graph, s0));
+    for (int r = 0; r < b->ninst; ++r)
+        CKB(cudaMemcpyAsync(&b->last[r], b->slot[b->order[r]]->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s0));
+    CKB(cudaStreamSynchronize(s0));
+    ep_status ret = EP_OK;
+    for (int r = 0; r < b->ninst; ++r) {
+        const int sl = b->order[r];
+        ep_sim *s = b->slot[sl];
+        const Ctl &c = b->last[r];
+        s->step = c.step;
+        ep_step_stats &x = b->stats[sl];
+        x.iters = c.iters;
+        x.rel_res = c.bnorm2 > 0.0 ? std::sqrt(c.rnorm2 / c.bnorm2) : 0.0;
+        x.converged = !c.noconv;
+        x.total_iters = c.total_iters;
+        x.step = c.step;
+        if (c.nonfinite) ret = EP_ENONFINITE;
+        else if (c.noconv && ret == EP_OK) ret = EP_ENOCONV;
+    }
+    if (ret == EP_ENOCONV) b->err = "an elliptic solve reached max_iter or diverged";
+    if (ret == EP_ENONFINITE) b->err = "non-finite value in a member's state";
+    return ret;
+}
+
+ep_status ep_batch_slot_stats(ep_batch *b, int slot, ep_step_stats *stats)
+{
+    if (!b || !stats || slot < 0 || slot >= b->max_inst || !b->slot[slot]) return EP_EINVAL;
+    *stats = b->stats[slot];
+    return EP_OK;
+}
+
+ep_status ep_batch_autotune(ep_batch *b, int trial_sweeps)
+{
+    if (!b || trial_sweeps < 1) return EP_EINVAL;
+    ep_status st;
+    if (b->dirty && (st = rebuild_tables(b)) != EP_OK) return st;
+    if (b->ninst == 0) return EP_OK;
+    cudaStream_t s0 = b->stream;
+    // snapshot the solve state of every member: v_e (x0) and the control block
+    std::vector<void *> saved(b->ninst, nullptr);
+    std::vector<Ctl> ctl0(b->ninst);
+    auto release = [&]() {
+        for (void *p : saved)
+            if (p) cudaFree(p);
+    };
+    for (int r = 0; r < b->ninst; ++r) {
+        ep_sim *s = b->slot[b->order[r]];
+        CKB(cudaStreamSynchronize(s->stream));
+        if (cudaMalloc(&saved[r], sizeof(float) * s->n) != cudaSuccess) {
+            cudaGetLastError();
+            release();
+            return bfail(b, EP_ENOMEM, "autotune: no room for the state snapshot");
+        }
+        CKB(cudaMemcpyAsync(saved[r], s->x[0], sizeof(float) * s->n, cudaMemcpyDeviceToDevice, s0));
+        CKB(cudaMemcpyAsync(&ctl0[r], s->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s0));
+    }
+    CKB(cudaStreamSynchronize(s0));
+    cudaEvent_t e0, e1;
+    CKB(cudaEventCreate(&e0));
+    CKB(cudaEventCreate(&e1));
+    const int zsegs[3] = {8, 16, 32};
+    const int ctas[3] = {1, 2, 3};
+    double best = 1e300;
+    int best_z = b->zseg, best_c = b->ctas_per_sm;
+    for (int zi = 0; zi < 3 && st == EP_OK; ++zi) {
+        for (int r = 0; r < b->ninst && st == EP_OK; ++r) st = relayout_segments(b->slot[b->order[r]], zsegs[zi]);
+        if (st != EP_OK || (st = rebuild_tables(b)) != EP_OK) break;
+        for (int ci = 0; ci < 3; ++ci) {
+            if (ctas[ci] > kMinBlocks) continue;
+            // never-converging solves so that every trial sweep does its full work
+            for (int r = 0; r < b->ninst; ++r) {
+                Ctl c = ctl0[r];
+                c.done = 0; c.sweep = 0; c.arrive = 0; c.thresh2 = -1.0; c.bnorm2 = 1e300;
+                CKB(cudaMemcpyAsync(b->slot[b->order[r]]->ctl, &c, sizeof(Ctl), cudaMemcpyHostToDevice, s0));
+            }
+            const int gs = grid_of(b->nseg_items, b->nsm * ctas[ci]);
+            k_stencil_batch<float, M_JAC><<<gs, kThreads, 0, s0>>>(b->d_inst, b->d_seg, (int)b->nseg_items);
+            CKB(cudaEventRecord(e0, s0));
+            for (int i = 0; i < trial_sweeps; ++i)
+                k_stencil_batch<float, M_JAC><<<gs, kThreads, 0, s0>>>(b->d_inst, b->d_seg, (int)b->nseg_items);
+            CKB(cudaEventRecord(e1, s0));
+            CKB(cudaEventSynchronize(e1));
+            float ms = 0.f;
+            CKB(cudaEventElapsedTime(&ms, e0, e1));
+            if (ms < best) {
+                best = ms;
+                best_z = zsegs[zi];
+                best_c = ctas[ci];
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    // restore the members' solve state and apply the best layout
+    for (int r = 0; r < b->ninst; ++r) {
+        ep_sim *s = b->slot[b->order[r]];
+        CKB(cudaMemcpyAsync(s->x[0], saved[r], sizeof(float) * s->n, cudaMemcpyDeviceToDevice, s0));
+        CKB(cudaMemcpyAsync(s->ctl, &ctl0[r], sizeof(Ctl), cudaMemcpyHostToDevice, s0));
+    }
+    CKB(cudaStreamSynchronize(s0));
+    release();
+    if (st != EP_OK) return st;
+    b->zseg = best_z;
+    b->ctas_per_sm = best_c;
+    // sweeps between device loop checks: about 100 us of sweeps, 4..64
+    const double per_sweep_us = 1e3 * best / trial_sweeps;
+    b->sweeps_per_check = (int)std::min(64.0, std::max(4.0, std::ceil(100.0 / std::max(per_sweep_us, 1e-3))));
+    for (int r = 0; r < b->ninst && st == EP_OK; ++r) st = relayout_segments(b->slot[b->order[r]], b->zseg);
+    if (st != EP_OK) return st;
+    return rebuild_tables(b);
+}
+
+ep_status ep_batch_get_info(ep_batch *b, ep_batch_info *info)
+{
+    if (!b || !info) return EP_EINVAL;
+    ep_status st;
+    if (b->dirty && (st = rebuild_tables(b)) != EP_OK) return st;
+    info->instances = b->ninst;
+    info->stencil_items = b->nseg_items;
+    info->chunk_items = b->nchunk_items;
+    size_t used = 0;
+    for (ep_sim *s : b->slot)
+        if (s) used += s->dev_bytes;
+    info->device_bytes = used;
+    info->budget_bytes = b->budget;
+    info->ctas_per_sm = b->ctas_per_sm;
+    info->sweeps_per_check = b->sweeps_per_check;
+    info->zseg = b->zseg;
+    return EP_OK;
+}
+
+const char *ep_batch_last_error(const ep_batch *b) { return b ? b->err.c_str() : "null batch"; }
+
+void ep_batch_destroy(ep_batch *b)
+{
+    if (!b) return;
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    if (b->graph) cudaGraphExecDestroy(b->graph);
+    if (b->d_inst) cudaFree(b->d_inst);
+    if (b->d_seg) cudaFree(b->d_seg);
+    if (b->d_chunk) cudaFree(b->d_chunk);
+    if (b->d_steps_left) cudaFree(b->d_steps_left);
+    if (b->side) cudaStreamDestroy(b->side);
+    if (b->own_stream) cudaStreamDestroy(b->stream);
+    delete b;
 }
 
 }  // extern "C"

@@ -155,85 +155,70 @@ __global__ void k_apply_simple(int nx, int ny, int nz, const ushort4 *rec, const
     }
 }
 
+
 // ---------------------------------------------------------------------------
 // Per-component reductions over the component-sorted tissue index list.
-// One CTA per chunk; the last CTA forms every component's mean in a fixed order.
+// One work item per chunk (2048 tissue voxels of one component); the item
+// that completes the launch for an instance finishes that instance in a fixed
+// order, so results do not depend on scheduling.
 // ---------------------------------------------------------------------------
-constexpr int kRedThreads = 256;
-constexpr int kChunk = 2048;
+struct RedSmem {
+    double sred[kRedThreads / 32];
+    int sflag;
+};
 
-template <typename real>
-__device__ __forceinline__ const real *pick_iterate(const real *x0, const real *x1, int by_parity, const Ctl *ctl)
-{
-    return (by_parity && (ctl->iters & 1)) ? x1 : x0;
-}
+enum RedField { RED_B = 0, RED_X_FINAL = 1 };
 
-// means[c] = mean over component c of x (x = x1 when by_parity and the finished
-// solve took an odd number of sweeps).
+// means[c] = mean over component c of b, or of the final iterate of the solve
+// (x1 when the solve took an odd number of sweeps).
 template <typename real>
-__global__ void __launch_bounds__(kRedThreads)
-k_comp_mean(const real *x0, const real *x1, int by_parity, const int *idx, const Chunk *chunks,
-            const int *comp_chunk0, const long long *comp_count, int ncomp, double *partials,
-            double *means, Ctl *ctl)
+__device__ __forceinline__ void comp_mean_item(const Inst<real> &I, int field, int item, int nitems, RedSmem &sm)
 {
-    __shared__ double sred[kRedThreads / 32];
-    __shared__ int sLast;
-    const real *x = pick_iterate(x0, x1, by_parity, ctl);
-    const Chunk ch = chunks[blockIdx.x];
+    Ctl *ctl = I.ctl;
+    const real *x = field == RED_B ? I.b : ((ctl->iters & 1) ? I.x1 : I.x0);
+    const Chunk ch = I.chunks[item];
     double s = 0.0;
-    for (int i = ch.start + threadIdx.x; i < ch.end; i += kRedThreads) s += (double)x[idx[i]];
-    s = block_sum<kRedThreads>(s, sred);
-    if (threadIdx.x == 0) {
-        partials[blockIdx.x] = s;
-        __threadfence();
-        sLast = (atomicAdd(&ctl->arrive, 1u) == gridDim.x - 1);
+    for (int i = ch.start + threadIdx.x; i < ch.end; i += kRedThreads) s += (double)x[I.idx[i]];
+    s = block_sum<kRedThreads>(s, sm.sred);
+    if (threadIdx.x == 0) I.partials[item] = s;
+    if (!arrive_last(ctl, nitems, &sm.sflag)) return;
+    for (int c = threadIdx.x; c < I.ncomp; c += kRedThreads) {
+        double t = 0.0;
+        for (int i = I.comp_chunk0[c]; i < I.comp_chunk0[c + 1]; ++i) t += ((volatile double *)I.partials)[i];
+        I.means[c] = t / (double)I.comp_count[c];
     }
     __syncthreads();
-    if (!sLast) return;
-    __threadfence();
-    for (int c = threadIdx.x; c < ncomp; c += kRedThreads) {
-        double t = 0.0;
-        for (int i = comp_chunk0[c]; i < comp_chunk0[c + 1]; ++i) t += ((volatile double *)partials)[i];
-        means[c] = t / (double)comp_count[c];
+    if (threadIdx.x == 0) {
+        ctl->arrive = 0;
+        __threadfence();
     }
-    if (threadIdx.x == 0) ctl->arrive = 0;
 }
 
-// x <- x - means[comp] on the tissue.  With want_norm the last CTA also forms
-// ||x||^2 (after the correction) and starts a new elliptic solve in ctl.
+// b <- b - means[comp] on the tissue; the item that completes the launch forms
+// ||b||^2 and starts a new elliptic solve in the control block.
 template <typename real>
-__global__ void __launch_bounds__(kRedThreads)
-k_comp_subtract(real *x, const int *idx, const Chunk *chunks, const double *means, int want_norm,
-                double rel_tol2, double *partials, Ctl *ctl)
+__device__ __forceinline__ void comp_subtract_item(const Inst<real> &I, int item, int nitems, RedSmem &sm)
 {
-    __shared__ double sred[kRedThreads / 32];
-    __shared__ int sLast;
-    const Chunk ch = chunks[blockIdx.x];
-    const double m = means[ch.comp];
+    Ctl *ctl = I.ctl;
+    const Chunk ch = I.chunks[item];
+    const double m = I.means[ch.comp];
     double s = 0.0;
     for (int i = ch.start + threadIdx.x; i < ch.end; i += kRedThreads) {
-        const int q = idx[i];
-        const real v = (real)((double)x[q] - m);
-        x[q] = v;
+        const int q = I.idx[i];
+        const real v = (real)((double)I.b[q] - m);
+        I.b[q] = v;
         s += (double)v * (double)v;
     }
-    if (!want_norm) return;
-    s = block_sum<kRedThreads>(s, sred);
-    if (threadIdx.x == 0) {
-        partials[blockIdx.x] = s;
-        __threadfence();
-        sLast = (atomicAdd(&ctl->arrive, 1u) == gridDim.x - 1);
-    }
-    __syncthreads();
-    if (!sLast) return;
-    __threadfence();
+    s = block_sum<kRedThreads>(s, sm.sred);
+    if (threadIdx.x == 0) I.partials[item] = s;
+    if (!arrive_last(ctl, nitems, &sm.sflag)) return;
     double t = 0.0;
-    for (int i = threadIdx.x; i < (int)gridDim.x; i += kRedThreads) t += ((volatile double *)partials)[i];
-    t = block_sum<kRedThreads>(t, sred);
+    for (int i = threadIdx.x; i < nitems; i += kRedThreads) t += ((volatile double *)I.partials)[i];
+    t = block_sum<kRedThreads>(t, sm.sred);
     if (threadIdx.x == 0) {
         ctl->arrive = 0;
         ctl->bnorm2 = t;
-        ctl->thresh2 = rel_tol2 * t;
+        ctl->thresh2 = I.rel_tol2 * t;
         ctl->sweep = 0;
         ctl->iters = 0;
         ctl->converged = (t == 0.0);
@@ -245,17 +230,87 @@ k_comp_subtract(real *x, const int *idx, const Chunk *chunks, const double *mean
     }
 }
 
-// ve <- x_final - means[comp]; x_final is x1 when the solve took an odd number of sweeps.
+// v_e <- x_final - means[comp] (written to x0, the warm start of the next solve).
+template <typename real>
+__device__ __forceinline__ void project_item(const Inst<real> &I, int item)
+{
+    const real *src = (I.ctl->iters & 1) ? I.x1 : I.x0;
+    const Chunk ch = I.chunks[item];
+    const double m = I.means[ch.comp];
+    for (int i = ch.start + threadIdx.x; i < ch.end; i += kRedThreads) {
+        const int q = I.idx[i];
+        I.x0[q] = (real)((double)src[q] - m);
+    }
+}
+
+template <typename real>
+__global__ void __launch_bounds__(kRedThreads) k_comp_mean(Inst<real> I, int field)
+{
+    __shared__ RedSmem sm;
+    comp_mean_item(I, field, blockIdx.x, gridDim.x, sm);
+}
+
+template <typename real>
+__global__ void __launch_bounds__(kRedThreads) k_comp_subtract(Inst<real> I)
+{
+    __shared__ RedSmem sm;
+    comp_subtract_item(I, blockIdx.x, gridDim.x, sm);
+}
+
+template <typename real>
+__global__ void __launch_bounds__(kRedThreads) k_project(Inst<real> I)
+{
+    project_item(I, blockIdx.x);
+}
+
+// Batched forms: one persistent launch over the packed (instance, chunk) list.
 template <typename real>
 __global__ void __launch_bounds__(kRedThreads)
-k_project(real *x0, const real *x1, const int *idx, const Chunk *chunks, const double *means, const Ctl *ctl)
+k_comp_mean_batch(const Inst<real> *insts, const BItem *items, int nitems, int field)
 {
-    const real *src = (ctl->iters & 1) ? x1 : x0;
-    const Chunk ch = chunks[blockIdx.x];
-    const double m = means[ch.comp];
-    for (int i = ch.start + threadIdx.x; i < ch.end; i += kRedThreads) {
-        const int q = idx[i];
-        x0[q] = (real)((double)src[q] - m);
+    __shared__ RedSmem sm;
+    for (int i = blockIdx.x; i < nitems; i += gridDim.x) {
+        const BItem it = items[i];
+        comp_mean_item(insts[it.inst], field, it.item, it.nitems, sm);
+        __syncthreads();
+    }
+}
+
+template <typename real>
+__global__ void __launch_bounds__(kRedThreads)
+k_comp_subtract_batch(const Inst<real> *insts, const BItem *items, int nitems)
+{
+    __shared__ RedSmem sm;
+    for (int i = blockIdx.x; i < nitems; i += gridDim.x) {
+        const BItem it = items[i];
+        comp_subtract_item(insts[it.inst], it.item, it.nitems, sm);
+        __syncthreads();
+    }
+}
+
+template <typename real>
+__global__ void __launch_bounds__(kRedThreads) k_project_batch(const Inst<real> *insts, const BItem *items, int nitems)
+{
+    for (int i = blockIdx.x; i < nitems; i += gridDim.x) {
+        const BItem it = items[i];
+        project_item(insts[it.inst], it.item);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Step control (single thread per instance).
+// ---------------------------------------------------------------------------
+
+// End of a step: the step counter moves on (v, w of the new step are in buffer
+// (step + 1) & 1 already); the solve's sweeps are added to the total.
+template <typename real>
+__global__ void k_end_step(const Inst<real> *insts, int ninst, Inst<real> one)
+{
+    for (int i = threadIdx.x + blockIdx.x * blockDim.x; i < (insts ? ninst : 1); i += blockDim.x * gridDim.x) {
+        Ctl *c = insts ? insts[i].ctl : one.ctl;
+        const int model = insts ? insts[i].model : one.model;
+        if (model == MODEL_BI) c->total_iters += c->iters;
+        c->step += 1;
     }
 }
 
@@ -264,6 +319,30 @@ __global__ void k_fill(real *p, long long n, real v)
 {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
         p[i] = v;
+}
+
+// Device-side loop control of the graph-captured batched step:
+// the solve continues while any instance's solve is unfinished.
+__global__ void k_set_cond(cudaGraphConditionalHandle h, unsigned value) { cudaGraphSetConditional(h, value); }
+
+template <typename real>
+__global__ void k_solve_cond(const Inst<real> *insts, int ninst, cudaGraphConditionalHandle h)
+{
+    __shared__ int any;
+    if (threadIdx.x == 0) any = 0;
+    __syncthreads();
+    for (int i = threadIdx.x; i < ninst; i += blockDim.x)
+        if (!*(volatile int *)&insts[i].ctl->done) any = 1;
+    __syncthreads();
+    if (threadIdx.x == 0) cudaGraphSetConditional(h, any ? 1u : 0u);
+}
+
+// Outer loop of a multi-step graph: counts down the steps left in the chunk.
+__global__ void k_steps_cond(long long *steps_left, cudaGraphConditionalHandle h)
+{
+    const long long left = *steps_left - 1;
+    *steps_left = left;
+    cudaGraphSetConditional(h, left > 0 ? 1u : 0u);
 }
 
 }  // namespace gbep

@@ -1,6 +1,6 @@
 // ep_common.cuh -- shared definitions of the sm_103a kernels of the voxel
-// electrophysiology step (work items, control block, kernel arguments, the
-// Mitchell-Schaeffer update and a fixed-order block reduction).
+// electrophysiology step: work items, the per-instance descriptor and control
+// block, the Mitchell-Schaeffer update and a fixed-order block reduction.
 #pragma once
 
 #include <cuda_fp16.h>
@@ -23,10 +23,13 @@ constexpr int kTileX = 30;                  // output voxels per row (lanes 1..3
 constexpr int kMaxStim = 8;
 constexpr unsigned kFull = 0xffffffffu;
 constexpr unsigned short kNonTissue = 0xBC00u;  // fp16 -1.0: record lane 3 of a non-tissue voxel
+constexpr int kRedThreads = 256;            // reduction kernels
+constexpr int kChunk = 2048;                // tissue voxels per reduction chunk
 
 enum Mode { M_APPLY = 0, M_RHS = 1, M_PAR_MONO = 2, M_PAR_BI = 3, M_JAC = 4 };
+enum Model { MODEL_MONO = 0, MODEL_BI = 1 };
 
-// One CTA's work: voxel columns x in [30 bx, 30 bx + 30), rows
+// One stencil work item: voxel columns x in [30 bx, 30 bx + 30), rows
 // y in [kTileY by, kTileY by + kTileY), output planes [k0, k1).
 struct Seg {
     int bx, by, k0, k1;
@@ -34,57 +37,64 @@ struct Seg {
 
 struct StimBox {
     int lo[3], hi[3];
+    double t0, t1;        // active while t0 <= t_n < t1 (t1 = t_start + dur, formed in double)
     double amp;
 };
 
 struct StimSet {
-    int n;                // boxes active at this step
+    int n;
     StimBox box[kMaxStim];
 };
 
-// Device control block of the elliptic solve.
+// Device control block of one instance: step counter and the elliptic solve.
 struct Ctl {
-    unsigned int arrive;  // CTAs that finished the current launch (reset by the last one)
+    unsigned int arrive;  // work items that finished the current launch (reset by the last one)
     int done;             // solve finished: converged, capped, diverged or empty rhs
     int sweep;            // sweeps done in the current solve
     int iters;            // sweeps of the finished solve
     int converged;
     int nonfinite;
     int diverged;
-    int pad;
+    int noconv;           // some solve of this run hit max_iter or diverged
     double bnorm2;        // ||b||^2 after the mean correction
     double thresh2;       // rel_tol^2 * ||b||^2
     double rnorm2;        // ||r||^2 at the last check
+    long long step;       // time step n (t_n = n dt); v, w of step n live in buffer n & 1
+    long long total_iters;
 };
 
 struct Chunk {
     int start, end, comp;  // [start, end) into the component-sorted tissue index list
 };
 
+// Everything a kernel needs about one simulation instance.  Passed by value
+// to the single-instance kernels and read from a device table by the
+// batched ones.
 template <typename real>
-struct StencilArgs {
-    int nx, ny, nz;
-    int nseg;             // work items (CTAs)
+struct Inst {
+    int nx, ny, nz, model;
+    int nseg, nchunk, ncomp, check_every;
+    int max_iter, pad;
     const Seg *segs;
     const ushort4 *rec;   // (fx, fy, fz, 1/Dhat) in fp16; lane 3 = -1 off the tissue
-    const real *u;        // APPLY/RHS: operand; PAR: v (old)
-    const real *w;        // PAR: w (old)
-    const real *ve;       // PAR_BI: ve
-    const real *b;        // JAC: right-hand side
-    real *out;            // APPLY: L u; RHS: b; PAR: v (new)
-    real *wout;           // PAR: w (new)
-    real *tact;           // PAR: activation times
-    real *x0, *x1;        // JAC: ping-pong iterates (x0 holds the warm start)
-    real sT, dS, C;       // operator: sigma_T, sigma_L - sigma_T, 1/(8 dx^2)
-    real coef;            // PAR: dt/K (times lambda/(1+lambda) for MONO); JAC: omega / C
+    real *v[2], *w[2];    // state, buffer = step & 1
+    real *x0, *x1;        // elliptic iterates; x0 holds v_e between steps
+    real *b;              // elliptic right-hand side
+    real *tact;           // activation times
+    const int *idx;       // component-sorted tissue voxels
+    const Chunk *chunks;
+    const int *comp_chunk0;
+    const long long *comp_count;
+    double *means, *partials;
+    Ctl *ctl;
+    real sTi, dSi;        // intracellular operator: sigma_T, sigma_L - sigma_T
+    real sTie, dSie;      // elliptic operator (intra + extra)
+    real C;               // 1 / (8 dx^2)
+    real coef_par;        // dt / K (times lambda / (1 + lambda) for the monodomain)
+    real coef_jac;        // omega / C
     real dt, inv_tin, inv_tout, inv_topen, inv_tclose, vgate;
-    double tn, dt_d;      // PAR: t_n and dt (activation time, double)
-    StimSet stim;         // PAR: boxes active at t_n
-    int check_every;      // JAC
-    int max_iter;         // JAC
-    double div_factor;    // JAC: stop as diverged when ||r||^2 > div_factor * ||b||^2
-    double *partials;     // JAC: one per CTA
-    Ctl *ctl;             // JAC (and PAR: non-finite flag)
+    double dt_d, rel_tol2, div_factor;
+    StimSet stim;
 };
 
 __device__ __forceinline__ float h2f(unsigned short b) { return __half2float(__ushort_as_half(b)); }
@@ -92,20 +102,21 @@ __device__ __forceinline__ bool rec_tissue(const ushort4 &r) { return (r.w & 0x8
 
 // Mitchell-Schaeffer explicit Euler (Eqs. ms1, ms2; closing branch -w/tau_close).
 template <typename real>
-__device__ __forceinline__ void ms_step(const StencilArgs<real> &a, real v, real w, int x, int y, int z,
+__device__ __forceinline__ void ms_step(const Inst<real> &I, double tn, real v, real w, int x, int y, int z,
                                         real &vstar, real &wnew)
 {
     real js = 0;
-    for (int s = 0; s < a.stim.n; ++s) {
-        const StimBox &bx = a.stim.box[s];
-        if (x >= bx.lo[0] && x < bx.hi[0] && y >= bx.lo[1] && y < bx.hi[1] && z >= bx.lo[2] && z < bx.hi[2])
+    for (int s = 0; s < I.stim.n; ++s) {
+        const StimBox &bx = I.stim.box[s];
+        if (tn >= bx.t0 && tn < bx.t1 && x >= bx.lo[0] && x < bx.hi[0] && y >= bx.lo[1] && y < bx.hi[1] &&
+            z >= bx.lo[2] && z < bx.hi[2])
             js += real(bx.amp);
     }
-    real jin = v * v * (real(1) - v) * w * a.inv_tin;
-    real jout = -v * a.inv_tout;
-    vstar = v + a.dt * (jin + jout + js);
-    real dw = (v < a.vgate) ? (real(1) - w) * a.inv_topen : -w * a.inv_tclose;
-    wnew = w + a.dt * dw;
+    real jin = v * v * (real(1) - v) * w * I.inv_tin;
+    real jout = -v * I.inv_tout;
+    vstar = v + I.dt * (jin + jout + js);
+    real dw = (v < I.vgate) ? (real(1) - w) * I.inv_topen : -w * I.inv_tclose;
+    wnew = w + I.dt * dw;
 }
 
 // Fixed-order block reduction of one double per thread; result valid in thread 0.
@@ -122,5 +133,26 @@ __device__ __forceinline__ double block_sum(double v, double *sred)
         for (int i = 0; i < NT / 32; ++i) s += sred[i];
     return s;
 }
+
+// Arrival of one work item of an instance; true in the CTA that completes the
+// launch for that instance (all its items' partial results are visible).
+__device__ __forceinline__ bool arrive_last(Ctl *ctl, int nitems, int *sflag)
+{
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        *sflag = (atomicAdd(&ctl->arrive, 1u) == (unsigned)nitems - 1u);
+    }
+    __syncthreads();
+    const bool last = *sflag != 0;
+    if (last) __threadfence();
+    return last;
+}
+
+// Work item of a batched launch: instance, item index within the instance,
+// and the instance's item count.
+struct BItem {
+    int inst, item, nitems, pad;
+};
 
 }  // namespace gbep

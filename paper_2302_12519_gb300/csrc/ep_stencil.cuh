@@ -1,4 +1,4 @@
-// ep_stencil.cuh -- the z-marching stencil kernel of the voxel electrophysiology step.
+// ep_stencil.cuh -- the z-marching stencil kernels of the voxel electrophysiology step.
 //
 // Operator (Sec. "Operators / Laplacian", Sec. "Matrix-Free Assembly",
 // Eq. ass3 with F = dx I, and the conductivity block S1 of Sec. "Diffusion"):
@@ -29,6 +29,10 @@
 // k + 1 are issued before plane k is processed.  The conductivity sums are
 // rebuilt from the fp16 fibres on every pass: on this GPU recomputing them
 // costs less than streaming precomputed FP32 coefficients.
+//
+// The same item body serves the single-instance kernels (descriptor passed by
+// value) and the batched persistent kernels (descriptor read from a device
+// table, items of all instances packed in one list).
 #pragma once
 
 #include "ep_common.cuh"
@@ -45,6 +49,25 @@ __device__ __forceinline__ float rcp_count<float>(float n)
 {
     return n > 0.5f ? __fdividef(1.0f, n) : 0.0f;   // n in {1, 2, 3, 4}
 }
+
+// Diagnostic operand for M_APPLY: out = L_{sL,sT} u.
+template <typename real>
+struct ApplyIO {
+    const real *u;
+    real *out;
+    real sT, dS;
+};
+
+// Per-item constants and pointers, resolved once at the start of an item.
+template <typename real>
+struct Op {
+    const ushort4 *rec;
+    const real *src, *w, *ve, *b;   // loads
+    real *out, *wout, *tact;        // stores (PAR: v, w, t_act; RHS: b; APPLY: out; JAC: next iterate)
+    real sT, dS, C, coef;
+    double tn, dt_d;
+    int nz;
+};
 
 // Loads of one plane for a lane's two voxel rows (lo = y0 + w - 1, hi = y0 + w).
 template <typename real, int MODE>
@@ -72,27 +95,27 @@ struct St {
 };
 
 template <typename real, int MODE>
-__device__ __forceinline__ void load_plane(const StencilArgs<real> &a, const real *src, int k, bool lo_in, bool hi_in,
-                                           int qlo, int qhi, int plane, Ld<real, MODE> &L)
+__device__ __forceinline__ void load_plane(const Op<real> &o, int k, bool lo_in, bool hi_in, int qlo, int qhi,
+                                           int plane, Ld<real, MODE> &L)
 {
-    const bool kin = (unsigned)k < (unsigned)a.nz;
+    const bool kin = (unsigned)k < (unsigned)o.nz;
     L.rLo = L.rHi = make_ushort4(0, 0, 0, kNonTissue);
     L.uLo = L.uHi = L.veLo = L.veHi = L.bLo = real(0);
     L.wLo = L.wHi = real(1);
     if (kin && lo_in) {
         const int q = qlo + k * plane;
-        L.rLo = __ldg(a.rec + q);
-        L.uLo = __ldg(src + q);
-        if (MODE == M_PAR_MONO || MODE == M_PAR_BI) L.wLo = __ldg(a.w + q);
-        if (MODE == M_PAR_BI) L.veLo = __ldg(a.ve + q);
-        if (MODE == M_JAC) L.bLo = __ldg(a.b + q);
+        L.rLo = __ldg(o.rec + q);
+        L.uLo = __ldg(o.src + q);
+        if (MODE == M_PAR_MONO || MODE == M_PAR_BI) L.wLo = __ldg(o.w + q);
+        if (MODE == M_PAR_BI) L.veLo = __ldg(o.ve + q);
+        if (MODE == M_JAC) L.bLo = __ldg(o.b + q);
     }
     if (kin && hi_in) {
         const int q = qhi + k * plane;
-        L.rHi = __ldg(a.rec + q);
-        L.uHi = __ldg(src + q);
-        if (MODE == M_PAR_MONO || MODE == M_PAR_BI) L.wHi = __ldg(a.w + q);
-        if (MODE == M_PAR_BI) L.veHi = __ldg(a.ve + q);
+        L.rHi = __ldg(o.rec + q);
+        L.uHi = __ldg(o.src + q);
+        if (MODE == M_PAR_MONO || MODE == M_PAR_BI) L.wHi = __ldg(o.w + q);
+        if (MODE == M_PAR_BI) L.veHi = __ldg(o.ve + q);
     }
 }
 
@@ -106,10 +129,10 @@ struct Lane {
 // Forms the vertex row between rows lo/hi at vertex plane k (k > kbeg) and
 // writes voxel (x, lo, k - 1) (k > kbeg + 1).
 template <typename real, int MODE>
-__device__ __forceinline__ void plane_step(const StencilArgs<real> &a, const Lane &g, int k, bool do_vertex,
-                                           bool do_output, const St<real> &P, St<real> &C, const Ld<real, MODE> &L,
-                                           real (*sF)[3][kWarps][32], real (*sT)[kWarps][32], real *dst, bool check,
-                                           float &acc)
+__device__ __forceinline__ void plane_step(const Inst<real> &I, const Op<real> &o, const Lane &g, int k,
+                                           bool do_vertex, bool do_output, const St<real> &P, St<real> &C,
+                                           const Ld<real, MODE> &L, real (*sF)[3][kWarps][32],
+                                           real (*sT)[kWarps][32], bool check, float &acc)
 {
     // ---- decode the two voxels of the lane ----
     const bool tlo = rec_tissue(L.rLo), thi = rec_tissue(L.rHi);
@@ -119,8 +142,8 @@ __device__ __forceinline__ void plane_step(const StencilArgs<real> &a, const Lan
     C.e0 = C.e1 = C.e2 = real(0);
     if (MODE == M_PAR_MONO || MODE == M_PAR_BI) {
         real vs, wn, vs2, wn2;
-        ms_step(a, L.uLo, L.wLo, g.x, g.ylo, k, vs, wn);
-        ms_step(a, L.uHi, L.wHi, g.x, g.ylo + 1, k, vs2, wn2);
+        ms_step(I, o.tn, L.uLo, L.wLo, g.x, g.ylo, k, vs, wn);
+        ms_step(I, o.tn, L.uHi, L.wHi, g.x, g.ylo + 1, k, vs2, wn2);
         ulo = tlo ? ((MODE == M_PAR_BI) ? vs + L.veLo : vs) : real(0);
         uhi = thi ? ((MODE == M_PAR_BI) ? vs2 + L.veHi : vs2) : real(0);
         C.e0 = vs; C.e1 = wn; C.e2 = L.uLo;
@@ -168,12 +191,12 @@ __device__ __forceinline__ void plane_step(const StencilArgs<real> &a, const Lan
         const real gy = P.sy + C.sy, ny = P.cy + C.cy;
         const real rx = rcp_count(nx), ry = rcp_count(ny), rz = rcp_count(nz);
         const real hx = gx * rx, hy = gy * ry, hz = gz * rz;
-        const real iso = a.sT * (P.nT + C.nT);
+        const real iso = o.sT * (P.nT + C.nT);
         const real M0 = P.Y[0] + C.Y[0], M1 = P.Y[1] + C.Y[1], M2 = P.Y[2] + C.Y[2];
         const real M3 = P.Y[3] + C.Y[3], M4 = P.Y[4] + C.Y[4], M5 = P.Y[5] + C.Y[5];
-        F0 = rx * (iso * hx + a.dS * (M0 * hx + M3 * hy + M4 * hz));
-        F1 = ry * (iso * hy + a.dS * (M3 * hx + M1 * hy + M5 * hz));
-        F2 = rz * (iso * hz + a.dS * (M4 * hx + M5 * hy + M2 * hz));
+        F0 = rx * (iso * hx + o.dS * (M0 * hx + M3 * hy + M4 * hz));
+        F1 = ry * (iso * hy + o.dS * (M3 * hx + M1 * hy + M5 * hz));
+        F2 = rz * (iso * hz + o.dS * (M4 * hx + M5 * hy + M2 * hz));
     }
     // ---- exchange vertex rows between warps (buffer by plane parity) ----
     const int par = k & 1;
@@ -205,27 +228,27 @@ __device__ __forceinline__ void plane_step(const StencilArgs<real> &a, const Lan
         const real tR = __shfl_down_sync(kFull, P.tLo, 1);
         if (g.out_lane && P.tLo != real(0)) {
             const real s = P.tLoL * phxm - tR * phxp + P.tYm * phym - P.tHi * phyp + P.tzm * phzm - C.tLo * phzp;
-            const real Lu = a.C * s;
+            const real Lu = o.C * s;
             const int q = g.qlo + (k - 1) * g.plane;
             if (MODE == M_APPLY) {
-                a.out[q] = Lu;
+                o.out[q] = Lu;
             } else if (MODE == M_RHS) {
-                a.out[q] = -Lu;
+                o.out[q] = -Lu;
             } else if (MODE == M_JAC) {
                 const real r = P.e0 - Lu;
-                dst[q] = P.uLo + a.coef * P.e1 * r;
+                o.out[q] = P.uLo + o.coef * P.e1 * r;
                 if (check) acc += (float)r * (float)r;
             } else {
-                const real vnew = P.e0 - a.coef * Lu;
-                a.out[q] = vnew;
-                a.wout[q] = P.e1;
+                const real vnew = P.e0 - o.coef * Lu;
+                o.out[q] = vnew;
+                o.wout[q] = P.e1;
                 const real vold = P.e2;
                 if (vold < real(0.5) && vnew >= real(0.5)) {
-                    const real t0 = a.tact[q];
+                    const real t0 = o.tact[q];
                     if (t0 < real(0))
-                        a.tact[q] = (real)(a.tn + a.dt_d * (0.5 - (double)vold) / ((double)vnew - (double)vold));
+                        o.tact[q] = (real)(o.tn + o.dt_d * (0.5 - (double)vold) / ((double)vnew - (double)vold));
                 }
-                if (!isfinite((double)vnew)) atomicOr(&a.ctl->nonfinite, 1);
+                if (!isfinite((double)vnew)) atomicOr(&I.ctl->nonfinite, 1);
             }
         }
     }
@@ -242,38 +265,75 @@ __device__ __forceinline__ void zero_state(St<real> &S)
     for (int j = 0; j < 3; ++j) S.FB[j] = S.FA[j] = real(0);
 }
 
-template <typename real, int MODE>
-__global__ void __launch_bounds__(kThreads, kMinBlocks) k_stencil(StencilArgs<real> a)
-{
-    __shared__ real sF[2][3][kWarps][32];   // vertex fluxes, double-buffered by plane parity
-    __shared__ real sT[2][kWarps][32];      // tissue of each warp's lower row
-    __shared__ double sred[kWarps];
-    __shared__ int sLast;
+struct StencilSmem {
+    // sized for double; float kernels use the first half of each row
+    double sF[2][3][kWarps][32];
+    double sT[2][kWarps][32];
+    double sred[kWarps];
+    int sflag;
+};
 
+// One work item (segment) of one instance.  item / nitems: index of this item
+// among the instance's items of the launch and their count (last-item logic).
+// Returns false for a sweep of an instance whose solve is finished.
+template <typename real, int MODE>
+__device__ __forceinline__ void stencil_item(const Inst<real> &I, int seg_index, int item, int nitems,
+                                             const ApplyIO<real> *io, StencilSmem &sm)
+{
+    real(*sF)[3][kWarps][32] = reinterpret_cast<real(*)[3][kWarps][32]>(&sm.sF[0][0][0][0]);
+    real(*sT)[kWarps][32] = reinterpret_cast<real(*)[kWarps][32]>(&sm.sT[0][0][0]);
+    Ctl *ctl = I.ctl;
+
+    Op<real> o;
+    o.rec = I.rec;
+    o.nz = I.nz;
+    o.C = I.C;
+    o.w = o.ve = o.b = nullptr;
+    o.out = o.wout = o.tact = nullptr;
+    o.tn = 0.0;
+    o.dt_d = I.dt_d;
     int sweep = 0;
     bool check = false;
-    const real *src = a.u;
-    real *dst = a.out;
+    const long long step = (MODE == M_APPLY) ? 0 : ctl->step;
+    const int cur = (int)(step & 1);
     if (MODE == M_JAC) {
-        if (a.ctl->done) return;            // converged earlier: queued sweeps are no-ops
-        sweep = a.ctl->sweep;
-        src = (sweep & 1) ? a.x1 : a.x0;
-        dst = (sweep & 1) ? a.x0 : a.x1;
-        check = (sweep % a.check_every) == 0;
+        sweep = ctl->sweep;
+        o.src = (sweep & 1) ? I.x1 : I.x0;
+        o.out = (sweep & 1) ? I.x0 : I.x1;
+        o.b = I.b;
+        o.sT = I.sTie; o.dS = I.dSie; o.coef = I.coef_jac;
+        check = (sweep % I.check_every) == 0;
+    } else if (MODE == M_RHS) {
+        o.src = I.v[cur ^ 1];        // v of step n + 1 (the step counter moves at the end of the step)
+        o.out = I.b;
+        o.sT = I.sTi; o.dS = I.dSi; o.coef = real(0);
+    } else if (MODE == M_APPLY) {
+        o.src = io->u;
+        o.out = io->out;
+        o.sT = io->sT; o.dS = io->dS; o.coef = real(0);
+    } else {
+        o.src = I.v[cur];
+        o.w = I.w[cur];
+        o.ve = I.x0;
+        o.out = I.v[cur ^ 1];
+        o.wout = I.w[cur ^ 1];
+        o.tact = I.tact;
+        o.sT = I.sTi; o.dS = I.dSi; o.coef = I.coef_par;
+        o.tn = (double)step * I.dt_d;
     }
 
     Lane g;
     g.lane = threadIdx.x & 31;
     g.wid = threadIdx.x >> 5;
-    const Seg sg = a.segs[blockIdx.x];
+    const Seg sg = I.segs[seg_index];
     g.x = sg.bx * kTileX - 1 + g.lane;
     g.ylo = sg.by * kTileY + g.wid - 1;
-    const bool xin = g.x >= 0 && g.x < a.nx;
-    const bool lo_in = xin && g.ylo >= 0 && g.ylo < a.ny;
-    const bool hi_in = xin && g.ylo + 1 >= 0 && g.ylo + 1 < a.ny;
-    g.plane = a.nx * a.ny;
-    g.qlo = lo_in ? g.x + a.nx * g.ylo : 0;
-    const int qhi = hi_in ? g.x + a.nx * (g.ylo + 1) : 0;
+    const bool xin = g.x >= 0 && g.x < I.nx;
+    const bool lo_in = xin && g.ylo >= 0 && g.ylo < I.ny;
+    const bool hi_in = xin && g.ylo + 1 >= 0 && g.ylo + 1 < I.ny;
+    g.plane = I.nx * I.ny;
+    g.qlo = lo_in ? g.x + I.nx * g.ylo : 0;
+    const int qhi = hi_in ? g.x + I.nx * (g.ylo + 1) : 0;
     g.out_lane = g.lane >= 1 && g.lane <= kTileX && g.wid >= 1 && lo_in;
 
     float acc = 0.f;
@@ -282,52 +342,71 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) k_stencil(StencilArgs<re
     zero_state(S1);
     Ld<real, MODE> L0, L1;
     const int kbeg = sg.k0 - 1, kend = sg.k1;
-    load_plane<real, MODE>(a, src, kbeg, lo_in, hi_in, g.qlo, qhi, g.plane, L0);
+    load_plane<real, MODE>(o, kbeg, lo_in, hi_in, g.qlo, qhi, g.plane, L0);
     // two planes per iteration; the state records swap roles
     for (int k = kbeg;;) {
-        if (k + 1 <= kend) load_plane<real, MODE>(a, src, k + 1, lo_in, hi_in, g.qlo, qhi, g.plane, L1);
-        plane_step<real, MODE>(a, g, k, k > kbeg, k > kbeg + 1, S1, S0, L0, sF, sT, dst, check, acc);
+        if (k + 1 <= kend) load_plane<real, MODE>(o, k + 1, lo_in, hi_in, g.qlo, qhi, g.plane, L1);
+        plane_step<real, MODE>(I, o, g, k, k > kbeg, k > kbeg + 1, S1, S0, L0, sF, sT, check, acc);
         if (++k > kend) break;
-        if (k + 1 <= kend) load_plane<real, MODE>(a, src, k + 1, lo_in, hi_in, g.qlo, qhi, g.plane, L0);
-        plane_step<real, MODE>(a, g, k, k > kbeg, k > kbeg + 1, S0, S1, L1, sF, sT, dst, check, acc);
+        if (k + 1 <= kend) load_plane<real, MODE>(o, k + 1, lo_in, hi_in, g.qlo, qhi, g.plane, L0);
+        plane_step<real, MODE>(I, o, g, k, k > kbeg, k > kbeg + 1, S0, S1, L1, sF, sT, check, acc);
         if (++k > kend) break;
     }
 
     if (MODE == M_JAC) {
         // residual norm of this sweep's input: per-thread FP32 partial over its
         // few voxels, FP64 above; deterministic fixed-order reduction
-        double tot = block_sum<kThreads>(check ? (double)acc : 0.0, sred);
-        if (threadIdx.x == 0) {
-            a.partials[blockIdx.x] = tot;
-            __threadfence();
-            sLast = (atomicAdd(&a.ctl->arrive, 1u) == gridDim.x - 1);
-        }
-        __syncthreads();
-        if (sLast) {
-            __threadfence();
+        const double tot = block_sum<kThreads>(check ? (double)acc : 0.0, sm.sred);
+        if (threadIdx.x == 0) I.partials[item] = tot;
+        if (arrive_last(ctl, nitems, &sm.sflag)) {
             double s = 0;
             if (check)
-                for (int i = threadIdx.x; i < (int)gridDim.x; i += kThreads) s += ((volatile double *)a.partials)[i];
-            s = block_sum<kThreads>(s, sred);
+                for (int i = threadIdx.x; i < nitems; i += kThreads) s += ((volatile double *)I.partials)[i];
+            s = block_sum<kThreads>(s, sm.sred);
             if (threadIdx.x == 0) {
-                Ctl *c = a.ctl;
-                c->arrive = 0;
+                ctl->arrive = 0;
                 const int j = sweep + 1;
-                c->sweep = j;
+                ctl->sweep = j;
                 if (check) {
-                    c->rnorm2 = s;
+                    ctl->rnorm2 = s;
                     if (!(s == s) || isinf(s)) {
-                        c->nonfinite = 1; c->done = 1; c->iters = j;
-                    } else if (s <= c->thresh2) {
-                        c->converged = 1; c->done = 1; c->iters = j;
-                    } else if (s > a.div_factor * c->bnorm2) {
-                        c->diverged = 1; c->done = 1; c->iters = j;
+                        ctl->nonfinite = 1; ctl->done = 1; ctl->iters = j;
+                    } else if (s <= ctl->thresh2) {
+                        ctl->converged = 1; ctl->done = 1; ctl->iters = j;
+                    } else if (s > I.div_factor * ctl->bnorm2) {
+                        ctl->diverged = 1; ctl->noconv = 1; ctl->done = 1; ctl->iters = j;
                     }
                 }
-                if (!c->done && j >= a.max_iter) { c->done = 1; c->iters = j; }
+                if (!ctl->done && j >= I.max_iter) { ctl->done = 1; ctl->noconv = 1; ctl->iters = j; }
                 __threadfence();
             }
+            __syncthreads();
         }
+    }
+}
+
+// Single instance: one CTA per segment.
+template <typename real, int MODE>
+__global__ void __launch_bounds__(kThreads, kMinBlocks) k_stencil(Inst<real> I, ApplyIO<real> io)
+{
+    __shared__ StencilSmem sm;
+    if (MODE == M_JAC && I.ctl->done) return;   // converged earlier: queued sweeps are no-ops
+    stencil_item<real, MODE>(I, blockIdx.x, blockIdx.x, gridDim.x, &io, sm);
+}
+
+// Batched: one persistent launch walks the packed (instance, segment) list of
+// all instances; items of instances whose solve is finished are skipped.
+template <typename real, int MODE>
+__global__ void __launch_bounds__(kThreads, kMinBlocks)
+k_stencil_batch(const Inst<real> *insts, const BItem *items, int nitems)
+{
+    __shared__ StencilSmem sm;
+    for (int i = blockIdx.x; i < nitems; i += gridDim.x) {
+        const BItem it = items[i];
+        const Inst<real> &I = insts[it.inst];
+        if (MODE == M_JAC && *(volatile int *)&I.ctl->done) continue;
+        stencil_item<real, MODE>(I, it.item, it.item, it.nitems, nullptr, sm);
+        __syncthreads();
     }
 }
 
