@@ -41,7 +41,8 @@ def _args():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["config2", "config1"], default="config2")
+    ap.add_argument("--workload", choices=["config2", "config1", "config3"], default="config2")
+    ap.add_argument("--instances", type=int, default=64, help="config3: number of instances")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--ref-sweeps-per-step", type=float, default=None)
@@ -321,8 +322,92 @@ def run_ours(a):
         dist.destroy_process_group()
 
 
+def run_batched(a):
+    """config3: uneven bidomain instances advanced together (ep_batch) versus the
+    same instances stepped one after another with ep_step, same steps, same
+    tolerance; the batched states must equal the standalone ones."""
+    import torch
+    import paper_2302_12519_gb300 as ep
+    import workloads as W
+    from paper_2302_12519_gb300 import build as epbuild
+
+    torch.cuda.set_device(0)
+    epbuild.build()
+    cases = W.config3_instances(seed=0, count=a.instances, steps=a.warmup + a.steps)
+    M = sum(c.n_tissue for c in cases)
+    stream = torch.cuda.Stream()
+
+    def handles():
+        hs = []
+        for c in cases:
+            h = ep.Sim(c.nx, c.ny, c.nz, c.dx, c.model, c.precision, use_torch=True, stream=stream.cuda_stream)
+            h.set_mask(c.mask_flat())
+            h.set_fibres(c.fib_flat())
+            h.set_params(c.params)
+            for st in c.stimuli:
+                h.add_stimulus(st.lo, st.hi, st.t_start, st.dur, st.amp)
+            h.info()
+            hs.append(h)
+        return hs
+
+    # batched
+    hb = handles()
+    b = ep.Batch(len(hb), stream=stream.cuda_stream)
+    for h in hb:
+        b.add(h)
+    t0 = time.perf_counter()
+    b.autotune(5)
+    tune_s = time.perf_counter() - t0
+    info = b.info()
+    b.step(a.warmup, allow_noconv=True)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    b.step(a.steps, allow_noconv=True)      # one graph launch for the whole window
+    e1.record(stream)
+    e1.synchronize()
+    batch_s = e0.elapsed_time(e1) / 1e3
+    vm_b = [h.read(ep.EP_VM_MV) for h in hb]
+    b.close()
+    for h in hb:
+        h.close()
+    # plain: the same instances one after another
+    hp = handles()
+    plain_s = 0.0
+    for h in hp:
+        h.step(a.warmup, allow_noconv=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        h.step(a.steps, allow_noconv=True)
+        e1.record(stream)
+        e1.synchronize()
+        plain_s += e0.elapsed_time(e1) / 1e3
+    dv = max(float(np.abs(h.read(ep.EP_VM_MV) - v).max()) for h, v in zip(hp, vm_b))
+    for h in hp:
+        h.close()
+    value = M * a.steps / batch_s
+    plain = M * a.steps / plain_s
+    line = {"metric": "voxel-steps/sec", "value": value, "unit": "tissue voxel-steps/s", "n_gpus": 1,
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1e3 * batch_s / a.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"config3: {len(cases)} bidomain FP32 shells, n ~ U{{48..160}}, sampled "
+                                   f"conductivities and stimulus sites (seed 0)",
+                       "tissue_voxels_total": M, "grids": [c.nx for c in cases],
+                       "autotuned": {"zseg": info.zseg, "ctas_per_sm": info.ctas_per_sm,
+                                     "sweeps_per_check": info.sweeps_per_check,
+                                     "group_bytes": info.group_bytes, "groups": info.groups, "tune_s": tune_s},
+                       "l2": "inputs larger than L2 (all instances' state)"},
+            "plain_sequential": {"value": plain, "unit": "tissue voxel-steps/s", "ms_per_step": 1e3 * plain_s / a.steps},
+            "speedup_vs_plain": value / plain,
+            "max_abs_dVm_batched_vs_alone_mV": dv}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     a = _args()
+    if a.workload == "config3" and a.impl == "ours":
+        run_batched(a)
+        return
     if a.impl == "reference":
         run_reference(a)
     else:

@@ -229,6 +229,9 @@ typedef struct {
     int ctas_per_sm;             /* persistent grid: CTAs per SM (tuned) */
     int sweeps_per_check;        /* sweep launches between device loop checks (tuned) */
     int zseg;                    /* z-planes per stencil work item (tuned) */
+    size_t group_bytes;          /* members are swept in groups whose working sets total at most
+                                    this many bytes, so a group's sweeps stay in L2 (0 = one group; tuned) */
+    int groups;                  /* number of such groups */
 } ep_batch_info;
 
 /* Create a batch of at most max_instances handles whose device memory may
@@ -250,9 +253,10 @@ ep_status ep_batch_step(ep_batch *b, int n_steps);
  * whether every solve converged, its step counter). */
 ep_status ep_batch_slot_stats(ep_batch *b, int slot, ep_step_stats *stats);
 
-/* Choose the persistent grid size, the sweeps per device loop check and the
- * z-planes per work item by timing trial_sweeps sweeps of each candidate on
- * the members' current states (states are restored afterwards). */
+/* Choose the persistent grid size, the z-planes per work item and the group
+ * size by timing trial_sweeps sweeps of each candidate on the members'
+ * current states (states are restored afterwards); the sweeps per device loop
+ * check follow from the measured sweep time. */
 ep_status ep_batch_autotune(ep_batch *b, int trial_sweeps);
 
 ep_status ep_batch_get_info(ep_batch *b, ep_batch_info *info);

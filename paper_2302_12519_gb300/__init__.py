@@ -69,7 +69,8 @@ class BatchInfo(ctypes.Structure):
     _fields_ = [("instances", ctypes.c_int), ("stencil_items", ctypes.c_longlong),
                 ("chunk_items", ctypes.c_longlong), ("device_bytes", ctypes.c_size_t),
                 ("budget_bytes", ctypes.c_size_t), ("ctas_per_sm", ctypes.c_int),
-                ("sweeps_per_check", ctypes.c_int), ("zseg", ctypes.c_int)]
+                ("sweeps_per_check", ctypes.c_int), ("zseg", ctypes.c_int),
+                ("group_bytes", ctypes.c_size_t), ("groups", ctypes.c_int)]
 
 
 class EPError(RuntimeError):

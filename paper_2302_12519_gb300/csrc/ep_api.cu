@@ -711,7 +711,13 @@ ep_status ep_set_state(ep_sim *s, const double *v, const double *w, const double
     if (step < 0) return fail(s, EP_EINVAL, "step must be >= 0");
     ep_status st = ensure_ready(s);
     if (st != EP_OK) return st;
-    // the state of step n lives in buffers n & 1: move the counter first
+    // the state of step n lives in buffers n & 1: carry the fields over when the parity
+    // changes (a NULL field keeps its value), then move the counter
+    if ((s->step ^ step) & 1) {
+        const size_t fb = s->rsz * (size_t)s->n;
+        CK(cudaMemcpyAsync(s->v[step & 1], s->v[s->step & 1], fb, cudaMemcpyDeviceToDevice, s->stream));
+        CK(cudaMemcpyAsync(s->w[step & 1], s->w[s->step & 1], fb, cudaMemcpyDeviceToDevice, s->stream));
+    }
     st = set_device_step(s, step);
     if (st != EP_OK) return st;
     return s->d.precision == EP_FP64 ? set_state_typed<double>(s, v, w, ve) : set_state_typed<float>(s, v, w, ve);
@@ -990,6 +996,14 @@ struct ep_batch {
     cudaGraphExec_t graph = nullptr;
     bool dirty = true;
     int nsm = 152, ctas_per_sm = kMinBlocks, sweeps_per_check = 16, zseg = kZSeg;
+    // members are swept in groups whose working sets fit the L2 cache together; each group
+    // has its own device-side convergence loop (0 = one group)
+    size_t group_bytes = 0;
+    struct Group {
+        int inst0, inst1;         // table rows [inst0, inst1)
+        long long seg0, nseg;     // range of its stencil items in d_seg
+    };
+    std::vector<Group> groups;
     std::vector<Ctl> last;         // per table row, after the last step
     std::vector<ep_step_stats> stats;
 };
@@ -1053,15 +1067,38 @@ ep_status rebuild_tables(ep_batch *b)
     for (int r = 0; r < b->ninst; ++r) {
         ep_sim *s = b->slot[b->order[r]];
         insts.push_back(make_inst<float>(s));
-        for (int i = 0; i < s->nseg; ++i) segs.push_back(BItem{r, i, s->nseg, 0});
         for (int i = 0; i < s->nchunk; ++i) chunks.push_back(BItem{r, i, s->nchunk, 0});
     }
-    // interleave instances so that every part of the persistent grid sees work of several
-    // instances (long instances do not end up on a few CTAs)
-    std::stable_sort(segs.begin(), segs.end(), [](const BItem &x, const BItem &y) {
-        const double fx = (x.item + 0.5) / x.nitems, fy = (y.item + 0.5) / y.nitems;
-        return fx < fy;
-    });
+    // groups of consecutive rows whose sweep working sets (iterate pair, right-hand side,
+    // records: 20 bytes per grid voxel) together stay within group_bytes
+    b->groups.clear();
+    for (int r = 0; r < b->ninst;) {
+        int r1 = r;
+        size_t bytes = 0;
+        do {
+            bytes += 20 * (size_t)b->slot[b->order[r1]]->n;
+            ++r1;
+        } while (r1 < b->ninst && (b->group_bytes == 0 ||
+                                   bytes + 20 * (size_t)b->slot[b->order[r1]]->n <= b->group_bytes));
+        ep_batch::Group g;
+        g.inst0 = r;
+        g.inst1 = r1;
+        g.seg0 = (long long)segs.size();
+        std::vector<BItem> gs;
+        for (int q = r; q < r1; ++q) {
+            ep_sim *s = b->slot[b->order[q]];
+            for (int i = 0; i < s->nseg; ++i) gs.push_back(BItem{q, i, s->nseg, 0});
+        }
+        // interleave the group's instances so that every part of the persistent grid sees
+        // work of several instances (long instances do not end up on a few CTAs)
+        std::stable_sort(gs.begin(), gs.end(), [](const BItem &x, const BItem &y) {
+            return (x.item + 0.5) / x.nitems < (y.item + 0.5) / y.nitems;
+        });
+        segs.insert(segs.end(), gs.begin(), gs.end());
+        g.nseg = (long long)gs.size();
+        b->groups.push_back(g);
+        r = r1;
+    }
     b->nseg_items = (long long)segs.size();
     b->nchunk_items = (long long)chunks.size();
     ep_status st;
@@ -1101,7 +1138,7 @@ ep_status build_batch_graph(ep_batch *b)
     std::memset(&none, 0, sizeof(none));
     cudaGraph_t g = nullptr;
     CKB(cudaGraphCreate(&g, 0));
-    cudaGraphConditionalHandle ho = 0, hi = 0;
+    cudaGraphConditionalHandle ho = 0;
     CKB(cudaGraphConditionalHandleCreate(&ho, g, 1, cudaGraphCondAssignDefault));
     alignas(cudaGraphNodeParams) unsigned char po_buf[sizeof(cudaGraphNodeParams)] = {};
     cudaGraphNodeParams &po = *reinterpret_cast<cudaGraphNodeParams *>(po_buf);
@@ -1112,40 +1149,48 @@ ep_status build_batch_graph(ep_batch *b)
     cudaGraphNode_t no;
     CKB(cudaGraphAddNode(&no, g, nullptr, nullptr, 0, &po));
     cudaGraph_t body = po.conditional.phGraph_out[0];
-    // inner loop handle (bidomain only: a handle without its conditional node is invalid);
-    // the first kernel of every step sets it to 1
-    if (b->model == EP_BI) CKB(cudaGraphConditionalHandleCreate(&hi, body, 1, 0));
+    // inner loop handles, one per group (bidomain only: a handle without its conditional
+    // node is invalid); each is set to 1 before its loop starts
+    const int ngroups = (int)b->groups.size();
+    std::vector<cudaGraphConditionalHandle> hg(ngroups, 0);
+    if (b->model == EP_BI)
+        for (int gi = 0; gi < ngroups; ++gi) CKB(cudaGraphConditionalHandleCreate(&hg[gi], body, 1, 0));
 
     CKB(cudaStreamBeginCaptureToGraph(st, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
-    if (b->model == EP_BI) k_set_cond<<<1, 1, 0, st>>>(hi, 1u);
     if (b->model == EP_MONO) k_stencil_batch<float, M_PAR_MONO><<<gs, kThreads, 0, st>>>(b->d_inst, b->d_seg, ns);
     else k_stencil_batch<float, M_PAR_BI><<<gs, kThreads, 0, st>>>(b->d_inst, b->d_seg, ns);
     if (b->model == EP_BI) {
         k_stencil_batch<float, M_RHS><<<gs, kThreads, 0, st>>>(b->d_inst, b->d_seg, ns);
         k_comp_mean_batch<float><<<gc, kRedThreads, 0, st>>>(b->d_inst, b->d_chunk, nc, (int)RED_B);
         k_comp_subtract_batch<float><<<gc, kRedThreads, 0, st>>>(b->d_inst, b->d_chunk, nc);
-        // inner loop: sweeps until every member's solve is finished
-        cudaStreamCaptureStatus cs;
-        cudaGraph_t cg = nullptr;
-        const cudaGraphNode_t *deps = nullptr;
-        const cudaGraphEdgeData *ed = nullptr;
-        size_t nd = 0;
-        CKB(cudaStreamGetCaptureInfo(st, &cs, nullptr, &cg, &deps, &ed, &nd));
-        alignas(cudaGraphNodeParams) unsigned char pi_buf[sizeof(cudaGraphNodeParams)] = {};
-        cudaGraphNodeParams &pi = *reinterpret_cast<cudaGraphNodeParams *>(pi_buf);
-        pi.type = cudaGraphNodeTypeConditional;
-        pi.conditional.handle = hi;
-        pi.conditional.type = cudaGraphCondTypeWhile;
-        pi.conditional.size = 1;
-        cudaGraphNode_t ni;
-        CKB(cudaGraphAddNode(&ni, cg, deps, ed, nd, &pi));
-        cudaGraph_t ibody = pi.conditional.phGraph_out[0];
-        CKB(cudaStreamUpdateCaptureDependencies(st, &ni, nullptr, 1, cudaStreamSetCaptureDependencies));
-        CKB(cudaStreamBeginCaptureToGraph(b->side, ibody, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
-        for (int i = 0; i < b->sweeps_per_check; ++i)
-            k_stencil_batch<float, M_JAC><<<gs, kThreads, 0, b->side>>>(b->d_inst, b->d_seg, ns);
-        k_solve_cond<float><<<1, 256, 0, b->side>>>(b->d_inst, b->ninst, hi);
-        CKB(cudaStreamEndCapture(b->side, nullptr));
+        for (int gi = 0; gi < ngroups; ++gi) {
+            const ep_batch::Group &gr = b->groups[gi];
+            const int ggs = grid_of(gr.nseg, b->nsm * b->ctas_per_sm);
+            k_set_cond<<<1, 1, 0, st>>>(hg[gi], 1u);
+            // inner loop: sweeps until every solve of the group is finished
+            cudaStreamCaptureStatus cs;
+            cudaGraph_t cg = nullptr;
+            const cudaGraphNode_t *deps = nullptr;
+            const cudaGraphEdgeData *ed = nullptr;
+            size_t nd = 0;
+            CKB(cudaStreamGetCaptureInfo(st, &cs, nullptr, &cg, &deps, &ed, &nd));
+            alignas(cudaGraphNodeParams) unsigned char pi_buf[sizeof(cudaGraphNodeParams)] = {};
+            cudaGraphNodeParams &pi = *reinterpret_cast<cudaGraphNodeParams *>(pi_buf);
+            pi.type = cudaGraphNodeTypeConditional;
+            pi.conditional.handle = hg[gi];
+            pi.conditional.type = cudaGraphCondTypeWhile;
+            pi.conditional.size = 1;
+            cudaGraphNode_t ni;
+            CKB(cudaGraphAddNode(&ni, cg, deps, ed, nd, &pi));
+            cudaGraph_t ibody = pi.conditional.phGraph_out[0];
+            CKB(cudaStreamUpdateCaptureDependencies(st, &ni, nullptr, 1, cudaStreamSetCaptureDependencies));
+            CKB(cudaStreamBeginCaptureToGraph(b->side, ibody, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+            for (int i = 0; i < b->sweeps_per_check; ++i)
+                k_stencil_batch<float, M_JAC><<<ggs, kThreads, 0, b->side>>>(b->d_inst, b->d_seg + gr.seg0,
+                                                                            (int)gr.nseg);
+            k_solve_cond<float><<<1, 256, 0, b->side>>>(b->d_inst + gr.inst0, gr.inst1 - gr.inst0, hg[gi]);
+            CKB(cudaStreamEndCapture(b->side, nullptr));
+        }
         k_comp_mean_batch<float><<<gc, kRedThreads, 0, st>>>(b->d_inst, b->d_chunk, nc, (int)RED_X_FINAL);
         k_project_batch<float><<<gc, kRedThreads, 0, st>>>(b->d_inst, b->d_chunk, nc);
     }
@@ -1338,32 +1383,47 @@ ep_status ep_batch_autotune(ep_batch *b, int trial_sweeps)
     CKB(cudaEventCreate(&e1));
     const int zsegs[3] = {8, 16, 32};
     const int ctas[3] = {1, 2, 3};
+    const size_t gbytes[4] = {0, (size_t)192 << 20, (size_t)96 << 20, (size_t)48 << 20};
     double best = 1e300;
     int best_z = b->zseg, best_c = b->ctas_per_sm;
+    size_t best_g = b->group_bytes;
     for (int zi = 0; zi < 3 && st == EP_OK; ++zi) {
         for (int r = 0; r < b->ninst && st == EP_OK; ++r) st = relayout_segments(b->slot[b->order[r]], zsegs[zi]);
-        if (st != EP_OK || (st = rebuild_tables(b)) != EP_OK) break;
-        for (int ci = 0; ci < 3; ++ci) {
-            if (ctas[ci] > kMinBlocks) continue;
-            // never-converging solves so that every trial sweep does its full work
-            for (int r = 0; r < b->ninst; ++r) {
-                Ctl c = ctl0[r];
-                c.done = 0; c.sweep = 0; c.arrive = 0; c.thresh2 = -1.0; c.bnorm2 = 1e300;
-                CKB(cudaMemcpyAsync(b->slot[b->order[r]]->ctl, &c, sizeof(Ctl), cudaMemcpyHostToDevice, s0));
-            }
-            const int gs = grid_of(b->nseg_items, b->nsm * ctas[ci]);
-            k_stencil_batch<float, M_JAC><<<gs, kThreads, 0, s0>>>(b->d_inst, b->d_seg, (int)b->nseg_items);
-            CKB(cudaEventRecord(e0, s0));
-            for (int i = 0; i < trial_sweeps; ++i)
-                k_stencil_batch<float, M_JAC><<<gs, kThreads, 0, s0>>>(b->d_inst, b->d_seg, (int)b->nseg_items);
-            CKB(cudaEventRecord(e1, s0));
-            CKB(cudaEventSynchronize(e1));
-            float ms = 0.f;
-            CKB(cudaEventElapsedTime(&ms, e0, e1));
-            if (ms < best) {
-                best = ms;
-                best_z = zsegs[zi];
-                best_c = ctas[ci];
+        if (st != EP_OK) break;
+        for (int gi = 0; gi < 4 && st == EP_OK; ++gi) {
+            b->group_bytes = gbytes[gi];
+            if ((st = rebuild_tables(b)) != EP_OK) break;
+            if (gi > 0 && b->groups.size() == 1) continue;   // same as one group
+            for (int ci = 0; ci < 3; ++ci) {
+                if (ctas[ci] > kMinBlocks) continue;
+                // never-converging solves so that every trial sweep does its full work
+                for (int r = 0; r < b->ninst; ++r) {
+                    Ctl c = ctl0[r];
+                    c.done = 0; c.sweep = 0; c.arrive = 0; c.thresh2 = -1.0; c.bnorm2 = 1e300;
+                    CKB(cudaMemcpyAsync(b->slot[b->order[r]]->ctl, &c, sizeof(Ctl), cudaMemcpyHostToDevice, s0));
+                }
+                // one sweep of every group in turn, each group swept trial_sweeps times
+                double ms_total = 0.0;
+                for (const ep_batch::Group &gr : b->groups) {
+                    const int gs = grid_of(gr.nseg, b->nsm * ctas[ci]);
+                    k_stencil_batch<float, M_JAC><<<gs, kThreads, 0, s0>>>(b->d_inst, b->d_seg + gr.seg0,
+                                                                           (int)gr.nseg);
+                    CKB(cudaEventRecord(e0, s0));
+                    for (int i = 0; i < trial_sweeps; ++i)
+                        k_stencil_batch<float, M_JAC><<<gs, kThreads, 0, s0>>>(b->d_inst, b->d_seg + gr.seg0,
+                                                                               (int)gr.nseg);
+                    CKB(cudaEventRecord(e1, s0));
+                    CKB(cudaEventSynchronize(e1));
+                    float ms = 0.f;
+                    CKB(cudaEventElapsedTime(&ms, e0, e1));
+                    ms_total += ms;
+                }
+                if (ms_total < best) {
+                    best = ms_total;
+                    best_z = zsegs[zi];
+                    best_c = ctas[ci];
+                    best_g = gbytes[gi];
+                }
             }
         }
     }
@@ -1380,6 +1440,7 @@ ep_status ep_batch_autotune(ep_batch *b, int trial_sweeps)
     if (st != EP_OK) return st;
     b->zseg = best_z;
     b->ctas_per_sm = best_c;
+    b->group_bytes = best_g;
     // sweeps between device loop checks: about 100 us of sweeps, 4..64
     const double per_sweep_us = 1e3 * best / trial_sweeps;
     b->sweeps_per_check = (int)std::min(64.0, std::max(4.0, std::ceil(100.0 / std::max(per_sweep_us, 1e-3))));
@@ -1404,6 +1465,8 @@ ep_status ep_batch_get_info(ep_batch *b, ep_batch_info *info)
     info->ctas_per_sm = b->ctas_per_sm;
     info->sweeps_per_check = b->sweeps_per_check;
     info->zseg = b->zseg;
+    info->group_bytes = b->group_bytes;
+    info->groups = (int)b->groups.size();
     return EP_OK;
 }
 

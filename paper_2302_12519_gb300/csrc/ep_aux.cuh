@@ -325,6 +325,7 @@ __global__ void k_fill(real *p, long long n, real v)
 // the solve continues while any instance's solve is unfinished.
 __global__ void k_set_cond(cudaGraphConditionalHandle h, unsigned value) { cudaGraphSetConditional(h, value); }
 
+// Condition of the device-side convergence loop: any of the instances unfinished.
 template <typename real>
 __global__ void k_solve_cond(const Inst<real> *insts, int ninst, cudaGraphConditionalHandle h)
 {
@@ -335,6 +336,28 @@ __global__ void k_solve_cond(const Inst<real> *insts, int ninst, cudaGraphCondit
         if (!*(volatile int *)&insts[i].ctl->done) any = 1;
     __syncthreads();
     if (threadIdx.x == 0) cudaGraphSetConditional(h, any ? 1u : 0u);
+}
+
+// List of the members of rows [0, n) whose solve is unfinished, with the prefix
+// counts of their stencil items (cum[n_active] = total), and the loop
+// condition of the device-side convergence loop (any member still active).
+template <typename real>
+__global__ void k_active_list(const Inst<real> *insts, int n, int *active, int *cum, int *counts,
+                              cudaGraphConditionalHandle h)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    int na = 0, tot = 0;
+    for (int i = 0; i < n; ++i) {
+        if (*(volatile int *)&insts[i].ctl->done) continue;
+        active[na] = i;
+        cum[na] = tot;
+        tot += insts[i].nseg;
+        ++na;
+    }
+    cum[na] = tot;
+    counts[0] = tot;
+    counts[1] = na;
+    if (h) cudaGraphSetConditional(h, na > 0 ? 1u : 0u);
 }
 
 // Outer loop of a multi-step graph: counts down the steps left in the chunk.

@@ -410,4 +410,36 @@ k_stencil_batch(const Inst<real> *insts, const BItem *items, int nitems)
     }
 }
 
+// Batched sweeps over the unfinished members only: item i of the launch maps
+// to member active[k] with cum[k] <= i < cum[k + 1] (list rebuilt at every
+// loop check by k_active_list).  Instances given as rows of insts + row0.
+constexpr int kMaxActiveSmem = 2048;
+
+template <typename real, int MODE>
+__global__ void __launch_bounds__(kThreads, kMinBlocks)
+k_stencil_active(const Inst<real> *insts, const int *active, const int *cum, const int *counts)
+{
+    __shared__ StencilSmem sm;
+    __shared__ int scum[kMaxActiveSmem + 1];
+    const int total = counts[0], na = counts[1];
+    const bool in_smem = na <= kMaxActiveSmem;
+    if (in_smem)
+        for (int i = threadIdx.x; i <= na; i += blockDim.x) scum[i] = cum[i];
+    __syncthreads();
+    const int *c = in_smem ? scum : cum;
+    for (int i = blockIdx.x; i < total; i += gridDim.x) {
+        int lo = 0, hi = na;   // largest k with c[k] <= i
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (c[mid] <= i) lo = mid;
+            else hi = mid;
+        }
+        const Inst<real> &I = insts[active[lo]];
+        if (MODE == M_JAC && *(volatile int *)&I.ctl->done) continue;   // converged at a check in this loop pass
+        const int item = i - c[lo];
+        stencil_item<real, MODE>(I, item, item, I.nseg, nullptr, sm);
+        __syncthreads();
+    }
+}
+
 }  // namespace gbep
