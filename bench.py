@@ -41,8 +41,14 @@ def _args():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["config2", "config1", "config3"], default="config2")
+    ap.add_argument("--workload", choices=["config2", "config1", "config3", "config4"], default="config2")
     ap.add_argument("--instances", type=int, default=64, help="config3: number of instances")
+    ap.add_argument("--requests", type=int, default=16, help="config4: number of requests")
+    ap.add_argument("--req-steps", type=int, default=4, help="config4: time steps per request")
+    ap.add_argument("--loads", default="0.5,1,2", help="config4: arrival rates as multiples of the plain service rate")
+    ap.add_argument("--hbm-budget-gb", type=float, default=16.0, help="config4: admission budget")
+    ap.add_argument("--max-slots", type=int, default=32, help="config4: requests stepped together")
+    ap.add_argument("--chunk-steps", type=int, default=2, help="config4: steps between admission points")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--ref-sweeps-per-step", type=float, default=None)
@@ -403,10 +409,104 @@ def run_batched(a):
     print(json.dumps(line), flush=True)
 
 
+def _pct(x, q):
+    return float(np.percentile(np.asarray(x, float), q)) if len(x) else None
+
+
+def run_served(a):
+    """config4: Poisson arrivals of bidomain requests of uneven size, served
+    with continuous batching under a device-memory budget (ep_server), against
+    the plain form running the same requests one after another.  The plain
+    form's latencies at each load come from its measured service times in
+    arrival order (first come, first served)."""
+    import paper_2302_12519_gb300 as ep
+    import torch
+    import workloads as W
+    from paper_2302_12519_gb300 import build as epbuild
+
+    torch.cuda.set_device(0)
+    epbuild.build()
+    unit_arrivals, cases = W.config4_requests(seed=0, count=a.requests, rate_per_s=1.0, lo=64, hi=256,
+                                              steps=a.req_steps)
+    for c in cases:
+        c.model, c.precision = W.BI, W.FP32
+    S = a.req_steps
+    vox = [c.n_tissue * S for c in cases]
+
+    # plain form: each request alone, set-up included, in arrival order
+    svc, vm_plain = [], []
+    for c in cases:
+        h = ep.sim_from_case(c, use_torch=False)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        h.step(S, allow_noconv=True)
+        torch.cuda.synchronize()
+        svc.append(time.perf_counter() - t0)
+        vm_plain.append(h.read(ep.EP_VM_MV))
+        h.close()
+    plain_total = sum(svc)
+    mu = len(cases) / plain_total   # plain service rate, requests/s
+    plain_value = sum(vox) / plain_total
+
+    loads = [float(x) for x in a.loads.split(",") if x.strip()]
+    budget = int(a.hbm_budget_gb * (1 << 30))
+    runs, dv = [], 0.0
+    for load in loads:
+        lam = load * mu
+        arr = np.asarray(unit_arrivals) / lam
+        # plain form at this load: first come, first served with the measured service times
+        fin, lat_plain = 0.0, []
+        for t_a, t_s in zip(arr, svc):
+            fin = max(fin, t_a) + t_s
+            lat_plain.append(fin - t_a)
+        sims = [ep.sim_from_case(c, use_torch=False) for c in cases]
+        srv = ep.Server(max_slots=a.max_slots, chunk_steps=a.chunk_steps, hbm_budget_bytes=budget,
+                        sweeps_per_check=4)
+        t_base = srv.now() + 0.05
+        ids = [srv.submit(h, S, release_s=t_base + float(t)) for h, t in zip(sims, arr)]
+        got = {r.id: (r, h) for r, h in srv.collect_n(len(ids), timeout_s=3600)}
+        st = srv.stats()
+        lat, t_end, bad = [], 0.0, 0
+        for q, rid in enumerate(ids):
+            r, h = got[rid]
+            if r.status not in (ep.EP_OK, ep.EP_ENOCONV) or r.steps_done != S:
+                bad += 1
+            lat.append(r.t_done_s - r.t_release_s)
+            t_end = max(t_end, r.t_done_s)
+            dv = max(dv, float(np.abs(h.read(ep.EP_VM_MV) - vm_plain[q]).max()))
+            h.close()
+        srv.close()
+        span = t_end - t_base
+        runs.append({"load": load, "rate_req_per_s": lam, "value": sum(vox) / span, "makespan_s": span,
+                     "p50_s": _pct(lat, 50), "p99_s": _pct(lat, 99),
+                     "plain_p50_s": _pct(lat_plain, 50), "plain_p99_s": _pct(lat_plain, 99),
+                     "plain_makespan_s": fin, "plain_value": sum(vox) / fin,
+                     "hbm_peak_bytes": st.hbm_peak, "chunks": st.chunks, "busy_s": st.busy_s, "failed": bad})
+    top = max(runs, key=lambda r: r["load"])
+    line = {"metric": "voxel-steps/sec", "value": top["value"], "unit": "tissue voxel-steps/s", "n_gpus": 1,
+            "steps": S, "warmup": 0, "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"config4: {len(cases)} bidomain FP32 shell requests, n ~ U{{64..256}}, "
+                                   f"{S} steps each, Poisson arrivals (seed 0)",
+                       "grids": [c.nx for c in cases], "tissue_voxels": [c.n_tissue for c in cases],
+                       "hbm_budget_bytes": budget, "max_slots": a.max_slots, "chunk_steps": a.chunk_steps,
+                       "l2": "inputs larger than L2 (all requests' state)"},
+            "served_at_load": top["load"],
+            "plain_sequential": {"value": plain_value, "unit": "tissue voxel-steps/s",
+                                 "service_s": svc, "rate_req_per_s": mu},
+            "speedup_vs_plain": top["value"] / plain_value,
+            "loads": runs,
+            "max_abs_dVm_served_vs_alone_mV": dv}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     a = _args()
     if a.workload == "config3" and a.impl == "ours":
         run_batched(a)
+        return
+    if a.workload == "config4" and a.impl == "ours":
+        run_served(a)
         return
     if a.impl == "reference":
         run_reference(a)

@@ -51,7 +51,8 @@ typedef enum {
     EP_ENONFINITE = 5,  /* a NaN / Inf appeared in the state */
     EP_ESTATE = 6,      /* call not valid in the handle's current state */
     EP_EBUSY = 7,       /* batch slot table full */
-    EP_EREJECTED = 8    /* batch admission refused: over the HBM budget */
+    EP_EREJECTED = 8,   /* batch admission refused: over the HBM budget */
+    EP_ECANCELLED = 9   /* served request cancelled before it finished */
 } ep_status;
 
 enum { EP_MONO = 0, EP_BI = 1 };          /* ep_grid_desc.model */
@@ -202,6 +203,15 @@ typedef struct {
     long long steps;             /* steps taken while enabled */
 } ep_profile;
 
+/* Device memory of the handle, from a host-side plan of its mask (face-
+ * connected components, reduction chunks, work items) made without touching
+ * the device: resident_bytes is what the handle holds once set up, peak_bytes
+ * the most it holds during set-up (staging of fibres, mask and records).
+ * After set-up both equal the bytes held.  EP_ESTATE without a mask,
+ * EP_EINVAL if the mask has no tissue.  Host-only; needs no GPU.  No
+ * counterpart in the paper: admission control of the served form. */
+ep_status ep_footprint(ep_sim *s, size_t *resident_bytes, size_t *peak_bytes);
+
 ep_status ep_profile_enable(ep_sim *s, int on);
 ep_status ep_get_profile(ep_sim *s, ep_profile *prof);
 
@@ -259,9 +269,99 @@ ep_status ep_batch_slot_stats(ep_batch *b, int slot, ep_step_stats *stats);
  * check follow from the measured sweep time. */
 ep_status ep_batch_autotune(ep_batch *b, int trial_sweeps);
 
+/* Set the schedule by hand: persistent CTAs per SM (1..8), sweep launches
+ * between device loop checks (1..1024), z-planes per work item (8..256) and
+ * the group budget in bytes.  0 (or a negative group_bytes) keeps a value.
+ * Results do not depend on the schedule. */
+ep_status ep_batch_set_schedule(ep_batch *b, int ctas_per_sm, int sweeps_per_check, int zseg, long long group_bytes);
+
 ep_status ep_batch_get_info(ep_batch *b, ep_batch_info *info);
 const char *ep_batch_last_error(const ep_batch *b);
 void ep_batch_destroy(ep_batch *b);
+
+/* ------------------------------------------------------------------------ */
+/* Served form: a request loop with continuous batching.                     */
+/* ------------------------------------------------------------------------ */
+/* The paper suggests running many cardiac simulations side by side rather
+ * than splitting one across processors (chapter "Review & Outlook", Sec.
+ * "Assesment"); it has no serving loop, so nothing here has a counterpart in
+ * it.
+ *
+ * A server owns a serving thread and one batch per model.  A request is a
+ * prepared FP32 handle (mask and parameters set; fibres and stimuli
+ * optional) plus a step count and a release time.  Released requests are
+ * admitted in release order while a slot is free and the request's set-up
+ * peak (ep_footprint) fits the budget next to the bytes of every request the
+ * server holds (running or finished and not yet collected); a request whose
+ * peak alone exceeds the budget finishes with EP_EREJECTED.  Admitted
+ * requests are set up on the device and stepped with the other members in
+ * chunks of at most chunk_steps steps; a chunk never takes a member past its
+ * step count, and requests join or leave only between chunks.  Each request
+ * computes exactly what ep_step on the handle alone computes.
+ *
+ * Ownership: ep_server_submit hands the handle to the server; it comes back
+ * in the ep_request_result of ep_server_collect (state on the device, read
+ * with ep_read; the caller destroys it).  ep_server_destroy destroys the
+ * handles it still holds.  All functions may be called from any host thread. */
+typedef struct ep_server ep_server;
+
+typedef struct {
+    int max_slots;              /* requests stepped together, >= 1 */
+    int chunk_steps;            /* steps between admission points, >= 1 */
+    int sweeps_per_check;       /* batch schedule (ep_batch_set_schedule); 0 = default */
+    size_t hbm_budget_bytes;    /* device bytes the held requests may total; 0 = no limit */
+    void *cuda_stream;          /* stream of the batched launches; NULL = a private one */
+} ep_server_config;
+
+typedef struct {
+    long long id;
+    int status;                 /* EP_OK, EP_ENOCONV (some solve hit max_iter; all steps done),
+                                   EP_ENONFINITE, EP_ECANCELLED, EP_EREJECTED, or the set-up error */
+    int steps_done;
+    long long n_tissue;
+    long long total_iters;      /* Jacobi sweeps of the request's solves */
+    double t_release_s, t_admit_s, t_done_s;   /* server clock (ep_server_now); t_admit_s < 0: never admitted */
+    size_t device_bytes;        /* device memory the handle holds */
+    ep_sim *sim;                /* the handle, returned to the caller */
+} ep_request_result;
+
+typedef struct {
+    int queued, active, finished;   /* finished = retired and not collected */
+    long long submitted, admitted, completed, cancelled, rejected;
+    long long chunks;               /* batched chunks run */
+    long long voxel_steps;          /* tissue voxel-steps done */
+    size_t hbm_in_use, hbm_peak;    /* bytes held (set-up reservations included), and the maximum */
+    double busy_s;                  /* wall time spent in batched chunks */
+    double now_s;
+} ep_server_stats;
+
+/* Start a server on the current device.  EP_ECUDA without a usable device. */
+ep_status ep_server_create(const ep_server_config *cfg, ep_server **out);
+
+/* Queue a request that is released at release_s on the server clock (a time
+ * already past means now).  *id receives its id.  EP_EINVAL for FP64 handles
+ * or a handle the server already holds. */
+ep_status ep_server_submit(ep_server *srv, ep_sim *sim, int n_steps, double release_s, long long *id);
+
+/* Cancel a queued request at once, or a running one at the next chunk
+ * boundary (status EP_ECANCELLED, steps_done says how far it got). */
+ep_status ep_server_cancel(ep_server *srv, long long id);
+
+/* Take up to max_results finished requests, waiting up to wait_s seconds for
+ * the first one.  *n_out = number returned (0 after a timeout). */
+ep_status ep_server_collect(ep_server *srv, ep_request_result *out, int max_results, int *n_out, double wait_s);
+
+/* Wait until no request is queued or running (timeout_s < 0: no limit);
+ * EP_EBUSY at the timeout.  Finished requests keep their device memory until
+ * collected, so under a tight budget admission can wait on the caller:
+ * drain then returns EP_EBUSY at once (nothing runs, the next request needs
+ * memory that uncollected results hold).  Collect and drain again. */
+ep_status ep_server_drain(ep_server *srv, double timeout_s);
+
+ep_status ep_server_get_stats(ep_server *srv, ep_server_stats *out);
+double ep_server_now(const ep_server *srv);
+const char *ep_server_last_error(const ep_server *srv);
+void ep_server_destroy(ep_server *srv);
 const char *ep_last_error(const ep_sim *s);
 void ep_destroy(ep_sim *s);
 

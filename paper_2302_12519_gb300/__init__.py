@@ -17,9 +17,10 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libep.so")
 
-EP_OK, EP_EINVAL, EP_ENOMEM, EP_ECUDA, EP_ENOCONV, EP_ENONFINITE, EP_ESTATE, EP_EBUSY, EP_EREJECTED = range(9)
+(EP_OK, EP_EINVAL, EP_ENOMEM, EP_ECUDA, EP_ENOCONV, EP_ENONFINITE, EP_ESTATE, EP_EBUSY, EP_EREJECTED,
+ EP_ECANCELLED) = range(10)
 STATUS_NAMES = ["EP_OK", "EP_EINVAL", "EP_ENOMEM", "EP_ECUDA", "EP_ENOCONV", "EP_ENONFINITE", "EP_ESTATE",
-                "EP_EBUSY", "EP_EREJECTED"]
+                "EP_EBUSY", "EP_EREJECTED", "EP_ECANCELLED"]
 EP_MONO, EP_BI = 0, 1
 EP_FP32, EP_FP64 = 0, 1
 EP_VM_MV, EP_W, EP_VE_MV, EP_TACT, EP_V, EP_VE = range(6)
@@ -30,7 +31,9 @@ EXPORTS = ["ep_create", "ep_set_mask", "ep_set_fibres", "ep_set_params", "ep_add
            "ep_get_info", "ep_step_noalloc", "ep_profile_enable", "ep_get_profile", "ep_last_error",
            "ep_destroy", "ep_batch_create", "ep_batch_add", "ep_batch_remove", "ep_batch_step",
            "ep_batch_slot_stats", "ep_batch_autotune", "ep_batch_get_info", "ep_batch_last_error",
-           "ep_batch_destroy"]
+           "ep_batch_destroy", "ep_footprint", "ep_batch_set_schedule", "ep_server_create", "ep_server_submit",
+           "ep_server_cancel", "ep_server_collect", "ep_server_drain", "ep_server_get_stats", "ep_server_now",
+           "ep_server_last_error", "ep_server_destroy"]
 
 _ALLOC_T = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
 _FREE_T = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
@@ -71,6 +74,26 @@ class BatchInfo(ctypes.Structure):
                 ("budget_bytes", ctypes.c_size_t), ("ctas_per_sm", ctypes.c_int),
                 ("sweeps_per_check", ctypes.c_int), ("zseg", ctypes.c_int),
                 ("group_bytes", ctypes.c_size_t), ("groups", ctypes.c_int)]
+
+
+class ServerConfig(ctypes.Structure):
+    _fields_ = [("max_slots", ctypes.c_int), ("chunk_steps", ctypes.c_int), ("sweeps_per_check", ctypes.c_int),
+                ("hbm_budget_bytes", ctypes.c_size_t), ("cuda_stream", ctypes.c_void_p)]
+
+
+class RequestResult(ctypes.Structure):
+    _fields_ = [("id", ctypes.c_longlong), ("status", ctypes.c_int), ("steps_done", ctypes.c_int),
+                ("n_tissue", ctypes.c_longlong), ("total_iters", ctypes.c_longlong),
+                ("t_release_s", ctypes.c_double), ("t_admit_s", ctypes.c_double), ("t_done_s", ctypes.c_double),
+                ("device_bytes", ctypes.c_size_t), ("sim", ctypes.c_void_p)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("queued", ctypes.c_int), ("active", ctypes.c_int), ("finished", ctypes.c_int)] + \
+               [(n, ctypes.c_longlong) for n in ("submitted", "admitted", "completed", "cancelled", "rejected",
+                                                  "chunks", "voxel_steps")] + \
+               [("hbm_in_use", ctypes.c_size_t), ("hbm_peak", ctypes.c_size_t), ("busy_s", ctypes.c_double),
+                ("now_s", ctypes.c_double)]
 
 
 class EPError(RuntimeError):
@@ -118,6 +141,17 @@ def load(path: str = LIB_PATH):
         "ep_batch_get_info": ([vp, ctypes.POINTER(BatchInfo)], ip),
         "ep_batch_last_error": ([vp], ctypes.c_char_p),
         "ep_batch_destroy": ([vp], None),
+        "ep_footprint": ([vp, ctypes.POINTER(sz), ctypes.POINTER(sz)], ip),
+        "ep_batch_set_schedule": ([vp, ip, ip, ip, ctypes.c_longlong], ip),
+        "ep_server_create": ([ctypes.POINTER(ServerConfig), ctypes.POINTER(vp)], ip),
+        "ep_server_submit": ([vp, vp, ip, dp, ctypes.POINTER(ctypes.c_longlong)], ip),
+        "ep_server_cancel": ([vp, ctypes.c_longlong], ip),
+        "ep_server_collect": ([vp, ctypes.POINTER(RequestResult), ip, ctypes.POINTER(ip), dp], ip),
+        "ep_server_drain": ([vp, dp], ip),
+        "ep_server_get_stats": ([vp, ctypes.POINTER(ServerStats)], ip),
+        "ep_server_now": ([vp], dp),
+        "ep_server_last_error": ([vp], ctypes.c_char_p),
+        "ep_server_destroy": ([vp], None),
         "ep_destroy": ([vp], None),
     }
     for name, (args, res) in sigs.items():
@@ -266,6 +300,12 @@ class Sim:
                                               self.n), "ep_apply_operator")
         return out
 
+    def footprint(self):
+        """(resident, peak) device bytes, planned on the host (ep_footprint)."""
+        r, p = ctypes.c_size_t(), ctypes.c_size_t()
+        self._check(self._L.ep_footprint(self._h, ctypes.byref(r), ctypes.byref(p)), "ep_footprint")
+        return r.value, p.value
+
     def profile_enable(self, on: bool = True):
         self._check(self._L.ep_profile_enable(self._h, int(bool(on))), "ep_profile_enable")
 
@@ -322,6 +362,10 @@ class Batch:
     def autotune(self, trial_sweeps: int = 20):
         self._check(self._L.ep_batch_autotune(self._h, int(trial_sweeps)), "ep_batch_autotune")
 
+    def set_schedule(self, ctas_per_sm: int = 0, sweeps_per_check: int = 0, zseg: int = 0, group_bytes: int = -1):
+        self._check(self._L.ep_batch_set_schedule(self._h, int(ctas_per_sm), int(sweeps_per_check), int(zseg),
+                                                  int(group_bytes)), "ep_batch_set_schedule")
+
     def info(self) -> BatchInfo:
         i = BatchInfo()
         self._check(self._L.ep_batch_get_info(self._h, ctypes.byref(i)), "ep_batch_get_info")
@@ -331,6 +375,94 @@ class Batch:
         if getattr(self, "_h", None):
             self._L.ep_batch_destroy(self._h)
             self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """Request loop with continuous batching (ep_server).  A submitted Sim is
+    handed to the server (its Python object stops owning the handle) and
+    comes back, attached again, in the result of ``collect``.  Handles must
+    use the library's own device allocations (``use_torch=False``): the
+    serving thread allocates them."""
+
+    def __init__(self, max_slots: int, chunk_steps: int = 10, hbm_budget_bytes: int = 0, sweeps_per_check: int = 0,
+                 stream: Optional[int] = None):
+        L = load()
+        self._L = L
+        c = ServerConfig()
+        c.max_slots, c.chunk_steps, c.sweeps_per_check = int(max_slots), int(chunk_steps), int(sweeps_per_check)
+        c.hbm_budget_bytes, c.cuda_stream = int(hbm_budget_bytes), stream
+        h = ctypes.c_void_p()
+        st = L.ep_server_create(ctypes.byref(c), ctypes.byref(h))
+        if st != EP_OK:
+            raise EPError(st, "ep_server_create")
+        self._h = h
+        self._held = {}
+
+    def _check(self, st: int, what: str):
+        if st != EP_OK:
+            raise EPError(st, f"{what}: {self._L.ep_server_last_error(self._h).decode()}")
+
+    def submit(self, sim: "Sim", n_steps: int, release_s: float = 0.0) -> int:
+        if sim._hooks is not None:
+            raise ValueError("served handles must be created with use_torch=False")
+        rid = ctypes.c_longlong()
+        self._check(self._L.ep_server_submit(self._h, sim._h, int(n_steps), float(release_s), ctypes.byref(rid)),
+                    "ep_server_submit")
+        self._held[rid.value] = (sim, sim._h)
+        sim._h = None   # the server owns the handle until collected
+        return rid.value
+
+    def cancel(self, rid: int):
+        self._check(self._L.ep_server_cancel(self._h, int(rid)), "ep_server_cancel")
+
+    def collect(self, max_results: int = 64, wait_s: float = 0.0):
+        """Finished requests: list of (RequestResult, Sim) with the Sim attached again."""
+        buf = (RequestResult * int(max_results))()
+        n = ctypes.c_int()
+        self._check(self._L.ep_server_collect(self._h, buf, int(max_results), ctypes.byref(n), float(wait_s)),
+                    "ep_server_collect")
+        out = []
+        for i in range(n.value):
+            r = buf[i]
+            sim, h = self._held.pop(r.id)
+            sim._h = h
+            out.append((r, sim))
+        return out
+
+    def collect_n(self, n: int, timeout_s: float = 600.0):
+        """Collect until n results arrived (collecting as they finish keeps
+        admission from waiting on memory held by results)."""
+        import time
+        out, t_end = [], time.monotonic() + timeout_s
+        while len(out) < n:
+            left = t_end - time.monotonic()
+            if left <= 0:
+                raise EPError(EP_EBUSY, f"collect_n: {len(out)} of {n} results after {timeout_s} s")
+            out += self.collect(max_results=max(1, n - len(out)), wait_s=min(left, 1.0))
+        return out
+
+    def drain(self, timeout_s: float = -1.0):
+        self._check(self._L.ep_server_drain(self._h, float(timeout_s)), "ep_server_drain")
+
+    def stats(self) -> ServerStats:
+        s = ServerStats()
+        self._check(self._L.ep_server_get_stats(self._h, ctypes.byref(s)), "ep_server_get_stats")
+        return s
+
+    def now(self) -> float:
+        return self._L.ep_server_now(self._h)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._L.ep_server_destroy(self._h)   # destroys the handles it still holds
+            self._h = None
+            self._held.clear()
 
     def __del__(self):
         try:

@@ -15,9 +15,13 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <chrono>
+#include <condition_variable>
+#include <deque>
 #include <mutex>
 #include <new>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "../../include/ep.h"
@@ -42,6 +46,18 @@ struct StimDef {
 
 }  // namespace
 
+// Host-side layout of a handle, computed from the mask alone (before any
+// device memory exists): tissue voxels sorted by face-connected component,
+// reduction chunks, and the z-march work items.
+struct HostPlan {
+    bool done = false;
+    std::vector<int> order;             // tissue voxels, sorted by component then index
+    std::vector<long long> comp_count;  // voxels per component
+    std::vector<Chunk> chunks;
+    std::vector<int> comp_chunk0;       // first chunk of each component (+ end)
+    std::vector<Seg> segs;
+};
+
 struct ep_sim {
     ep_grid_desc d{};
     long long n = 0;
@@ -53,6 +69,8 @@ struct ep_sim {
     bool have_mask = false, have_params = false;
     ep_params p{};
     std::vector<StimDef> stims;
+    HostPlan plan;
+    size_t fp_resident = 0, fp_peak = 0;   // device bytes after / during set-up (from the plan)
     bool ready = false;
     // derived layout
     long long n_tissue = 0;
@@ -192,17 +210,39 @@ std::vector<Seg> build_segments(const uint8_t *m, int nx, int ny, int nz, int zs
 // ---------------------------------------------------------------------------
 // set-up: layout built on the host from the mask, records on the device
 // ---------------------------------------------------------------------------
-template <typename real>
-ep_status setup_typed(ep_sim *s)
+size_t abytes(size_t b) { return b ? b : 16; }   // dalloc's size of a request
+
+// Device bytes of a handle after set-up (resident) and during it (peak, which
+// adds the staging buffers of fibres, mask and raw records).  Matches the
+// allocations of setup_typed exactly.
+void footprint(const ep_sim *s, size_t rb, size_t *resident, size_t *peak)
 {
+    const HostPlan &P = s->plan;
+    const size_t n = (size_t)s->n;
+    size_t r = abytes(sizeof(ushort4) * n) + 8 * abytes(rb * n);
+    r += abytes(sizeof(Seg) * (size_t)s->max_items) + abytes(sizeof(int) * P.order.size());
+    r += abytes(sizeof(Chunk) * P.chunks.size()) + abytes(sizeof(int) * P.comp_chunk0.size());
+    r += abytes(sizeof(long long) * P.comp_count.size()) + abytes(sizeof(double) * (size_t)s->ncomp);
+    r += abytes(sizeof(double) * (size_t)std::max<long long>(s->max_items, s->nchunk)) + abytes(sizeof(Ctl));
+    *resident = r;
+    *peak = r + abytes(sizeof(float) * 3 * n) + abytes(n) + abytes(sizeof(ushort4) * n);
+}
+
+// Host analysis of the mask: face-connected components (breadth-first), the
+// component-sorted tissue index list, reduction chunks and z-march segments.
+// Fills s->plan and the derived counts; touches no device state.
+ep_status plan_layout(ep_sim *s)
+{
+    if (s->plan.done) return EP_OK;
+    if (!s->have_mask) return fail(s, EP_ESTATE, "ep_set_mask must be called first");
     const int nx = s->d.nx, ny = s->d.ny, nz = s->d.nz;
     const long long n = s->n;
     const uint8_t *m = s->mask.data();
-    // face-connected components (breadth-first), tissue index list sorted by component
+    HostPlan &P = s->plan;
     std::vector<int> comp(n, -1);
-    std::vector<int> order;
-    order.reserve((size_t)std::count_if(s->mask.begin(), s->mask.end(), [](uint8_t c) { return c != 0; }));
-    std::vector<long long> comp_count;
+    P.order.clear();
+    P.order.reserve((size_t)std::count_if(s->mask.begin(), s->mask.end(), [](uint8_t c) { return c != 0; }));
+    P.comp_count.clear();
     std::vector<long long> queue;
     int nc = 0;
     for (long long q = 0; q < n; ++q) {
@@ -225,32 +265,52 @@ ep_status setup_typed(ep_sim *s)
             }
         }
         std::sort(queue.begin(), queue.end());
-        for (long long r : queue) order.push_back((int)r);
-        comp_count.push_back((long long)queue.size());
+        for (long long r : queue) P.order.push_back((int)r);
+        P.comp_count.push_back((long long)queue.size());
         ++nc;
     }
-    s->n_tissue = (long long)order.size();
-    s->ncomp = nc;
-    if (s->n_tissue == 0) return fail(s, EP_EINVAL, "mask has no tissue voxel");
-    if (n > 2147483647LL) return fail(s, EP_EINVAL, "grid too large for 32-bit voxel indices");
-    std::vector<Chunk> chunks;
-    std::vector<int> comp_chunk0(nc + 1, 0);
-    {
-        long long pos = 0;
-        for (int c = 0; c < nc; ++c) {
-            comp_chunk0[c] = (int)chunks.size();
-            const long long end = pos + comp_count[c];
-            for (long long st = pos; st < end; st += kChunk)
-                chunks.push_back(Chunk{(int)st, (int)std::min<long long>(st + kChunk, end), c});
-            pos = end;
-        }
-        comp_chunk0[nc] = (int)chunks.size();
+    if (P.order.empty()) return fail(s, EP_EINVAL, "mask has no tissue voxel");
+    P.chunks.clear();
+    P.comp_chunk0.assign(nc + 1, 0);
+    long long pos = 0;
+    for (int c = 0; c < nc; ++c) {
+        P.comp_chunk0[c] = (int)P.chunks.size();
+        const long long end = pos + P.comp_count[c];
+        for (long long st = pos; st < end; st += kChunk)
+            P.chunks.push_back(Chunk{(int)st, (int)std::min<long long>(st + kChunk, end), c});
+        pos = end;
     }
-    s->nchunk = (int)chunks.size();
-    // z-march segments over tile columns with tissue
-    std::vector<Seg> segs = build_segments(m, nx, ny, nz, s->zseg);
-    s->nseg = (int)segs.size();
+    P.comp_chunk0[nc] = (int)P.chunks.size();
+    P.segs = build_segments(m, nx, ny, nz, s->zseg);
+    s->n_tissue = (long long)P.order.size();
+    s->ncomp = nc;
+    s->nchunk = (int)P.chunks.size();
+    s->nseg = (int)P.segs.size();
     s->max_items = std::max<long long>((long long)build_segments(m, nx, ny, nz, kZSegMin).size(), s->nseg);
+    footprint(s, s->d.precision == EP_FP64 ? sizeof(double) : sizeof(float), &s->fp_resident, &s->fp_peak);
+    P.done = true;
+    return EP_OK;
+}
+
+
+// Device set-up of a handle from its host plan.
+template <typename real>
+ep_status setup_typed(ep_sim *s)
+{
+    ep_status pst = plan_layout(s);
+    if (pst != EP_OK) return pst;
+    const int nx = s->d.nx, ny = s->d.ny, nz = s->d.nz;
+    const long long n = s->n;
+    const uint8_t *m = s->mask.data();
+    if (n > 2147483647LL) return fail(s, EP_EINVAL, "grid too large for 32-bit voxel indices");
+    const HostPlan &P = s->plan;
+    const std::vector<int> &order = P.order;
+    const std::vector<Chunk> &chunks = P.chunks;
+    const std::vector<int> &comp_chunk0 = P.comp_chunk0;
+    const std::vector<long long> &comp_count = P.comp_count;
+    const std::vector<Seg> &segs = P.segs;
+    const int nc = s->ncomp;
+    const size_t want_resident = s->fp_resident, want_peak = s->fp_peak;
 
     // device buffers
     const size_t rb = sizeof(real);
@@ -279,6 +339,7 @@ ep_status setup_typed(ep_sim *s)
                          tmp_fib, tmp_mask, tmp_rec};
     for (const void *p : all)
         if (!p) return fail(s, EP_ENOMEM, "device allocation failed");
+    if (s->dev_bytes != want_peak) return fail(s, EP_ECUDA, "internal: set-up allocations differ from the footprint");
     cudaStream_t st = s->stream;
     CK(cudaMemcpyAsync(s->segs, segs.data(), sizeof(Seg) * segs.size(), cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(s->idx, order.data(), sizeof(int) * order.size(), cudaMemcpyHostToDevice, st));
@@ -314,7 +375,13 @@ ep_status setup_typed(ep_sim *s)
             s->allocs.erase(it);
         }
     }
-    s->dev_bytes -= sizeof(float) * 3 * n + n + sizeof(ushort4) * n;
+    s->dev_bytes = want_resident;
+    // the host plan is not needed once on the device (counts stay in the handle)
+    s->plan.order = std::vector<int>();
+    s->plan.comp_count = std::vector<long long>();
+    s->plan.chunks = std::vector<Chunk>();
+    s->plan.comp_chunk0 = std::vector<int>();
+    s->plan.segs = std::vector<Seg>();
     CK(cudaMallocHost((void **)&s->ctl_host, 2 * sizeof(Ctl)));
     std::memset(s->ctl_host, 0, 2 * sizeof(Ctl));
     CK(cudaEventCreateWithFlags(&s->ev[0], cudaEventDisableTiming));
@@ -657,6 +724,7 @@ ep_status ep_set_mask(ep_sim *s, const uint8_t *mask, size_t n)
     s->mask.assign(mask, mask + n);
     for (auto &c : s->mask) c = c ? 1 : 0;
     s->have_mask = true;
+    s->plan = HostPlan();   // layout of the previous mask, if planned, is stale
     return EP_OK;
 }
 
@@ -837,6 +905,20 @@ ep_status ep_get_info(ep_sim *s, ep_info *info)
     return EP_OK;
 }
 
+ep_status ep_footprint(ep_sim *s, size_t *resident_bytes, size_t *peak_bytes)
+{
+    if (!s || !resident_bytes || !peak_bytes) return EP_EINVAL;
+    if (s->ready) {
+        *resident_bytes = *peak_bytes = s->dev_bytes;
+        return EP_OK;
+    }
+    const ep_status st = plan_layout(s);
+    if (st != EP_OK) return st;
+    *resident_bytes = s->fp_resident;
+    *peak_bytes = s->fp_peak;
+    return EP_OK;
+}
+
 ep_status ep_profile_enable(ep_sim *s, int on)
 {
     if (!s) return EP_EINVAL;
@@ -989,7 +1071,9 @@ struct ep_batch {
     Inst<float> *d_inst = nullptr;
     BItem *d_seg = nullptr, *d_chunk = nullptr;
     long long *d_steps_left = nullptr;
-    size_t cap_inst = 0, cap_seg = 0, cap_chunk = 0;
+    // unfinished members of the group being solved and their item prefix counts
+    int *d_active = nullptr, *d_cum = nullptr, *d_counts = nullptr;
+    size_t cap_inst = 0, cap_seg = 0, cap_chunk = 0, cap_active = 0, cap_cum = 0;
     int ninst = 0;
     long long nseg_items = 0, nchunk_items = 0;
     std::vector<int> order;        // slot of each table row
@@ -1105,6 +1189,8 @@ ep_status rebuild_tables(ep_batch *b)
     if ((st = grow(b, &b->d_inst, &b->cap_inst, insts.size())) != EP_OK) return st;
     if ((st = grow(b, &b->d_seg, &b->cap_seg, segs.size())) != EP_OK) return st;
     if ((st = grow(b, &b->d_chunk, &b->cap_chunk, chunks.size())) != EP_OK) return st;
+    if ((st = grow(b, &b->d_active, &b->cap_active, insts.size())) != EP_OK) return st;
+    if ((st = grow(b, &b->d_cum, &b->cap_cum, insts.size() + 1)) != EP_OK) return st;
     if (!insts.empty()) {
         CKB(cudaMemcpyAsync(b->d_inst, insts.data(), sizeof(Inst<float>) * insts.size(), cudaMemcpyHostToDevice,
                             b->stream));
@@ -1166,8 +1252,10 @@ ep_status build_batch_graph(ep_batch *b)
         for (int gi = 0; gi < ngroups; ++gi) {
             const ep_batch::Group &gr = b->groups[gi];
             const int ggs = grid_of(gr.nseg, b->nsm * b->ctas_per_sm);
-            k_set_cond<<<1, 1, 0, st>>>(hg[gi], 1u);
-            // inner loop: sweeps until every solve of the group is finished
+            const int gn = gr.inst1 - gr.inst0;
+            const Inst<float> *gi_inst = b->d_inst + gr.inst0;
+            k_active_list<float><<<1, kActThreads, 0, st>>>(gi_inst, gn, b->d_active, b->d_cum, b->d_counts, hg[gi]);
+            // inner loop: sweeps of the unfinished members until every solve of the group is finished
             cudaStreamCaptureStatus cs;
             cudaGraph_t cg = nullptr;
             const cudaGraphNode_t *deps = nullptr;
@@ -1186,9 +1274,10 @@ ep_status build_batch_graph(ep_batch *b)
             CKB(cudaStreamUpdateCaptureDependencies(st, &ni, nullptr, 1, cudaStreamSetCaptureDependencies));
             CKB(cudaStreamBeginCaptureToGraph(b->side, ibody, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
             for (int i = 0; i < b->sweeps_per_check; ++i)
-                k_stencil_batch<float, M_JAC><<<ggs, kThreads, 0, b->side>>>(b->d_inst, b->d_seg + gr.seg0,
-                                                                            (int)gr.nseg);
-            k_solve_cond<float><<<1, 256, 0, b->side>>>(b->d_inst + gr.inst0, gr.inst1 - gr.inst0, hg[gi]);
+                k_stencil_active<float, M_JAC><<<ggs, kThreads, 0, b->side>>>(gi_inst, b->d_active, b->d_cum,
+                                                                             b->d_counts);
+            k_active_list<float><<<1, kActThreads, 0, b->side>>>(gi_inst, gn, b->d_active, b->d_cum, b->d_counts,
+                                                                 hg[gi]);
             CKB(cudaStreamEndCapture(b->side, nullptr));
         }
         k_comp_mean_batch<float><<<gc, kRedThreads, 0, st>>>(b->d_inst, b->d_chunk, nc, (int)RED_X_FINAL);
@@ -1240,6 +1329,7 @@ ep_status ep_batch_create(int max_instances, size_t hbm_budget_bytes, void *cuda
         if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
         if (b->side) cudaStreamDestroy(b->side);
         if (b->d_steps_left) cudaFree(b->d_steps_left);
+        if (b->d_counts) cudaFree(b->d_counts);
         delete b;
         return EP_ECUDA;
     };
@@ -1255,6 +1345,7 @@ ep_status ep_batch_create(int max_instances, size_t hbm_budget_bytes, void *cuda
     if ((e = cudaGetDevice(&dev)) != cudaSuccess) return bad(e);
     if ((e = cudaDeviceGetAttribute(&b->nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return bad(e);
     if ((e = cudaMalloc((void **)&b->d_steps_left, sizeof(long long))) != cudaSuccess) return bad(e);
+    if ((e = cudaMalloc((void **)&b->d_counts, 2 * sizeof(int))) != cudaSuccess) return bad(e);
     *out = b;
     return EP_OK;
 }
@@ -1449,6 +1540,28 @@ ep_status ep_batch_autotune(ep_batch *b, int trial_sweeps)
     return rebuild_tables(b);
 }
 
+ep_status ep_batch_set_schedule(ep_batch *b, int ctas_per_sm, int sweeps_per_check, int zseg, long long group_bytes)
+{
+    if (!b) return EP_EINVAL;
+    if (ctas_per_sm < 0 || ctas_per_sm > 8) return bfail(b, EP_EINVAL, "ctas_per_sm must be in [1, 8] (0 keeps)");
+    if (sweeps_per_check < 0 || sweeps_per_check > 1024)
+        return bfail(b, EP_EINVAL, "sweeps_per_check must be in [1, 1024] (0 keeps)");
+    if (zseg != 0 && (zseg < kZSegMin || zseg > 256)) return bfail(b, EP_EINVAL, "zseg must be in [8, 256] (0 keeps)");
+    if (ctas_per_sm) b->ctas_per_sm = ctas_per_sm;
+    if (sweeps_per_check) b->sweeps_per_check = sweeps_per_check;
+    if (group_bytes >= 0) b->group_bytes = (size_t)group_bytes;
+    if (zseg && zseg != b->zseg) {
+        b->zseg = zseg;
+        for (ep_sim *t : b->slot) {
+            if (!t) continue;
+            const ep_status st = relayout_segments(t, zseg);
+            if (st != EP_OK) return bfail(b, st, t->err);
+        }
+    }
+    b->dirty = true;
+    return EP_OK;
+}
+
 ep_status ep_batch_get_info(ep_batch *b, ep_batch_info *info)
 {
     if (!b || !info) return EP_EINVAL;
@@ -1480,10 +1593,427 @@ void ep_batch_destroy(ep_batch *b)
     if (b->d_inst) cudaFree(b->d_inst);
     if (b->d_seg) cudaFree(b->d_seg);
     if (b->d_chunk) cudaFree(b->d_chunk);
+    if (b->d_active) cudaFree(b->d_active);
+    if (b->d_cum) cudaFree(b->d_cum);
+    if (b->d_counts) cudaFree(b->d_counts);
     if (b->d_steps_left) cudaFree(b->d_steps_left);
     if (b->side) cudaStreamDestroy(b->side);
     if (b->own_stream) cudaStreamDestroy(b->stream);
     delete b;
+}
+
+}  // extern "C"
+
+// ===========================================================================
+// Served form: requests arrive over time and join a running batch
+// (continuous batching).  One serving thread admits released requests in
+// release order while a slot is free and the request's device footprint
+// (set-up peak) fits the budget beside everything the server holds, sets them
+// up, runs the batched step in chunks and retires each request when its steps
+// are done.  Membership changes only between chunks; the batch rebuilds its
+// tables and graph then.  Monodomain and bidomain requests go to separate
+// batches, stepped one after the other in each chunk.
+// ===========================================================================
+namespace {
+
+using SrvClock = std::chrono::steady_clock;
+
+struct SrvReq {
+    long long id = 0;
+    ep_sim *sim = nullptr;
+    int n_steps = 0, steps_done = 0, slot = -1, model = 0;
+    int status = EP_OK;
+    bool cancel = false, busy = false, planned = false;
+    double release = 0, t_admit = -1, t_done = -1;
+    long long iters_base = 0, total_iters = 0;
+    size_t peak = 0, bytes = 0;
+};
+
+}  // namespace
+
+struct ep_server {
+    ep_server_config cfg{};
+    int device = 0;
+    ep_batch *batch[2] = {nullptr, nullptr};   // by model
+    std::thread thr;
+    std::mutex mu;
+    std::condition_variable cv_work, cv_done;
+    bool stop = false;
+    bool blocked_on_results = false;   // nothing runs and the next request waits for memory held by results
+    std::string err;
+    SrvClock::time_point t0;
+    std::deque<SrvReq *> queue;      // submitted, by release time then id
+    std::vector<SrvReq *> active;    // batch members
+    SrvReq *admitting = nullptr;     // being set up (between queue and active)
+    std::deque<SrvReq *> finished;   // retired, not collected
+    long long next_id = 1;
+    size_t hbm_in_use = 0;           // bytes of held requests, plus the set-up reservation
+    ep_server_stats st{};
+    double now() const { return std::chrono::duration<double>(SrvClock::now() - t0).count(); }
+};
+
+namespace {
+
+ep_status sfail(ep_server *v, ep_status st, const std::string &msg)
+{
+    v->err = msg;
+    return st;
+}
+
+// Control block of a member after the batch's last step (nullptr if absent).
+const Ctl *batch_member_ctl(const ep_batch *b, int slot)
+{
+    for (int r = 0; r < b->ninst && r < (int)b->last.size(); ++r)
+        if (b->order[r] == slot) return &b->last[r];
+    return nullptr;
+}
+
+// mu held.  A request leaves the server's queue or batch.
+void srv_finish(ep_server *v, SrvReq *r, int status)
+{
+    if (status != EP_OK) r->status = status;
+    r->t_done = v->now();
+    v->finished.push_back(r);
+    v->cv_done.notify_all();
+}
+
+void srv_erase(std::deque<SrvReq *> &q, SrvReq *r)
+{
+    auto it = std::find(q.begin(), q.end(), r);
+    if (it != q.end()) q.erase(it);
+}
+
+void serve_loop(ep_server *v)
+{
+    cudaSetDevice(v->device);
+    const size_t budget = v->cfg.hbm_budget_bytes;
+    std::unique_lock<std::mutex> lk(v->mu);
+    while (!v->stop) {
+        // 1. cancelled members leave at this chunk boundary
+        for (size_t i = 0; i < v->active.size();) {
+            SrvReq *r = v->active[i];
+            if (!r->cancel) {
+                ++i;
+                continue;
+            }
+            ep_batch_remove(v->batch[r->model], r->slot);
+            v->active.erase(v->active.begin() + i);
+            ++v->st.cancelled;
+            srv_finish(v, r, EP_ECANCELLED);
+        }
+        // 2. admission of released requests, in release order
+        while (!v->stop && !v->queue.empty() && v->queue.front()->release <= v->now() &&
+               (int)v->active.size() < v->cfg.max_slots) {
+            SrvReq *r = v->queue.front();
+            if (!r->planned) {   // host layout and exact footprint (no device work), outside the lock
+                r->busy = true;
+                lk.unlock();
+                const ep_status ps = plan_layout(r->sim);
+                lk.lock();
+                r->busy = false;
+                r->planned = true;
+                r->peak = r->sim->ready ? r->sim->dev_bytes : r->sim->fp_peak;
+                if (ps != EP_OK) {
+                    srv_erase(v->queue, r);
+                    srv_finish(v, r, ps);
+                    continue;
+                }
+                if (budget && r->peak > budget) {
+                    srv_erase(v->queue, r);
+                    ++v->st.rejected;
+                    srv_finish(v, r, EP_EREJECTED);
+                    continue;
+                }
+            }
+            if (r->cancel) {
+                srv_erase(v->queue, r);
+                ++v->st.cancelled;
+                srv_finish(v, r, EP_ECANCELLED);
+                continue;
+            }
+            if (budget && v->hbm_in_use + r->peak > budget) {   // wait for memory to be released
+                if (v->active.empty() && !v->finished.empty() && !v->blocked_on_results) {
+                    v->blocked_on_results = true;
+                    v->cv_done.notify_all();
+                }
+                break;
+            }
+            v->blocked_on_results = false;
+            srv_erase(v->queue, r);
+            v->admitting = r;
+            v->hbm_in_use += r->peak;
+            v->st.hbm_peak = std::max(v->st.hbm_peak, v->hbm_in_use);
+            lk.unlock();
+            ep_status as = ensure_ready(r->sim);
+            int slot = -1;
+            Ctl c0;
+            std::memset(&c0, 0, sizeof(c0));
+            if (as == EP_OK) as = ep_batch_add(v->batch[r->model], r->sim, &slot);
+            if (as == EP_OK) {
+                if (cudaMemcpyAsync(&c0, r->sim->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, r->sim->stream) != cudaSuccess ||
+                    cudaStreamSynchronize(r->sim->stream) != cudaSuccess) {
+                    cudaGetLastError();
+                    as = EP_ECUDA;
+                }
+            }
+            lk.lock();
+            v->admitting = nullptr;
+            v->hbm_in_use -= r->peak;
+            r->bytes = r->sim->dev_bytes;
+            v->hbm_in_use += r->bytes;
+            if (as != EP_OK) {
+                if (slot >= 0) ep_batch_remove(v->batch[r->model], slot);
+                v->err = std::string("admission of request ") + std::to_string(r->id) + " failed: " + r->sim->err +
+                         " " + ep_batch_last_error(v->batch[r->model]);
+                srv_finish(v, r, as);
+                continue;
+            }
+            r->slot = slot;
+            r->iters_base = c0.total_iters;
+            r->t_admit = v->now();
+            v->active.push_back(r);
+            ++v->st.admitted;
+        }
+        if (v->stop) break;
+        // 3. nothing to run: sleep until the next release, a submission, a collect or a cancel
+        if (v->active.empty()) {
+            if (v->queue.empty()) {
+                v->cv_work.wait(lk);
+            } else {
+                const double wait = v->queue.front()->release - v->now();
+                if (wait > 0) v->cv_work.wait_for(lk, std::chrono::duration<double>(std::min(wait, 3600.0)));
+                else v->cv_work.wait_for(lk, std::chrono::milliseconds(100));   // blocked on memory held by results
+            }
+            continue;
+        }
+        // 4. one chunk: at most chunk_steps, and no member passes its step count
+        int k[2] = {v->cfg.chunk_steps, v->cfg.chunk_steps};
+        bool has[2] = {false, false};
+        for (SrvReq *r : v->active) {
+            k[r->model] = std::min(k[r->model], r->n_steps - r->steps_done);
+            has[r->model] = true;
+        }
+        lk.unlock();
+        const double tb = v->now();
+        ep_status bs[2] = {EP_OK, EP_OK};
+        for (int m = 0; m < 2; ++m)
+            if (has[m]) bs[m] = ep_batch_step(v->batch[m], k[m]);
+        const double te = v->now();
+        lk.lock();
+        v->st.busy_s += te - tb;
+        ++v->st.chunks;
+        long long vs = 0;
+        for (size_t i = 0; i < v->active.size();) {
+            SrvReq *r = v->active[i];
+            const ep_status b = bs[r->model];
+            int stat = EP_OK;
+            if (b == EP_OK || b == EP_ENOCONV || b == EP_ENONFINITE) {
+                r->steps_done += k[r->model];
+                vs += (long long)k[r->model] * r->sim->n_tissue;
+                if (const Ctl *c = batch_member_ctl(v->batch[r->model], r->slot)) {
+                    r->total_iters = c->total_iters - r->iters_base;
+                    if (c->nonfinite) stat = EP_ENONFINITE;
+                    else if (c->noconv) r->status = EP_ENOCONV;   // kept: the request still runs to its end
+                }
+            } else {   // the batched launch failed: its members fail with it
+                stat = b;
+                v->err = std::string("batched step failed: ") + ep_batch_last_error(v->batch[r->model]);
+            }
+            if (stat != EP_OK || r->steps_done >= r->n_steps) {
+                ep_batch_remove(v->batch[r->model], r->slot);
+                r->slot = -1;
+                v->active.erase(v->active.begin() + i);
+                ++v->st.completed;
+                srv_finish(v, r, stat);
+                continue;
+            }
+            ++i;
+        }
+        v->st.voxel_steps += vs;
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+ep_status ep_server_create(const ep_server_config *cfg, ep_server **out)
+{
+    if (!out) return EP_EINVAL;
+    *out = nullptr;
+    if (!cfg || cfg->max_slots < 1 || cfg->max_slots > 65536 || cfg->chunk_steps < 1 || cfg->sweeps_per_check < 0 ||
+        cfg->sweeps_per_check > 1024)
+        return EP_EINVAL;
+    ep_server *v = new (std::nothrow) ep_server();
+    if (!v) return EP_ENOMEM;
+    v->cfg = *cfg;
+    v->t0 = SrvClock::now();
+    cudaError_t e = cudaGetDevice(&v->device);
+    ep_status st = e == cudaSuccess ? EP_OK : EP_ECUDA;
+    for (int m = 0; m < 2 && st == EP_OK; ++m) {
+        st = ep_batch_create(cfg->max_slots, 0, cfg->cuda_stream, &v->batch[m]);
+        if (st == EP_OK && cfg->sweeps_per_check) st = ep_batch_set_schedule(v->batch[m], 0, cfg->sweeps_per_check, 0, -1);
+    }
+    if (st != EP_OK) {
+        cudaGetLastError();
+        for (ep_batch *b : v->batch) ep_batch_destroy(b);
+        delete v;
+        return st;
+    }
+    try {
+        v->thr = std::thread(serve_loop, v);
+    } catch (...) {
+        for (ep_batch *b : v->batch) ep_batch_destroy(b);
+        delete v;
+        return EP_ENOMEM;
+    }
+    *out = v;
+    return EP_OK;
+}
+
+ep_status ep_server_submit(ep_server *v, ep_sim *sim, int n_steps, double release_s, long long *id)
+{
+    if (!v || !sim || !id || n_steps < 1) return EP_EINVAL;
+    if (sim->d.precision != EP_FP32) return sfail(v, EP_EINVAL, "served requests must be FP32 handles");
+    if (!sim->have_mask || !sim->have_params) return sfail(v, EP_ESTATE, "a request needs its mask and parameters set");
+    std::lock_guard<std::mutex> lk(v->mu);
+    if (v->stop) return sfail(v, EP_ESTATE, "server is shutting down");
+    auto holds = [&](const SrvReq *r) { return r && r->sim == sim; };
+    if (std::any_of(v->queue.begin(), v->queue.end(), holds) || std::any_of(v->active.begin(), v->active.end(), holds) ||
+        std::any_of(v->finished.begin(), v->finished.end(), holds) || holds(v->admitting))
+        return sfail(v, EP_EINVAL, "handle is already held by the server");
+    SrvReq *r = new (std::nothrow) SrvReq();
+    if (!r) return EP_ENOMEM;
+    r->id = v->next_id++;
+    r->sim = sim;
+    r->n_steps = n_steps;
+    r->model = sim->d.model == EP_BI ? 1 : 0;
+    r->release = std::max(release_s, v->now());
+    auto pos = std::upper_bound(v->queue.begin(), v->queue.end(), r->release,
+                                [](double t, const SrvReq *q) { return t < q->release; });
+    v->queue.insert(pos, r);
+    ++v->st.submitted;
+    *id = r->id;
+    v->cv_work.notify_all();
+    return EP_OK;
+}
+
+ep_status ep_server_cancel(ep_server *v, long long id)
+{
+    if (!v) return EP_EINVAL;
+    std::lock_guard<std::mutex> lk(v->mu);
+    for (SrvReq *r : v->queue) {
+        if (r->id != id) continue;
+        if (r->busy) {
+            r->cancel = true;
+        } else {
+            srv_erase(v->queue, r);
+            ++v->st.cancelled;
+            srv_finish(v, r, EP_ECANCELLED);
+        }
+        v->cv_work.notify_all();
+        return EP_OK;
+    }
+    for (SrvReq *r : v->active)
+        if (r->id == id) {
+            r->cancel = true;
+            return EP_OK;
+        }
+    if (v->admitting && v->admitting->id == id) {
+        v->admitting->cancel = true;
+        return EP_OK;
+    }
+    return sfail(v, EP_EINVAL, "no queued or running request with this id");
+}
+
+ep_status ep_server_collect(ep_server *v, ep_request_result *out, int max_results, int *n_out, double wait_s)
+{
+    if (!v || !out || max_results < 1 || !n_out) return EP_EINVAL;
+    *n_out = 0;
+    std::unique_lock<std::mutex> lk(v->mu);
+    if (v->finished.empty() && wait_s > 0)
+        v->cv_done.wait_for(lk, std::chrono::duration<double>(std::min(wait_s, 1e6)),
+                            [&] { return !v->finished.empty() || v->stop; });
+    int n = 0;
+    if (!v->finished.empty()) v->blocked_on_results = false;
+    while (n < max_results && !v->finished.empty()) {
+        SrvReq *r = v->finished.front();
+        v->finished.pop_front();
+        ep_request_result &o = out[n++];
+        o.id = r->id;
+        o.status = r->status;
+        o.steps_done = r->steps_done;
+        o.n_tissue = r->sim->n_tissue;
+        o.total_iters = r->total_iters;
+        o.t_release_s = r->release;
+        o.t_admit_s = r->t_admit;
+        o.t_done_s = r->t_done;
+        o.device_bytes = r->bytes;
+        o.sim = r->sim;
+        v->hbm_in_use -= r->bytes;
+        delete r;
+    }
+    *n_out = n;
+    if (n) v->cv_work.notify_all();
+    return EP_OK;
+}
+
+ep_status ep_server_drain(ep_server *v, double timeout_s)
+{
+    if (!v) return EP_EINVAL;
+    std::unique_lock<std::mutex> lk(v->mu);
+    auto idle = [&] { return (v->queue.empty() && v->active.empty() && !v->admitting) || v->stop; };
+    auto stuck = [&] { return v->blocked_on_results && v->active.empty() && !v->admitting; };
+    auto done = [&] { return idle() || stuck(); };
+    if (timeout_s < 0) v->cv_done.wait(lk, done);
+    else if (!v->cv_done.wait_for(lk, std::chrono::duration<double>(std::min(timeout_s, 1e6)), done))
+        return sfail(v, EP_EBUSY, "requests still pending at the timeout");
+    if (!idle()) return sfail(v, EP_EBUSY, "admission waits for device memory held by uncollected results");
+    return EP_OK;
+}
+
+ep_status ep_server_get_stats(ep_server *v, ep_server_stats *out)
+{
+    if (!v || !out) return EP_EINVAL;
+    std::lock_guard<std::mutex> lk(v->mu);
+    *out = v->st;
+    out->queued = (int)v->queue.size();
+    out->active = (int)v->active.size() + (v->admitting ? 1 : 0);
+    out->finished = (int)v->finished.size();
+    out->hbm_in_use = v->hbm_in_use;
+    out->now_s = v->now();
+    return EP_OK;
+}
+
+double ep_server_now(const ep_server *v)
+{
+    return v ? v->now() : 0.0;
+}
+
+const char *ep_server_last_error(const ep_server *v) { return v ? v->err.c_str() : "null server"; }
+
+void ep_server_destroy(ep_server *v)
+{
+    if (!v) return;
+    {
+        std::lock_guard<std::mutex> lk(v->mu);
+        v->stop = true;
+    }
+    v->cv_work.notify_all();
+    v->cv_done.notify_all();
+    if (v->thr.joinable()) v->thr.join();
+    for (SrvReq *r : v->active) {
+        ep_batch_remove(v->batch[r->model], r->slot);
+        ep_destroy(r->sim);
+        delete r;
+    }
+    for (auto *q : {&v->queue, &v->finished})
+        for (SrvReq *r : *q) {
+            ep_destroy(r->sim);
+            delete r;
+        }
+    for (ep_batch *b : v->batch) ep_batch_destroy(b);
+    delete v;
 }
 
 }  // extern "C"

@@ -321,43 +321,74 @@ __global__ void k_fill(real *p, long long n, real v)
         p[i] = v;
 }
 
-// Device-side loop control of the graph-captured batched step:
-// the solve continues while any instance's solve is unfinished.
-__global__ void k_set_cond(cudaGraphConditionalHandle h, unsigned value) { cudaGraphSetConditional(h, value); }
+// Members of rows [0, n) whose solve is unfinished, in row order, with the
+// exclusive prefix counts of their stencil items (cum[n_active] = total);
+// counts = {total items, n_active}.  Sets the condition of the device-side
+// convergence loop (any member still active).  One CTA of kActThreads.
+constexpr int kActThreads = 1024;
 
-// Condition of the device-side convergence loop: any of the instances unfinished.
 template <typename real>
-__global__ void k_solve_cond(const Inst<real> *insts, int ninst, cudaGraphConditionalHandle h)
+__global__ void __launch_bounds__(kActThreads)
+k_active_list(const Inst<real> *insts, int n, int *active, int *cum, int *counts, cudaGraphConditionalHandle h)
 {
-    __shared__ int any;
-    if (threadIdx.x == 0) any = 0;
+    __shared__ int swa[32], swc[32];
+    __shared__ int base_a, base_c;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    if (threadIdx.x == 0) base_a = base_c = 0;
     __syncthreads();
-    for (int i = threadIdx.x; i < ninst; i += blockDim.x)
-        if (!*(volatile int *)&insts[i].ctl->done) any = 1;
-    __syncthreads();
-    if (threadIdx.x == 0) cudaGraphSetConditional(h, any ? 1u : 0u);
-}
-
-// List of the members of rows [0, n) whose solve is unfinished, with the prefix
-// counts of their stencil items (cum[n_active] = total), and the loop
-// condition of the device-side convergence loop (any member still active).
-template <typename real>
-__global__ void k_active_list(const Inst<real> *insts, int n, int *active, int *cum, int *counts,
-                              cudaGraphConditionalHandle h)
-{
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    int na = 0, tot = 0;
-    for (int i = 0; i < n; ++i) {
-        if (*(volatile int *)&insts[i].ctl->done) continue;
-        active[na] = i;
-        cum[na] = tot;
-        tot += insts[i].nseg;
-        ++na;
+    for (int i0 = 0; i0 < n; i0 += blockDim.x) {
+        const int i = i0 + threadIdx.x;
+        int a = 0, c = 0;
+        if (i < n && !*(volatile int *)&insts[i].ctl->done) {
+            a = 1;
+            c = insts[i].nseg;
+        }
+        int sa = a, sc = c;   // inclusive scans within the warp
+        for (int o = 1; o < 32; o <<= 1) {
+            const int ta = __shfl_up_sync(kFull, sa, o), tc = __shfl_up_sync(kFull, sc, o);
+            if (lane >= o) {
+                sa += ta;
+                sc += tc;
+            }
+        }
+        if (lane == 31) {
+            swa[wid] = sa;
+            swc[wid] = sc;
+        }
+        __syncthreads();
+        if (wid == 0) {   // inclusive scan of the warp totals
+            int va = lane < nw ? swa[lane] : 0, vc = lane < nw ? swc[lane] : 0;
+            for (int o = 1; o < 32; o <<= 1) {
+                const int ta = __shfl_up_sync(kFull, va, o), tc = __shfl_up_sync(kFull, vc, o);
+                if (lane >= o) {
+                    va += ta;
+                    vc += tc;
+                }
+            }
+            if (lane < nw) {
+                swa[lane] = va;
+                swc[lane] = vc;
+            }
+        }
+        __syncthreads();
+        if (a) {
+            const int pa = base_a + (wid ? swa[wid - 1] : 0) + sa - a;
+            active[pa] = i;
+            cum[pa] = base_c + (wid ? swc[wid - 1] : 0) + sc - c;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            base_a += swa[nw - 1];
+            base_c += swc[nw - 1];
+        }
+        __syncthreads();
     }
-    cum[na] = tot;
-    counts[0] = tot;
-    counts[1] = na;
-    if (h) cudaGraphSetConditional(h, na > 0 ? 1u : 0u);
+    if (threadIdx.x == 0) {
+        cum[base_a] = base_c;
+        counts[0] = base_c;
+        counts[1] = base_a;
+        if (h) cudaGraphSetConditional(h, base_a > 0 ? 1u : 0u);
+    }
 }
 
 // Outer loop of a multi-step graph: counts down the steps left in the chunk.

@@ -265,20 +265,87 @@ __device__ __forceinline__ void zero_state(St<real> &S)
     for (int j = 0; j < 3; ++j) S.FB[j] = S.FA[j] = real(0);
 }
 
+// Jacobi sweeps stage their loads through a per-thread ring in shared memory
+// filled by cp.async kJacDepth - 1 planes ahead: each thread reads back only
+// what it copied itself, so the ring needs no barrier, and the prefetched
+// planes hold no registers.
+template <typename real>
+struct JacRing {
+    static constexpr int D = sizeof(real) == 4 ? 4 : 3;   // static shared memory stays below 48 KB
+    uint2 rec[D][2][kThreads];   // fp16 records of rows lo / hi
+    real u[D][2][kThreads];
+    real b[D][kThreads];
+};
+struct NoRing {};
+
+template <typename real, int MODE>
 struct StencilSmem {
-    // sized for double; float kernels use the first half of each row
-    double sF[2][3][kWarps][32];
-    double sT[2][kWarps][32];
+    real sF[2][3][kWarps][32];
+    real sT[2][kWarps][32];
     double sred[kWarps];
     int sflag;
+    typename std::conditional<MODE == M_JAC, JacRing<real>, NoRing>::type ring;
 };
+
+template <int BYTES>
+__device__ __forceinline__ void cp_async_n(void *dst, const void *src)
+{
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(d), "l"(src), "n"(BYTES) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+// Stage plane k of this thread's two voxels (and b of the lower one) into ring slot `slot`.
+template <typename real>
+__device__ __forceinline__ void jac_issue(const Op<real> &o, JacRing<real> &R, int slot, int k, bool lo_in,
+                                          bool hi_in, int qlo, int qhi, int plane)
+{
+    const int t = threadIdx.x;
+    const bool kin = (unsigned)k < (unsigned)o.nz;
+    if (kin && lo_in) {
+        const int q = qlo + k * plane;
+        cp_async_n<8>(&R.rec[slot][0][t], o.rec + q);
+        cp_async_n<sizeof(real)>(&R.u[slot][0][t], o.src + q);
+        cp_async_n<sizeof(real)>(&R.b[slot][t], o.b + q);
+    } else {
+        R.rec[slot][0][t] = make_uint2(0u, (unsigned)kNonTissue << 16);
+        R.u[slot][0][t] = real(0);
+        R.b[slot][t] = real(0);
+    }
+    if (kin && hi_in) {
+        const int q = qhi + k * plane;
+        cp_async_n<8>(&R.rec[slot][1][t], o.rec + q);
+        cp_async_n<sizeof(real)>(&R.u[slot][1][t], o.src + q);
+    } else {
+        R.rec[slot][1][t] = make_uint2(0u, (unsigned)kNonTissue << 16);
+        R.u[slot][1][t] = real(0);
+    }
+}
+
+template <typename real>
+__device__ __forceinline__ void jac_read(const JacRing<real> &R, int slot, Ld<real, M_JAC> &L)
+{
+    const int t = threadIdx.x;
+    const uint2 a = R.rec[slot][0][t], c = R.rec[slot][1][t];
+    L.rLo = make_ushort4((unsigned short)(a.x & 0xffffu), (unsigned short)(a.x >> 16), (unsigned short)(a.y & 0xffffu),
+                         (unsigned short)(a.y >> 16));
+    L.rHi = make_ushort4((unsigned short)(c.x & 0xffffu), (unsigned short)(c.x >> 16), (unsigned short)(c.y & 0xffffu),
+                         (unsigned short)(c.y >> 16));
+    L.uLo = R.u[slot][0][t];
+    L.uHi = R.u[slot][1][t];
+    L.bLo = R.b[slot][t];
+    L.wLo = L.wHi = real(1);
+    L.veLo = L.veHi = real(0);
+}
 
 // One work item (segment) of one instance.  item / nitems: index of this item
 // among the instance's items of the launch and their count (last-item logic).
 // Returns false for a sweep of an instance whose solve is finished.
 template <typename real, int MODE>
 __device__ __forceinline__ void stencil_item(const Inst<real> &I, int seg_index, int item, int nitems,
-                                             const ApplyIO<real> *io, StencilSmem &sm)
+                                             const ApplyIO<real> *io, StencilSmem<real, MODE> &sm)
 {
     real(*sF)[3][kWarps][32] = reinterpret_cast<real(*)[3][kWarps][32]>(&sm.sF[0][0][0][0]);
     real(*sT)[kWarps][32] = reinterpret_cast<real(*)[kWarps][32]>(&sm.sT[0][0][0]);
@@ -342,15 +409,50 @@ __device__ __forceinline__ void stencil_item(const Inst<real> &I, int seg_index,
     zero_state(S1);
     Ld<real, MODE> L0, L1;
     const int kbeg = sg.k0 - 1, kend = sg.k1;
-    load_plane<real, MODE>(o, kbeg, lo_in, hi_in, g.qlo, qhi, g.plane, L0);
-    // two planes per iteration; the state records swap roles
-    for (int k = kbeg;;) {
-        if (k + 1 <= kend) load_plane<real, MODE>(o, k + 1, lo_in, hi_in, g.qlo, qhi, g.plane, L1);
-        plane_step<real, MODE>(I, o, g, k, k > kbeg, k > kbeg + 1, S1, S0, L0, sF, sT, check, acc);
-        if (++k > kend) break;
-        if (k + 1 <= kend) load_plane<real, MODE>(o, k + 1, lo_in, hi_in, g.qlo, qhi, g.plane, L0);
-        plane_step<real, MODE>(I, o, g, k, k > kbeg, k > kbeg + 1, S0, S1, L1, sF, sT, check, acc);
-        if (++k > kend) break;
+    if constexpr (MODE == M_JAC) {
+        // planes staged kJacDepth - 1 ahead through the shared-memory ring
+        constexpr int D = JacRing<real>::D;
+        JacRing<real> &R = sm.ring;
+#pragma unroll
+        for (int j = 0; j < D - 1; ++j) {
+            if (kbeg + j <= kend) jac_issue<real>(o, R, j, kbeg + j, lo_in, hi_in, g.qlo, qhi, g.plane);
+            cp_async_commit();
+        }
+        int slot = 0;   // ring slot of plane k
+        for (int k = kbeg;;) {
+            {
+                const int kn = k + D - 1, sn = slot == 0 ? D - 1 : slot - 1;
+                if (kn <= kend) jac_issue<real>(o, R, sn, kn, lo_in, hi_in, g.qlo, qhi, g.plane);
+                cp_async_commit();
+                cp_async_wait<D - 1>();
+                jac_read<real>(R, slot, L0);
+                plane_step<real, MODE>(I, o, g, k, k > kbeg, k > kbeg + 1, S1, S0, L0, sF, sT, check, acc);
+                slot = slot == D - 1 ? 0 : slot + 1;
+            }
+            if (++k > kend) break;
+            {
+                const int kn = k + D - 1, sn = slot == 0 ? D - 1 : slot - 1;
+                if (kn <= kend) jac_issue<real>(o, R, sn, kn, lo_in, hi_in, g.qlo, qhi, g.plane);
+                cp_async_commit();
+                cp_async_wait<D - 1>();
+                jac_read<real>(R, slot, L1);
+                plane_step<real, MODE>(I, o, g, k, k > kbeg, k > kbeg + 1, S0, S1, L1, sF, sT, check, acc);
+                slot = slot == D - 1 ? 0 : slot + 1;
+            }
+            if (++k > kend) break;
+        }
+        cp_async_wait<0>();
+    } else {
+        load_plane<real, MODE>(o, kbeg, lo_in, hi_in, g.qlo, qhi, g.plane, L0);
+        // two planes per iteration; the state records swap roles
+        for (int k = kbeg;;) {
+            if (k + 1 <= kend) load_plane<real, MODE>(o, k + 1, lo_in, hi_in, g.qlo, qhi, g.plane, L1);
+            plane_step<real, MODE>(I, o, g, k, k > kbeg, k > kbeg + 1, S1, S0, L0, sF, sT, check, acc);
+            if (++k > kend) break;
+            if (k + 1 <= kend) load_plane<real, MODE>(o, k + 1, lo_in, hi_in, g.qlo, qhi, g.plane, L0);
+            plane_step<real, MODE>(I, o, g, k, k > kbeg, k > kbeg + 1, S0, S1, L1, sF, sT, check, acc);
+            if (++k > kend) break;
+        }
     }
 
     if (MODE == M_JAC) {
@@ -389,7 +491,7 @@ __device__ __forceinline__ void stencil_item(const Inst<real> &I, int seg_index,
 template <typename real, int MODE>
 __global__ void __launch_bounds__(kThreads, kMinBlocks) k_stencil(Inst<real> I, ApplyIO<real> io)
 {
-    __shared__ StencilSmem sm;
+    __shared__ StencilSmem<real, MODE> sm;
     if (MODE == M_JAC && I.ctl->done) return;   // converged earlier: queued sweeps are no-ops
     stencil_item<real, MODE>(I, blockIdx.x, blockIdx.x, gridDim.x, &io, sm);
 }
@@ -400,7 +502,7 @@ template <typename real, int MODE>
 __global__ void __launch_bounds__(kThreads, kMinBlocks)
 k_stencil_batch(const Inst<real> *insts, const BItem *items, int nitems)
 {
-    __shared__ StencilSmem sm;
+    __shared__ StencilSmem<real, MODE> sm;
     for (int i = blockIdx.x; i < nitems; i += gridDim.x) {
         const BItem it = items[i];
         const Inst<real> &I = insts[it.inst];
@@ -411,15 +513,16 @@ k_stencil_batch(const Inst<real> *insts, const BItem *items, int nitems)
 }
 
 // Batched sweeps over the unfinished members only: item i of the launch maps
-// to member active[k] with cum[k] <= i < cum[k + 1] (list rebuilt at every
-// loop check by k_active_list).  Instances given as rows of insts + row0.
-constexpr int kMaxActiveSmem = 2048;
+// to member active[k] with cum[k] <= i < cum[k + 1] (the list is rebuilt at
+// every convergence check).  The prefix counts are searched in shared memory
+// when they fit, else in global memory.
+constexpr int kMaxActiveSmem = 1024;
 
 template <typename real, int MODE>
 __global__ void __launch_bounds__(kThreads, kMinBlocks)
 k_stencil_active(const Inst<real> *insts, const int *active, const int *cum, const int *counts)
 {
-    __shared__ StencilSmem sm;
+    __shared__ StencilSmem<real, MODE> sm;
     __shared__ int scum[kMaxActiveSmem + 1];
     const int total = counts[0], na = counts[1];
     const bool in_smem = na <= kMaxActiveSmem;

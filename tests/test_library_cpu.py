@@ -89,3 +89,52 @@ def test_binding_fails_loudly_without_library(tmp_path):
             ep.load(str(tmp_path / "missing.so"))
         finally:
             ep._lib = ep._lib_backup
+
+
+def test_footprint_is_planned_on_the_host(lib):
+    """ep_footprint needs no device: the layout plan is host work.  The peak
+    adds the set-up staging (fp32 fibres, mask bytes, raw fp16 records: 21
+    bytes a voxel) to the resident bytes, and an FP64 handle holds its eight
+    state and solve fields at 8 instead of 4 bytes a voxel."""
+    import workloads as W
+    c = W.random_case(3, 19, 13, 11)
+    got = {}
+    for prec in (ep.EP_FP32, ep.EP_FP64):
+        s = ep.sim_from_case(c, use_torch=False, precision=prec)
+        got[prec] = s.footprint()
+        s.close()
+    n = c.n
+    (r32, p32), (r64, p64) = got[ep.EP_FP32], got[ep.EP_FP64]
+    assert p32 - r32 == 21 * n and p64 - r64 == 21 * n
+    assert r64 - r32 == 8 * 4 * n
+    assert r32 >= 40 * n + 4 * c.n_tissue
+    s = ep.Sim(5, 4, 3, 0.5, use_torch=False)
+    with pytest.raises(ep.EPError) as e:
+        s.footprint()
+    assert e.value.status == ep.EP_ESTATE
+    s.set_mask(np.zeros(s.n, np.uint8))
+    with pytest.raises(ep.EPError) as e:
+        s.footprint()
+    assert e.value.status == ep.EP_EINVAL
+    m = np.zeros(s.n, np.uint8)
+    m[:7] = 1
+    s.set_mask(m)   # a new mask is planned afresh
+    r_a, _ = s.footprint()
+    m[:30] = 1
+    s.set_mask(m)
+    r_b, _ = s.footprint()
+    assert r_b > r_a
+    s.close()
+
+
+def test_server_needs_a_device(lib):
+    """Without a GPU the server cannot start and says so (no host fallback)."""
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    srv = ctypes.c_void_p()
+    cfg = ep.ServerConfig()
+    cfg.max_slots, cfg.chunk_steps = 2, 1
+    assert lib.ep_server_create(ctypes.byref(cfg), ctypes.byref(srv)) == ep.EP_ECUDA
+    cfg.max_slots = 0
+    assert lib.ep_server_create(ctypes.byref(cfg), ctypes.byref(srv)) == ep.EP_EINVAL
