@@ -399,7 +399,7 @@ def run_batched(a):
             "config": {"workload": f"config3: {len(cases)} bidomain FP32 shells, n ~ U{{48..160}}, sampled "
                                    f"conductivities and stimulus sites (seed 0)",
                        "tissue_voxels_total": M, "grids": [c.nx for c in cases],
-                       "autotuned": {"zseg": info.zseg, "ctas_per_sm": info.ctas_per_sm,
+                       "autotuned": {"zseg": info.zseg,
                                      "sweeps_per_check": info.sweeps_per_check,
                                      "group_bytes": info.group_bytes, "groups": info.groups, "tune_s": tune_s},
                        "l2": "inputs larger than L2 (all instances' state)"},

@@ -236,7 +236,6 @@ typedef struct {
     long long chunk_items;       /* packed reduction chunks per launch */
     size_t device_bytes;         /* device memory of the member handles */
     size_t budget_bytes;         /* admission budget */
-    int ctas_per_sm;             /* persistent grid: CTAs per SM (tuned) */
     int sweeps_per_check;        /* sweep launches between device loop checks (tuned) */
     int zseg;                    /* z-planes per stencil work item (tuned) */
     size_t group_bytes;          /* members are swept in groups whose working sets total at most
@@ -263,17 +262,17 @@ ep_status ep_batch_step(ep_batch *b, int n_steps);
  * whether every solve converged, its step counter). */
 ep_status ep_batch_slot_stats(ep_batch *b, int slot, ep_step_stats *stats);
 
-/* Choose the persistent grid size, the z-planes per work item and the group
- * size by timing trial_sweeps sweeps of each candidate on the members'
- * current states (states are restored afterwards); the sweeps per device loop
- * check follow from the measured sweep time. */
+/* Choose the z-planes per work item and the group size by timing
+ * trial_sweeps sweeps of each candidate on the members' current states
+ * (states are restored afterwards); the sweeps per device loop check follow
+ * from the measured sweep time. */
 ep_status ep_batch_autotune(ep_batch *b, int trial_sweeps);
 
-/* Set the schedule by hand: persistent CTAs per SM (1..8), sweep launches
- * between device loop checks (1..1024), z-planes per work item (8..256) and
- * the group budget in bytes.  0 (or a negative group_bytes) keeps a value.
- * Results do not depend on the schedule. */
-ep_status ep_batch_set_schedule(ep_batch *b, int ctas_per_sm, int sweeps_per_check, int zseg, long long group_bytes);
+/* Set the schedule by hand: sweep launches between device loop checks
+ * (1..1024), z-planes per work item (8..256) and the group budget in bytes.
+ * 0 (or a negative group_bytes) keeps a value.  Results do not depend on the
+ * schedule. */
+ep_status ep_batch_set_schedule(ep_batch *b, int sweeps_per_check, int zseg, long long group_bytes);
 
 ep_status ep_batch_get_info(ep_batch *b, ep_batch_info *info);
 const char *ep_batch_last_error(const ep_batch *b);

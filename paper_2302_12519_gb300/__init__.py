@@ -71,7 +71,7 @@ class Profile(ctypes.Structure):
 class BatchInfo(ctypes.Structure):
     _fields_ = [("instances", ctypes.c_int), ("stencil_items", ctypes.c_longlong),
                 ("chunk_items", ctypes.c_longlong), ("device_bytes", ctypes.c_size_t),
-                ("budget_bytes", ctypes.c_size_t), ("ctas_per_sm", ctypes.c_int),
+                ("budget_bytes", ctypes.c_size_t),
                 ("sweeps_per_check", ctypes.c_int), ("zseg", ctypes.c_int),
                 ("group_bytes", ctypes.c_size_t), ("groups", ctypes.c_int)]
 
@@ -142,7 +142,7 @@ def load(path: str = LIB_PATH):
         "ep_batch_last_error": ([vp], ctypes.c_char_p),
         "ep_batch_destroy": ([vp], None),
         "ep_footprint": ([vp, ctypes.POINTER(sz), ctypes.POINTER(sz)], ip),
-        "ep_batch_set_schedule": ([vp, ip, ip, ip, ctypes.c_longlong], ip),
+        "ep_batch_set_schedule": ([vp, ip, ip, ctypes.c_longlong], ip),
         "ep_server_create": ([ctypes.POINTER(ServerConfig), ctypes.POINTER(vp)], ip),
         "ep_server_submit": ([vp, vp, ip, dp, ctypes.POINTER(ctypes.c_longlong)], ip),
         "ep_server_cancel": ([vp, ctypes.c_longlong], ip),
@@ -362,9 +362,9 @@ class Batch:
     def autotune(self, trial_sweeps: int = 20):
         self._check(self._L.ep_batch_autotune(self._h, int(trial_sweeps)), "ep_batch_autotune")
 
-    def set_schedule(self, ctas_per_sm: int = 0, sweeps_per_check: int = 0, zseg: int = 0, group_bytes: int = -1):
-        self._check(self._L.ep_batch_set_schedule(self._h, int(ctas_per_sm), int(sweeps_per_check), int(zseg),
-                                                  int(group_bytes)), "ep_batch_set_schedule")
+    def set_schedule(self, sweeps_per_check: int = 0, zseg: int = 0, group_bytes: int = -1):
+        self._check(self._L.ep_batch_set_schedule(self._h, int(sweeps_per_check), int(zseg), int(group_bytes)),
+                    "ep_batch_set_schedule")
 
     def info(self) -> BatchInfo:
         i = BatchInfo()

@@ -1072,14 +1072,15 @@ struct ep_batch {
     BItem *d_seg = nullptr, *d_chunk = nullptr;
     long long *d_steps_left = nullptr;
     // unfinished members of the group being solved and their item prefix counts
-    int *d_active = nullptr, *d_cum = nullptr, *d_counts = nullptr;
-    size_t cap_inst = 0, cap_seg = 0, cap_chunk = 0, cap_active = 0, cap_cum = 0;
+    ActRec *d_act = nullptr;
+    int *d_counts = nullptr;
+    size_t cap_inst = 0, cap_seg = 0, cap_chunk = 0, cap_act = 0;
     int ninst = 0;
     long long nseg_items = 0, nchunk_items = 0;
     std::vector<int> order;        // slot of each table row
     cudaGraphExec_t graph = nullptr;
     bool dirty = true;
-    int nsm = 152, ctas_per_sm = kMinBlocks, sweeps_per_check = 16, zseg = kZSeg;
+    int nsm = 152, sweeps_per_check = 16, zseg = kZSeg;
     // members are swept in groups whose working sets fit the L2 cache together; each group
     // has its own device-side convergence loop (0 = one group)
     size_t group_bytes = 0;
@@ -1189,8 +1190,7 @@ ep_status rebuild_tables(ep_batch *b)
     if ((st = grow(b, &b->d_inst, &b->cap_inst, insts.size())) != EP_OK) return st;
     if ((st = grow(b, &b->d_seg, &b->cap_seg, segs.size())) != EP_OK) return st;
     if ((st = grow(b, &b->d_chunk, &b->cap_chunk, chunks.size())) != EP_OK) return st;
-    if ((st = grow(b, &b->d_active, &b->cap_active, insts.size())) != EP_OK) return st;
-    if ((st = grow(b, &b->d_cum, &b->cap_cum, insts.size() + 1)) != EP_OK) return st;
+    if ((st = grow(b, &b->d_act, &b->cap_act, insts.size() + 1)) != EP_OK) return st;
     if (!insts.empty()) {
         CKB(cudaMemcpyAsync(b->d_inst, insts.data(), sizeof(Inst<float>) * insts.size(), cudaMemcpyHostToDevice,
                             b->stream));
@@ -1217,7 +1217,7 @@ ep_status build_batch_graph(ep_batch *b)
 {
     if (b->graph) return EP_OK;
     cudaStream_t st = b->stream;
-    const int gs = grid_of(b->nseg_items, b->nsm * b->ctas_per_sm);
+    const int gs = grid_of(b->nseg_items, 1 << 30);   // one CTA per stencil item
     const int gc = grid_of(b->nchunk_items, b->nsm * 4);
     const int ns = (int)b->nseg_items, nc = (int)b->nchunk_items;
     Inst<float> none;
@@ -1243,18 +1243,18 @@ ep_status build_batch_graph(ep_batch *b)
         for (int gi = 0; gi < ngroups; ++gi) CKB(cudaGraphConditionalHandleCreate(&hg[gi], body, 1, 0));
 
     CKB(cudaStreamBeginCaptureToGraph(st, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
-    if (b->model == EP_MONO) k_stencil_batch<float, M_PAR_MONO><<<gs, kThreads, 0, st>>>(b->d_inst, b->d_seg, ns);
-    else k_stencil_batch<float, M_PAR_BI><<<gs, kThreads, 0, st>>>(b->d_inst, b->d_seg, ns);
+    if (b->model == EP_MONO) k_stencil_batch<float, M_PAR_MONO><<<gs, kThreads, 0, st>>>(b->d_inst, b->d_seg);
+    else k_stencil_batch<float, M_PAR_BI><<<gs, kThreads, 0, st>>>(b->d_inst, b->d_seg);
     if (b->model == EP_BI) {
-        k_stencil_batch<float, M_RHS><<<gs, kThreads, 0, st>>>(b->d_inst, b->d_seg, ns);
+        k_stencil_batch<float, M_RHS><<<gs, kThreads, 0, st>>>(b->d_inst, b->d_seg);
         k_comp_mean_batch<float><<<gc, kRedThreads, 0, st>>>(b->d_inst, b->d_chunk, nc, (int)RED_B);
         k_comp_subtract_batch<float><<<gc, kRedThreads, 0, st>>>(b->d_inst, b->d_chunk, nc);
         for (int gi = 0; gi < ngroups; ++gi) {
             const ep_batch::Group &gr = b->groups[gi];
-            const int ggs = grid_of(gr.nseg, b->nsm * b->ctas_per_sm);
+            const int ggs = grid_of(gr.nseg, 1 << 30);   // sized for every member of the group
             const int gn = gr.inst1 - gr.inst0;
             const Inst<float> *gi_inst = b->d_inst + gr.inst0;
-            k_active_list<float><<<1, kActThreads, 0, st>>>(gi_inst, gn, b->d_active, b->d_cum, b->d_counts, hg[gi]);
+            k_active_list<float><<<1, kActThreads, 0, st>>>(gi_inst, gn, b->d_act, b->d_counts, hg[gi]);
             // inner loop: sweeps of the unfinished members until every solve of the group is finished
             cudaStreamCaptureStatus cs;
             cudaGraph_t cg = nullptr;
@@ -1274,10 +1274,8 @@ ep_status build_batch_graph(ep_batch *b)
             CKB(cudaStreamUpdateCaptureDependencies(st, &ni, nullptr, 1, cudaStreamSetCaptureDependencies));
             CKB(cudaStreamBeginCaptureToGraph(b->side, ibody, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
             for (int i = 0; i < b->sweeps_per_check; ++i)
-                k_stencil_active<float, M_JAC><<<ggs, kThreads, 0, b->side>>>(gi_inst, b->d_active, b->d_cum,
-                                                                             b->d_counts);
-            k_active_list<float><<<1, kActThreads, 0, b->side>>>(gi_inst, gn, b->d_active, b->d_cum, b->d_counts,
-                                                                 hg[gi]);
+                k_stencil_active<float, M_JAC><<<ggs, kThreads, 0, b->side>>>(gi_inst, b->d_act, gn);
+            k_active_list<float><<<1, kActThreads, 0, b->side>>>(gi_inst, gn, b->d_act, b->d_counts, hg[gi]);
             CKB(cudaStreamEndCapture(b->side, nullptr));
         }
         k_comp_mean_batch<float><<<gc, kRedThreads, 0, st>>>(b->d_inst, b->d_chunk, nc, (int)RED_X_FINAL);
@@ -1473,10 +1471,9 @@ ep_status ep_batch_autotune(ep_batch *b, int trial_sweeps)
     CKB(cudaEventCreate(&e0));
     CKB(cudaEventCreate(&e1));
     const int zsegs[3] = {8, 16, 32};
-    const int ctas[3] = {1, 2, 3};
     const size_t gbytes[4] = {0, (size_t)192 << 20, (size_t)96 << 20, (size_t)48 << 20};
     double best = 1e300;
-    int best_z = b->zseg, best_c = b->ctas_per_sm;
+    int best_z = b->zseg;
     size_t best_g = b->group_bytes;
     for (int zi = 0; zi < 3 && st == EP_OK; ++zi) {
         for (int r = 0; r < b->ninst && st == EP_OK; ++r) st = relayout_segments(b->slot[b->order[r]], zsegs[zi]);
@@ -1485,36 +1482,30 @@ ep_status ep_batch_autotune(ep_batch *b, int trial_sweeps)
             b->group_bytes = gbytes[gi];
             if ((st = rebuild_tables(b)) != EP_OK) break;
             if (gi > 0 && b->groups.size() == 1) continue;   // same as one group
-            for (int ci = 0; ci < 3; ++ci) {
-                if (ctas[ci] > kMinBlocks) continue;
-                // never-converging solves so that every trial sweep does its full work
-                for (int r = 0; r < b->ninst; ++r) {
-                    Ctl c = ctl0[r];
-                    c.done = 0; c.sweep = 0; c.arrive = 0; c.thresh2 = -1.0; c.bnorm2 = 1e300;
-                    CKB(cudaMemcpyAsync(b->slot[b->order[r]]->ctl, &c, sizeof(Ctl), cudaMemcpyHostToDevice, s0));
-                }
-                // one sweep of every group in turn, each group swept trial_sweeps times
-                double ms_total = 0.0;
-                for (const ep_batch::Group &gr : b->groups) {
-                    const int gs = grid_of(gr.nseg, b->nsm * ctas[ci]);
-                    k_stencil_batch<float, M_JAC><<<gs, kThreads, 0, s0>>>(b->d_inst, b->d_seg + gr.seg0,
-                                                                           (int)gr.nseg);
-                    CKB(cudaEventRecord(e0, s0));
-                    for (int i = 0; i < trial_sweeps; ++i)
-                        k_stencil_batch<float, M_JAC><<<gs, kThreads, 0, s0>>>(b->d_inst, b->d_seg + gr.seg0,
-                                                                               (int)gr.nseg);
-                    CKB(cudaEventRecord(e1, s0));
-                    CKB(cudaEventSynchronize(e1));
-                    float ms = 0.f;
-                    CKB(cudaEventElapsedTime(&ms, e0, e1));
-                    ms_total += ms;
-                }
-                if (ms_total < best) {
-                    best = ms_total;
-                    best_z = zsegs[zi];
-                    best_c = ctas[ci];
-                    best_g = gbytes[gi];
-                }
+            // never-converging solves so that every trial sweep does its full work
+            for (int r = 0; r < b->ninst; ++r) {
+                Ctl c = ctl0[r];
+                c.done = 0; c.sweep = 0; c.arrive = 0; c.thresh2 = -1.0; c.bnorm2 = 1e300;
+                CKB(cudaMemcpyAsync(b->slot[b->order[r]]->ctl, &c, sizeof(Ctl), cudaMemcpyHostToDevice, s0));
+            }
+            // one sweep of every group in turn, each group swept trial_sweeps times
+            double ms_total = 0.0;
+            for (const ep_batch::Group &gr : b->groups) {
+                const int gs = grid_of(gr.nseg, 1 << 30);
+                k_stencil_batch<float, M_JAC><<<gs, kThreads, 0, s0>>>(b->d_inst, b->d_seg + gr.seg0);
+                CKB(cudaEventRecord(e0, s0));
+                for (int i = 0; i < trial_sweeps; ++i)
+                    k_stencil_batch<float, M_JAC><<<gs, kThreads, 0, s0>>>(b->d_inst, b->d_seg + gr.seg0);
+                CKB(cudaEventRecord(e1, s0));
+                CKB(cudaEventSynchronize(e1));
+                float ms = 0.f;
+                CKB(cudaEventElapsedTime(&ms, e0, e1));
+                ms_total += ms;
+            }
+            if (ms_total < best) {
+                best = ms_total;
+                best_z = zsegs[zi];
+                best_g = gbytes[gi];
             }
         }
     }
@@ -1530,24 +1521,21 @@ ep_status ep_batch_autotune(ep_batch *b, int trial_sweeps)
     release();
     if (st != EP_OK) return st;
     b->zseg = best_z;
-    b->ctas_per_sm = best_c;
     b->group_bytes = best_g;
-    // sweeps between device loop checks: about 100 us of sweeps, 4..64
+    // sweeps between device loop checks: about 200 us of sweeps, 4..64 (a check costs a few us)
     const double per_sweep_us = 1e3 * best / trial_sweeps;
-    b->sweeps_per_check = (int)std::min(64.0, std::max(4.0, std::ceil(100.0 / std::max(per_sweep_us, 1e-3))));
+    b->sweeps_per_check = (int)std::min(64.0, std::max(4.0, std::ceil(200.0 / std::max(per_sweep_us, 1e-3))));
     for (int r = 0; r < b->ninst && st == EP_OK; ++r) st = relayout_segments(b->slot[b->order[r]], b->zseg);
     if (st != EP_OK) return st;
     return rebuild_tables(b);
 }
 
-ep_status ep_batch_set_schedule(ep_batch *b, int ctas_per_sm, int sweeps_per_check, int zseg, long long group_bytes)
+ep_status ep_batch_set_schedule(ep_batch *b, int sweeps_per_check, int zseg, long long group_bytes)
 {
     if (!b) return EP_EINVAL;
-    if (ctas_per_sm < 0 || ctas_per_sm > 8) return bfail(b, EP_EINVAL, "ctas_per_sm must be in [1, 8] (0 keeps)");
     if (sweeps_per_check < 0 || sweeps_per_check > 1024)
         return bfail(b, EP_EINVAL, "sweeps_per_check must be in [1, 1024] (0 keeps)");
     if (zseg != 0 && (zseg < kZSegMin || zseg > 256)) return bfail(b, EP_EINVAL, "zseg must be in [8, 256] (0 keeps)");
-    if (ctas_per_sm) b->ctas_per_sm = ctas_per_sm;
     if (sweeps_per_check) b->sweeps_per_check = sweeps_per_check;
     if (group_bytes >= 0) b->group_bytes = (size_t)group_bytes;
     if (zseg && zseg != b->zseg) {
@@ -1575,7 +1563,6 @@ ep_status ep_batch_get_info(ep_batch *b, ep_batch_info *info)
         if (s) used += s->dev_bytes;
     info->device_bytes = used;
     info->budget_bytes = b->budget;
-    info->ctas_per_sm = b->ctas_per_sm;
     info->sweeps_per_check = b->sweeps_per_check;
     info->zseg = b->zseg;
     info->group_bytes = b->group_bytes;
@@ -1593,8 +1580,7 @@ void ep_batch_destroy(ep_batch *b)
     if (b->d_inst) cudaFree(b->d_inst);
     if (b->d_seg) cudaFree(b->d_seg);
     if (b->d_chunk) cudaFree(b->d_chunk);
-    if (b->d_active) cudaFree(b->d_active);
-    if (b->d_cum) cudaFree(b->d_cum);
+    if (b->d_act) cudaFree(b->d_act);
     if (b->d_counts) cudaFree(b->d_counts);
     if (b->d_steps_left) cudaFree(b->d_steps_left);
     if (b->side) cudaStreamDestroy(b->side);
@@ -1622,7 +1608,7 @@ struct SrvReq {
     long long id = 0;
     ep_sim *sim = nullptr;
     int n_steps = 0, steps_done = 0, slot = -1, model = 0;
-    int status = EP_OK;
+    int status = EP_OK, plan_status = EP_OK;
     bool cancel = false, busy = false, planned = false;
     double release = 0, t_admit = -1, t_done = -1;
     long long iters_base = 0, total_iters = 0;
@@ -1635,9 +1621,9 @@ struct ep_server {
     ep_server_config cfg{};
     int device = 0;
     ep_batch *batch[2] = {nullptr, nullptr};   // by model
-    std::thread thr;
+    std::thread thr, planner;
     std::mutex mu;
-    std::condition_variable cv_work, cv_done;
+    std::condition_variable cv_work, cv_done, cv_plan;
     bool stop = false;
     bool blocked_on_results = false;   // nothing runs and the next request waits for memory held by results
     std::string err;
@@ -1705,25 +1691,17 @@ void serve_loop(ep_server *v)
         while (!v->stop && !v->queue.empty() && v->queue.front()->release <= v->now() &&
                (int)v->active.size() < v->cfg.max_slots) {
             SrvReq *r = v->queue.front();
-            if (!r->planned) {   // host layout and exact footprint (no device work), outside the lock
-                r->busy = true;
-                lk.unlock();
-                const ep_status ps = plan_layout(r->sim);
-                lk.lock();
-                r->busy = false;
-                r->planned = true;
-                r->peak = r->sim->ready ? r->sim->dev_bytes : r->sim->fp_peak;
-                if (ps != EP_OK) {
-                    srv_erase(v->queue, r);
-                    srv_finish(v, r, ps);
-                    continue;
-                }
-                if (budget && r->peak > budget) {
-                    srv_erase(v->queue, r);
-                    ++v->st.rejected;
-                    srv_finish(v, r, EP_EREJECTED);
-                    continue;
-                }
+            if (!r->planned) break;   // the planner thread is on it; chunks go on meanwhile
+            if (r->plan_status != EP_OK) {
+                srv_erase(v->queue, r);
+                srv_finish(v, r, r->plan_status);
+                continue;
+            }
+            if (budget && r->peak > budget) {
+                srv_erase(v->queue, r);
+                ++v->st.rejected;
+                srv_finish(v, r, EP_EREJECTED);
+                continue;
             }
             if (r->cancel) {
                 srv_erase(v->queue, r);
@@ -1833,6 +1811,37 @@ void serve_loop(ep_server *v)
     }
 }
 
+// Host planning of released requests (mask analysis and exact footprint),
+// ahead of admission and while the GPU runs chunks.
+void plan_loop(ep_server *v)
+{
+    std::unique_lock<std::mutex> lk(v->mu);
+    while (!v->stop) {
+        SrvReq *r = nullptr;
+        double next = -1.0;   // release time of the next unplanned request, if not yet released
+        for (SrvReq *q : v->queue) {
+            if (q->planned || q->busy) continue;
+            if (q->release <= v->now()) r = q;
+            else next = q->release;
+            break;
+        }
+        if (!r) {
+            if (next >= 0.0) v->cv_plan.wait_for(lk, std::chrono::duration<double>(std::min(next - v->now(), 3600.0)));
+            else v->cv_plan.wait(lk);
+            continue;
+        }
+        r->busy = true;
+        lk.unlock();
+        const ep_status ps = plan_layout(r->sim);
+        lk.lock();
+        r->busy = false;
+        r->planned = true;
+        r->plan_status = ps;
+        r->peak = r->sim->ready ? r->sim->dev_bytes : r->sim->fp_peak;
+        v->cv_work.notify_all();
+    }
+}
+
 }  // namespace
 
 extern "C" {
@@ -1852,7 +1861,7 @@ ep_status ep_server_create(const ep_server_config *cfg, ep_server **out)
     ep_status st = e == cudaSuccess ? EP_OK : EP_ECUDA;
     for (int m = 0; m < 2 && st == EP_OK; ++m) {
         st = ep_batch_create(cfg->max_slots, 0, cfg->cuda_stream, &v->batch[m]);
-        if (st == EP_OK && cfg->sweeps_per_check) st = ep_batch_set_schedule(v->batch[m], 0, cfg->sweeps_per_check, 0, -1);
+        if (st == EP_OK && cfg->sweeps_per_check) st = ep_batch_set_schedule(v->batch[m], cfg->sweeps_per_check, 0, -1);
     }
     if (st != EP_OK) {
         cudaGetLastError();
@@ -1861,8 +1870,15 @@ ep_status ep_server_create(const ep_server_config *cfg, ep_server **out)
         return st;
     }
     try {
+        v->planner = std::thread(plan_loop, v);
         v->thr = std::thread(serve_loop, v);
     } catch (...) {
+        {
+            std::lock_guard<std::mutex> lk(v->mu);
+            v->stop = true;
+        }
+        v->cv_plan.notify_all();
+        if (v->planner.joinable()) v->planner.join();
         for (ep_batch *b : v->batch) ep_batch_destroy(b);
         delete v;
         return EP_ENOMEM;
@@ -1895,6 +1911,7 @@ ep_status ep_server_submit(ep_server *v, ep_sim *sim, int n_steps, double releas
     ++v->st.submitted;
     *id = r->id;
     v->cv_work.notify_all();
+    v->cv_plan.notify_all();
     return EP_OK;
 }
 
@@ -2001,7 +2018,9 @@ void ep_server_destroy(ep_server *v)
     }
     v->cv_work.notify_all();
     v->cv_done.notify_all();
+    v->cv_plan.notify_all();
     if (v->thr.joinable()) v->thr.join();
+    if (v->planner.joinable()) v->planner.join();
     for (SrvReq *r : v->active) {
         ep_batch_remove(v->batch[r->model], r->slot);
         ep_destroy(r->sim);

@@ -321,15 +321,17 @@ __global__ void k_fill(real *p, long long n, real v)
         p[i] = v;
 }
 
-// Members of rows [0, n) whose solve is unfinished, in row order, with the
-// exclusive prefix counts of their stencil items (cum[n_active] = total);
-// counts = {total items, n_active}.  Sets the condition of the device-side
-// convergence loop (any member still active).  One CTA of kActThreads.
+// Members of rows [0, n) whose solve is unfinished, in row order: act[k] =
+// {items before member k, its row, its control block}; entries n_active ..
+// n hold {total items, -1, null}, so the rest of the list never matches an
+// item; counts = {total items, n_active}.  Sets the condition of the
+// device-side convergence loop (any member still active).  One CTA of
+// kActThreads.
 constexpr int kActThreads = 1024;
 
 template <typename real>
 __global__ void __launch_bounds__(kActThreads)
-k_active_list(const Inst<real> *insts, int n, int *active, int *cum, int *counts, cudaGraphConditionalHandle h)
+k_active_list(const Inst<real> *insts, int n, ActRec *act, int *counts, cudaGraphConditionalHandle h)
 {
     __shared__ int swa[32], swc[32];
     __shared__ int base_a, base_c;
@@ -339,7 +341,8 @@ k_active_list(const Inst<real> *insts, int n, int *active, int *cum, int *counts
     for (int i0 = 0; i0 < n; i0 += blockDim.x) {
         const int i = i0 + threadIdx.x;
         int a = 0, c = 0;
-        if (i < n && !*(volatile int *)&insts[i].ctl->done) {
+        Ctl *ctl = i < n ? insts[i].ctl : nullptr;
+        if (i < n && !*(volatile int *)&ctl->done) {
             a = 1;
             c = insts[i].nseg;
         }
@@ -373,8 +376,7 @@ k_active_list(const Inst<real> *insts, int n, int *active, int *cum, int *counts
         __syncthreads();
         if (a) {
             const int pa = base_a + (wid ? swa[wid - 1] : 0) + sa - a;
-            active[pa] = i;
-            cum[pa] = base_c + (wid ? swc[wid - 1] : 0) + sc - c;
+            act[pa] = ActRec{base_c + (wid ? swc[wid - 1] : 0) + sc - c, i, ctl};
         }
         __syncthreads();
         if (threadIdx.x == 0) {
@@ -384,11 +386,12 @@ k_active_list(const Inst<real> *insts, int n, int *active, int *cum, int *counts
         __syncthreads();
     }
     if (threadIdx.x == 0) {
-        cum[base_a] = base_c;
         counts[0] = base_c;
         counts[1] = base_a;
         if (h) cudaGraphSetConditional(h, base_a > 0 ? 1u : 0u);
     }
+    __syncthreads();
+    for (int k = base_a + threadIdx.x; k <= n; k += blockDim.x) act[k] = ActRec{base_c, -1, nullptr};
 }
 
 // Outer loop of a multi-step graph: counts down the steps left in the chunk.

@@ -151,6 +151,13 @@ __device__ __forceinline__ bool arrive_last(Ctl *ctl, int nitems, int *sflag)
     return last;
 }
 
+// Entry of the list of unfinished members of a batched solve: prefix count of
+// the items before it, its descriptor row and its control block.
+struct ActRec {
+    int cum, inst;
+    Ctl *ctl;
+};
+
 // Work item of a batched launch: instance, item index within the instance,
 // and the instance's item count.
 struct BItem {

@@ -496,53 +496,63 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) k_stencil(Inst<real> I, 
     stencil_item<real, MODE>(I, blockIdx.x, blockIdx.x, gridDim.x, &io, sm);
 }
 
-// Batched: one persistent launch walks the packed (instance, segment) list of
-// all instances; items of instances whose solve is finished are skipped.
-template <typename real, int MODE>
-__global__ void __launch_bounds__(kThreads, kMinBlocks)
-k_stencil_batch(const Inst<real> *insts, const BItem *items, int nitems)
+// Copies a member's descriptor into shared memory (read there, like the
+// by-value parameter of the single-instance kernel, instead of from global
+// memory through a pointer the compiler must keep live).
+template <typename real>
+__device__ __forceinline__ const Inst<real> &stage_inst(const Inst<real> *src, Inst<real> &dst)
 {
-    __shared__ StencilSmem<real, MODE> sm;
-    for (int i = blockIdx.x; i < nitems; i += gridDim.x) {
-        const BItem it = items[i];
-        const Inst<real> &I = insts[it.inst];
-        if (MODE == M_JAC && *(volatile int *)&I.ctl->done) continue;
-        stencil_item<real, MODE>(I, it.item, it.item, it.nitems, nullptr, sm);
-        __syncthreads();
-    }
+    static_assert(sizeof(Inst<real>) % 8 == 0, "descriptor copied in 8-byte words");
+    const unsigned long long *a = reinterpret_cast<const unsigned long long *>(src);
+    unsigned long long *d = reinterpret_cast<unsigned long long *>(&dst);
+    for (int i = threadIdx.x; i < (int)(sizeof(Inst<real>) / 8); i += blockDim.x) d[i] = a[i];
+    __syncthreads();
+    return dst;
 }
 
-// Batched sweeps over the unfinished members only: item i of the launch maps
-// to member active[k] with cum[k] <= i < cum[k + 1] (the list is rebuilt at
-// every convergence check).  The prefix counts are searched in shared memory
-// when they fit, else in global memory.
-constexpr int kMaxActiveSmem = 1024;
-
+// Batched: one CTA per entry of the packed (instance, item) list of all
+// instances, so the hardware balances uneven items as in the single-instance
+// launch; items of instances whose solve is finished return at once.
 template <typename real, int MODE>
 __global__ void __launch_bounds__(kThreads, kMinBlocks)
-k_stencil_active(const Inst<real> *insts, const int *active, const int *cum, const int *counts)
+k_stencil_batch(const Inst<real> *insts, const BItem *items)
 {
     __shared__ StencilSmem<real, MODE> sm;
-    __shared__ int scum[kMaxActiveSmem + 1];
-    const int total = counts[0], na = counts[1];
-    const bool in_smem = na <= kMaxActiveSmem;
-    if (in_smem)
-        for (int i = threadIdx.x; i <= na; i += blockDim.x) scum[i] = cum[i];
+    __shared__ Inst<real> sI;
+    const BItem it = items[blockIdx.x];
+    if (MODE == M_JAC && *(volatile int *)&insts[it.inst].ctl->done) return;
+    const Inst<real> &I = stage_inst(insts + it.inst, sI);
+    stencil_item<real, MODE>(I, it.item, it.item, it.nitems, nullptr, sm);
+}
+
+// Batched sweeps over the unfinished members only (the list is rebuilt at
+// every convergence check): CTA i takes item i - act[k].cum of member k,
+// act[k].cum <= i < act[k + 1].cum, found by one parallel lookup over the
+// entries of the group's n members (the list has n + 1 entries); a CTA that
+// matches none (i past the total) returns.  The
+// descriptor and the control block are then fetched together, so a CTA waits
+// on three dependent loads before its data (the single-instance kernel, two).
+template <typename real, int MODE>
+__global__ void __launch_bounds__(kThreads, kMinBlocks)
+k_stencil_active(const Inst<real> *insts, const ActRec *act, int n)
+{
+    __shared__ StencilSmem<real, MODE> sm;
+    __shared__ Inst<real> sI;
+    __shared__ int sk;
+    const int i = blockIdx.x;
+    if (threadIdx.x == 0) sk = -1;
     __syncthreads();
-    const int *c = in_smem ? scum : cum;
-    for (int i = blockIdx.x; i < total; i += gridDim.x) {
-        int lo = 0, hi = na;   // largest k with c[k] <= i
-        while (hi - lo > 1) {
-            const int mid = (lo + hi) >> 1;
-            if (c[mid] <= i) lo = mid;
-            else hi = mid;
-        }
-        const Inst<real> &I = insts[active[lo]];
-        if (MODE == M_JAC && *(volatile int *)&I.ctl->done) continue;   // converged at a check in this loop pass
-        const int item = i - c[lo];
-        stencil_item<real, MODE>(I, item, item, I.nseg, nullptr, sm);
-        __syncthreads();
+    for (int k = threadIdx.x; k < n; k += blockDim.x) {
+        const ActRec a = act[k];
+        if (a.inst >= 0 && a.cum <= i && i < act[k + 1].cum) sk = k;   // at most one entry matches
     }
+    __syncthreads();
+    if (sk < 0) return;
+    const ActRec r = act[sk];
+    if (MODE == M_JAC && *(volatile int *)&r.ctl->done) return;   // converged at a check in this loop pass
+    const Inst<real> &I = stage_inst(insts + r.inst, sI);
+    const int item = i - r.cum;
+    stencil_item<real, MODE>(I, item, item, I.nseg, nullptr, sm);
 }
 
 }  // namespace gbep

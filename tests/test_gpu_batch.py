@@ -91,7 +91,7 @@ def test_autotune_keeps_results_within_tolerance():
         b.add(s)
     b.autotune(5)
     info = b.info()
-    assert info.zseg in (8, 16, 32) and 1 <= info.ctas_per_sm <= 3 and 4 <= info.sweeps_per_check <= 64
+    assert info.zseg in (8, 16, 32) and 4 <= info.sweeps_per_check <= 64
     b.step(3, allow_noconv=True)
     for s_alone, s_mix in zip(alone, mixed):
         # a different segment length changes only the order of the FP32 residual partial sums
