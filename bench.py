@@ -31,6 +31,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 BYTES_PER_SWEEP_VOXEL = 19      # x 4 + b 4 + x' 4 + fibre 6 + mask 1 (algorithmic, per tissue voxel)
+BYTES_PER_MONO_VOXEL = 23       # fused monodomain step: v, w read 8 + written 8 + fibre 6 + mask 1
 REF_SAMPLE_SWEEPS = (8, 64)     # oracle sweeps timed per sample step (two caps -> per-sweep cost)
 DEFAULT_REF_SWEEPS_PER_STEP = 4000  # elliptic sweeps per step assumed by the reference arm when no GPU figure exists
 
@@ -41,7 +42,8 @@ def _args():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["config2", "config1", "config3", "config4"], default="config2")
+    ap.add_argument("--workload", choices=["config2", "config1", "config3", "config4", "slab512"], default="config2")
+    ap.add_argument("--model", choices=["mono", "bi"], default="mono", help="slab512: model")
     ap.add_argument("--instances", type=int, default=64, help="config3: number of instances")
     ap.add_argument("--requests", type=int, default=16, help="config4: number of requests")
     ap.add_argument("--req-steps", type=int, default=4, help="config4: time steps per request")
@@ -55,8 +57,14 @@ def _args():
     return ap.parse_args()
 
 
-def _workload(name):
+def _workload(name, model="mono"):
     import workloads as W
+    if name == "slab512":
+        bi = model == "bi"
+        c = W.slab(512, W.BI if bi else W.MONO, unequal=bi)
+        desc = (f"slab512: {'bidomain (sigma_eT 0.10)' if bi else 'monodomain'} FP32, dense all-tissue 512^3 slab, "
+                f"fibres rotating -60..+60 deg through z, dx 0.5 mm")
+        return c, desc
     if name == "config1":
         c = W.config1()
         desc = "config1: bidomain FP32, 128^3 ellipsoidal shell (55,40,40) wall 10, 9.5% tissue"
@@ -177,26 +185,38 @@ def oracle_sample(case, sweeps_per_step, n_samples=1):
             "sample_s": float(sum(fixed) + sum(per) * sum(REF_SAMPLE_SWEEPS))}
 
 
+def _oracle_case(a, case):
+    """The case the oracle is timed on: the workload itself, except for the
+    512^3 slab, whose bounded sample is a 256^3 slab of the same construction
+    (the rate is per tissue voxel)."""
+    if a.workload == "slab512":
+        import workloads as W
+        return W.slab(256, case.model, unequal=case.model == 1)
+    return case
+
+
 def run_reference(a):
     world, rank, local = _dist()
     if rank != 0:
         return
-    case, desc = _workload(a.workload)
+    case, desc = _workload(a.workload, a.model)
     M = case.n_tissue
     k_ref = a.ref_sweeps_per_step or DEFAULT_REF_SWEEPS_PER_STEP
     times = []
     info = None
+    oc = _oracle_case(a, case)
     for i in range(a.warmup + a.steps):
-        info = oracle_sample(case, k_ref)
+        info = oracle_sample(oc, k_ref)
         if i >= a.warmup:
             times.append(info["step_s"])
     tot = sum(times)
-    value = M * a.steps / tot
-    sample = (f"per step: one oracle step of the workload with the Jacobi solve capped at "
+    value = oc.n_tissue * a.steps / tot   # tissue voxel-steps/s of the sampled case
+    what = "a 256^3 slab of the same construction" if oc is not case else "the workload"
+    sample = (f"per step: one oracle step of {what} with the Jacobi solve capped at "
               f"{REF_SAMPLE_SWEEPS[0]} and {REF_SAMPLE_SWEEPS[1]} sweeps (fixed {info['fixed_s']:.2f} s, "
               f"{info['per_sweep_s']:.3f} s/sweep), extrapolated to {k_ref:.0f} sweeps per step")
     line = {"impl": "reference", "metric": "voxel-steps/sec", "value": value, "unit": "tissue voxel-steps/s",
-            "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1e3 * tot / a.steps,
+            "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1e3 * M / value,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": desc, "tissue_voxels": M},
             "cpu_baseline": {"value": value, "unit": "tissue voxel-steps/s", "cores": info["cores"],
@@ -218,8 +238,9 @@ def run_ours(a):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     epbuild.build()
-    case, desc = _workload(a.workload)
+    case, desc = _workload(a.workload, a.model)
     M = case.n_tissue
+    mono = case.model == 0
     stream = torch.cuda.Stream()
     # run on a torch stream so torch events bracket the library's kernels
     sim = ep.Sim(case.nx, case.ny, case.nz, case.dx, case.model, case.precision, use_torch=True,
@@ -272,16 +293,23 @@ def run_ours(a):
     peaks = _peaks()
     peak = float(peaks["hbm_gbs"]) if peaks else 6800.0
     peak_src = "of measured" if peaks else "of fallback"
-    sweep_s = prof.sweep_ms / 1e3
-    per_sweep_s = sweep_s / max(prof.sweeps, 1)
-    alg_bytes = BYTES_PER_SWEEP_VOXEL * M
-    achieved = alg_bytes / per_sweep_s / 1e9 if prof.sweeps else 0.0
-    tpv = _traffic_record(a.workload)
-    roofline = {"bound": "hbm", "kernel": "k_stencil<float,M_JAC> (damped Jacobi sweep)",
+    if mono:
+        # the fused reaction + diffusion launch is the step (plus a one-thread step-counter kernel)
+        launch_s = prof.other_ms / 1e3 / max(prof.steps, 1)
+        alg_bytes = BYTES_PER_MONO_VOXEL * M
+        kname, share = "k_stencil<float,M_PAR_MONO> (fused reaction + diffusion)", prof.other_ms / 1e3 / total_s
+    else:
+        sweep_s = prof.sweep_ms / 1e3
+        launch_s = sweep_s / max(prof.sweeps, 1)
+        alg_bytes = BYTES_PER_SWEEP_VOXEL * M
+        kname, share = "k_stencil<float,M_JAC> (damped Jacobi sweep)", sweep_s / total_s
+    achieved = alg_bytes / launch_s / 1e9 if launch_s > 0 else 0.0
+    tpv = _traffic_record(a.workload if not mono else a.workload + "_mono")
+    roofline = {"bound": "hbm", "kernel": kname,
                 "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": (tpv * M) if tpv is not None else None,
-                "algorithmic_bytes_per_launch": alg_bytes, "avg_launch_us": per_sweep_s * 1e6,
-                "sweep_share_of_step": sweep_s / total_s if world == 1 else None, "peak_source": peak_src}
+                "algorithmic_bytes_per_launch": alg_bytes, "avg_launch_us": launch_s * 1e6,
+                "kernel_share_of_step": share if world == 1 else None, "peak_source": peak_src}
 
     # end to end through the C ABI with host buffers: the same steps as the timed
     # window, each step's state in from pinned host memory and its new state out
@@ -301,9 +329,11 @@ def run_ours(a):
     cpu = None
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
         k = float(np.mean(iters)) if iters else DEFAULT_REF_SWEEPS_PER_STEP
-        info = oracle_sample(case, k)
-        cpu = {"value": M / info["step_s"], "unit": "tissue voxel-steps/s", "cores": info["cores"], "kind": "oracle",
-               "sample": (f"one oracle step of this workload with the Jacobi solve capped at {REF_SAMPLE_SWEEPS[0]} "
+        oc = _oracle_case(a, case)
+        info = oracle_sample(oc, k)
+        cpu = {"value": oc.n_tissue / info["step_s"], "unit": "tissue voxel-steps/s", "cores": info["cores"],
+               "kind": "oracle",
+               "sample": (f"one oracle step of {'a 256^3 slab of the same construction (1/8 of the workload)' if oc is not case else 'this workload'} with the Jacobi solve capped at {REF_SAMPLE_SWEEPS[0]} "
                           f"and {REF_SAMPLE_SWEEPS[1]} sweeps (fixed {info['fixed_s']:.2f} s + "
                           f"{info['per_sweep_s']:.3f} s/sweep, {info['sample_s']:.1f} s of CPU work), extrapolated "
                           f"to the {k:.0f} sweeps per step of the timed GPU steps")}

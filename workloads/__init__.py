@@ -191,6 +191,22 @@ def config0() -> Case:
                 model=MONO, precision=FP64, steps=1000)
 
 
+def slab(n: int = 512, model: int = MONO, unequal: bool = False) -> Case:
+    """Dense all-tissue n^3 slab, the roofline workload whose working set is far
+    above L2: fibres in the x-y plane rotating from -60 to +60 degrees through
+    z (the config 0 rule), dx 0.5 mm, dt 0.05 ms, corner stimulus 8^3, FP32.
+    ``unequal`` sets sigma_eT = 0.10 so that the bidomain solve is not the
+    trivial equal-anisotropy one."""
+    k = np.arange(n, dtype=np.float64)
+    theta = np.deg2rad(-60.0 + 120.0 * k / max(n - 1, 1))
+    fz = np.stack([np.cos(theta), np.sin(theta), np.zeros(n)], axis=-1)   # (n, 3), per z plane
+    fz = _fp16_exact(fz).astype(np.float32)
+    fib = np.broadcast_to(fz[:, None, None, :], (n, n, n, 3))
+    p = Params(dt=0.05, sig_iL=0.20, sig_iT=0.05, sig_eL=0.20, sig_eT=0.10 if unequal else 0.05)
+    return Case(f"slab{n}_{'bi' if model == BI else 'mono'}", n, n, n, 0.5, np.ones((n, n, n), np.uint8), fib, p,
+                [Stimulus((0, 0, 0), (8, 8, 8), 0.0, 1.0, 0.5)], model=model, precision=FP32, steps=100)
+
+
 def shell_case(n: int = 128, semi=(40.0, 40.0, 55.0), wall: float = 10.0,
                sig=(0.20, 0.05, 0.20, 0.05), dt: float = 0.05, steps: int = 5000,
                stim_size: int = 4, name: Optional[str] = None) -> Case:
