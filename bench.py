@@ -42,8 +42,9 @@ def _args():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["config2", "config1", "config3", "config4", "slab512"], default="config2")
-    ap.add_argument("--model", choices=["mono", "bi"], default="mono", help="slab512: model")
+    ap.add_argument("--workload", choices=["config2", "config1", "config3", "config4", "slab"], default="config2")
+    ap.add_argument("--model", choices=["mono", "bi"], default="mono", help="slab: model")
+    ap.add_argument("--slab-n", type=int, default=512, help="slab: voxels per side")
     ap.add_argument("--instances", type=int, default=64, help="config3: number of instances")
     ap.add_argument("--requests", type=int, default=16, help="config4: number of requests")
     ap.add_argument("--req-steps", type=int, default=4, help="config4: time steps per request")
@@ -57,13 +58,13 @@ def _args():
     return ap.parse_args()
 
 
-def _workload(name, model="mono"):
+def _workload(name, model="mono", slab_n=512):
     import workloads as W
-    if name == "slab512":
+    if name == "slab":
         bi = model == "bi"
-        c = W.slab(512, W.BI if bi else W.MONO, unequal=bi)
-        desc = (f"slab512: {'bidomain (sigma_eT 0.10)' if bi else 'monodomain'} FP32, dense all-tissue 512^3 slab, "
-                f"fibres rotating -60..+60 deg through z, dx 0.5 mm")
+        c = W.slab(slab_n, W.BI if bi else W.MONO, unequal=bi)
+        desc = (f"slab{slab_n}: {'bidomain (sigma_eT 0.10)' if bi else 'monodomain'} FP32, dense all-tissue "
+                f"{slab_n}^3 slab, fibres rotating -60..+60 deg through z, dx 0.5 mm")
         return c, desc
     if name == "config1":
         c = W.config1()
@@ -88,10 +89,11 @@ def _kernel_hash():
     return h.hexdigest()[:16]
 
 
-def _traffic_record(workload):
-    """Per-tissue-voxel DRAM traffic of one sweep launch from the committed ncu
-    summary, if it was taken on the current kernel source."""
-    path = os.path.join(ROOT, "profiles", f"jacobi_sweep_{workload}.md")
+def _traffic_record(stem):
+    """Per-tissue-voxel DRAM traffic of one launch of the dominant kernel from
+    the committed ncu summary profiles/<stem>.md, if it was taken on the
+    current kernel source."""
+    path = os.path.join(ROOT, "profiles", f"{stem}.md")
     try:
         rec = {}
         for line in open(path):
@@ -187,9 +189,9 @@ def oracle_sample(case, sweeps_per_step, n_samples=1):
 
 def _oracle_case(a, case):
     """The case the oracle is timed on: the workload itself, except for the
-    512^3 slab, whose bounded sample is a 256^3 slab of the same construction
-    (the rate is per tissue voxel)."""
-    if a.workload == "slab512":
+    slab above 256^3, whose bounded sample is a 256^3 slab of the same
+    construction (the rate is per tissue voxel)."""
+    if a.workload == "slab" and a.slab_n > 256:
         import workloads as W
         return W.slab(256, case.model, unequal=case.model == 1)
     return case
@@ -199,7 +201,7 @@ def run_reference(a):
     world, rank, local = _dist()
     if rank != 0:
         return
-    case, desc = _workload(a.workload, a.model)
+    case, desc = _workload(a.workload, a.model, a.slab_n)
     M = case.n_tissue
     k_ref = a.ref_sweeps_per_step or DEFAULT_REF_SWEEPS_PER_STEP
     times = []
@@ -238,7 +240,7 @@ def run_ours(a):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     epbuild.build()
-    case, desc = _workload(a.workload, a.model)
+    case, desc = _workload(a.workload, a.model, a.slab_n)
     M = case.n_tissue
     mono = case.model == 0
     stream = torch.cuda.Stream()
@@ -304,7 +306,9 @@ def run_ours(a):
         alg_bytes = BYTES_PER_SWEEP_VOXEL * M
         kname, share = "k_stencil<float,M_JAC> (damped Jacobi sweep)", sweep_s / total_s
     achieved = alg_bytes / launch_s / 1e9 if launch_s > 0 else 0.0
-    tpv = _traffic_record(a.workload if not mono else a.workload + "_mono")
+    stem = (f"fused_step_slab{a.slab_n}_mono" if mono else
+            f"jacobi_sweep_slab{a.slab_n}_bi" if a.workload == "slab" else f"jacobi_sweep_{a.workload}")
+    tpv = _traffic_record(stem)
     roofline = {"bound": "hbm", "kernel": kname,
                 "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": (tpv * M) if tpv is not None else None,
@@ -333,7 +337,7 @@ def run_ours(a):
         info = oracle_sample(oc, k)
         cpu = {"value": oc.n_tissue / info["step_s"], "unit": "tissue voxel-steps/s", "cores": info["cores"],
                "kind": "oracle",
-               "sample": (f"one oracle step of {'a 256^3 slab of the same construction (1/8 of the workload)' if oc is not case else 'this workload'} with the Jacobi solve capped at {REF_SAMPLE_SWEEPS[0]} "
+               "sample": (f"one oracle step of {'a 256^3 slab of the same construction' if oc is not case else 'this workload'} with the Jacobi solve capped at {REF_SAMPLE_SWEEPS[0]} "
                           f"and {REF_SAMPLE_SWEEPS[1]} sweeps (fixed {info['fixed_s']:.2f} s + "
                           f"{info['per_sweep_s']:.3f} s/sweep, {info['sample_s']:.1f} s of CPU work), extrapolated "
                           f"to the {k:.0f} sweeps per step of the timed GPU steps")}
@@ -345,7 +349,7 @@ def run_ours(a):
                 "data": "synthetic",
                 "config": {"workload": desc, "grid": [case.nx, case.ny, case.nz], "tissue_voxels": M,
                            "dt_ms": case.params.dt, "rel_tol": case.params.rel_tol,
-                           "window": f"steps {a.warmup}..{a.warmup + a.steps - 1} from rest, apex stimulus at t=0",
+                           "window": f"steps {a.warmup}..{a.warmup + a.steps - 1} from rest, stimulus at t=0",
                            "sweeps_per_step": iters, "step_status": statuses,
                            "l2": "flushed between timed steps (256 MB write)",
                            "parallelism": f"replicas x{world}"},

@@ -241,6 +241,9 @@ typedef struct {
     size_t group_bytes;          /* members are swept in groups whose working sets total at most
                                     this many bytes, so a group's sweeps stay in L2 (0 = one group; tuned) */
     int groups;                  /* number of such groups */
+    int solo_members;            /* members with at least half a wave of stencil items (3 CTAs per SM x
+                                    SMs / 2, 228 on 152 SMs): their Jacobi sweeps run as their own
+                                    launches, concurrent with the packed launch of the others */
 } ep_batch_info;
 
 /* Create a batch of at most max_instances handles whose device memory may

@@ -73,7 +73,7 @@ class BatchInfo(ctypes.Structure):
                 ("chunk_items", ctypes.c_longlong), ("device_bytes", ctypes.c_size_t),
                 ("budget_bytes", ctypes.c_size_t),
                 ("sweeps_per_check", ctypes.c_int), ("zseg", ctypes.c_int),
-                ("group_bytes", ctypes.c_size_t), ("groups", ctypes.c_int)]
+                ("group_bytes", ctypes.c_size_t), ("groups", ctypes.c_int), ("solo_members", ctypes.c_int)]
 
 
 class ServerConfig(ctypes.Structure):

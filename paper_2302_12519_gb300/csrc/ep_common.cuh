@@ -31,10 +31,10 @@ constexpr int kChunk = 2048;                // tissue voxels per reduction chunk
 enum Mode { M_APPLY = 0, M_RHS = 1, M_PAR_MONO = 2, M_PAR_BI = 3, M_JAC = 4 };
 enum Model { MODEL_MONO = 0, MODEL_BI = 1 };
 
-// One stencil work item: voxel columns x in [30 bx, 30 bx + 30), rows
+// One stencil work item: voxel columns x in [x0, x0 + 30), rows
 // y in [kTileY by, kTileY by + kTileY), output planes [k0, k1).
 struct Seg {
-    int bx, by, k0, k1;
+    int x0, by, k0, k1;
 };
 
 struct StimBox {
@@ -101,6 +101,9 @@ struct Inst {
 
 __device__ __forceinline__ float h2f(unsigned short b) { return __half2float(__ushort_as_half(b)); }
 __device__ __forceinline__ bool rec_tissue(const ushort4 &r) { return (r.w & 0x8000u) == 0; }
+// The same record as two packed 32-bit words: (fx | fy << 16, fz | w << 16).
+__device__ __forceinline__ bool rec_tissue(const uint2 &r) { return (int)r.y >= 0; }
+__device__ __forceinline__ float2 lo_hi_f(unsigned w) { return __half22float2(*reinterpret_cast<const __half2 *>(&w)); }
 
 // Mitchell-Schaeffer explicit Euler (Eqs. ms1, ms2; closing branch -w/tau_close).
 template <typename real>

@@ -72,7 +72,7 @@ struct Op {
 // Loads of one plane for a lane's two voxel rows (lo = y0 + w - 1, hi = y0 + w).
 template <typename real, int MODE>
 struct Ld {
-    ushort4 rLo, rHi;
+    uint2 rLo, rHi;    // fp16 records as packed words
     real uLo, uHi;
     real wLo, wHi;     // PAR
     real veLo, veHi;   // PAR_BI
@@ -99,12 +99,12 @@ __device__ __forceinline__ void load_plane(const Op<real> &o, int k, bool lo_in,
                                            int plane, Ld<real, MODE> &L)
 {
     const bool kin = (unsigned)k < (unsigned)o.nz;
-    L.rLo = L.rHi = make_ushort4(0, 0, 0, kNonTissue);
+    L.rLo = L.rHi = make_uint2(0u, (unsigned)kNonTissue << 16);
     L.uLo = L.uHi = L.veLo = L.veHi = L.bLo = real(0);
     L.wLo = L.wHi = real(1);
     if (kin && lo_in) {
         const int q = qlo + k * plane;
-        L.rLo = __ldg(o.rec + q);
+        L.rLo = __ldg(reinterpret_cast<const uint2 *>(o.rec) + q);
         L.uLo = __ldg(o.src + q);
         if (MODE == M_PAR_MONO || MODE == M_PAR_BI) L.wLo = __ldg(o.w + q);
         if (MODE == M_PAR_BI) L.veLo = __ldg(o.ve + q);
@@ -112,7 +112,7 @@ __device__ __forceinline__ void load_plane(const Op<real> &o, int k, bool lo_in,
     }
     if (kin && hi_in) {
         const int q = qhi + k * plane;
-        L.rHi = __ldg(o.rec + q);
+        L.rHi = __ldg(reinterpret_cast<const uint2 *>(o.rec) + q);
         L.uHi = __ldg(o.src + q);
         if (MODE == M_PAR_MONO || MODE == M_PAR_BI) L.wHi = __ldg(o.w + q);
         if (MODE == M_PAR_BI) L.veHi = __ldg(o.ve + q);
@@ -136,8 +136,9 @@ __device__ __forceinline__ void plane_step(const Inst<real> &I, const Op<real> &
 {
     // ---- decode the two voxels of the lane ----
     const bool tlo = rec_tissue(L.rLo), thi = rec_tissue(L.rHi);
-    const real flo0 = (real)h2f(L.rLo.x), flo1 = (real)h2f(L.rLo.y), flo2 = (real)h2f(L.rLo.z);
-    const real fhi0 = (real)h2f(L.rHi.x), fhi1 = (real)h2f(L.rHi.y), fhi2 = (real)h2f(L.rHi.z);
+    const float2 alo = lo_hi_f(L.rLo.x), blo = lo_hi_f(L.rLo.y), ahi = lo_hi_f(L.rHi.x), bhi = lo_hi_f(L.rHi.y);
+    const real flo0 = (real)alo.x, flo1 = (real)alo.y, flo2 = (real)blo.x;
+    const real fhi0 = (real)ahi.x, fhi1 = (real)ahi.y, fhi2 = (real)bhi.x;
     real ulo, uhi;
     C.e0 = C.e1 = C.e2 = real(0);
     if (MODE == M_PAR_MONO || MODE == M_PAR_BI) {
@@ -150,7 +151,7 @@ __device__ __forceinline__ void plane_step(const Inst<real> &I, const Op<real> &
     } else {
         ulo = tlo ? L.uLo : real(0);
         uhi = thi ? L.uHi : real(0);
-        if (MODE == M_JAC) { C.e0 = L.bLo; C.e1 = (real)h2f(L.rLo.w); }
+        if (MODE == M_JAC) { C.e0 = L.bLo; C.e1 = (real)blo.y; }
     }
     C.uLo = ulo;
     C.uHi = uhi;
@@ -271,7 +272,7 @@ __device__ __forceinline__ void zero_state(St<real> &S)
 // planes hold no registers.
 template <typename real>
 struct JacRing {
-    static constexpr int D = sizeof(real) == 4 ? 4 : 3;   // static shared memory stays below 48 KB
+    static constexpr int D = sizeof(real) == 4 ? 4 : 2;   // divides the unroll of 4; static smem < 48 KB
     uint2 rec[D][2][kThreads];   // fp16 records of rows lo / hi
     real u[D][2][kThreads];
     real b[D][kThreads];
@@ -328,16 +329,29 @@ template <typename real>
 __device__ __forceinline__ void jac_read(const JacRing<real> &R, int slot, Ld<real, M_JAC> &L)
 {
     const int t = threadIdx.x;
-    const uint2 a = R.rec[slot][0][t], c = R.rec[slot][1][t];
-    L.rLo = make_ushort4((unsigned short)(a.x & 0xffffu), (unsigned short)(a.x >> 16), (unsigned short)(a.y & 0xffffu),
-                         (unsigned short)(a.y >> 16));
-    L.rHi = make_ushort4((unsigned short)(c.x & 0xffffu), (unsigned short)(c.x >> 16), (unsigned short)(c.y & 0xffffu),
-                         (unsigned short)(c.y >> 16));
+    L.rLo = R.rec[slot][0][t];
+    L.rHi = R.rec[slot][1][t];
     L.uLo = R.u[slot][0][t];
     L.uHi = R.u[slot][1][t];
     L.bLo = R.b[slot][t];
     L.wLo = L.wHi = real(1);
     L.veLo = L.veHi = real(0);
+}
+
+// One Jacobi plane: stage plane k + D - 1, wait for plane k (ring slot S % D), process it.
+template <typename real, int S>
+__device__ __forceinline__ void jac_plane(const Inst<real> &I, const Op<real> &o, const Lane &g, int k, int kbeg,
+                                          int kend, bool lo_in, bool hi_in, int qhi, JacRing<real> &R,
+                                          const St<real> &P, St<real> &Cn, Ld<real, M_JAC> &L,
+                                          real (*sF)[3][kWarps][32], real (*sT)[kWarps][32], bool check, float &acc)
+{
+    constexpr int D = JacRing<real>::D;
+    constexpr int slot = S % D, next = (S + D - 1) % D;
+    if (k + D - 1 <= kend) jac_issue<real>(o, R, next, k + D - 1, lo_in, hi_in, g.qlo, qhi, g.plane);
+    cp_async_commit();
+    cp_async_wait<D - 1>();
+    jac_read<real>(R, slot, L);
+    plane_step<real, M_JAC>(I, o, g, k, k > kbeg, k > kbeg + 1, P, Cn, L, sF, sT, check, acc);
 }
 
 // One work item (segment) of one instance.  item / nitems: index of this item
@@ -393,7 +407,7 @@ __device__ __forceinline__ void stencil_item(const Inst<real> &I, int seg_index,
     g.lane = threadIdx.x & 31;
     g.wid = threadIdx.x >> 5;
     const Seg sg = I.segs[seg_index];
-    g.x = sg.bx * kTileX - 1 + g.lane;
+    g.x = sg.x0 - 1 + g.lane;
     g.ylo = sg.by * kTileY + g.wid - 1;
     const bool xin = g.x >= 0 && g.x < I.nx;
     const bool lo_in = xin && g.ylo >= 0 && g.ylo < I.ny;
@@ -410,7 +424,8 @@ __device__ __forceinline__ void stencil_item(const Inst<real> &I, int seg_index,
     Ld<real, MODE> L0, L1;
     const int kbeg = sg.k0 - 1, kend = sg.k1;
     if constexpr (MODE == M_JAC) {
-        // planes staged kJacDepth - 1 ahead through the shared-memory ring
+        // planes staged D - 1 ahead through the shared-memory ring; the loop is
+        // unrolled by 4 so that every ring slot is a compile-time constant
         constexpr int D = JacRing<real>::D;
         JacRing<real> &R = sm.ring;
 #pragma unroll
@@ -418,27 +433,14 @@ __device__ __forceinline__ void stencil_item(const Inst<real> &I, int seg_index,
             if (kbeg + j <= kend) jac_issue<real>(o, R, j, kbeg + j, lo_in, hi_in, g.qlo, qhi, g.plane);
             cp_async_commit();
         }
-        int slot = 0;   // ring slot of plane k
         for (int k = kbeg;;) {
-            {
-                const int kn = k + D - 1, sn = slot == 0 ? D - 1 : slot - 1;
-                if (kn <= kend) jac_issue<real>(o, R, sn, kn, lo_in, hi_in, g.qlo, qhi, g.plane);
-                cp_async_commit();
-                cp_async_wait<D - 1>();
-                jac_read<real>(R, slot, L0);
-                plane_step<real, MODE>(I, o, g, k, k > kbeg, k > kbeg + 1, S1, S0, L0, sF, sT, check, acc);
-                slot = slot == D - 1 ? 0 : slot + 1;
-            }
+            jac_plane<real, 0>(I, o, g, k, kbeg, kend, lo_in, hi_in, qhi, R, S1, S0, L0, sF, sT, check, acc);
             if (++k > kend) break;
-            {
-                const int kn = k + D - 1, sn = slot == 0 ? D - 1 : slot - 1;
-                if (kn <= kend) jac_issue<real>(o, R, sn, kn, lo_in, hi_in, g.qlo, qhi, g.plane);
-                cp_async_commit();
-                cp_async_wait<D - 1>();
-                jac_read<real>(R, slot, L1);
-                plane_step<real, MODE>(I, o, g, k, k > kbeg, k > kbeg + 1, S0, S1, L1, sF, sT, check, acc);
-                slot = slot == D - 1 ? 0 : slot + 1;
-            }
+            jac_plane<real, 1>(I, o, g, k, kbeg, kend, lo_in, hi_in, qhi, R, S0, S1, L1, sF, sT, check, acc);
+            if (++k > kend) break;
+            jac_plane<real, 2>(I, o, g, k, kbeg, kend, lo_in, hi_in, qhi, R, S1, S0, L0, sF, sT, check, acc);
+            if (++k > kend) break;
+            jac_plane<real, 3>(I, o, g, k, kbeg, kend, lo_in, hi_in, qhi, R, S0, S1, L1, sF, sT, check, acc);
             if (++k > kend) break;
         }
         cp_async_wait<0>();
