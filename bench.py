@@ -52,6 +52,7 @@ def _args():
     ap.add_argument("--hbm-budget-gb", type=float, default=16.0, help="config4: admission budget")
     ap.add_argument("--max-slots", type=int, default=32, help="config4: requests stepped together")
     ap.add_argument("--chunk-steps", type=int, default=2, help="config4: steps between admission points")
+    ap.add_argument("--max-active-items", type=int, default=0, help="config4: work-based admission limit (0: none)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--ref-sweeps-per-step", type=float, default=None)
@@ -495,7 +496,7 @@ def run_served(a):
             lat_plain.append(fin - t_a)
         sims = [ep.sim_from_case(c, use_torch=False) for c in cases]
         srv = ep.Server(max_slots=a.max_slots, chunk_steps=a.chunk_steps, hbm_budget_bytes=budget,
-                        sweeps_per_check=4)
+                        max_active_items=a.max_active_items)
         t_base = srv.now() + 0.05
         ids = [srv.submit(h, S, release_s=t_base + float(t)) for h, t in zip(sims, arr)]
         got = {r.id: (r, h) for r, h in srv.collect_n(len(ids), timeout_s=3600)}
@@ -524,6 +525,7 @@ def run_served(a):
                                    f"{S} steps each, Poisson arrivals (seed 0)",
                        "grids": [c.nx for c in cases], "tissue_voxels": [c.n_tissue for c in cases],
                        "hbm_budget_bytes": budget, "max_slots": a.max_slots, "chunk_steps": a.chunk_steps,
+                       "max_active_items": a.max_active_items,
                        "l2": "inputs larger than L2 (all requests' state)"},
             "served_at_load": top["load"],
             "plain_sequential": {"value": plain_value, "unit": "tissue voxel-steps/s",

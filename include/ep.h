@@ -236,14 +236,16 @@ typedef struct {
     long long chunk_items;       /* packed reduction chunks per launch */
     size_t device_bytes;         /* device memory of the member handles */
     size_t budget_bytes;         /* admission budget */
-    int sweeps_per_check;        /* sweep launches between device loop checks (tuned) */
+    int sweeps_per_check;        /* sweep launches between device loop checks (set or tuned; untouched,
+                                    each group takes about 1 ms of its sweeps, 8..64) */
     int zseg;                    /* z-planes per stencil work item (tuned) */
     size_t group_bytes;          /* members are swept in groups whose working sets total at most
                                     this many bytes, so a group's sweeps stay in L2 (0 = one group; tuned) */
     int groups;                  /* number of such groups */
-    int solo_members;            /* members with at least half a wave of stencil items (3 CTAs per SM x
-                                    SMs / 2, 228 on 152 SMs): their Jacobi sweeps run as their own
-                                    launches, concurrent with the packed launch of the others */
+    int solo_members;            /* members whose Jacobi sweeps run as their own launches, concurrent
+                                    with the packed launch of the others: those with at least half a
+                                    wave of stencil items (3 CTAs per SM x SMs / 2, 228 on 152 SMs),
+                                    and every member of a group of at most 8 */
 } ep_batch_info;
 
 /* Create a batch of at most max_instances handles whose device memory may
@@ -268,7 +270,7 @@ ep_status ep_batch_slot_stats(ep_batch *b, int slot, ep_step_stats *stats);
 /* Choose the z-planes per work item and the group size by timing
  * trial_sweeps sweeps of each candidate on the members' current states
  * (states are restored afterwards); the sweeps per device loop check follow
- * from the measured sweep time. */
+ * from the measured sweep time (about 1 ms of sweeps, 8..64). */
 ep_status ep_batch_autotune(ep_batch *b, int trial_sweeps);
 
 /* Set the schedule by hand: sweep launches between device loop checks
@@ -313,6 +315,9 @@ typedef struct {
     int sweeps_per_check;       /* batch schedule (ep_batch_set_schedule); 0 = default */
     size_t hbm_budget_bytes;    /* device bytes the held requests may total; 0 = no limit */
     void *cuda_stream;          /* stream of the batched launches; NULL = a private one */
+    long long max_active_items; /* admit while the running requests' stencil work items (one z-march
+                                   tile each) stay within this many; a request is always admitted onto an
+                                   idle device; 0 = no limit */
 } ep_server_config;
 
 typedef struct {

@@ -78,7 +78,8 @@ class BatchInfo(ctypes.Structure):
 
 class ServerConfig(ctypes.Structure):
     _fields_ = [("max_slots", ctypes.c_int), ("chunk_steps", ctypes.c_int), ("sweeps_per_check", ctypes.c_int),
-                ("hbm_budget_bytes", ctypes.c_size_t), ("cuda_stream", ctypes.c_void_p)]
+                ("hbm_budget_bytes", ctypes.c_size_t), ("cuda_stream", ctypes.c_void_p),
+                ("max_active_items", ctypes.c_longlong)]
 
 
 class RequestResult(ctypes.Structure):
@@ -391,12 +392,13 @@ class Server:
     serving thread allocates them."""
 
     def __init__(self, max_slots: int, chunk_steps: int = 10, hbm_budget_bytes: int = 0, sweeps_per_check: int = 0,
-                 stream: Optional[int] = None):
+                 stream: Optional[int] = None, max_active_items: int = 0):
         L = load()
         self._L = L
         c = ServerConfig()
         c.max_slots, c.chunk_steps, c.sweeps_per_check = int(max_slots), int(chunk_steps), int(sweeps_per_check)
         c.hbm_budget_bytes, c.cuda_stream = int(hbm_budget_bytes), stream
+        c.max_active_items = int(max_active_items)
         h = ctypes.c_void_p()
         st = L.ep_server_create(ctypes.byref(c), ctypes.byref(h))
         if st != EP_OK:

@@ -37,6 +37,7 @@ namespace {
 constexpr int kZSeg = EP_ZSEG;     // default output planes per z-march segment
 constexpr int kZSegMin = 8;        // smallest segment length the batch autotuner tries
 constexpr int kSweepChunk = 64;    // sweeps per queued graph chunk
+constexpr int kSoloAllMembers = 8; // batch groups this small sweep every member in its own launches
 constexpr double kDivFactor = 1e16;
 
 struct StimDef {
@@ -556,20 +557,21 @@ ep_status solve_elliptic(ep_sim *s, const Inst<real> &I, int &iters, double &rel
         if (gs != EP_OK) return gs;
     }
     if (s->prof_on) CK(cudaEventRecord(s->pev[2], st));
-    const long long maxit = s->p.max_iter;
+    // at most max_iter sweeps do work; launch max_iter + 1 marks a capped solve done
+    const long long limit = (long long)s->p.max_iter + 1;
     long long queued = 0;
     for (int c = 0;; ++c) {
-        if (!s->noalloc_call && queued + kSweepChunk <= maxit) {
+        if (!s->noalloc_call && queued + kSweepChunk <= limit) {
             CK(cudaGraphLaunch(s->sweep_graph, st));
             queued += kSweepChunk;
         } else {
-            const long long stop = std::min(maxit, queued + (long long)kSweepChunk);
+            const long long stop = std::min(limit, queued + (long long)kSweepChunk);
             for (; queued < stop; ++queued) k_stencil<real, M_JAC><<<stencil_blocks(s), kThreads, 0, st>>>(I, io);
             CK(cudaGetLastError());
         }
         CK(cudaMemcpyAsync(&s->ctl_host[c & 1], s->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
         CK(cudaEventRecord(s->ev[c & 1], st));
-        if (queued >= maxit) {   // everything up to the cap is queued; the last sweep marks done
+        if (queued >= limit) {   // everything up to the cap is queued; the last launch marks done
             CK(cudaEventSynchronize(s->ev[c & 1]));
             break;
         }
@@ -1093,8 +1095,9 @@ struct ep_batch {
     int *d_counts = nullptr;
     int *d_packed = nullptr;       // per table row: 1 if its sweeps go through the packed kernel
     size_t cap_inst = 0, cap_seg = 0, cap_chunk = 0, cap_act = 0, cap_packed = 0;
-    // members with at least solo_items stencil items sweep in their own launches (descriptor
-    // by value, as in the single-instance step), concurrently on their own capture streams
+    // members with at least solo_items stencil items, and every member of a group of at most
+    // kSoloAllMembers, sweep in their own launches (descriptor by value, as in the
+    // single-instance step), concurrently on their own capture streams
     int solo_items = 0;
     std::vector<cudaStream_t> aux;
     std::vector<cudaEvent_t> ev_join;
@@ -1105,6 +1108,7 @@ struct ep_batch {
     cudaGraphExec_t graph = nullptr;
     bool dirty = true;
     int nsm = 152, sweeps_per_check = 16, zseg = kZSeg;
+    bool spc_auto = true;          // sweeps_per_check sized per group from its work at graph build
     // members are swept in groups whose working sets fit the L2 cache together; each group
     // has its own device-side convergence loop (0 = one group)
     size_t group_bytes = 0;
@@ -1208,9 +1212,10 @@ ep_status rebuild_tables(ep_batch *b)
         segs.insert(segs.end(), gs.begin(), gs.end());
         g.nseg = (long long)gs.size();
         g.packed_items = 0;
+        const bool few = r1 - r <= kSoloAllMembers;
         for (int q = r; q < r1; ++q) {
             ep_sim *s = b->slot[b->order[q]];
-            if (s->nseg >= b->solo_items) g.solo.push_back(q);
+            if (few || s->nseg >= b->solo_items) g.solo.push_back(q);
             else g.packed_items += s->nseg;
         }
         b->groups.push_back(g);
@@ -1325,17 +1330,25 @@ ep_status build_batch_graph(ep_batch *b)
             // solo members: their own sweep chains on forked streams (parallel graph branches)
             const int nsolo = (int)gr.solo.size();
             if (nsolo) CKB(cudaEventRecord(b->ev_fork, b->side));
+            // sweeps between loop checks: about 1 ms of sweeps (a loop pass costs tens of us), or as set
+            int spc = b->sweeps_per_check;
+            if (b->spc_auto) {
+                long long widest = gr.packed_items;
+                for (int q : gr.solo) widest = std::max<long long>(widest, b->slot[b->order[q]]->nseg);
+                const double waves = std::max(1.0, (double)widest / (double)(b->nsm * kMinBlocks));
+                spc = (int)std::min(64.0, std::max(8.0, std::round(1000.0 / (15.0 * waves))));
+            }
             for (int j = 0; j < nsolo; ++j) {
                 cudaStream_t a = b->aux[j];
                 CKB(cudaStreamWaitEvent(a, b->ev_fork, 0));
                 const Inst<float> I = make_inst<float>(b->slot[b->order[gr.solo[j]]]);
-                for (int i = 0; i < b->sweeps_per_check; ++i)
+                for (int i = 0; i < spc; ++i)
                     k_stencil<float, M_JAC><<<I.nseg, kThreads, 0, a>>>(I, no_io<float>());
                 CKB(cudaEventRecord(b->ev_join[j], a));
             }
             // the other members: packed sweeps over the unfinished ones
             if (gr.packed_items > 0)
-                for (int i = 0; i < b->sweeps_per_check; ++i)
+                for (int i = 0; i < spc; ++i)
                     k_stencil_active<float, M_JAC><<<grid_of(gr.packed_items, 1 << 30), kThreads, 0, b->side>>>(
                         gi_inst, b->d_act, gn);
             for (int j = 0; j < nsolo; ++j) CKB(cudaStreamWaitEvent(b->side, b->ev_join[j], 0));
@@ -1551,7 +1564,7 @@ ep_status ep_batch_autotune(ep_batch *b, int trial_sweeps)
             // never-converging solves so that every trial sweep does its full work
             for (int r = 0; r < b->ninst; ++r) {
                 Ctl c = ctl0[r];
-                c.done = 0; c.sweep = 0; c.arrive = 0; c.thresh2 = -1.0; c.bnorm2 = 1e300;
+                c.done = 0; c.sweep = 0; c.arrive = 0; c.jarrive = 0; c.thresh2 = -1.0; c.bnorm2 = 1e300;
                 CKB(cudaMemcpyAsync(b->slot[b->order[r]]->ctl, &c, sizeof(Ctl), cudaMemcpyHostToDevice, s0));
             }
             // one sweep of every group in turn, each group swept trial_sweeps times
@@ -1588,9 +1601,10 @@ ep_status ep_batch_autotune(ep_batch *b, int trial_sweeps)
     if (st != EP_OK) return st;
     b->zseg = best_z;
     b->group_bytes = best_g;
-    // sweeps between device loop checks: about 200 us of sweeps, 4..64 (a check costs a few us)
+    // sweeps between device loop checks: about 1 ms of sweeps, 8..64 (a loop pass costs tens of us)
     const double per_sweep_us = 1e3 * best / trial_sweeps;
-    b->sweeps_per_check = (int)std::min(64.0, std::max(4.0, std::ceil(200.0 / std::max(per_sweep_us, 1e-3))));
+    b->sweeps_per_check = (int)std::min(64.0, std::max(8.0, std::ceil(1000.0 / std::max(per_sweep_us, 1e-3))));
+    b->spc_auto = false;
     for (int r = 0; r < b->ninst && st == EP_OK; ++r) st = relayout_segments(b->slot[b->order[r]], b->zseg);
     if (st != EP_OK) return st;
     return rebuild_tables(b);
@@ -1602,7 +1616,10 @@ ep_status ep_batch_set_schedule(ep_batch *b, int sweeps_per_check, int zseg, lon
     if (sweeps_per_check < 0 || sweeps_per_check > 1024)
         return bfail(b, EP_EINVAL, "sweeps_per_check must be in [1, 1024] (0 keeps)");
     if (zseg != 0 && (zseg < kZSegMin || zseg > 256)) return bfail(b, EP_EINVAL, "zseg must be in [8, 256] (0 keeps)");
-    if (sweeps_per_check) b->sweeps_per_check = sweeps_per_check;
+    if (sweeps_per_check) {
+        b->sweeps_per_check = sweeps_per_check;
+        b->spc_auto = false;
+    }
     if (group_bytes >= 0) b->group_bytes = (size_t)group_bytes;
     if (zseg && zseg != b->zseg) {
         b->zseg = zseg;
@@ -1782,6 +1799,11 @@ void serve_loop(ep_server *v)
                 srv_finish(v, r, EP_ECANCELLED);
                 continue;
             }
+            if (v->cfg.max_active_items > 0 && !v->active.empty()) {   // enough work on the device already
+                long long items = r->sim->nseg;
+                for (const SrvReq *q : v->active) items += q->sim->nseg;
+                if (items > v->cfg.max_active_items) break;
+            }
             if (budget && v->hbm_in_use + r->peak > budget) {   // wait for memory to be released
                 if (v->active.empty() && !v->finished.empty() && !v->blocked_on_results) {
                     v->blocked_on_results = true;
@@ -1924,7 +1946,7 @@ ep_status ep_server_create(const ep_server_config *cfg, ep_server **out)
     if (!out) return EP_EINVAL;
     *out = nullptr;
     if (!cfg || cfg->max_slots < 1 || cfg->max_slots > 65536 || cfg->chunk_steps < 1 || cfg->sweeps_per_check < 0 ||
-        cfg->sweeps_per_check > 1024)
+        cfg->sweeps_per_check > 1024 || cfg->max_active_items < 0)
         return EP_EINVAL;
     ep_server *v = new (std::nothrow) ep_server();
     if (!v) return EP_ENOMEM;

@@ -220,6 +220,7 @@ __device__ __forceinline__ void comp_subtract_item(const Inst<real> &I, int item
         ctl->bnorm2 = t;
         ctl->thresh2 = I.rel_tol2 * t;
         ctl->sweep = 0;
+        ctl->jarrive = 0;
         ctl->iters = 0;
         ctl->converged = (t == 0.0);
         ctl->diverged = 0;

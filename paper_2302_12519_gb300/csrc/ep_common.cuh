@@ -52,7 +52,7 @@ struct StimSet {
 struct Ctl {
     unsigned int arrive;  // work items that finished the current launch (reset by the last one)
     int done;             // solve finished: converged, capped, diverged or empty rhs
-    int sweep;            // sweeps done in the current solve
+    int sweep;            // sweeps done in the current solve, as of its last residual check
     int iters;            // sweeps of the finished solve
     int converged;
     int nonfinite;
@@ -63,6 +63,10 @@ struct Ctl {
     double rnorm2;        // ||r||^2 at the last check
     long long step;       // time step n (t_n = n dt); v, w of step n live in buffer n & 1
     long long total_iters;
+    // work items of the current solve that finished a sweep, cumulative: when an item of sweep j
+    // starts, every item of sweeps < j has arrived and fewer than nitems of sweep j have, so
+    // jarrive / nitems = j; sweeps that do not check the residual only add to it
+    unsigned long long jarrive;
 };
 
 struct Chunk {

@@ -266,16 +266,21 @@ __device__ __forceinline__ void zero_state(St<real> &S)
     for (int j = 0; j < 3; ++j) S.FB[j] = S.FA[j] = real(0);
 }
 
-// Jacobi sweeps stage their loads through a per-thread ring in shared memory
-// filled by cp.async kJacDepth - 1 planes ahead: each thread reads back only
-// what it copied itself, so the ring needs no barrier, and the prefetched
-// planes hold no registers.
-template <typename real>
-struct JacRing {
+// The Jacobi sweep and the monodomain step stage their loads through a
+// per-thread ring in shared memory filled by cp.async D - 1 planes ahead:
+// each thread reads back only what it copied itself, so the ring needs no
+// barrier, and the prefetched planes hold no registers.  The other modes run
+// once per step and prefetch one plane into registers.
+template <int MODE>
+constexpr bool kRinged = MODE == M_JAC || MODE == M_PAR_MONO;
+
+template <typename real, int MODE>
+struct Ring {
     static constexpr int D = sizeof(real) == 4 ? 4 : 2;   // divides the unroll of 4; static smem < 48 KB
+    static constexpr int NX = MODE == M_JAC ? 1 : 2;      // b of row lo (Jacobi) or w of rows lo, hi
     uint2 rec[D][2][kThreads];   // fp16 records of rows lo / hi
     real u[D][2][kThreads];
-    real b[D][kThreads];
+    real x[D][NX][kThreads];
 };
 struct NoRing {};
 
@@ -285,7 +290,7 @@ struct StencilSmem {
     real sT[2][kWarps][32];
     double sred[kWarps];
     int sflag;
-    typename std::conditional<MODE == M_JAC, JacRing<real>, NoRing>::type ring;
+    typename std::conditional<kRinged<MODE>, Ring<real, MODE>, NoRing>::type ring;
 };
 
 template <int BYTES>
@@ -298,10 +303,11 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
-// Stage plane k of this thread's two voxels (and b of the lower one) into ring slot `slot`.
-template <typename real>
-__device__ __forceinline__ void jac_issue(const Op<real> &o, JacRing<real> &R, int slot, int k, bool lo_in,
-                                          bool hi_in, int qlo, int qhi, int plane)
+// Stage plane k of this thread's two voxels into ring slot `slot`; off the
+// grid the slot gets the values load_plane uses there.
+template <typename real, int MODE>
+__device__ __forceinline__ void ring_issue(const Op<real> &o, Ring<real, MODE> &R, int slot, int k, bool lo_in,
+                                           bool hi_in, int qlo, int qhi, int plane)
 {
     const int t = threadIdx.x;
     const bool kin = (unsigned)k < (unsigned)o.nz;
@@ -309,49 +315,57 @@ __device__ __forceinline__ void jac_issue(const Op<real> &o, JacRing<real> &R, i
         const int q = qlo + k * plane;
         cp_async_n<8>(&R.rec[slot][0][t], o.rec + q);
         cp_async_n<sizeof(real)>(&R.u[slot][0][t], o.src + q);
-        cp_async_n<sizeof(real)>(&R.b[slot][t], o.b + q);
+        cp_async_n<sizeof(real)>(&R.x[slot][0][t], (MODE == M_JAC ? o.b : o.w) + q);
     } else {
         R.rec[slot][0][t] = make_uint2(0u, (unsigned)kNonTissue << 16);
         R.u[slot][0][t] = real(0);
-        R.b[slot][t] = real(0);
+        R.x[slot][0][t] = MODE == M_JAC ? real(0) : real(1);
     }
     if (kin && hi_in) {
         const int q = qhi + k * plane;
         cp_async_n<8>(&R.rec[slot][1][t], o.rec + q);
         cp_async_n<sizeof(real)>(&R.u[slot][1][t], o.src + q);
+        if (MODE == M_PAR_MONO) cp_async_n<sizeof(real)>(&R.x[slot][Ring<real, MODE>::NX - 1][t], o.w + q);
     } else {
         R.rec[slot][1][t] = make_uint2(0u, (unsigned)kNonTissue << 16);
         R.u[slot][1][t] = real(0);
+        if (MODE == M_PAR_MONO) R.x[slot][Ring<real, MODE>::NX - 1][t] = real(1);
     }
 }
 
-template <typename real>
-__device__ __forceinline__ void jac_read(const JacRing<real> &R, int slot, Ld<real, M_JAC> &L)
+template <typename real, int MODE>
+__device__ __forceinline__ void ring_read(const Ring<real, MODE> &R, int slot, Ld<real, MODE> &L)
 {
     const int t = threadIdx.x;
     L.rLo = R.rec[slot][0][t];
     L.rHi = R.rec[slot][1][t];
     L.uLo = R.u[slot][0][t];
     L.uHi = R.u[slot][1][t];
-    L.bLo = R.b[slot][t];
-    L.wLo = L.wHi = real(1);
+    if (MODE == M_JAC) {
+        L.bLo = R.x[slot][0][t];
+        L.wLo = L.wHi = real(1);
+    } else {
+        L.bLo = real(0);
+        L.wLo = R.x[slot][0][t];
+        L.wHi = R.x[slot][Ring<real, MODE>::NX - 1][t];
+    }
     L.veLo = L.veHi = real(0);
 }
 
-// One Jacobi plane: stage plane k + D - 1, wait for plane k (ring slot S % D), process it.
-template <typename real, int S>
-__device__ __forceinline__ void jac_plane(const Inst<real> &I, const Op<real> &o, const Lane &g, int k, int kbeg,
-                                          int kend, bool lo_in, bool hi_in, int qhi, JacRing<real> &R,
-                                          const St<real> &P, St<real> &Cn, Ld<real, M_JAC> &L,
-                                          real (*sF)[3][kWarps][32], real (*sT)[kWarps][32], bool check, float &acc)
+// One plane: stage plane k + D - 1, wait for plane k (ring slot S % D), process it.
+template <typename real, int MODE, int S>
+__device__ __forceinline__ void ring_plane(const Inst<real> &I, const Op<real> &o, const Lane &g, int k, int kbeg,
+                                           int kend, bool lo_in, bool hi_in, int qhi, Ring<real, MODE> &R,
+                                           const St<real> &P, St<real> &Cn, Ld<real, MODE> &L,
+                                           real (*sF)[3][kWarps][32], real (*sT)[kWarps][32], bool check, float &acc)
 {
-    constexpr int D = JacRing<real>::D;
+    constexpr int D = Ring<real, MODE>::D;
     constexpr int slot = S % D, next = (S + D - 1) % D;
-    if (k + D - 1 <= kend) jac_issue<real>(o, R, next, k + D - 1, lo_in, hi_in, g.qlo, qhi, g.plane);
+    if (k + D - 1 <= kend) ring_issue<real, MODE>(o, R, next, k + D - 1, lo_in, hi_in, g.qlo, qhi, g.plane);
     cp_async_commit();
     cp_async_wait<D - 1>();
-    jac_read<real>(R, slot, L);
-    plane_step<real, M_JAC>(I, o, g, k, k > kbeg, k > kbeg + 1, P, Cn, L, sF, sT, check, acc);
+    ring_read<real, MODE>(R, slot, L);
+    plane_step<real, MODE>(I, o, g, k, k > kbeg, k > kbeg + 1, P, Cn, L, sF, sT, check, acc);
 }
 
 // One work item (segment) of one instance.  item / nitems: index of this item
@@ -378,7 +392,16 @@ __device__ __forceinline__ void stencil_item(const Inst<real> &I, int seg_index,
     const long long step = (MODE == M_APPLY) ? 0 : ctl->step;
     const int cur = (int)(step & 1);
     if (MODE == M_JAC) {
-        sweep = ctl->sweep;
+        sweep = (int)(*(volatile unsigned long long *)&ctl->jarrive / (unsigned long long)nitems);
+        if (sweep >= I.max_iter) {   // sweep cap reached: the solve ends with the last iterate
+            if (threadIdx.x == 0) {
+                ctl->noconv = 1;
+                ctl->iters = sweep;
+                __threadfence();
+                ctl->done = 1;
+            }
+            return;
+        }
         o.src = (sweep & 1) ? I.x1 : I.x0;
         o.out = (sweep & 1) ? I.x0 : I.x1;
         o.b = I.b;
@@ -423,24 +446,24 @@ __device__ __forceinline__ void stencil_item(const Inst<real> &I, int seg_index,
     zero_state(S1);
     Ld<real, MODE> L0, L1;
     const int kbeg = sg.k0 - 1, kend = sg.k1;
-    if constexpr (MODE == M_JAC) {
+    if constexpr (kRinged<MODE>) {
         // planes staged D - 1 ahead through the shared-memory ring; the loop is
         // unrolled by 4 so that every ring slot is a compile-time constant
-        constexpr int D = JacRing<real>::D;
-        JacRing<real> &R = sm.ring;
+        constexpr int D = Ring<real, MODE>::D;
+        Ring<real, MODE> &R = sm.ring;
 #pragma unroll
         for (int j = 0; j < D - 1; ++j) {
-            if (kbeg + j <= kend) jac_issue<real>(o, R, j, kbeg + j, lo_in, hi_in, g.qlo, qhi, g.plane);
+            if (kbeg + j <= kend) ring_issue<real, MODE>(o, R, j, kbeg + j, lo_in, hi_in, g.qlo, qhi, g.plane);
             cp_async_commit();
         }
         for (int k = kbeg;;) {
-            jac_plane<real, 0>(I, o, g, k, kbeg, kend, lo_in, hi_in, qhi, R, S1, S0, L0, sF, sT, check, acc);
+            ring_plane<real, MODE, 0>(I, o, g, k, kbeg, kend, lo_in, hi_in, qhi, R, S1, S0, L0, sF, sT, check, acc);
             if (++k > kend) break;
-            jac_plane<real, 1>(I, o, g, k, kbeg, kend, lo_in, hi_in, qhi, R, S0, S1, L1, sF, sT, check, acc);
+            ring_plane<real, MODE, 1>(I, o, g, k, kbeg, kend, lo_in, hi_in, qhi, R, S0, S1, L1, sF, sT, check, acc);
             if (++k > kend) break;
-            jac_plane<real, 2>(I, o, g, k, kbeg, kend, lo_in, hi_in, qhi, R, S1, S0, L0, sF, sT, check, acc);
+            ring_plane<real, MODE, 2>(I, o, g, k, kbeg, kend, lo_in, hi_in, qhi, R, S1, S0, L0, sF, sT, check, acc);
             if (++k > kend) break;
-            jac_plane<real, 3>(I, o, g, k, kbeg, kend, lo_in, hi_in, qhi, R, S0, S1, L1, sF, sT, check, acc);
+            ring_plane<real, MODE, 3>(I, o, g, k, kbeg, kend, lo_in, hi_in, qhi, R, S0, S1, L1, sF, sT, check, acc);
             if (++k > kend) break;
         }
         cp_async_wait<0>();
@@ -458,30 +481,37 @@ __device__ __forceinline__ void stencil_item(const Inst<real> &I, int seg_index,
     }
 
     if (MODE == M_JAC) {
+        if (!check) {   // count the arrival; nobody waits on it within this launch
+            if (threadIdx.x == 0) atomicAdd(&ctl->jarrive, 1ull);
+            return;
+        }
         // residual norm of this sweep's input: per-thread FP32 partial over its
-        // few voxels, FP64 above; deterministic fixed-order reduction
-        const double tot = block_sum<kThreads>(check ? (double)acc : 0.0, sm.sred);
-        if (threadIdx.x == 0) I.partials[item] = tot;
-        if (arrive_last(ctl, nitems, &sm.sflag)) {
+        // few voxels, FP64 above; deterministic fixed-order reduction by the
+        // item that arrives last
+        const double tot = block_sum<kThreads>((double)acc, sm.sred);
+        if (threadIdx.x == 0) {
+            I.partials[item] = tot;
+            __threadfence();
+            const unsigned long long last = (unsigned long long)(sweep + 1) * (unsigned long long)nitems - 1ull;
+            sm.sflag = atomicAdd(&ctl->jarrive, 1ull) == last;
+        }
+        __syncthreads();
+        if (sm.sflag) {
+            __threadfence();
             double s = 0;
-            if (check)
-                for (int i = threadIdx.x; i < nitems; i += kThreads) s += ((volatile double *)I.partials)[i];
+            for (int i = threadIdx.x; i < nitems; i += kThreads) s += ((volatile double *)I.partials)[i];
             s = block_sum<kThreads>(s, sm.sred);
             if (threadIdx.x == 0) {
-                ctl->arrive = 0;
                 const int j = sweep + 1;
                 ctl->sweep = j;
-                if (check) {
-                    ctl->rnorm2 = s;
-                    if (!(s == s) || isinf(s)) {
-                        ctl->nonfinite = 1; ctl->done = 1; ctl->iters = j;
-                    } else if (s <= ctl->thresh2) {
-                        ctl->converged = 1; ctl->done = 1; ctl->iters = j;
-                    } else if (s > I.div_factor * ctl->bnorm2) {
-                        ctl->diverged = 1; ctl->noconv = 1; ctl->done = 1; ctl->iters = j;
-                    }
+                ctl->rnorm2 = s;
+                if (!(s == s) || isinf(s)) {
+                    ctl->nonfinite = 1; ctl->done = 1; ctl->iters = j;
+                } else if (s <= ctl->thresh2) {
+                    ctl->converged = 1; ctl->done = 1; ctl->iters = j;
+                } else if (s > I.div_factor * ctl->bnorm2) {
+                    ctl->diverged = 1; ctl->noconv = 1; ctl->done = 1; ctl->iters = j;
                 }
-                if (!ctl->done && j >= I.max_iter) { ctl->done = 1; ctl->noconv = 1; ctl->iters = j; }
                 __threadfence();
             }
             __syncthreads();
