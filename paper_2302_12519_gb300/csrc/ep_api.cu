@@ -56,8 +56,11 @@ struct HostPlan {
     std::vector<long long> comp_count;  // voxels per component
     std::vector<Chunk> chunks;
     std::vector<int> comp_chunk0;       // first chunk of each component (+ end)
-    std::vector<Seg> segs;
+    std::vector<Seg> segs;              // work items at the handle's z-planes per item
+    std::vector<Seg> segs_z[4];         // work items at kZLens[i] planes per item (set-up picks one)
 };
+
+constexpr int kZLens[4] = {8, 16, 24, 32};
 
 struct ep_sim {
     ep_grid_desc d{};
@@ -296,15 +299,18 @@ ep_status plan_layout(ep_sim *s)
         pos = end;
     }
     P.comp_chunk0[nc] = (int)P.chunks.size();
+    long long most = 0;
+    for (int i = 0; i < 4; ++i) {
+        P.segs_z[i] = build_segments(m, nx, ny, nz, kZLens[i]);
+        most = std::max<long long>(most, (long long)P.segs_z[i].size());
+    }
     P.segs = build_segments(m, nx, ny, nz, s->zseg);
     s->n_tissue = (long long)P.order.size();
     s->ncomp = nc;
     s->nchunk = (int)P.chunks.size();
     s->nseg = (int)P.segs.size();
-    // capacity of the item buffers: the largest item count of the z-lengths the batch autotuner tries
-    s->max_items = s->nseg;
-    for (int zs : {8, 16, 32})
-        s->max_items = std::max<long long>((long long)build_segments(m, nx, ny, nz, zs).size(), s->max_items);
+    // capacity of the item buffers: the largest item count of the z-lengths set-up and the batch use
+    s->max_items = std::max<long long>(most, s->nseg);
     footprint(s, s->d.precision == EP_FP64 ? sizeof(double) : sizeof(float), &s->fp_resident, &s->fp_peak);
     P.done = true;
     return EP_OK;
@@ -321,6 +327,23 @@ ep_status setup_typed(ep_sim *s)
     const long long n = s->n;
     const uint8_t *m = s->mask.data();
     if (n > 2147483647LL) return fail(s, EP_EINVAL, "grid too large for 32-bit voxel indices");
+    // z-planes per work item on this device: the longest item (fewer halo planes) that still
+    // leaves two waves of resident sweep CTAs, else 16, else 8 for small grids
+    {
+        int dev = 0, nsm = 0;
+        CK(cudaGetDevice(&dev));
+        CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+        const long long wave = (long long)nsm * kMinBlocks;
+        int pick = 0;   // index into kZLens
+        for (int i = 3; i >= 1; --i)
+            if ((long long)s->plan.segs_z[i].size() >= (kZLens[i] == 16 ? wave : 2 * wave)) {
+                pick = i;
+                break;
+            }
+        s->plan.segs = s->plan.segs_z[pick];
+        s->nseg = (int)s->plan.segs.size();
+        s->zseg = kZLens[pick];
+    }
     const HostPlan &P = s->plan;
     const std::vector<int> &order = P.order;
     const std::vector<Chunk> &chunks = P.chunks;
@@ -400,6 +423,7 @@ ep_status setup_typed(ep_sim *s)
     s->plan.chunks = std::vector<Chunk>();
     s->plan.comp_chunk0 = std::vector<int>();
     s->plan.segs = std::vector<Seg>();
+    for (auto &v : s->plan.segs_z) v = std::vector<Seg>();
     CK(cudaMallocHost((void **)&s->ctl_host, 2 * sizeof(Ctl)));
     std::memset(s->ctl_host, 0, 2 * sizeof(Ctl));
     CK(cudaEventCreateWithFlags(&s->ev[0], cudaEventDisableTiming));
