@@ -49,7 +49,8 @@ class _Params(ctypes.Structure):
     _fields_ = [(n, ctypes.c_double) for n in
                 ("tau_in", "tau_out", "tau_open", "tau_close", "v_gate",
                  "sig_iL", "sig_iT", "sig_eL", "sig_eT", "lam", "K", "dt", "omega", "rel_tol")] + \
-               [("check_every", ctypes.c_int), ("max_iter", ctypes.c_int), ("model", ctypes.c_int)]
+               [("check_every", ctypes.c_int), ("max_iter", ctypes.c_int), ("model", ctypes.c_int),
+                ("diffusion", ctypes.c_int)]
 
 
 class _Stim(ctypes.Structure):
@@ -70,6 +71,9 @@ def lib():
         L.og_jacobi.argtypes = [ctypes.POINTER(_Grid), dp, dp, vp, vp, dp, dp, ip, ip,
                                 ctypes.POINTER(ip), ctypes.POINTER(dp)]
         L.og_jacobi.restype = ip
+        L.og_ie_jacobi.argtypes = [ctypes.POINTER(_Grid), dp, dp, dp, vp, vp, dp, ip, ip,
+                                   ctypes.POINTER(ip), ctypes.POINTER(dp)]
+        L.og_ie_jacobi.restype = ip
         L.og_default_omega.argtypes = [dp, dp]
         L.og_default_omega.restype = dp
         L.og_create.argtypes = [ip, ip, ip, dp, vp, vp, ctypes.POINTER(_Params),
@@ -86,6 +90,8 @@ def lib():
         L.og_ncomp.restype = ip
         L.og_total_iters.argtypes = [vp]
         L.og_total_iters.restype = ctypes.c_long
+        L.og_ie_total_iters.argtypes = [vp]
+        L.og_ie_total_iters.restype = ctypes.c_long
         L.og_num_threads.restype = ip
         _lib = L
     return _lib
@@ -138,11 +144,22 @@ class Grid:
                              max_iter, ctypes.byref(it), ctypes.byref(rr))
         return x, it.value, rr.value, st
 
+    def ie_jacobi(self, sL, sT, alpha, f, x0, tol=1e-6, m=10, max_iter=100000):
+        """Implicit-Euler Jacobi (Eq. iejac1) for (I + alpha L) x = f."""
+        f = np.ascontiguousarray(np.asarray(f, dtype=np.float64).reshape(-1))
+        x = np.ascontiguousarray(np.array(x0, dtype=np.float64).reshape(-1))
+        it = ctypes.c_int(0)
+        rr = ctypes.c_double(0.0)
+        st = lib().og_ie_jacobi(ctypes.byref(self._g), sL, sT, alpha, _ptr(f), _ptr(x), tol, m, max_iter,
+                                ctypes.byref(it), ctypes.byref(rr))
+        return x, it.value, rr.value, st
+
 
 def _params_struct(p, model: int) -> _Params:
     return _Params(p.tau_in, p.tau_out, p.tau_open, p.tau_close, p.v_gate,
                    p.sig_iL, p.sig_iT, p.sig_eL, p.sig_eT, p.lam, p.K, p.dt, p.omega,
-                   p.rel_tol, int(p.check_every), int(p.max_iter), int(model))
+                   p.rel_tol, int(p.check_every), int(p.max_iter), int(model),
+                   int(getattr(p, "diffusion", 0)))
 
 
 class Sim:
@@ -184,6 +201,10 @@ class Sim:
     @property
     def total_iters(self) -> int:
         return lib().og_total_iters(self._h)
+
+    @property
+    def ie_total_iters(self) -> int:
+        return lib().og_ie_total_iters(self._h)
 
     def set_state(self, v=None, w=None, ve=None, step: int = 0):
         arrs = [None if a is None else np.ascontiguousarray(np.asarray(a, np.float64).reshape(-1))

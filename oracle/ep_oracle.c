@@ -29,10 +29,15 @@
  *    average is over the contributing pairs.  L u approximates -div(Sigma grad u).
  *  - Operator splitting (Sec. "Algorithm Details / Electrophysiology"):
  *    reaction, then diffusion, then (bidomain) the elliptic equation of
- *    Eq. bidomain1 (second line).  Diffusion is explicit Euler.
+ *    Eq. bidomain1 (second line).  Diffusion is explicit Euler:
  *      monodomain  v+ = v* - dt/K * lambda/(1+lambda) * L_i v*     (Eq. monodomain1)
  *      bidomain    v+ = v* - dt/K * L_i (v* + ve^n)                (Eq. bidomain1, line 1)
  *                  (L_i + L_e) ve^{n+1} = -L_i v+                   (Eq. bidomain1, line 2)
+ *    or implicit Euler (Sec. "Implicit Euler", Sec. "Diffusion"), whose linear
+ *    system (I - alpha A) u^{t+1} = u^t is solved by the Jacobi step of
+ *    Eq. iejac1 with A = -L (L approximates -div Sigma grad):
+ *      monodomain  (I + a L_i) v+ = v*,             a = dt/K lambda/(1+lambda)
+ *      bidomain    (I + a L_i) v+ = v* - a L_i ve^n, a = dt/K   (ve lagged to step n)
  *  - Elliptic solve by damped Jacobi, Eq. dampjac1, from the previous ve,
  *    stopping when ||b - A x||_2 <= tol ||b||_2 (checked every m sweeps), then
  *    the reference potential is fixed by subtracting the mean over every
@@ -354,6 +359,75 @@ int og_jacobi(const og_grid *g, double sL, double sT, const double *b, double *x
     return status;
 }
 
+/* Implicit-Euler Jacobi, Eq. iejac1, for (I + alpha L) x = f on the tissue
+ * (the thesis writes (I - alpha A) with A = D + L + U its operator; here
+ * A = -L_{sL,sT}, so its diagonal is -D and its off-diagonal part -(L - D)):
+ *   x^{k+1} = [I + alpha D]^{-1} [ f - alpha (L - D) x^k ].
+ * The stop rule is the one of og_jacobi: at k = 0, m, 2m, ... the relative
+ * residual ||f - (I + alpha L) x^k|| / ||f|| is formed, and when it is <= tol
+ * the sweep that used it is the last one.  Status 1 after max_iter sweeps;
+ * ||f|| = 0 gives x = 0 after 0 sweeps. */
+int og_ie_jacobi(const og_grid *g, double sL, double sT, double alpha, const double *f, double *x,
+                 double tol, int m, int max_iter, int *iters, double *relres)
+{
+    long n = (long)g->nx * g->ny * g->nz, q;
+    double *diag = (double *)malloc(sizeof(double) * (size_t)n);
+    double *Lx = (double *)malloc(sizeof(double) * (size_t)n);
+    double *xn = (double *)malloc(sizeof(double) * (size_t)n);
+    double nf = 0.0, nr = 0.0;
+    int k = 0, status = 1;
+    for (q = 0; q < n; q++)
+        if (g->mask[q])
+            nf += f[q] * f[q];
+    nf = sqrt(nf);
+    *relres = 0.0;
+    if (nf == 0.0) {
+        for (q = 0; q < n; q++)
+            if (g->mask[q])
+                x[q] = 0.0;
+        *iters = 0;
+        free(diag);
+        free(Lx);
+        free(xn);
+        return 0;
+    }
+    if (m < 1)
+        m = 1;
+    og_diag_L(g, sL, sT, diag);
+    for (k = 0; k < max_iter; k++) {
+        og_apply_L(g, sL, sT, x, Lx);
+        int check = (k % m) == 0;
+        if (check)
+            nr = 0.0;
+        for (q = 0; q < n; q++) {
+            if (!g->mask[q])
+                continue;
+            if (check) {
+                double r = f[q] - (x[q] + alpha * Lx[q]);
+                nr += r * r;
+            }
+            /* off-diagonal part of L applied to x^k: (L x)_q - D_q x_q */
+            xn[q] = (f[q] - alpha * (Lx[q] - diag[q] * x[q])) / (1.0 + alpha * diag[q]);
+        }
+        for (q = 0; q < n; q++)
+            if (g->mask[q])
+                x[q] = xn[q];
+        if (check) {
+            *relres = sqrt(nr) / nf;
+            if (*relres <= tol) {
+                status = 0;
+                k++;
+                break;
+            }
+        }
+    }
+    *iters = k;
+    free(diag);
+    free(Lx);
+    free(xn);
+    return status;
+}
+
 /* ------------------------------------------------------------------------ */
 /* time stepping                                                            */
 /* ------------------------------------------------------------------------ */
@@ -372,6 +446,7 @@ struct og_sim {
     double *vs, *tmp, *b, *u;
     long step;
     long total_iters;
+    long ie_total_iters;
 };
 
 og_sim *og_create(int nx, int ny, int nz, double dx, const unsigned char *mask,
@@ -464,6 +539,7 @@ void og_get_state(const og_sim *s, double *v, double *w, double *ve, double *tac
 
 int og_ncomp(const og_sim *s) { return s->ncomp; }
 long og_total_iters(const og_sim *s) { return s->total_iters; }
+long og_ie_total_iters(const og_sim *s) { return s->ie_total_iters; }
 
 /* One step n -> n+1 (t_n = n dt).  Returns 0, or 1 if the elliptic solve hit
  * its sweep cap (the step is still completed with the last iterate). */
@@ -499,8 +575,25 @@ int og_step(og_sim *s, int *iters, double *relres)
         s->w[q] = w + p->dt * dw;
     }
 
-    /* 2. parabolic diffusion, explicit Euler */
-    if (p->model == OG_MONO) {
+    /* 2. parabolic diffusion, implicit Euler (Eq. iejac1) or explicit Euler */
+    if (p->diffusion == OG_IMPLICIT) {
+        double a = p->model == OG_MONO ? p->dt / p->K * p->lam / (1.0 + p->lam) : p->dt / p->K;
+        int ie_it = 0;
+        double ie_rr = 0.0;
+        if (p->model == OG_MONO) {
+            for (q = 0; q < n; q++)
+                s->b[q] = s->mask[q] ? s->vs[q] : 0.0;
+        } else {
+            og_apply_L(g, p->sig_iL, p->sig_iT, s->ve, s->u);
+            for (q = 0; q < n; q++)
+                s->b[q] = s->mask[q] ? s->vs[q] - a * s->u[q] : 0.0;
+        }
+        for (q = 0; q < n; q++)          /* first iterate: the reaction update */
+            s->tmp[q] = s->mask[q] ? s->vs[q] : 0.0;
+        status |= og_ie_jacobi(g, p->sig_iL, p->sig_iT, a, s->b, s->tmp, p->rel_tol, p->check_every,
+                               p->max_iter, &ie_it, &ie_rr);
+        s->ie_total_iters += ie_it;
+    } else if (p->model == OG_MONO) {
         og_apply_L(g, p->sig_iL, p->sig_iT, s->vs, s->tmp);
         double c = p->dt / p->K * p->lam / (1.0 + p->lam);
         for (q = 0; q < n; q++)

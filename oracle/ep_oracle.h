@@ -24,7 +24,11 @@ typedef struct {
     double sig_iL, sig_iT, sig_eL, sig_eT;
     double lam, K, dt, omega, rel_tol;
     int check_every, max_iter, model;
+    int diffusion;              /* OG_EXPLICIT or OG_IMPLICIT (Eq. iejac1) */
 } og_params;
+
+#define OG_EXPLICIT 0
+#define OG_IMPLICIT 1
 
 typedef struct {
     int lo[3], hi[3];           /* voxel box [lo, hi) */
@@ -39,6 +43,8 @@ int og_components(const og_grid *g, int *comp);
 double og_default_omega(double sL, double sT);
 int og_jacobi(const og_grid *g, double sL, double sT, const double *b, double *x,
               double omega, double tol, int m, int max_iter, int *iters, double *relres);
+int og_ie_jacobi(const og_grid *g, double sL, double sT, double alpha, const double *f, double *x,
+                 double tol, int m, int max_iter, int *iters, double *relres);
 
 og_sim *og_create(int nx, int ny, int nz, double dx, const unsigned char *mask,
                   const double *fib, const og_params *p, const og_stim *stim, int nstim);
@@ -49,6 +55,7 @@ int og_step(og_sim *s, int *iters, double *relres);
 int og_run(og_sim *s, int nsteps, int *last_iters, double *last_relres);
 int og_ncomp(const og_sim *s);
 long og_total_iters(const og_sim *s);
+long og_ie_total_iters(const og_sim *s);
 int og_num_threads(void);
 
 #ifdef __cplusplus

@@ -73,7 +73,8 @@ class Params:
     omega: float = 0.0        # Jacobi damping; <= 0 selects 1.8 / (8 sL / (sL + 2 sT))
     rel_tol: float = 1e-6     # elliptic stop: ||b - A x|| <= rel_tol ||b||
     check_every: int = 10     # residual check interval (sweeps)
-    max_iter: int = 100000    # sweep cap per elliptic solve
+    max_iter: int = 100000    # sweep cap per solve
+    diffusion: int = 0        # 0 explicit Euler, 1 implicit Euler (Eq. iejac1)
 
 
 @dataclasses.dataclass
