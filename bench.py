@@ -32,6 +32,7 @@ sys.path.insert(0, ROOT)
 
 BYTES_PER_SWEEP_VOXEL = 19      # x 4 + b 4 + x' 4 + fibre 6 + mask 1 (algorithmic, per tissue voxel)
 BYTES_PER_MONO_VOXEL = 23       # fused monodomain step: v, w read 8 + written 8 + fibre 6 + mask 1
+BYTES_PER_IE_SWEEP_VOXEL = 23   # implicit sweep: x, f, 1/(1 + a D) read 12 + fibre 6 + mask 1 + x' written 4
 REF_SAMPLE_SWEEPS = (8, 64)     # oracle sweeps timed per sample step (two caps -> per-sweep cost)
 DEFAULT_REF_SWEEPS_PER_STEP = 4000  # elliptic sweeps per step assumed by the reference arm when no GPU figure exists
 
@@ -45,6 +46,8 @@ def _args():
     ap.add_argument("--workload", choices=["config2", "config1", "config3", "config4", "slab"], default="config2")
     ap.add_argument("--model", choices=["mono", "bi"], default="mono", help="slab: model")
     ap.add_argument("--slab-n", type=int, default=512, help="slab: voxels per side")
+    ap.add_argument("--diffusion", choices=["explicit", "implicit"], default="explicit",
+                    help="parabolic step: explicit Euler, or implicit Euler solved by Jacobi (Eq. iejac1)")
     ap.add_argument("--instances", type=int, default=64, help="config3: number of instances")
     ap.add_argument("--requests", type=int, default=16, help="config4: number of requests")
     ap.add_argument("--req-steps", type=int, default=4, help="config4: time steps per request")
@@ -59,7 +62,15 @@ def _args():
     return ap.parse_args()
 
 
-def _workload(name, model="mono", slab_n=512):
+def _workload(name, model="mono", slab_n=512, diffusion="explicit"):
+    c, desc = _workload_case(name, model, slab_n)
+    if diffusion == "implicit":
+        c.params.diffusion = 1
+        desc += "; implicit-Euler diffusion (Jacobi, Eq. iejac1)"
+    return c, desc
+
+
+def _workload_case(name, model, slab_n):
     import workloads as W
     if name == "slab":
         bi = model == "bi"
@@ -161,11 +172,17 @@ def _dist():
     return world, rank, local
 
 
+def _solves_per_step(case):
+    """Jacobi solves in one step: the elliptic one (bidomain) and the implicit
+    parabolic one (implicit diffusion)."""
+    return (1 if case.model == 1 else 0) + (1 if getattr(case.params, "diffusion", 0) == 1 else 0)
+
+
 def oracle_sample(case, sweeps_per_step, n_samples=1):
     """Time the FP64 oracle on a bounded sample of one step of the workload:
-    the reaction, diffusion, right-hand-side and projection passes plus two
-    capped Jacobi solves give the fixed and the per-sweep cost; the full step
-    is fixed + sweeps_per_step * per-sweep."""
+    the step with every Jacobi solve capped at two sweep counts gives the
+    fixed and the per-sweep cost; the full step is fixed + sweeps_per_step *
+    per-sweep, sweeps_per_step summed over the step's solves."""
     import oracle
     import workloads as W
     oracle.build()
@@ -179,13 +196,14 @@ def oracle_sample(case, sweeps_per_step, n_samples=1):
             sim.step()
             t.append(time.perf_counter() - t0)
             sim.close()
-        ps = (t[1] - t[0]) / (REF_SAMPLE_SWEEPS[1] - REF_SAMPLE_SWEEPS[0])
+        ns = max(_solves_per_step(case), 1)   # every solve of the step runs to the cap
+        ps = (t[1] - t[0]) / ((REF_SAMPLE_SWEEPS[1] - REF_SAMPLE_SWEEPS[0]) * ns)
         per.append(max(ps, 1e-9))
-        fixed.append(max(t[0] - REF_SAMPLE_SWEEPS[0] * ps, 0.0))
+        fixed.append(max(t[0] - REF_SAMPLE_SWEEPS[0] * ns * ps, 0.0))
     f, p = float(np.median(fixed)), float(np.median(per))
     step_s = f + sweeps_per_step * p
     return {"step_s": step_s, "fixed_s": f, "per_sweep_s": p, "cores": oracle.num_threads(),
-            "sample_s": float(sum(fixed) + sum(per) * sum(REF_SAMPLE_SWEEPS))}
+            "sample_s": float(sum(fixed) + sum(per) * sum(REF_SAMPLE_SWEEPS) * max(_solves_per_step(case), 1))}
 
 
 def _oracle_case(a, case):
@@ -194,7 +212,9 @@ def _oracle_case(a, case):
     construction (the rate is per tissue voxel)."""
     if a.workload == "slab" and a.slab_n > 256:
         import workloads as W
-        return W.slab(256, case.model, unequal=case.model == 1)
+        oc = W.slab(256, case.model, unequal=case.model == 1)
+        oc.params.diffusion = case.params.diffusion
+        return oc
     return case
 
 
@@ -202,7 +222,7 @@ def run_reference(a):
     world, rank, local = _dist()
     if rank != 0:
         return
-    case, desc = _workload(a.workload, a.model, a.slab_n)
+    case, desc = _workload(a.workload, a.model, a.slab_n, a.diffusion)
     M = case.n_tissue
     k_ref = a.ref_sweeps_per_step or DEFAULT_REF_SWEEPS_PER_STEP
     times = []
@@ -241,7 +261,7 @@ def run_ours(a):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     epbuild.build()
-    case, desc = _workload(a.workload, a.model, a.slab_n)
+    case, desc = _workload(a.workload, a.model, a.slab_n, a.diffusion)
     M = case.n_tissue
     mono = case.model == 0
     stream = torch.cuda.Stream()
@@ -269,6 +289,7 @@ def run_ours(a):
     clocks.start()
     ms = []
     iters = []
+    ie_iters = []
     statuses = []
     for _ in range(a.steps):
         with torch.cuda.stream(stream):
@@ -280,6 +301,7 @@ def run_ours(a):
         e1.synchronize()
         ms.append(e0.elapsed_time(e1))
         iters.append(st.iters)
+        ie_iters.append(st.ie_total_iters)
         statuses.append(sim.last_status)
     torch.cuda.synchronize()
     clk = clocks.stop()
@@ -296,7 +318,13 @@ def run_ours(a):
     peaks = _peaks()
     peak = float(peaks["hbm_gbs"]) if peaks else 6800.0
     peak_src = "of measured" if peaks else "of fallback"
-    if mono:
+    implicit = a.diffusion == "implicit"
+    if mono and implicit:
+        # the implicit sweeps dominate the step
+        launch_s = prof.ie_sweep_ms / 1e3 / max(prof.ie_sweeps, 1)
+        alg_bytes = BYTES_PER_IE_SWEEP_VOXEL * M
+        kname, share = "k_stencil<float,M_IE> (implicit-Euler Jacobi sweep)", prof.ie_sweep_ms / 1e3 / total_s
+    elif mono:
         # the fused reaction + diffusion launch is the step (plus a one-thread step-counter kernel)
         launch_s = prof.other_ms / 1e3 / max(prof.steps, 1)
         alg_bytes = BYTES_PER_MONO_VOXEL * M
@@ -307,7 +335,8 @@ def run_ours(a):
         alg_bytes = BYTES_PER_SWEEP_VOXEL * M
         kname, share = "k_stencil<float,M_JAC> (damped Jacobi sweep)", sweep_s / total_s
     achieved = alg_bytes / launch_s / 1e9 if launch_s > 0 else 0.0
-    stem = (f"fused_step_slab{a.slab_n}_mono" if mono else
+    stem = (f"ie_sweep_slab{a.slab_n}_mono" if mono and implicit else
+            f"fused_step_slab{a.slab_n}_mono" if mono else
             f"jacobi_sweep_slab{a.slab_n}_bi" if a.workload == "slab" else f"jacobi_sweep_{a.workload}")
     tpv = _traffic_record(stem)
     roofline = {"bound": "hbm", "kernel": kname,
@@ -333,7 +362,7 @@ def run_ours(a):
 
     cpu = None
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
-        k = float(np.mean(iters)) if iters else DEFAULT_REF_SWEEPS_PER_STEP
+        k = float(np.mean(iters)) + float(np.mean(ie_iters)) if iters else DEFAULT_REF_SWEEPS_PER_STEP
         oc = _oracle_case(a, case)
         info = oracle_sample(oc, k)
         cpu = {"value": oc.n_tissue / info["step_s"], "unit": "tissue voxel-steps/s", "cores": info["cores"],
@@ -352,6 +381,7 @@ def run_ours(a):
                            "dt_ms": case.params.dt, "rel_tol": case.params.rel_tol,
                            "window": f"steps {a.warmup}..{a.warmup + a.steps - 1} from rest, stimulus at t=0",
                            "sweeps_per_step": iters, "step_status": statuses,
+                           "implicit_sweeps_per_step": ie_iters if a.diffusion == "implicit" else None,
                            "l2": "flushed between timed steps (256 MB write)",
                            "parallelism": f"replicas x{world}"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,

@@ -91,9 +91,18 @@ typedef struct {
     double jacobi_omega;  /* damping of Eq. dampjac1; <= 0 selects 1.8 / (8 sL / (sL + 2 sT))
                              for the elliptic operator's sL = sig_iL + sig_eL, sT = sig_iT + sig_eT */
     double rel_tol;       /* stop when ||b - A x||_2 <= rel_tol ||b||_2 */
-    int check_every;      /* residual check interval in sweeps, >= 1 */
-    int max_iter;         /* sweep cap per elliptic solve, >= 1 */
+    int check_every;      /* residual check interval in sweeps, >= 1 (both solves) */
+    int max_iter;         /* sweep cap per solve, >= 1 (both solves) */
+    int diffusion;        /* EP_EXPLICIT: the parabolic part by explicit Euler (default);
+                             EP_IMPLICIT: by implicit Euler, (I + a L_i) v+ = v* for the monodomain
+                             (a = dt/K lambda/(1+lambda)) or v* - a L_i ve^n for the bidomain
+                             (a = dt/K, ve of step n), solved by the undamped Jacobi step of
+                             Eq. iejac1 from v* to rel_tol (Sec. "Implicit Euler", "Diffusion").
+                             Implicit handles are stepped by ep_step only, not in a batch. */
 } ep_params;
+
+#define EP_EXPLICIT 0
+#define EP_IMPLICIT 1
 
 typedef struct {
     int iters;               /* Jacobi sweeps of the last elliptic solve (0 for monodomain) */
@@ -101,6 +110,7 @@ typedef struct {
     int converged;           /* 1 if every solve in the call met rel_tol */
     long long total_iters;   /* sweeps summed over the steps of the call */
     long long step;          /* step counter after the call (t = step * dt) */
+    long long ie_total_iters;   /* implicit-diffusion Jacobi sweeps summed over the steps of the call */
 } ep_step_stats;
 
 typedef struct {
@@ -201,6 +211,8 @@ typedef struct {
     long long sweeps;            /* sweeps that did work */
     long long other_launches;    /* all other kernels launched by ep_step */
     long long steps;             /* steps taken while enabled */
+    double ie_sweep_ms;          /* implicit-diffusion sweep launches (included in other_ms) */
+    long long ie_sweeps;         /* implicit-diffusion sweeps that did work */
 } ep_profile;
 
 /* Device memory of the handle, from a host-side plan of its mask (face-

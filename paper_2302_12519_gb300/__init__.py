@@ -22,6 +22,7 @@ LIB_PATH = os.path.join(_HERE, "libep.so")
 STATUS_NAMES = ["EP_OK", "EP_EINVAL", "EP_ENOMEM", "EP_ECUDA", "EP_ENOCONV", "EP_ENONFINITE", "EP_ESTATE",
                 "EP_EBUSY", "EP_EREJECTED", "EP_ECANCELLED"]
 EP_MONO, EP_BI = 0, 1
+EP_EXPLICIT, EP_IMPLICIT = 0, 1
 EP_FP32, EP_FP64 = 0, 1
 EP_VM_MV, EP_W, EP_VE_MV, EP_TACT, EP_V, EP_VE = range(6)
 
@@ -49,12 +50,13 @@ class Params(ctypes.Structure):
     _fields_ = [(n, ctypes.c_double) for n in
                 ("tau_in", "tau_out", "tau_open", "tau_close", "v_gate", "sig_iL", "sig_iT", "sig_eL", "sig_eT",
                  "lambda_", "K", "dt_ms", "jacobi_omega", "rel_tol")] + \
-               [("check_every", ctypes.c_int), ("max_iter", ctypes.c_int)]
+               [("check_every", ctypes.c_int), ("max_iter", ctypes.c_int), ("diffusion", ctypes.c_int)]
 
 
 class StepStats(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int), ("rel_res", ctypes.c_double), ("converged", ctypes.c_int),
-                ("total_iters", ctypes.c_longlong), ("step", ctypes.c_longlong)]
+                ("total_iters", ctypes.c_longlong), ("step", ctypes.c_longlong),
+                ("ie_total_iters", ctypes.c_longlong)]
 
 
 class Info(ctypes.Structure):
@@ -65,7 +67,8 @@ class Info(ctypes.Structure):
 class Profile(ctypes.Structure):
     _fields_ = [("sweep_ms", ctypes.c_double), ("other_ms", ctypes.c_double),
                 ("sweep_launches", ctypes.c_longlong), ("sweeps", ctypes.c_longlong),
-                ("other_launches", ctypes.c_longlong), ("steps", ctypes.c_longlong)]
+                ("other_launches", ctypes.c_longlong), ("steps", ctypes.c_longlong),
+                ("ie_sweep_ms", ctypes.c_double), ("ie_sweeps", ctypes.c_longlong)]
 
 
 class BatchInfo(ctypes.Structure):
@@ -242,7 +245,8 @@ class Sim:
 
     def set_params(self, p):
         P = Params(p.tau_in, p.tau_out, p.tau_open, p.tau_close, p.v_gate, p.sig_iL, p.sig_iT, p.sig_eL, p.sig_eT,
-                   p.lam, p.K, p.dt, p.omega, p.rel_tol, int(p.check_every), int(p.max_iter))
+                   p.lam, p.K, p.dt, p.omega, p.rel_tol, int(p.check_every), int(p.max_iter),
+                   int(getattr(p, "diffusion", 0)))
         self._check(self._L.ep_set_params(self._h, ctypes.byref(P)), "ep_set_params")
 
     def add_stimulus(self, lo: Sequence[int], hi: Sequence[int], t_start: float, dur: float, amp: float):

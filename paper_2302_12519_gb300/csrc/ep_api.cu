@@ -99,11 +99,14 @@ struct ep_sim {
     Ctl *ctl_host = nullptr;   // pinned, 2 slots
     cudaEvent_t ev[2] = {nullptr, nullptr};
     cudaGraphExec_t sweep_graph = nullptr;
+    cudaGraphExec_t ie_graph = nullptr;   // implicit-diffusion sweeps
+    void *ie_x = nullptr, *ie_inv = nullptr;
+    long long ie_seen = 0;                // implicit sweeps counted by earlier calls
     long long step = 0;
     bool noalloc_call = false;   // inside ep_step_noalloc: scratch is the static array, no graph
     // device-time accounting (ep_profile_enable)
     bool prof_on = false;
-    cudaEvent_t pev[4] = {nullptr, nullptr, nullptr, nullptr};
+    cudaEvent_t pev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
     ep_profile prof{};
 };
 
@@ -169,6 +172,7 @@ bool params_ok(const ep_params &p, std::string &why)
     if (!std::isfinite(p.jacobi_omega) || p.jacobi_omega >= 2.0) { why = "jacobi_omega must be < 2 (<= 0 selects the default)"; return false; }
     if (!std::isfinite(p.rel_tol) || p.rel_tol < 0.0) { why = "rel_tol must be >= 0"; return false; }
     if (p.check_every < 1 || p.max_iter < 1) { why = "check_every and max_iter must be >= 1"; return false; }
+    if (p.diffusion != EP_EXPLICIT && p.diffusion != EP_IMPLICIT) { why = "diffusion must be EP_EXPLICIT or EP_IMPLICIT"; return false; }
     return true;
 }
 
@@ -242,6 +246,7 @@ void footprint(const ep_sim *s, size_t rb, size_t *resident, size_t *peak)
     r += abytes(sizeof(Chunk) * P.chunks.size()) + abytes(sizeof(int) * P.comp_chunk0.size());
     r += abytes(sizeof(long long) * P.comp_count.size()) + abytes(sizeof(double) * (size_t)s->ncomp);
     r += abytes(sizeof(double) * (size_t)std::max<long long>(s->max_items, s->nchunk)) + abytes(sizeof(Ctl));
+    if (s->have_params && s->p.diffusion == EP_IMPLICIT) r += 2 * abytes(rb * n);   // second iterate, 1/(1 + a D)
     *resident = r;
     *peak = r + abytes(sizeof(float) * 3 * n) + abytes(n) + abytes(sizeof(ushort4) * n);
 }
@@ -251,7 +256,10 @@ void footprint(const ep_sim *s, size_t rb, size_t *resident, size_t *peak)
 // Fills s->plan and the derived counts; touches no device state.
 ep_status plan_layout(ep_sim *s)
 {
-    if (s->plan.done) return EP_OK;
+    if (s->plan.done) {   // the parameters may have changed since (implicit diffusion adds buffers)
+        footprint(s, s->d.precision == EP_FP64 ? sizeof(double) : sizeof(float), &s->fp_resident, &s->fp_peak);
+        return EP_OK;
+    }
     if (!s->have_mask) return fail(s, EP_ESTATE, "ep_set_mask must be called first");
     const int nx = s->d.nx, ny = s->d.ny, nz = s->d.nz;
     const long long n = s->n;
@@ -351,7 +359,9 @@ ep_status setup_typed(ep_sim *s)
     const std::vector<long long> &comp_count = P.comp_count;
     const std::vector<Seg> &segs = P.segs;
     const int nc = s->ncomp;
+    footprint(s, sizeof(real), &s->fp_resident, &s->fp_peak);   // the parameters are known now
     const size_t want_resident = s->fp_resident, want_peak = s->fp_peak;
+    const bool ie = s->p.diffusion == EP_IMPLICIT;
 
     // device buffers
     const size_t rb = sizeof(real);
@@ -372,6 +382,11 @@ ep_status setup_typed(ep_sim *s)
     s->means = (double *)dalloc(s, sizeof(double) * nc);
     s->partials = (double *)dalloc(s, sizeof(double) * std::max<long long>(s->max_items, s->nchunk));
     s->ctl = (Ctl *)dalloc(s, sizeof(Ctl));
+    if (ie) {
+        s->ie_x = dalloc(s, rb * n);
+        s->ie_inv = dalloc(s, rb * n);
+        if (!s->ie_x || !s->ie_inv) return fail(s, EP_ENOMEM, "device allocation failed");
+    }
     void *tmp_fib = dalloc(s, sizeof(float) * 3 * n);
     void *tmp_mask = dalloc(s, n);
     void *tmp_rec = dalloc(s, sizeof(ushort4) * n);
@@ -396,6 +411,15 @@ ep_status setup_typed(ep_sim *s)
     const double sL = s->p.sig_iL + s->p.sig_eL, sT = s->p.sig_iT + s->p.sig_eT;
     k_build_diag<<<grid_for(n, 128), 128, 0, st>>>(nx, ny, nz, sT, sL - sT, (const ushort4 *)tmp_rec, s->rec);
     CK(cudaGetLastError());
+    if (ie) {   // implicit diffusion: 1 / (1 + a D_i) for the intracellular operator, second iterate
+        const double C = 1.0 / (8.0 * s->d.dx_mm * s->d.dx_mm);
+        const double fac = s->d.model == EP_MONO ? s->p.lambda / (1.0 + s->p.lambda) : 1.0;
+        const double aC = s->p.dt_ms / s->p.K * fac * C;
+        k_build_ie_diag<real><<<grid_for(n, 128), 128, 0, st>>>(nx, ny, nz, s->p.sig_iT, s->p.sig_iL - s->p.sig_iT,
+                                                                 aC, s->rec, (real *)s->ie_inv);
+        k_fill<real><<<grid_for(n, 256), 256, 0, st>>>((real *)s->ie_x, n, real(0));
+        CK(cudaGetLastError());
+    }
     // rest state
     for (int i = 0; i < 2; ++i) {
         k_fill<real><<<grid_for(n, 256), 256, 0, st>>>((real *)s->v[i], n, real(0));
@@ -464,6 +488,10 @@ Inst<real> make_inst(const ep_sim *s)
     I.means = s->means;
     I.partials = s->partials;
     I.ctl = s->ctl;
+    I.diffusion = s->p.diffusion;
+    I.pad2 = 0;
+    I.ie_x = (real *)s->ie_x;
+    I.ie_inv = (const real *)s->ie_inv;
     const double C = 1.0 / (8.0 * s->d.dx_mm * s->d.dx_mm);
     const double sLie = s->p.sig_iL + s->p.sig_eL, sTie = s->p.sig_iT + s->p.sig_eT;
     const double fac = s->d.model == EP_MONO ? s->p.lambda / (1.0 + s->p.lambda) : 1.0;
@@ -474,6 +502,7 @@ Inst<real> make_inst(const ep_sim *s)
     I.C = (real)C;
     I.coef_par = (real)(s->p.dt_ms / s->p.K * fac);
     I.coef_jac = (real)(s->omega / C);
+    I.alpha_ie = (real)(s->p.dt_ms / s->p.K * fac);
     I.dt = (real)s->p.dt_ms;
     I.inv_tin = (real)(1.0 / s->p.tau_in);
     I.inv_tout = (real)(1.0 / s->p.tau_out);
@@ -505,24 +534,64 @@ ApplyIO<real> no_io()
     return io;
 }
 
-template <typename real>
-ep_status build_sweep_graph(ep_sim *s)
+// A CUDA graph of kSweepChunk sweep launches of one solve (MODE = M_JAC or M_IE).
+template <typename real, int MODE>
+ep_status build_sweep_graph(ep_sim *s, cudaGraphExec_t *out)
 {
-    if (s->sweep_graph) return EP_OK;
+    if (*out) return EP_OK;
     const Inst<real> I = make_inst<real>(s);
     const ApplyIO<real> io = no_io<real>();
     cudaGraph_t g = nullptr;
     CK(cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeThreadLocal));
     for (int i = 0; i < kSweepChunk; ++i)
-        k_stencil<real, M_JAC><<<stencil_blocks(s), kThreads, 0, s->stream>>>(I, io);
+        k_stencil<real, MODE><<<stencil_blocks(s), kThreads, 0, s->stream>>>(I, io);
     cudaError_t e = cudaStreamEndCapture(s->stream, &g);
     if (e != cudaSuccess) return fail(s, EP_ECUDA, std::string("sweep graph capture: ") + cudaGetErrorString(e));
-    e = cudaGraphInstantiate(&s->sweep_graph, g, 0);
+    e = cudaGraphInstantiate(out, g, 0);
     cudaGraphDestroy(g);
     if (e != cudaSuccess) {
-        s->sweep_graph = nullptr;
+        *out = nullptr;
         return fail(s, EP_ECUDA, std::string("sweep graph instantiate: ") + cudaGetErrorString(e));
     }
+    return EP_OK;
+}
+
+// Queues the sweeps of one solve in graph chunks with one chunk of look-ahead:
+// the host reads the control block one chunk behind, so the GPU never waits
+// for it.  At most max_iter sweeps do work; launch max_iter + 1 marks a capped
+// solve done.  Returns the launches queued in *queued_out.
+template <typename real, int MODE>
+ep_status run_sweeps(ep_sim *s, const Inst<real> &I, cudaGraphExec_t *graph, long long *queued_out)
+{
+    cudaStream_t st = s->stream;
+    const ApplyIO<real> io = no_io<real>();
+    if (!s->noalloc_call) {
+        ep_status gs = build_sweep_graph<real, MODE>(s, graph);
+        if (gs != EP_OK) return gs;
+    }
+    const long long limit = (long long)s->p.max_iter + 1;
+    long long queued = 0;
+    for (int c = 0;; ++c) {
+        if (!s->noalloc_call && queued + kSweepChunk <= limit) {
+            CK(cudaGraphLaunch(*graph, st));
+            queued += kSweepChunk;
+        } else {
+            const long long stop = std::min(limit, queued + (long long)kSweepChunk);
+            for (; queued < stop; ++queued) k_stencil<real, MODE><<<stencil_blocks(s), kThreads, 0, st>>>(I, io);
+            CK(cudaGetLastError());
+        }
+        CK(cudaMemcpyAsync(&s->ctl_host[c & 1], s->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
+        CK(cudaEventRecord(s->ev[c & 1], st));
+        if (queued >= limit) {   // everything up to the cap is queued; the last launch marks done
+            CK(cudaEventSynchronize(s->ev[c & 1]));
+            break;
+        }
+        if (c >= 1) {            // one chunk of look-ahead keeps the GPU busy while the host checks
+            CK(cudaEventSynchronize(s->ev[(c - 1) & 1]));
+            if (s->ctl_host[(c - 1) & 1].done) break;
+        }
+    }
+    *queued_out = queued;
     return EP_OK;
 }
 
@@ -576,34 +645,10 @@ ep_status solve_elliptic(ep_sim *s, const Inst<real> &I, int &iters, double &rel
     k_comp_subtract<real><<<s->nchunk, kRedThreads, 0, st>>>(I);
     CK(cudaGetLastError());
     // sweeps, queued in graph chunks, one chunk of look-ahead
-    if (!s->noalloc_call) {
-        ep_status gs = build_sweep_graph<real>(s);
-        if (gs != EP_OK) return gs;
-    }
     if (s->prof_on) CK(cudaEventRecord(s->pev[2], st));
-    // at most max_iter sweeps do work; launch max_iter + 1 marks a capped solve done
-    const long long limit = (long long)s->p.max_iter + 1;
     long long queued = 0;
-    for (int c = 0;; ++c) {
-        if (!s->noalloc_call && queued + kSweepChunk <= limit) {
-            CK(cudaGraphLaunch(s->sweep_graph, st));
-            queued += kSweepChunk;
-        } else {
-            const long long stop = std::min(limit, queued + (long long)kSweepChunk);
-            for (; queued < stop; ++queued) k_stencil<real, M_JAC><<<stencil_blocks(s), kThreads, 0, st>>>(I, io);
-            CK(cudaGetLastError());
-        }
-        CK(cudaMemcpyAsync(&s->ctl_host[c & 1], s->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
-        CK(cudaEventRecord(s->ev[c & 1], st));
-        if (queued >= limit) {   // everything up to the cap is queued; the last launch marks done
-            CK(cudaEventSynchronize(s->ev[c & 1]));
-            break;
-        }
-        if (c >= 1) {            // one chunk of look-ahead keeps the GPU busy while the host checks
-            CK(cudaEventSynchronize(s->ev[(c - 1) & 1]));
-            if (s->ctl_host[(c - 1) & 1].done) break;
-        }
-    }
+    ep_status rs = run_sweeps<real, M_JAC>(s, I, &s->sweep_graph, &queued);
+    if (rs != EP_OK) return rs;
     if (s->prof_on) {
         CK(cudaEventRecord(s->pev[3], st));
         s->prof.sweep_launches += queued;
@@ -639,12 +684,36 @@ ep_status step_typed(ep_sim *s, int n_steps, ep_step_stats *stats)
     long long total = 0;
     const Inst<real> I = make_inst<real>(s);
     const ApplyIO<real> io = no_io<real>();
+    const bool ie = s->p.diffusion == EP_IMPLICIT;
+    {   // the non-convergence flag of this call starts clear
+        const int zero = 0;
+        CK(cudaMemcpyAsync((char *)s->ctl + offsetof(Ctl, noconv), &zero, sizeof(int), cudaMemcpyHostToDevice, st));
+    }
     for (int it = 0; it < n_steps; ++it) {
         const double sweep_ms0 = s->prof.sweep_ms;
         if (s->prof_on) CK(cudaEventRecord(s->pev[0], st));
-        // reaction + diffusion: reads v, w of step n (buffer n & 1), writes buffer (n + 1) & 1
-        if (s->d.model == EP_MONO) k_stencil<real, M_PAR_MONO><<<stencil_blocks(s), kThreads, 0, st>>>(I, io);
-        else k_stencil<real, M_PAR_BI><<<stencil_blocks(s), kThreads, 0, st>>>(I, io);
+        if (ie) {
+            // implicit Euler (Eq. iejac1): reaction and right-hand side f, ||f||, Jacobi sweeps
+            // from v* to rel_tol, then the final iterate, activation times and the flags
+            const int gt = grid_for(s->n_tissue, kRedThreads);
+            if (s->d.model == EP_MONO) k_ie_react<real><<<gt, kRedThreads, 0, st>>>(I);
+            else k_stencil<real, M_IE_RHS><<<stencil_blocks(s), kThreads, 0, st>>>(I, io);
+            k_ie_start<real><<<s->nchunk, kRedThreads, 0, st>>>(I);
+            CK(cudaGetLastError());
+            if (s->prof_on) CK(cudaEventRecord(s->pev[4], st));
+            long long queued = 0;
+            ep_status e = run_sweeps<real, M_IE>(s, I, &s->ie_graph, &queued);
+            if (e != EP_OK) return e;
+            if (s->prof_on) {
+                CK(cudaEventRecord(s->pev[5], st));
+                s->prof.other_launches += 3 + queued;
+            }
+            k_ie_finish<real><<<gt, kRedThreads, 0, st>>>(I);
+        } else {
+            // reaction + diffusion: reads v, w of step n (buffer n & 1), writes buffer (n + 1) & 1
+            if (s->d.model == EP_MONO) k_stencil<real, M_PAR_MONO><<<stencil_blocks(s), kThreads, 0, st>>>(I, io);
+            else k_stencil<real, M_PAR_BI><<<stencil_blocks(s), kThreads, 0, st>>>(I, io);
+        }
         CK(cudaGetLastError());
         if (s->d.model == EP_BI) {
             int iters = 0, conv = 0, flags = 0;
@@ -668,20 +737,30 @@ ep_status step_typed(ep_sim *s, int n_steps, ep_step_stats *stats)
             s->prof.other_ms += ms - (s->prof.sweep_ms - sweep_ms0);
             s->prof.other_launches += 2;
             s->prof.steps += 1;
+            if (ie) {
+                CK(cudaEventElapsedTime(&ms, s->pev[4], s->pev[5]));
+                s->prof.ie_sweep_ms += ms;
+            }
         }
         s->step++;
     }
     CK(cudaMemcpyAsync(&s->ctl_host[1], s->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
-    if (s->ctl_host[1].nonfinite) ret = EP_ENONFINITE;
+    const Ctl &h = s->ctl_host[1];
+    if (h.nonfinite) ret = EP_ENONFINITE;
+    else if (h.noconv && ret == EP_OK) ret = EP_ENOCONV;   // an implicit solve hit its cap or diverged
+    const long long ie_calls = h.ie_total - s->ie_seen;
+    s->ie_seen = h.ie_total;
+    if (s->prof_on) s->prof.ie_sweeps += ie_calls;
     if (stats) {
         stats->iters = last_iters;
         stats->rel_res = last_rr;
-        stats->converged = all_conv;
+        stats->converged = all_conv && !h.noconv;
         stats->total_iters = total;
         stats->step = s->step;
+        stats->ie_total_iters = ie_calls;
     }
-    if (ret == EP_ENOCONV) s->err = "elliptic solve reached max_iter or diverged";
+    if (ret == EP_ENOCONV) s->err = "a solve reached max_iter or diverged";
     if (ret == EP_ENONFINITE) s->err = "non-finite value in the state";
     return ret;
 }
@@ -1064,7 +1143,10 @@ ep_status ep_step_noalloc(ep_sim *s, int n_steps, ep_step_stats *stats)
     s->means = means;
     s->partials = partials;
     s->noalloc_call = true;
+    const long long ie_seen0 = s->ie_seen;
+    s->ie_seen = 0;   // the static control block counts implicit sweeps from zero
     st = s->d.precision == EP_FP64 ? step_typed<double>(s, n_steps, stats) : step_typed<float>(s, n_steps, stats);
+    s->ie_seen = ie_seen0;
     s->ctl = ctl0;
     s->means = means0;
     s->partials = partials0;
@@ -1087,6 +1169,7 @@ void ep_destroy(ep_sim *s)
     if (!s) return;
     if (s->ready && s->stream) cudaStreamSynchronize(s->stream);
     if (s->sweep_graph) cudaGraphExecDestroy(s->sweep_graph);
+    if (s->ie_graph) cudaGraphExecDestroy(s->ie_graph);
     for (auto &e : s->ev)
         if (e) cudaEventDestroy(e);
     for (auto &e : s->pev)
@@ -1178,6 +1261,10 @@ ep_status relayout_segments(ep_sim *s, int zseg)
     if (s->sweep_graph) {
         cudaGraphExecDestroy(s->sweep_graph);
         s->sweep_graph = nullptr;
+    }
+    if (s->ie_graph) {
+        cudaGraphExecDestroy(s->ie_graph);
+        s->ie_graph = nullptr;
     }
     return EP_OK;
 }
@@ -1455,6 +1542,8 @@ ep_status ep_batch_add(ep_batch *b, ep_sim *s, int *slot)
 {
     if (!b || !s || !slot) return EP_EINVAL;
     if (s->d.precision != EP_FP32) return bfail(b, EP_EINVAL, "batched members must be FP32 handles");
+    if (s->have_params && s->p.diffusion != EP_EXPLICIT)
+        return bfail(b, EP_EINVAL, "implicit-diffusion handles are stepped by ep_step only");
     if (b->model >= 0 && s->d.model != b->model)
         return bfail(b, EP_EINVAL, "batched members must share the model (monodomain or bidomain)");
     for (ep_sim *t : b->slot)
@@ -2010,6 +2099,8 @@ ep_status ep_server_submit(ep_server *v, ep_sim *sim, int n_steps, double releas
 {
     if (!v || !sim || !id || n_steps < 1) return EP_EINVAL;
     if (sim->d.precision != EP_FP32) return sfail(v, EP_EINVAL, "served requests must be FP32 handles");
+    if (sim->have_params && sim->p.diffusion != EP_EXPLICIT)
+        return sfail(v, EP_EINVAL, "implicit-diffusion handles are stepped by ep_step only");
     if (!sim->have_mask || !sim->have_params) return sfail(v, EP_ESTATE, "a request needs its mask and parameters set");
     std::lock_guard<std::mutex> lk(v->mu);
     if (v->stop) return sfail(v, EP_ESTATE, "server is shutting down");

@@ -71,6 +71,35 @@ __global__ void k_build_records(int nx, int ny, int nz, const float *fib, const 
     }
 }
 
+// Dhat of tissue voxel (i, j, k) for the operator with sigma_T = sT and
+// sigma_L - sigma_T = dS: the diagonal of L is C Dhat, C = 1 / (8 dx^2).
+__device__ inline double diag_hat(int nx, int ny, int nz, const ushort4 *rec, int i, int j, int k, double sT,
+                                  double dS)
+{
+    double D = 0.0;
+    for (int u = 0; u < 2; ++u)
+        for (int t = 0; t < 2; ++t)
+            for (int s = 0; s < 2; ++s) {
+                int cnt[3], nT;
+                double M[6];
+                bool T[2][2][2];
+                vertex_static(nx, ny, nz, rec, i + s, j + t, k + u, cnt, nT, M, T);
+                // q sits at block offset (1-s, 1-t, 1-u); partner along a flips that offset
+                const int os = 1 - s, ot = 1 - t, ou = 1 - u;
+                double c[3];
+                c[0] = T[ou][ot][1 - os] && cnt[0] ? (os ? 1.0 : -1.0) / cnt[0] : 0.0;
+                c[1] = T[ou][1 - ot][os] && cnt[1] ? (ot ? 1.0 : -1.0) / cnt[1] : 0.0;
+                c[2] = T[1 - ou][ot][os] && cnt[2] ? (ou ? 1.0 : -1.0) / cnt[2] : 0.0;
+                const double iso = sT * nT;
+                const double S[3][3] = {{iso + dS * M[0], dS * M[3], dS * M[4]},
+                                        {dS * M[3], iso + dS * M[1], dS * M[5]},
+                                        {dS * M[4], dS * M[5], iso + dS * M[2]}};
+                for (int x = 0; x < 3; ++x)
+                    for (int y = 0; y < 3; ++y) D += c[x] * S[x][y] * c[y];
+            }
+    return D;
+}
+
 __global__ void k_build_diag(int nx, int ny, int nz, double sT, double dS, const ushort4 *rec,
                              ushort4 *rec_out)
 {
@@ -79,29 +108,23 @@ __global__ void k_build_diag(int nx, int ny, int nz, double sT, double dS, const
         ushort4 r = rec[q];
         if (!rec_tissue(r)) { rec_out[q] = r; continue; }
         const int i = (int)(q % nx), j = (int)((q / nx) % ny), k = (int)(q / ((long long)nx * ny));
-        double D = 0.0;
-        for (int u = 0; u < 2; ++u)
-            for (int t = 0; t < 2; ++t)
-                for (int s = 0; s < 2; ++s) {
-                    int cnt[3], nT;
-                    double M[6];
-                    bool T[2][2][2];
-                    vertex_static(nx, ny, nz, rec, i + s, j + t, k + u, cnt, nT, M, T);
-                    // q sits at block offset (1-s, 1-t, 1-u); partner along a flips that offset
-                    const int os = 1 - s, ot = 1 - t, ou = 1 - u;
-                    double c[3];
-                    c[0] = T[ou][ot][1 - os] && cnt[0] ? (os ? 1.0 : -1.0) / cnt[0] : 0.0;
-                    c[1] = T[ou][1 - ot][os] && cnt[1] ? (ot ? 1.0 : -1.0) / cnt[1] : 0.0;
-                    c[2] = T[1 - ou][ot][os] && cnt[2] ? (ou ? 1.0 : -1.0) / cnt[2] : 0.0;
-                    const double iso = sT * nT;
-                    const double S[3][3] = {{iso + dS * M[0], dS * M[3], dS * M[4]},
-                                            {dS * M[3], iso + dS * M[1], dS * M[5]},
-                                            {dS * M[4], dS * M[5], iso + dS * M[2]}};
-                    for (int x = 0; x < 3; ++x)
-                        for (int y = 0; y < 3; ++y) D += c[x] * S[x][y] * c[y];
-                }
+        const double D = diag_hat(nx, ny, nz, rec, i, j, k, sT, dS);
         r.w = D > 0.0 ? __half_as_ushort(__float2half_rn((float)(1.0 / D))) : (unsigned short)0;
         rec_out[q] = r;
+    }
+}
+
+// Implicit-Euler Jacobi (Eq. iejac1): inv_q = 1 / (1 + a C Dhat_q) for the
+// intracellular operator on the tissue, 0 elsewhere.
+template <typename real>
+__global__ void k_build_ie_diag(int nx, int ny, int nz, double sT, double dS, double aC, const ushort4 *rec,
+                                real *inv)
+{
+    const long long n = (long long)nx * ny * nz;
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
+        if (!rec_tissue(rec[q])) { inv[q] = real(0); continue; }
+        const int i = (int)(q % nx), j = (int)((q / nx) % ny), k = (int)(q / ((long long)nx * ny));
+        inv[q] = (real)(1.0 / (1.0 + aC * diag_hat(nx, ny, nz, rec, i, j, k, sT, dS)));
     }
 }
 
@@ -229,6 +252,94 @@ __device__ __forceinline__ void comp_subtract_item(const Inst<real> &I, int item
         if (!(t == t) || isinf(t)) ctl->nonfinite = 1;
         __threadfence();
     }
+}
+
+// ---------------------------------------------------------------------------
+// Implicit-Euler diffusion (Sec. "Implicit Euler", Eq. iejac1).
+// ---------------------------------------------------------------------------
+
+// Monodomain: the reaction alone, one thread per tissue voxel of the list:
+// f = v* (right-hand side, in b), first iterate v* (in the new v buffer), w+.
+template <typename real>
+__global__ void __launch_bounds__(kRedThreads) k_ie_react(Inst<real> I)
+{
+    const long long step = I.ctl->step;
+    const int cur = (int)(step & 1);
+    const double tn = (double)step * I.dt_d;
+    const real *v = I.v[cur], *w = I.w[cur];
+    real *vn = I.v[cur ^ 1], *wn = I.w[cur ^ 1];
+    const long long nt = (long long)I.chunks[I.nchunk - 1].end;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nt; i += (long long)gridDim.x * blockDim.x) {
+        const int q = I.idx[i];
+        const int x = q % I.nx, y = (q / I.nx) % I.ny, z = q / (I.nx * I.ny);
+        real vs, ws;
+        ms_step(I, tn, v[q], w[q], x, y, z, vs, ws);
+        I.b[q] = vs;
+        vn[q] = vs;
+        wn[q] = ws;
+    }
+}
+
+// Start of an implicit solve: ||f||^2 over the tissue chunks (FP64, fixed
+// order); the item that completes the launch resets the solve in the
+// control block.
+template <typename real>
+__global__ void __launch_bounds__(kRedThreads) k_ie_start(Inst<real> I)
+{
+    __shared__ RedSmem sm;
+    Ctl *ctl = I.ctl;
+    const Chunk ch = I.chunks[blockIdx.x];
+    double s = 0.0;
+    for (int i = ch.start + threadIdx.x; i < ch.end; i += kRedThreads) {
+        const double f = (double)I.b[I.idx[i]];
+        s += f * f;
+    }
+    s = block_sum<kRedThreads>(s, sm.sred);
+    if (threadIdx.x == 0) I.partials[blockIdx.x] = s;
+    if (!arrive_last(ctl, gridDim.x, &sm.sflag)) return;
+    double t = 0.0;
+    for (int i = threadIdx.x; i < (int)gridDim.x; i += kRedThreads) t += ((volatile double *)I.partials)[i];
+    t = block_sum<kRedThreads>(t, sm.sred);
+    if (threadIdx.x == 0) {
+        ctl->arrive = 0;
+        ctl->bnorm2 = t;
+        ctl->thresh2 = I.rel_tol2 * t;
+        ctl->sweep = 0;
+        ctl->jarrive = 0;
+        ctl->iters = 0;
+        ctl->converged = (t == 0.0);
+        ctl->diverged = 0;
+        ctl->rnorm2 = 0.0;
+        ctl->done = (t == 0.0) || !(t == t) || isinf(t);
+        if (!(t == t) || isinf(t)) ctl->nonfinite = 1;
+        __threadfence();
+    }
+}
+
+// End of an implicit solve: the final iterate (in ie_x after an odd number of
+// sweeps) becomes v of the new step; activation times (first upward crossing
+// of 0.5, linear in t) and the non-finite flag as in the explicit step.
+template <typename real>
+__global__ void __launch_bounds__(kRedThreads) k_ie_finish(Inst<real> I)
+{
+    Ctl *ctl = I.ctl;
+    const long long step = ctl->step;
+    const int cur = (int)(step & 1);
+    const int iters = ctl->iters;
+    const double tn = (double)step * I.dt_d;
+    const real *vold = I.v[cur];
+    real *vnew = I.v[cur ^ 1];
+    const long long nt = (long long)I.chunks[I.nchunk - 1].end;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nt; i += (long long)gridDim.x * blockDim.x) {
+        const int q = I.idx[i];
+        const real v1 = (iters & 1) ? I.ie_x[q] : vnew[q];
+        if (iters & 1) vnew[q] = v1;
+        const real v0 = vold[q];
+        if (v0 < real(0.5) && v1 >= real(0.5) && I.tact[q] < real(0))
+            I.tact[q] = (real)(tn + I.dt_d * (0.5 - (double)v0) / ((double)v1 - (double)v0));
+        if (!isfinite((double)v1)) atomicOr(&ctl->nonfinite, 1);
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) ctl->ie_total += iters;
 }
 
 // v_e <- x_final - means[comp] (written to x0, the warm start of the next solve).

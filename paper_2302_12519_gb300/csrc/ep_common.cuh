@@ -28,7 +28,14 @@ constexpr unsigned short kNonTissue = 0xBC00u;  // fp16 -1.0: record lane 3 of a
 constexpr int kRedThreads = 256;            // reduction kernels
 constexpr int kChunk = 2048;                // tissue voxels per reduction chunk
 
-enum Mode { M_APPLY = 0, M_RHS = 1, M_PAR_MONO = 2, M_PAR_BI = 3, M_JAC = 4 };
+// M_IE_RHS: reaction plus f = v* - a L_i ve of the implicit bidomain step;
+// M_IE: one Jacobi sweep of (I + a L_i) x = f (Eq. iejac1).
+enum Mode { M_APPLY = 0, M_RHS = 1, M_PAR_MONO = 2, M_PAR_BI = 3, M_JAC = 4, M_IE_RHS = 5, M_IE = 6 };
+enum Diffusion { DIFF_EXPLICIT = 0, DIFF_IMPLICIT = 1 };
+
+// Modes that run a solve sweep (Jacobi of the elliptic or the implicit parabolic system).
+template <int MODE>
+constexpr bool kSweep = MODE == M_JAC || MODE == M_IE;
 enum Model { MODEL_MONO = 0, MODEL_BI = 1 };
 
 // One stencil work item: voxel columns x in [x0, x0 + 30), rows
@@ -67,6 +74,7 @@ struct Ctl {
     // starts, every item of sweeps < j has arrived and fewer than nitems of sweep j have, so
     // jarrive / nitems = j; sweeps that do not check the residual only add to it
     unsigned long long jarrive;
+    long long ie_total;   // sweeps of the implicit parabolic solves, summed over steps
 };
 
 struct Chunk {
@@ -101,6 +109,12 @@ struct Inst {
     real dt, inv_tin, inv_tout, inv_topen, inv_tclose, vgate;
     double dt_d, rel_tol2, div_factor;
     StimSet stim;
+    // implicit-Euler diffusion (diffusion == DIFF_IMPLICIT): second iterate buffer,
+    // 1 / (1 + a D_i) per voxel and a = dt/K (times lambda/(1+lambda) for the monodomain)
+    int diffusion, pad2;
+    real *ie_x;
+    const real *ie_inv;
+    real alpha_ie;
 };
 
 __device__ __forceinline__ float h2f(unsigned short b) { return __half2float(__ushort_as_half(b)); }

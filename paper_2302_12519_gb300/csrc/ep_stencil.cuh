@@ -63,7 +63,9 @@ template <typename real>
 struct Op {
     const ushort4 *rec;
     const real *src, *w, *ve, *b;   // loads
-    real *out, *wout, *tact;        // stores (PAR: v, w, t_act; RHS: b; APPLY: out; JAC: next iterate)
+    const real *inv;                // implicit sweep: 1 / (1 + a D_i)
+    real *out, *wout, *tact;        // stores (PAR: v, w, t_act; RHS: b; APPLY: out; JAC, IE: next iterate;
+    real *out2;                     //         IE_RHS: f, w, and v* in out2)
     real sT, dS, C, coef;
     double tn, dt_d;
     int nz;
@@ -76,7 +78,8 @@ struct Ld {
     real uLo, uHi;
     real wLo, wHi;     // PAR
     real veLo, veHi;   // PAR_BI
-    real bLo;          // JAC
+    real bLo;          // JAC: b; IE: f
+    real iLo;          // IE: 1 / (1 + a D_i)
 };
 
 // What the next plane needs from this one.
@@ -100,22 +103,22 @@ __device__ __forceinline__ void load_plane(const Op<real> &o, int k, bool lo_in,
 {
     const bool kin = (unsigned)k < (unsigned)o.nz;
     L.rLo = L.rHi = make_uint2(0u, (unsigned)kNonTissue << 16);
-    L.uLo = L.uHi = L.veLo = L.veHi = L.bLo = real(0);
+    L.uLo = L.uHi = L.veLo = L.veHi = L.bLo = L.iLo = real(0);
     L.wLo = L.wHi = real(1);
     if (kin && lo_in) {
         const int q = qlo + k * plane;
         L.rLo = __ldg(reinterpret_cast<const uint2 *>(o.rec) + q);
         L.uLo = __ldg(o.src + q);
-        if (MODE == M_PAR_MONO || MODE == M_PAR_BI) L.wLo = __ldg(o.w + q);
-        if (MODE == M_PAR_BI) L.veLo = __ldg(o.ve + q);
+        if (MODE == M_PAR_MONO || MODE == M_PAR_BI || MODE == M_IE_RHS) L.wLo = __ldg(o.w + q);
+        if (MODE == M_PAR_BI || MODE == M_IE_RHS) L.veLo = __ldg(o.ve + q);
         if (MODE == M_JAC) L.bLo = __ldg(o.b + q);
     }
     if (kin && hi_in) {
         const int q = qhi + k * plane;
         L.rHi = __ldg(reinterpret_cast<const uint2 *>(o.rec) + q);
         L.uHi = __ldg(o.src + q);
-        if (MODE == M_PAR_MONO || MODE == M_PAR_BI) L.wHi = __ldg(o.w + q);
-        if (MODE == M_PAR_BI) L.veHi = __ldg(o.ve + q);
+        if (MODE == M_PAR_MONO || MODE == M_PAR_BI || MODE == M_IE_RHS) L.wHi = __ldg(o.w + q);
+        if (MODE == M_PAR_BI || MODE == M_IE_RHS) L.veHi = __ldg(o.ve + q);
     }
 }
 
@@ -141,17 +144,23 @@ __device__ __forceinline__ void plane_step(const Inst<real> &I, const Op<real> &
     const real fhi0 = (real)ahi.x, fhi1 = (real)ahi.y, fhi2 = (real)bhi.x;
     real ulo, uhi;
     C.e0 = C.e1 = C.e2 = real(0);
-    if (MODE == M_PAR_MONO || MODE == M_PAR_BI) {
+    if (MODE == M_PAR_MONO || MODE == M_PAR_BI || MODE == M_IE_RHS) {
         real vs, wn, vs2, wn2;
         ms_step(I, o.tn, L.uLo, L.wLo, g.x, g.ylo, k, vs, wn);
         ms_step(I, o.tn, L.uHi, L.wHi, g.x, g.ylo + 1, k, vs2, wn2);
-        ulo = tlo ? ((MODE == M_PAR_BI) ? vs + L.veLo : vs) : real(0);
-        uhi = thi ? ((MODE == M_PAR_BI) ? vs2 + L.veHi : vs2) : real(0);
+        if (MODE == M_IE_RHS) {   // the stencil acts on ve alone
+            ulo = tlo ? L.veLo : real(0);
+            uhi = thi ? L.veHi : real(0);
+        } else {
+            ulo = tlo ? ((MODE == M_PAR_BI) ? vs + L.veLo : vs) : real(0);
+            uhi = thi ? ((MODE == M_PAR_BI) ? vs2 + L.veHi : vs2) : real(0);
+        }
         C.e0 = vs; C.e1 = wn; C.e2 = L.uLo;
     } else {
         ulo = tlo ? L.uLo : real(0);
         uhi = thi ? L.uHi : real(0);
         if (MODE == M_JAC) { C.e0 = L.bLo; C.e1 = (real)blo.y; }
+        if (MODE == M_IE) { C.e0 = L.bLo; C.e1 = L.iLo; }
     }
     C.uLo = ulo;
     C.uHi = uhi;
@@ -239,6 +248,14 @@ __device__ __forceinline__ void plane_step(const Inst<real> &I, const Op<real> &
                 const real r = P.e0 - Lu;
                 o.out[q] = P.uLo + o.coef * P.e1 * r;
                 if (check) acc += (float)r * (float)r;
+            } else if (MODE == M_IE) {   // r = f - (I + a L) x;  x+ = x + r / (1 + a D)  (Eq. iejac1)
+                const real r = P.e0 - P.uLo - o.coef * Lu;
+                o.out[q] = P.uLo + P.e1 * r;
+                if (check) acc += (float)r * (float)r;
+            } else if (MODE == M_IE_RHS) {
+                o.out[q] = P.e0 - o.coef * Lu;   // f = v* - a L_i ve
+                o.out2[q] = P.e0;                // first iterate: v*
+                o.wout[q] = P.e1;
             } else {
                 const real vnew = P.e0 - o.coef * Lu;
                 o.out[q] = vnew;
@@ -272,12 +289,13 @@ __device__ __forceinline__ void zero_state(St<real> &S)
 // barrier, and the prefetched planes hold no registers.  The other modes run
 // once per step and prefetch one plane into registers.
 template <int MODE>
-constexpr bool kRinged = MODE == M_JAC || MODE == M_PAR_MONO;
+constexpr bool kRinged = MODE == M_JAC || MODE == M_IE || MODE == M_PAR_MONO;
 
 template <typename real, int MODE>
 struct Ring {
     static constexpr int D = sizeof(real) == 4 ? 4 : 2;   // divides the unroll of 4; static smem < 48 KB
-    static constexpr int NX = MODE == M_JAC ? 1 : 2;      // b of row lo (Jacobi) or w of rows lo, hi
+    static constexpr int NX = MODE == M_JAC ? 1 : 2;      // b of row lo (Jacobi), f and 1/(1+aD) of row lo
+                                                          // (implicit sweep) or w of rows lo, hi
     uint2 rec[D][2][kThreads];   // fp16 records of rows lo / hi
     real u[D][2][kThreads];
     real x[D][NX][kThreads];
@@ -315,11 +333,13 @@ __device__ __forceinline__ void ring_issue(const Op<real> &o, Ring<real, MODE> &
         const int q = qlo + k * plane;
         cp_async_n<8>(&R.rec[slot][0][t], o.rec + q);
         cp_async_n<sizeof(real)>(&R.u[slot][0][t], o.src + q);
-        cp_async_n<sizeof(real)>(&R.x[slot][0][t], (MODE == M_JAC ? o.b : o.w) + q);
+        cp_async_n<sizeof(real)>(&R.x[slot][0][t], (MODE == M_PAR_MONO ? o.w : o.b) + q);
+        if (MODE == M_IE) cp_async_n<sizeof(real)>(&R.x[slot][1][t], o.inv + q);
     } else {
         R.rec[slot][0][t] = make_uint2(0u, (unsigned)kNonTissue << 16);
         R.u[slot][0][t] = real(0);
-        R.x[slot][0][t] = MODE == M_JAC ? real(0) : real(1);
+        R.x[slot][0][t] = MODE == M_PAR_MONO ? real(1) : real(0);
+        if (MODE == M_IE) R.x[slot][1][t] = real(0);
     }
     if (kin && hi_in) {
         const int q = qhi + k * plane;
@@ -341,8 +361,9 @@ __device__ __forceinline__ void ring_read(const Ring<real, MODE> &R, int slot, L
     L.rHi = R.rec[slot][1][t];
     L.uLo = R.u[slot][0][t];
     L.uHi = R.u[slot][1][t];
-    if (MODE == M_JAC) {
+    if (MODE == M_JAC || MODE == M_IE) {
         L.bLo = R.x[slot][0][t];
+        L.iLo = MODE == M_IE ? R.x[slot][1][t] : real(0);
         L.wLo = L.wHi = real(1);
     } else {
         L.bLo = real(0);
@@ -383,15 +404,15 @@ __device__ __forceinline__ void stencil_item(const Inst<real> &I, int seg_index,
     o.rec = I.rec;
     o.nz = I.nz;
     o.C = I.C;
-    o.w = o.ve = o.b = nullptr;
-    o.out = o.wout = o.tact = nullptr;
+    o.w = o.ve = o.b = o.inv = nullptr;
+    o.out = o.wout = o.tact = o.out2 = nullptr;
     o.tn = 0.0;
     o.dt_d = I.dt_d;
     int sweep = 0;
     bool check = false;
     const long long step = (MODE == M_APPLY) ? 0 : ctl->step;
     const int cur = (int)(step & 1);
-    if (MODE == M_JAC) {
+    if (kSweep<MODE>) {
         sweep = (int)(*(volatile unsigned long long *)&ctl->jarrive / (unsigned long long)nitems);
         if (sweep >= I.max_iter) {   // sweep cap reached: the solve ends with the last iterate
             if (threadIdx.x == 0) {
@@ -402,11 +423,27 @@ __device__ __forceinline__ void stencil_item(const Inst<real> &I, int seg_index,
             }
             return;
         }
-        o.src = (sweep & 1) ? I.x1 : I.x0;
-        o.out = (sweep & 1) ? I.x0 : I.x1;
+        if (MODE == M_JAC) {
+            o.src = (sweep & 1) ? I.x1 : I.x0;
+            o.out = (sweep & 1) ? I.x0 : I.x1;
+            o.sT = I.sTie; o.dS = I.dSie; o.coef = I.coef_jac;
+        } else {   // implicit sweep: iterates in the new v buffer and ie_x
+            o.src = (sweep & 1) ? I.ie_x : I.v[cur ^ 1];
+            o.out = (sweep & 1) ? I.v[cur ^ 1] : I.ie_x;
+            o.inv = I.ie_inv;
+            o.sT = I.sTi; o.dS = I.dSi; o.coef = I.alpha_ie;
+        }
         o.b = I.b;
-        o.sT = I.sTie; o.dS = I.dSie; o.coef = I.coef_jac;
         check = (sweep % I.check_every) == 0;
+    } else if (MODE == M_IE_RHS) {
+        o.src = I.v[cur];
+        o.w = I.w[cur];
+        o.ve = I.x0;
+        o.out = I.b;
+        o.out2 = I.v[cur ^ 1];
+        o.wout = I.w[cur ^ 1];
+        o.sT = I.sTi; o.dS = I.dSi; o.coef = I.alpha_ie;
+        o.tn = (double)step * I.dt_d;
     } else if (MODE == M_RHS) {
         o.src = I.v[cur ^ 1];        // v of step n + 1 (the step counter moves at the end of the step)
         o.out = I.b;
@@ -480,7 +517,7 @@ __device__ __forceinline__ void stencil_item(const Inst<real> &I, int seg_index,
         }
     }
 
-    if (MODE == M_JAC) {
+    if (kSweep<MODE>) {
         if (!check) {   // count the arrival; nobody waits on it within this launch
             if (threadIdx.x == 0) atomicAdd(&ctl->jarrive, 1ull);
             return;
@@ -524,7 +561,7 @@ template <typename real, int MODE>
 __global__ void __launch_bounds__(kThreads, kMinBlocks) k_stencil(Inst<real> I, ApplyIO<real> io)
 {
     __shared__ StencilSmem<real, MODE> sm;
-    if (MODE == M_JAC && I.ctl->done) return;   // converged earlier: queued sweeps are no-ops
+    if (kSweep<MODE> && I.ctl->done) return;   // converged earlier: queued sweeps are no-ops
     stencil_item<real, MODE>(I, blockIdx.x, blockIdx.x, gridDim.x, &io, sm);
 }
 

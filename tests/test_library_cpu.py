@@ -138,3 +138,23 @@ def test_server_needs_a_device(lib):
     assert lib.ep_server_create(ctypes.byref(cfg), ctypes.byref(srv)) == ep.EP_ECUDA
     cfg.max_slots = 0
     assert lib.ep_server_create(ctypes.byref(cfg), ctypes.byref(srv)) == ep.EP_EINVAL
+
+
+def test_diffusion_scheme_is_validated(lib):
+    import workloads as W
+    s = ep.Sim(4, 4, 4, 0.5, use_torch=False)
+    p = W.Params()
+    p.diffusion = 2
+    with pytest.raises(ep.EPError) as e:
+        s.set_params(p)
+    assert e.value.status == ep.EP_EINVAL and "diffusion" in str(e.value)
+    p.diffusion = ep.EP_IMPLICIT
+    s.set_params(p)
+    # the implicit scheme's two extra fields show in the planned footprint
+    s.set_mask(np.ones(s.n, np.uint8))
+    r_ie, _ = s.footprint()
+    p.diffusion = ep.EP_EXPLICIT
+    s.set_params(p)
+    r_ex, _ = s.footprint()
+    assert r_ie - r_ex == 2 * 4 * s.n
+    s.close()
