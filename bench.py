@@ -43,7 +43,8 @@ def _args():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["config2", "config1", "config3", "config4", "slab"], default="config2")
+    ap.add_argument("--workload", choices=["config2", "config0", "config1", "config3", "config4", "slab"],
+                    default="config2")
     ap.add_argument("--model", choices=["mono", "bi"], default="mono", help="slab: model")
     ap.add_argument("--slab-n", type=int, default=512, help="slab: voxels per side")
     ap.add_argument("--diffusion", choices=["explicit", "implicit"], default="explicit",
@@ -77,6 +78,10 @@ def _workload_case(name, model, slab_n):
         c = W.slab(slab_n, W.BI if bi else W.MONO, unequal=bi)
         desc = (f"slab{slab_n}: {'bidomain (sigma_eT 0.10)' if bi else 'monodomain'} FP32, dense all-tissue "
                 f"{slab_n}^3 slab, fibres rotating -60..+60 deg through z, dx 0.5 mm")
+        return c, desc
+    if name == "config0":
+        c = W.config0()
+        desc = "config0: monodomain FP64, 32^3 all-tissue slab, dx 0.25 mm, dt 0.01 ms (latency-bound, L2-resident)"
         return c, desc
     if name == "config1":
         c = W.config1()
@@ -327,8 +332,10 @@ def run_ours(a):
     elif mono:
         # the fused reaction + diffusion launch is the step (plus a one-thread step-counter kernel)
         launch_s = prof.other_ms / 1e3 / max(prof.steps, 1)
-        alg_bytes = BYTES_PER_MONO_VOXEL * M
-        kname, share = "k_stencil<float,M_PAR_MONO> (fused reaction + diffusion)", prof.other_ms / 1e3 / total_s
+        # v, w read and written at the state precision, fibre 6, mask 1
+        alg_bytes = (BYTES_PER_MONO_VOXEL if case.precision == 0 else 4 * 8 + 7) * M
+        kname = "k_stencil<%s,M_PAR_MONO> (fused reaction + diffusion)" % ("float" if case.precision == 0 else "double")
+        share = prof.other_ms / 1e3 / total_s
     else:
         sweep_s = prof.sweep_ms / 1e3
         launch_s = sweep_s / max(prof.sweeps, 1)
@@ -375,8 +382,8 @@ def run_ours(a):
     if rank == 0:
         line = {"metric": "voxel-steps/sec", "value": value, "unit": "tissue voxel-steps/s", "n_gpus": world,
                 "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1e3 * total_s / a.steps,
-                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-                "data": "synthetic",
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f32" if case.precision == 0 else "f64", "data": "synthetic",
                 "config": {"workload": desc, "grid": [case.nx, case.ny, case.nz], "tissue_voxels": M,
                            "dt_ms": case.params.dt, "rel_tol": case.params.rel_tol,
                            "window": f"steps {a.warmup}..{a.warmup + a.steps - 1} from rest, stimulus at t=0",
