@@ -177,6 +177,24 @@ def _dist():
     return world, rank, local
 
 
+def max_over_ranks(seconds, dist):
+    """The slowest rank's time (replicas: the job ends when the last one does),
+    then a barrier; NCCL reduces on the GPU, gloo on the host."""
+    import torch
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(seconds)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.barrier()
+    return float(t.item())
+
+
+def replica_rate(world, tissue_voxels, steps, seconds):
+    """Whole-job tissue voxel-steps/s of `world` independent replicas that
+    each advance `tissue_voxels` voxels `steps` steps in `seconds` (the max
+    over ranks)."""
+    return world * tissue_voxels * steps / seconds
+
+
 def _solves_per_step(case):
     """Jacobi solves in one step: the elliptic one (bidomain) and the implicit
     parabolic one (implicit diffusion)."""
@@ -313,11 +331,8 @@ def run_ours(a):
     prof = sim.profile()
     total_s = sum(ms) / 1e3
     if dist is not None:
-        t = torch.tensor([total_s], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_s = float(t.item())
-        dist.barrier()
-    value = world * M * a.steps / total_s
+        total_s = max_over_ranks(total_s, dist)
+    value = replica_rate(world, M, a.steps, total_s)
 
     # roofline of the dominant kernel (Jacobi sweep)
     peaks = _peaks()
