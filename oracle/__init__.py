@@ -50,7 +50,8 @@ class _Params(ctypes.Structure):
                 ("tau_in", "tau_out", "tau_open", "tau_close", "v_gate",
                  "sig_iL", "sig_iT", "sig_eL", "sig_eT", "lam", "K", "dt", "omega", "rel_tol")] + \
                [("check_every", ctypes.c_int), ("max_iter", ctypes.c_int), ("model", ctypes.c_int),
-                ("diffusion", ctypes.c_int)]
+                ("diffusion", ctypes.c_int), ("solver", ctypes.c_int),
+                ("cheb_lmin", ctypes.c_double), ("cheb_lmax", ctypes.c_double)]
 
 
 class _Stim(ctypes.Structure):
@@ -74,6 +75,9 @@ def lib():
         L.og_ie_jacobi.argtypes = [ctypes.POINTER(_Grid), dp, dp, dp, vp, vp, dp, ip, ip,
                                    ctypes.POINTER(ip), ctypes.POINTER(dp)]
         L.og_ie_jacobi.restype = ip
+        L.og_chebyshev.argtypes = [ctypes.POINTER(_Grid), dp, dp, vp, vp, dp, dp, dp, ip, ip,
+                                   ctypes.POINTER(ip), ctypes.POINTER(dp)]
+        L.og_chebyshev.restype = ip
         L.og_default_omega.argtypes = [dp, dp]
         L.og_default_omega.restype = dp
         L.og_create.argtypes = [ip, ip, ip, dp, vp, vp, ctypes.POINTER(_Params),
@@ -144,6 +148,16 @@ class Grid:
                              max_iter, ctypes.byref(it), ctypes.byref(rr))
         return x, it.value, rr.value, st
 
+    def chebyshev(self, sL, sT, b, x0, lmin, lmax, tol=1e-6, m=10, max_iter=100000):
+        """Chebyshev-accelerated Jacobi for L x = b with D^-1 L's interval [lmin, lmax]."""
+        b = np.ascontiguousarray(np.asarray(b, dtype=np.float64).reshape(-1))
+        x = np.ascontiguousarray(np.array(x0, dtype=np.float64).reshape(-1))
+        it = ctypes.c_int(0)
+        rr = ctypes.c_double(0.0)
+        st = lib().og_chebyshev(ctypes.byref(self._g), sL, sT, _ptr(b), _ptr(x), lmin, lmax, tol, m, max_iter,
+                                ctypes.byref(it), ctypes.byref(rr))
+        return x, it.value, rr.value, st
+
     def ie_jacobi(self, sL, sT, alpha, f, x0, tol=1e-6, m=10, max_iter=100000):
         """Implicit-Euler Jacobi (Eq. iejac1) for (I + alpha L) x = f."""
         f = np.ascontiguousarray(np.asarray(f, dtype=np.float64).reshape(-1))
@@ -159,7 +173,8 @@ def _params_struct(p, model: int) -> _Params:
     return _Params(p.tau_in, p.tau_out, p.tau_open, p.tau_close, p.v_gate,
                    p.sig_iL, p.sig_iT, p.sig_eL, p.sig_eT, p.lam, p.K, p.dt, p.omega,
                    p.rel_tol, int(p.check_every), int(p.max_iter), int(model),
-                   int(getattr(p, "diffusion", 0)))
+                   int(getattr(p, "diffusion", 0)), int(getattr(p, "solver", 0)),
+                   float(getattr(p, "cheb_lmin", 0.0)), float(getattr(p, "cheb_lmax", 0.0)))
 
 
 class Sim:

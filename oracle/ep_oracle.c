@@ -428,6 +428,83 @@ int og_ie_jacobi(const og_grid *g, double sL, double sT, double alpha, const dou
     return status;
 }
 
+/* Chebyshev semi-iterative acceleration of the Jacobi iteration (not in the
+ * thesis: its faster-solver future work; the method is Golub and Varga's,
+ * 1961, as stated in Varga, "Matrix Iterative Analysis", Ch. 5).  For
+ * A x = b with A = L_{sL,sT}, D = diag(A) and the eigenvalues of D^-1 A that
+ * matter in [lmin, lmax], the basic step y -> y + tau D^-1 (b - A y),
+ * tau = 2 / (lmin + lmax), has spectral radius rho = (lmax - lmin) / (lmax +
+ * lmin) on that interval, and the semi-iteration is
+ *   y_{k+1} = w_{k+1} (y_k + tau D^-1 (b - A y_k) - y_{k-1}) + y_{k-1},
+ *   w_1 = 1,  w_2 = 2 / (2 - rho^2),  w_{k+1} = 1 / (1 - rho^2 w_k / 4).
+ * Eigenvalue 0 (constants per component) is left alone, as in Jacobi.  Stop
+ * rule and cap as og_jacobi. */
+int og_chebyshev(const og_grid *g, double sL, double sT, const double *b, double *x, double lmin, double lmax,
+                 double tol, int m, int max_iter, int *iters, double *relres)
+{
+    long n = (long)g->nx * g->ny * g->nz, q;
+    double *diag = (double *)malloc(sizeof(double) * (size_t)n);
+    double *Ax = (double *)malloc(sizeof(double) * (size_t)n);
+    double *prev = (double *)malloc(sizeof(double) * (size_t)n);
+    double nb = 0.0, nr = 0.0, w = 1.0;
+    const double tau = 2.0 / (lmin + lmax), rho = (lmax - lmin) / (lmax + lmin);
+    int k = 0, status = 1;
+    for (q = 0; q < n; q++) {
+        prev[q] = x[q];
+        if (g->mask[q])
+            nb += b[q] * b[q];
+    }
+    nb = sqrt(nb);
+    *relres = 0.0;
+    if (nb == 0.0) {
+        *iters = 0;
+        free(diag);
+        free(Ax);
+        free(prev);
+        return 0;
+    }
+    if (m < 1)
+        m = 1;
+    og_diag_L(g, sL, sT, diag);
+    for (k = 0; k < max_iter; k++) {
+        /* weight of this step: w_1 = 1, w_2 = 2 / (2 - rho^2), then the recurrence */
+        if (k == 0)
+            w = 1.0;
+        else if (k == 1)
+            w = 2.0 / (2.0 - rho * rho);
+        else
+            w = 1.0 / (1.0 - rho * rho * w / 4.0);
+        og_apply_L(g, sL, sT, x, Ax);
+        int check = (k % m) == 0;
+        if (check)
+            nr = 0.0;
+        for (q = 0; q < n; q++) {
+            if (!g->mask[q])
+                continue;
+            double r = b[q] - Ax[q];
+            if (check)
+                nr += r * r;
+            double basic = diag[q] > 0.0 ? x[q] + tau * r / diag[q] : x[q];
+            double next = w * (basic - prev[q]) + prev[q];
+            prev[q] = x[q];
+            x[q] = next;
+        }
+        if (check) {
+            *relres = sqrt(nr) / nb;
+            if (*relres <= tol) {
+                status = 0;
+                k++;
+                break;
+            }
+        }
+    }
+    *iters = k;
+    free(diag);
+    free(Ax);
+    free(prev);
+    return status;
+}
+
 /* ------------------------------------------------------------------------ */
 /* time stepping                                                            */
 /* ------------------------------------------------------------------------ */
@@ -625,8 +702,12 @@ int og_step(og_sim *s, int *iters, double *relres)
         for (q = 0; q < n; q++)
             s->b[q] = s->mask[q] ? -s->b[q] : 0.0;
         og_project(n, s->ncomp, s->comp, s->b);
-        status = og_jacobi(g, p->sig_iL + p->sig_eL, p->sig_iT + p->sig_eT, s->b, s->ve,
-                           p->omega, p->rel_tol, p->check_every, p->max_iter, iters, relres);
+        if (p->solver == OG_CHEBYSHEV)
+            status = og_chebyshev(g, p->sig_iL + p->sig_eL, p->sig_iT + p->sig_eT, s->b, s->ve, p->cheb_lmin,
+                                  p->cheb_lmax, p->rel_tol, p->check_every, p->max_iter, iters, relres);
+        else
+            status = og_jacobi(g, p->sig_iL + p->sig_eL, p->sig_iT + p->sig_eT, s->b, s->ve,
+                               p->omega, p->rel_tol, p->check_every, p->max_iter, iters, relres);
         og_project(n, s->ncomp, s->comp, s->ve);
         s->total_iters += *iters;
     }

@@ -25,7 +25,12 @@ typedef struct {
     double lam, K, dt, omega, rel_tol;
     int check_every, max_iter, model;
     int diffusion;              /* OG_EXPLICIT or OG_IMPLICIT (Eq. iejac1) */
+    int solver;                 /* elliptic solve: OG_JACOBI (Eq. dampjac1) or OG_CHEBYSHEV */
+    double cheb_lmin, cheb_lmax;   /* spectral interval of D^-1 A for OG_CHEBYSHEV */
 } og_params;
+
+#define OG_JACOBI 0
+#define OG_CHEBYSHEV 1
 
 #define OG_EXPLICIT 0
 #define OG_IMPLICIT 1
@@ -44,6 +49,8 @@ double og_default_omega(double sL, double sT);
 int og_jacobi(const og_grid *g, double sL, double sT, const double *b, double *x,
               double omega, double tol, int m, int max_iter, int *iters, double *relres);
 int og_ie_jacobi(const og_grid *g, double sL, double sT, double alpha, const double *f, double *x,
+                 double tol, int m, int max_iter, int *iters, double *relres);
+int og_chebyshev(const og_grid *g, double sL, double sT, const double *b, double *x, double lmin, double lmax,
                  double tol, int m, int max_iter, int *iters, double *relres);
 
 og_sim *og_create(int nx, int ny, int nz, double dx, const unsigned char *mask,

@@ -75,6 +75,9 @@ class Params:
     check_every: int = 10     # residual check interval (sweeps)
     max_iter: int = 100000    # sweep cap per solve
     diffusion: int = 0        # 0 explicit Euler, 1 implicit Euler (Eq. iejac1)
+    solver: int = 0           # elliptic solve: 0 damped Jacobi (Eq. dampjac1), 1 Chebyshev-accelerated Jacobi
+    cheb_lmin: float = 0.0    # spectral interval of D^-1 A for the Chebyshev solver (<= 0: estimated)
+    cheb_lmax: float = 0.0
 
 
 @dataclasses.dataclass
