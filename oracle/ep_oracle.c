@@ -485,7 +485,7 @@ int og_chebyshev(const og_grid *g, double sL, double sT, const double *b, double
             if (check)
                 nr += r * r;
             double basic = diag[q] > 0.0 ? x[q] + tau * r / diag[q] : x[q];
-            double next = w * (basic - prev[q]) + prev[q];
+            double next = k == 0 ? basic : w * (basic - prev[q]) + prev[q];   /* y_1 = G y_0 + g */
             prev[q] = x[q];
             x[q] = next;
         }
