@@ -47,6 +47,8 @@ def _args():
                     default="config2")
     ap.add_argument("--model", choices=["mono", "bi"], default="mono", help="slab: model")
     ap.add_argument("--slab-n", type=int, default=512, help="slab: voxels per side")
+    ap.add_argument("--solver", choices=["jacobi", "chebyshev"], default="jacobi",
+                    help="elliptic solve: the paper's damped Jacobi, or Chebyshev-accelerated Jacobi")
     ap.add_argument("--diffusion", choices=["explicit", "implicit"], default="explicit",
                     help="parabolic step: explicit Euler, or implicit Euler solved by Jacobi (Eq. iejac1)")
     ap.add_argument("--instances", type=int, default=64, help="config3: number of instances")
@@ -63,11 +65,14 @@ def _args():
     return ap.parse_args()
 
 
-def _workload(name, model="mono", slab_n=512, diffusion="explicit"):
+def _workload(name, model="mono", slab_n=512, diffusion="explicit", solver="jacobi"):
     c, desc = _workload_case(name, model, slab_n)
     if diffusion == "implicit":
         c.params.diffusion = 1
         desc += "; implicit-Euler diffusion (Jacobi, Eq. iejac1)"
+    if solver == "chebyshev":
+        c.params.solver = 1
+        desc += "; elliptic solve by Chebyshev-accelerated Jacobi (interval estimated at set-up)"
     return c, desc
 
 
@@ -214,6 +219,8 @@ def oracle_sample(case, sweeps_per_step, n_samples=1):
         t = []
         for cap in REF_SAMPLE_SWEEPS:
             p = W.Params(**{**case.params.__dict__, "max_iter": cap, "check_every": 10 ** 9})
+            if p.solver == 1 and not p.cheb_lmin > 0.0:
+                p.solver = 0   # no interval known here: a Jacobi sweep costs the oracle the same
             sim = oracle.Sim(case, params=p)
             t0 = time.perf_counter()
             sim.step()
@@ -245,7 +252,7 @@ def run_reference(a):
     world, rank, local = _dist()
     if rank != 0:
         return
-    case, desc = _workload(a.workload, a.model, a.slab_n, a.diffusion)
+    case, desc = _workload(a.workload, a.model, a.slab_n, a.diffusion, a.solver)
     M = case.n_tissue
     k_ref = a.ref_sweeps_per_step or DEFAULT_REF_SWEEPS_PER_STEP
     times = []
@@ -284,7 +291,7 @@ def run_ours(a):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     epbuild.build()
-    case, desc = _workload(a.workload, a.model, a.slab_n, a.diffusion)
+    case, desc = _workload(a.workload, a.model, a.slab_n, a.diffusion, a.solver)
     M = case.n_tissue
     mono = case.model == 0
     stream = torch.cuda.Stream()
@@ -296,6 +303,9 @@ def run_ours(a):
     sim.set_params(case.params)
     for s in case.stimuli:
         sim.add_stimulus(s.lo, s.hi, s.t_start, s.dur, s.amp)
+    if a.solver == "chebyshev":   # the oracle baseline runs the same semi-iteration on the same interval
+        info = sim.info()
+        case.params.cheb_lmin, case.params.cheb_lmax = info.cheb_lmin, info.cheb_lmax
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
     for _ in range(a.warmup):

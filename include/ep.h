@@ -99,10 +99,20 @@ typedef struct {
                              (a = dt/K, ve of step n), solved by the undamped Jacobi step of
                              Eq. iejac1 from v* to rel_tol (Sec. "Implicit Euler", "Diffusion").
                              Implicit handles are stepped by ep_step only, not in a batch. */
+    int solver;           /* elliptic solve: EP_SOLVER_JACOBI, the damped Jacobi of Eq. dampjac1 (default),
+                             or EP_SOLVER_CHEBYSHEV, Golub and Varga's Chebyshev semi-iteration on
+                             the Jacobi step (no counterpart in the paper, whose future work names
+                             faster solvers).  Same stop rule, FP64 norms and cap. */
+    double cheb_lmin, cheb_lmax;  /* EP_SOLVER_CHEBYSHEV: interval of the eigenvalues of D^-1 A that the
+                             polynomial targets (A the elliptic operator, D its diagonal as stored);
+                             both <= 0: estimated at set-up (Lanczos, 40 steps), read back with
+                             ep_get_info; else 0 < lmin < lmax */
 } ep_params;
 
 #define EP_EXPLICIT 0
 #define EP_IMPLICIT 1
+#define EP_SOLVER_JACOBI 0
+#define EP_SOLVER_CHEBYSHEV 1
 
 typedef struct {
     int iters;               /* Jacobi sweeps of the last elliptic solve (0 for monodomain) */
@@ -120,6 +130,7 @@ typedef struct {
     int n_segments;          /* z-march work items of the stencil kernels */
     double omega;            /* damping in use */
     size_t device_bytes;     /* device memory held by the handle */
+    double cheb_lmin, cheb_lmax;   /* Chebyshev interval in use (0 for the Jacobi solver) */
 } ep_info;
 
 typedef struct ep_sim ep_sim;

@@ -23,6 +23,7 @@ STATUS_NAMES = ["EP_OK", "EP_EINVAL", "EP_ENOMEM", "EP_ECUDA", "EP_ENOCONV", "EP
                 "EP_EBUSY", "EP_EREJECTED", "EP_ECANCELLED"]
 EP_MONO, EP_BI = 0, 1
 EP_EXPLICIT, EP_IMPLICIT = 0, 1
+EP_SOLVER_JACOBI, EP_SOLVER_CHEBYSHEV = 0, 1
 EP_FP32, EP_FP64 = 0, 1
 EP_VM_MV, EP_W, EP_VE_MV, EP_TACT, EP_V, EP_VE = range(6)
 
@@ -50,7 +51,8 @@ class Params(ctypes.Structure):
     _fields_ = [(n, ctypes.c_double) for n in
                 ("tau_in", "tau_out", "tau_open", "tau_close", "v_gate", "sig_iL", "sig_iT", "sig_eL", "sig_eT",
                  "lambda_", "K", "dt_ms", "jacobi_omega", "rel_tol")] + \
-               [("check_every", ctypes.c_int), ("max_iter", ctypes.c_int), ("diffusion", ctypes.c_int)]
+               [("check_every", ctypes.c_int), ("max_iter", ctypes.c_int), ("diffusion", ctypes.c_int),
+                ("solver", ctypes.c_int), ("cheb_lmin", ctypes.c_double), ("cheb_lmax", ctypes.c_double)]
 
 
 class StepStats(ctypes.Structure):
@@ -61,7 +63,8 @@ class StepStats(ctypes.Structure):
 
 class Info(ctypes.Structure):
     _fields_ = [("n_voxels", ctypes.c_longlong), ("n_tissue", ctypes.c_longlong), ("n_components", ctypes.c_int),
-                ("n_segments", ctypes.c_int), ("omega", ctypes.c_double), ("device_bytes", ctypes.c_size_t)]
+                ("n_segments", ctypes.c_int), ("omega", ctypes.c_double), ("device_bytes", ctypes.c_size_t),
+                ("cheb_lmin", ctypes.c_double), ("cheb_lmax", ctypes.c_double)]
 
 
 class Profile(ctypes.Structure):
@@ -246,7 +249,8 @@ class Sim:
     def set_params(self, p):
         P = Params(p.tau_in, p.tau_out, p.tau_open, p.tau_close, p.v_gate, p.sig_iL, p.sig_iT, p.sig_eL, p.sig_eT,
                    p.lam, p.K, p.dt, p.omega, p.rel_tol, int(p.check_every), int(p.max_iter),
-                   int(getattr(p, "diffusion", 0)))
+                   int(getattr(p, "diffusion", 0)), int(getattr(p, "solver", 0)),
+                   float(getattr(p, "cheb_lmin", 0.0)), float(getattr(p, "cheb_lmax", 0.0)))
         self._check(self._L.ep_set_params(self._h, ctypes.byref(P)), "ep_set_params")
 
     def add_stimulus(self, lo: Sequence[int], hi: Sequence[int], t_start: float, dur: float, amp: float):

@@ -82,6 +82,7 @@ struct ep_sim {
     int zseg = kZSeg;            // z-planes per stencil work item
     long long max_items = 0;     // segment capacity of the segs / partials buffers
     double omega = 0.0;
+    double cheb_lmin = 0.0, cheb_lmax = 0.0;   // Chebyshev interval in use
     size_t rsz = 4;
     // device memory
     std::vector<void *> allocs;
@@ -173,6 +174,12 @@ bool params_ok(const ep_params &p, std::string &why)
     if (!std::isfinite(p.rel_tol) || p.rel_tol < 0.0) { why = "rel_tol must be >= 0"; return false; }
     if (p.check_every < 1 || p.max_iter < 1) { why = "check_every and max_iter must be >= 1"; return false; }
     if (p.diffusion != EP_EXPLICIT && p.diffusion != EP_IMPLICIT) { why = "diffusion must be EP_EXPLICIT or EP_IMPLICIT"; return false; }
+    if (p.solver != EP_SOLVER_JACOBI && p.solver != EP_SOLVER_CHEBYSHEV) { why = "solver must be EP_SOLVER_JACOBI or EP_SOLVER_CHEBYSHEV"; return false; }
+    if (p.solver == EP_SOLVER_CHEBYSHEV && !(p.cheb_lmin <= 0.0 && p.cheb_lmax <= 0.0) &&
+        !(std::isfinite(p.cheb_lmin) && std::isfinite(p.cheb_lmax) && p.cheb_lmin > 0.0 && p.cheb_lmin < p.cheb_lmax)) {
+        why = "Chebyshev interval must satisfy 0 < cheb_lmin < cheb_lmax (both <= 0: estimated)";
+        return false;
+    }
     return true;
 }
 
@@ -325,6 +332,144 @@ ep_status plan_layout(ep_sim *s)
 }
 
 
+template <typename real>
+Inst<real> make_inst(const ep_sim *s);
+int stencil_blocks(const ep_sim *s);
+
+// Extreme eigenvalues of the symmetric tridiagonal (a, b) by Sturm bisection:
+// the number of eigenvalues below x is the number of negative pivots of T - x I.
+static int sturm_count(const std::vector<double> &a, const std::vector<double> &b, double x)
+{
+    int neg = 0;
+    double d = 1.0;
+    for (size_t i = 0; i < a.size(); ++i) {
+        d = a[i] - x - (i ? b[i] * b[i] / d : 0.0);
+        if (d == 0.0) d = -1e-300;
+        if (d < 0.0) ++neg;
+    }
+    return neg;
+}
+
+static double tridiag_eig(const std::vector<double> &a, const std::vector<double> &b, int which)
+{
+    double lo = 1e300, hi = -1e300;   // Gershgorin interval
+    for (size_t i = 0; i < a.size(); ++i) {
+        const double r = (i ? std::fabs(b[i]) : 0.0) + (i + 1 < a.size() ? std::fabs(b[i + 1]) : 0.0);
+        lo = std::min(lo, a[i] - r);
+        hi = std::max(hi, a[i] + r);
+    }
+    const int target = which == 0 ? 1 : (int)a.size();   // eigenvalue index (1-based, ascending)
+    for (int it = 0; it < 200; ++it) {
+        const double mid = 0.5 * (lo + hi);
+        if (sturm_count(a, b, mid) >= target) hi = mid;
+        else lo = mid;
+    }
+    return 0.5 * (lo + hi);
+}
+
+// Interval [lmin, lmax] of the eigenvalues of D^-1 A (A the elliptic operator,
+// D its diagonal as the sweeps use it) for the Chebyshev semi-iteration: 40
+// Lanczos steps on D^-1/2 A D^-1/2 over the coupled tissue voxels, the null
+// space (D^1/2 times each component's indicator) projected out, A applied by
+// the library's own operator kernel; the smallest Ritz value is scaled by 0.8
+// (Ritz values approach it from above) and the largest by 1.05.
+template <typename real>
+ep_status estimate_cheb_interval(ep_sim *s, real *u_dev, real *out_dev)
+{
+    const HostPlan &P = s->plan;
+    const long long n = s->n;
+    const size_t nt = P.order.size();
+    cudaStream_t st = s->stream;
+    std::vector<ushort4> rec(n);
+    CK(cudaMemcpyAsync(rec.data(), s->rec, sizeof(ushort4) * n, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    const double C = 1.0 / (8.0 * s->d.dx_mm * s->d.dx_mm);
+    std::vector<double> sc(nt);   // D^-1/2 per tissue voxel (0 for voxels with an empty row)
+    for (size_t i = 0; i < nt; ++i) {
+        __half h;
+        std::memcpy(&h, &rec[P.order[i]].w, sizeof(h));
+        const double inv_dhat = (double)__half2float(h);
+        sc[i] = inv_dhat > 0.0 ? std::sqrt(inv_dhat / C) : 0.0;
+    }
+    // null space: per component, D^1/2 on its coupled voxels, normalised
+    std::vector<double> nullv(nt, 0.0);
+    {
+        size_t pos = 0;
+        for (long long cnt : P.comp_count) {
+            double nn = 0.0;
+            for (size_t i = pos; i < pos + (size_t)cnt; ++i) {
+                nullv[i] = sc[i] > 0.0 ? 1.0 / sc[i] : 0.0;
+                nn += nullv[i] * nullv[i];
+            }
+            nn = std::sqrt(nn);
+            for (size_t i = pos; i < pos + (size_t)cnt; ++i) nullv[i] = nn > 0.0 ? nullv[i] / nn : 0.0;
+            pos += (size_t)cnt;
+        }
+    }
+    auto project = [&](std::vector<double> &v) {
+        size_t pos = 0;
+        for (long long cnt : P.comp_count) {
+            double d = 0.0;
+            for (size_t i = pos; i < pos + (size_t)cnt; ++i) d += v[i] * nullv[i];
+            for (size_t i = pos; i < pos + (size_t)cnt; ++i) v[i] -= d * nullv[i];
+            pos += (size_t)cnt;
+        }
+    };
+    auto norm = [](const std::vector<double> &v) {
+        double t = 0.0;
+        for (double x : v) t += x * x;
+        return std::sqrt(t);
+    };
+    std::vector<double> v(nt), vprev(nt, 0.0), w(nt);
+    uint64_t seed = 0x9E3779B97F4A7C15ull;   // fixed start vector (splitmix64)
+    for (size_t i = 0; i < nt; ++i) {
+        seed += 0x9E3779B97F4A7C15ull;
+        uint64_t z = seed;
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        z ^= z >> 31;
+        v[i] = sc[i] > 0.0 ? ((double)(z >> 11) * 0x1.0p-53 - 0.5) : 0.0;
+    }
+    project(v);
+    double nv = norm(v);
+    if (nv == 0.0) return fail(s, EP_EINVAL, "Chebyshev interval: no coupled tissue voxels");
+    for (double &x : v) x /= nv;
+    const double sT = s->p.sig_iT + s->p.sig_eT, sL = s->p.sig_iL + s->p.sig_eL;
+    ApplyIO<real> io;
+    io.u = u_dev;
+    io.out = out_dev;
+    io.sT = (real)sT;
+    io.dS = (real)(sL - sT);
+    const Inst<real> I = make_inst<real>(s);
+    std::vector<real> hu(n, real(0)), hout(n);
+    std::vector<double> alpha, beta(1, 0.0);
+    for (int j = 0; j < 40; ++j) {
+        for (size_t i = 0; i < nt; ++i) hu[P.order[i]] = (real)(sc[i] * v[i]);
+        CK(cudaMemcpyAsync(u_dev, hu.data(), sizeof(real) * n, cudaMemcpyHostToDevice, st));
+        k_stencil<real, M_APPLY><<<stencil_blocks(s), kThreads, 0, st>>>(I, io);
+        CK(cudaGetLastError());
+        CK(cudaMemcpyAsync(hout.data(), out_dev, sizeof(real) * n, cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        for (size_t i = 0; i < nt; ++i) w[i] = sc[i] * (double)hout[P.order[i]] - beta.back() * vprev[i];
+        double a = 0.0;
+        for (size_t i = 0; i < nt; ++i) a += w[i] * v[i];
+        for (size_t i = 0; i < nt; ++i) w[i] -= a * v[i];
+        project(w);
+        alpha.push_back(a);
+        const double b = norm(w);
+        if (!(b > 1e-12 * std::fabs(a))) break;   // invariant subspace: the Ritz values are exact
+        beta.push_back(b);
+        vprev.swap(v);
+        for (size_t i = 0; i < nt; ++i) v[i] = w[i] / b;
+    }
+    beta.resize(alpha.size());   // beta[i] couples rows i-1 and i
+    const double tmin = tridiag_eig(alpha, beta, 0), tmax = tridiag_eig(alpha, beta, 1);
+    if (!(tmin > 0.0) || !(tmax > tmin)) return fail(s, EP_EINVAL, "Chebyshev interval: estimate failed");
+    s->cheb_lmin = 0.8 * tmin;
+    s->cheb_lmax = 1.05 * tmax;
+    return EP_OK;
+}
+
 // Device set-up of a handle from its host plan.
 template <typename real>
 ep_status setup_typed(ep_sim *s)
@@ -431,6 +576,15 @@ ep_status setup_typed(ep_sim *s)
     CK(cudaGetLastError());
     CK(cudaMemsetAsync(s->ctl, 0, sizeof(Ctl), st));
     CK(cudaStreamSynchronize(st));
+    if (s->p.solver == EP_SOLVER_CHEBYSHEV && s->d.model == EP_BI) {
+        if (s->p.cheb_lmin > 0.0) {
+            s->cheb_lmin = s->p.cheb_lmin;
+            s->cheb_lmax = s->p.cheb_lmax;
+        } else {   // staging buffers serve as the operator's input and output
+            ep_status es = estimate_cheb_interval<real>(s, (real *)tmp_fib, (real *)tmp_rec);
+            if (es != EP_OK) return es;
+        }
+    }
     // free the set-up temporaries
     for (void *t : {tmp_fib, tmp_mask, tmp_rec}) {
         auto it = std::find(s->allocs.begin(), s->allocs.end(), t);
@@ -503,6 +657,17 @@ Inst<real> make_inst(const ep_sim *s)
     I.coef_par = (real)(s->p.dt_ms / s->p.K * fac);
     I.coef_jac = (real)(s->omega / C);
     I.alpha_ie = (real)(s->p.dt_ms / s->p.K * fac);
+    I.solver = s->p.solver == EP_SOLVER_CHEBYSHEV && s->cheb_lmax > 0.0 ? 1 : 0;
+    I.pad3 = 0;
+    I.cheb_tau_c = real(0);
+    I.cheb_rho = I.cheb_theta = 0.0;
+    if (I.solver) {
+        const double lo = s->cheb_lmin, hi = s->cheb_lmax;
+        const double rho = (hi - lo) / (hi + lo);
+        I.cheb_tau_c = (real)(2.0 / (lo + hi) / C);
+        I.cheb_rho = rho;
+        I.cheb_theta = std::acosh(1.0 / rho);
+    }
     I.dt = (real)s->p.dt_ms;
     I.inv_tin = (real)(1.0 / s->p.tau_in);
     I.inv_tout = (real)(1.0 / s->p.tau_out);
@@ -1023,6 +1188,8 @@ ep_status ep_get_info(ep_sim *s, ep_info *info)
     info->n_components = s->ncomp;
     info->n_segments = s->nseg;
     info->omega = s->omega;
+    info->cheb_lmin = s->cheb_lmin;
+    info->cheb_lmax = s->cheb_lmax;
     info->device_bytes = s->dev_bytes;
     return EP_OK;
 }

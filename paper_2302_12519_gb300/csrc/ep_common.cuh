@@ -115,7 +115,22 @@ struct Inst {
     real *ie_x;
     const real *ie_inv;
     real alpha_ie;
+    // Chebyshev semi-iteration of the elliptic solve (solver == 1): tau / C for the
+    // basic step, rho and theta = acosh(1 / rho) for the weights
+    int solver, pad3;
+    real cheb_tau_c;
+    double cheb_rho, cheb_theta;
 };
+
+// Weight of sweep k of the Chebyshev semi-iteration: w = 1 for k = 0, else
+// w_{k+1} = 2 T_k(1/rho) / (rho T_{k+1}(1/rho)) in the overflow-free form
+// (2 / rho) e^-theta (1 + e^-2k theta) / (1 + e^-2(k+1) theta).
+__device__ __forceinline__ double cheb_weight(int k, double rho, double theta)
+{
+    if (k == 0) return 1.0;
+    const double a = exp(-2.0 * theta * k);
+    return (2.0 / rho) * exp(-theta) * (1.0 + a) / (1.0 + a * exp(-2.0 * theta));
+}
 
 __device__ __forceinline__ float h2f(unsigned short b) { return __half2float(__ushort_as_half(b)); }
 __device__ __forceinline__ bool rec_tissue(const ushort4 &r) { return (r.w & 0x8000u) == 0; }

@@ -69,6 +69,8 @@ struct Op {
     real sT, dS, C, coef;
     double tn, dt_d;
     int nz;
+    int cheb;          // Jacobi sweep accelerated by the Chebyshev semi-iteration
+    real cheb_w;       // its weight for this sweep
 };
 
 // Loads of one plane for a lane's two voxel rows (lo = y0 + w - 1, hi = y0 + w).
@@ -246,7 +248,13 @@ __device__ __forceinline__ void plane_step(const Inst<real> &I, const Op<real> &
                 o.out[q] = -Lu;
             } else if (MODE == M_JAC) {
                 const real r = P.e0 - Lu;
-                o.out[q] = P.uLo + o.coef * P.e1 * r;
+                const real basic = P.uLo + o.coef * P.e1 * r;
+                if (o.cheb) {   // x_{k+1} = w (basic - x_{k-1}) + x_{k-1}; x_{k-1} is in the output buffer
+                    const real prev = o.out[q];
+                    o.out[q] = o.cheb_w * (basic - prev) + prev;
+                } else {
+                    o.out[q] = basic;
+                }
                 if (check) acc += (float)r * (float)r;
             } else if (MODE == M_IE) {   // r = f - (I + a L) x;  x+ = x + r / (1 + a D)  (Eq. iejac1)
                 const real r = P.e0 - P.uLo - o.coef * Lu;
@@ -406,6 +414,8 @@ __device__ __forceinline__ void stencil_item(const Inst<real> &I, int seg_index,
     o.C = I.C;
     o.w = o.ve = o.b = o.inv = nullptr;
     o.out = o.wout = o.tact = o.out2 = nullptr;
+    o.cheb = 0;
+    o.cheb_w = real(1);
     o.tn = 0.0;
     o.dt_d = I.dt_d;
     int sweep = 0;
@@ -427,6 +437,13 @@ __device__ __forceinline__ void stencil_item(const Inst<real> &I, int seg_index,
             o.src = (sweep & 1) ? I.x1 : I.x0;
             o.out = (sweep & 1) ? I.x0 : I.x1;
             o.sT = I.sTie; o.dS = I.dSie; o.coef = I.coef_jac;
+            if (I.solver == 1 && sweep > 0) {   // sweep 0 is the basic step itself
+                o.cheb = 1;
+                o.cheb_w = (real)cheb_weight(sweep, I.cheb_rho, I.cheb_theta);
+                o.coef = I.cheb_tau_c;
+            } else if (I.solver == 1) {
+                o.coef = I.cheb_tau_c;
+            }
         } else {   // implicit sweep: iterates in the new v buffer and ie_x
             o.src = (sweep & 1) ? I.ie_x : I.v[cur ^ 1];
             o.out = (sweep & 1) ? I.v[cur ^ 1] : I.ie_x;
