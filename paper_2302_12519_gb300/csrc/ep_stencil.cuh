@@ -81,7 +81,7 @@ struct Ld {
     real wLo, wHi;     // PAR
     real veLo, veHi;   // PAR_BI
     real bLo;          // JAC: b; IE: f
-    real iLo;          // IE: 1 / (1 + a D_i)
+    real iLo;          // IE: 1 / (1 + a D_i); JAC with the Chebyshev solver: x_{k-1} of row lo
 };
 
 // What the next plane needs from this one.
@@ -161,7 +161,7 @@ __device__ __forceinline__ void plane_step(const Inst<real> &I, const Op<real> &
     } else {
         ulo = tlo ? L.uLo : real(0);
         uhi = thi ? L.uHi : real(0);
-        if (MODE == M_JAC) { C.e0 = L.bLo; C.e1 = (real)blo.y; }
+        if (MODE == M_JAC) { C.e0 = L.bLo; C.e1 = (real)blo.y; C.e2 = L.iLo; }
         if (MODE == M_IE) { C.e0 = L.bLo; C.e1 = L.iLo; }
     }
     C.uLo = ulo;
@@ -249,8 +249,8 @@ __device__ __forceinline__ void plane_step(const Inst<real> &I, const Op<real> &
             } else if (MODE == M_JAC) {
                 const real r = P.e0 - Lu;
                 const real basic = P.uLo + o.coef * P.e1 * r;
-                if (o.cheb) {   // x_{k+1} = w (basic - x_{k-1}) + x_{k-1}; x_{k-1} is in the output buffer
-                    const real prev = o.out[q];
+                if (o.cheb) {   // x_{k+1} = w (basic - x_{k-1}) + x_{k-1}; x_{k-1} came through the ring
+                    const real prev = P.e2;
                     o.out[q] = o.cheb_w * (basic - prev) + prev;
                 } else {
                     o.out[q] = basic;
@@ -302,8 +302,8 @@ constexpr bool kRinged = MODE == M_JAC || MODE == M_IE || MODE == M_PAR_MONO;
 template <typename real, int MODE>
 struct Ring {
     static constexpr int D = sizeof(real) == 4 ? 4 : 2;   // divides the unroll of 4; static smem < 48 KB
-    static constexpr int NX = MODE == M_JAC ? 1 : 2;      // b of row lo (Jacobi), f and 1/(1+aD) of row lo
-                                                          // (implicit sweep) or w of rows lo, hi
+    static constexpr int NX = 2;   // b and x_{k-1} (Chebyshev) of row lo (Jacobi sweep), f and 1/(1+aD) of
+                                   // row lo (implicit sweep), or w of rows lo, hi (monodomain step)
     uint2 rec[D][2][kThreads];   // fp16 records of rows lo / hi
     real u[D][2][kThreads];
     real x[D][NX][kThreads];
@@ -315,6 +315,7 @@ struct StencilSmem {
     real sF[2][3][kWarps][32];
     real sT[2][kWarps][32];
     double sred[kWarps];
+    double cheb_w;   // Chebyshev weight of the sweep, formed by one thread (FP64 is slow here)
     int sflag;
     typename std::conditional<kRinged<MODE>, Ring<real, MODE>, NoRing>::type ring;
 };
@@ -343,11 +344,13 @@ __device__ __forceinline__ void ring_issue(const Op<real> &o, Ring<real, MODE> &
         cp_async_n<sizeof(real)>(&R.u[slot][0][t], o.src + q);
         cp_async_n<sizeof(real)>(&R.x[slot][0][t], (MODE == M_PAR_MONO ? o.w : o.b) + q);
         if (MODE == M_IE) cp_async_n<sizeof(real)>(&R.x[slot][1][t], o.inv + q);
+        // x_{k-1} sits where this thread will write x_{k+1} of this voxel, one plane later
+        if (MODE == M_JAC && o.cheb) cp_async_n<sizeof(real)>(&R.x[slot][1][t], o.out + q);
     } else {
         R.rec[slot][0][t] = make_uint2(0u, (unsigned)kNonTissue << 16);
         R.u[slot][0][t] = real(0);
         R.x[slot][0][t] = MODE == M_PAR_MONO ? real(1) : real(0);
-        if (MODE == M_IE) R.x[slot][1][t] = real(0);
+        if (MODE == M_IE || MODE == M_JAC) R.x[slot][1][t] = real(0);
     }
     if (kin && hi_in) {
         const int q = qhi + k * plane;
@@ -362,7 +365,7 @@ __device__ __forceinline__ void ring_issue(const Op<real> &o, Ring<real, MODE> &
 }
 
 template <typename real, int MODE>
-__device__ __forceinline__ void ring_read(const Ring<real, MODE> &R, int slot, Ld<real, MODE> &L)
+__device__ __forceinline__ void ring_read(const Ring<real, MODE> &R, int slot, Ld<real, MODE> &L, bool o_cheb)
 {
     const int t = threadIdx.x;
     L.rLo = R.rec[slot][0][t];
@@ -371,7 +374,7 @@ __device__ __forceinline__ void ring_read(const Ring<real, MODE> &R, int slot, L
     L.uHi = R.u[slot][1][t];
     if (MODE == M_JAC || MODE == M_IE) {
         L.bLo = R.x[slot][0][t];
-        L.iLo = MODE == M_IE ? R.x[slot][1][t] : real(0);
+        L.iLo = (MODE == M_IE || o_cheb) ? R.x[slot][1][t] : real(0);
         L.wLo = L.wHi = real(1);
     } else {
         L.bLo = real(0);
@@ -393,7 +396,7 @@ __device__ __forceinline__ void ring_plane(const Inst<real> &I, const Op<real> &
     if (k + D - 1 <= kend) ring_issue<real, MODE>(o, R, next, k + D - 1, lo_in, hi_in, g.qlo, qhi, g.plane);
     cp_async_commit();
     cp_async_wait<D - 1>();
-    ring_read<real, MODE>(R, slot, L);
+    ring_read<real, MODE>(R, slot, L, o.cheb != 0);
     plane_step<real, MODE>(I, o, g, k, k > kbeg, k > kbeg + 1, P, Cn, L, sF, sT, check, acc);
 }
 
@@ -437,12 +440,14 @@ __device__ __forceinline__ void stencil_item(const Inst<real> &I, int seg_index,
             o.src = (sweep & 1) ? I.x1 : I.x0;
             o.out = (sweep & 1) ? I.x0 : I.x1;
             o.sT = I.sTie; o.dS = I.dSie; o.coef = I.coef_jac;
-            if (I.solver == 1 && sweep > 0) {   // sweep 0 is the basic step itself
-                o.cheb = 1;
-                o.cheb_w = (real)cheb_weight(sweep, I.cheb_rho, I.cheb_theta);
+            if (I.solver == 1) {
                 o.coef = I.cheb_tau_c;
-            } else if (I.solver == 1) {
-                o.coef = I.cheb_tau_c;
+                if (sweep > 0) {   // sweep 0 is the basic step itself
+                    if (threadIdx.x == 0) sm.cheb_w = cheb_weight(sweep, I.cheb_rho, I.cheb_theta);
+                    __syncthreads();
+                    o.cheb = 1;
+                    o.cheb_w = (real)sm.cheb_w;
+                }
             }
         } else {   // implicit sweep: iterates in the new v buffer and ie_x
             o.src = (sweep & 1) ? I.ie_x : I.v[cur ^ 1];
