@@ -531,6 +531,8 @@ def run_served(a):
                                               steps=a.req_steps)
     for c in cases:
         c.model, c.precision = W.BI, W.FP32
+        if a.solver == "chebyshev":
+            c.params.solver = 1   # each request estimates its interval at set-up
     S = a.req_steps
     vox = [c.n_tissue * S for c in cases]
 
@@ -588,7 +590,8 @@ def run_served(a):
             "steps": S, "warmup": 0, "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": f"config4: {len(cases)} bidomain FP32 shell requests, n ~ U{{64..256}}, "
-                                   f"{S} steps each, Poisson arrivals (seed 0)",
+                                   f"{S} steps each, Poisson arrivals (seed 0)" +
+                                   ("; Chebyshev-accelerated elliptic solves" if a.solver == "chebyshev" else ""),
                        "grids": [c.nx for c in cases], "tissue_voxels": [c.n_tissue for c in cases],
                        "hbm_budget_bytes": budget, "max_slots": a.max_slots, "chunk_steps": a.chunk_steps,
                        "max_active_items": a.max_active_items,
