@@ -244,6 +244,18 @@ size_t abytes(size_t b) { return b ? b : 16; }   // dalloc's size of a request
 // Device bytes of a handle after set-up (resident) and during it (peak, which
 // adds the staging buffers of fibres, mask and raw records).  Matches the
 // allocations of setup_typed exactly.
+constexpr int kLanczosSteps = 40;
+constexpr int kLanczosScalars = 2 + 2 * kLanczosSteps;   // alpha, beta of the current step; alpha_j, beta_{j+1}
+
+// Set-up scratch of the Chebyshev interval estimate (0 when the interval is
+// given or the solver is damped Jacobi): the Lanczos scalars and two partial
+// sums per reduction chunk.
+size_t lanczos_bytes(const ep_sim *s)
+{
+    if (!s->have_params || s->p.solver != EP_SOLVER_CHEBYSHEV || s->d.model != EP_BI || s->p.cheb_lmin > 0.0) return 0;
+    return sizeof(double) * ((size_t)kLanczosScalars + 2 * (size_t)s->nchunk);
+}
+
 void footprint(const ep_sim *s, size_t rb, size_t *resident, size_t *peak)
 {
     const HostPlan &P = s->plan;
@@ -255,7 +267,7 @@ void footprint(const ep_sim *s, size_t rb, size_t *resident, size_t *peak)
     r += abytes(sizeof(double) * (size_t)std::max<long long>(s->max_items, s->nchunk)) + abytes(sizeof(Ctl));
     if (s->have_params && s->p.diffusion == EP_IMPLICIT) r += 2 * abytes(rb * n);   // second iterate, 1/(1 + a D)
     *resident = r;
-    *peak = r + abytes(sizeof(float) * 3 * n) + abytes(n) + abytes(sizeof(ushort4) * n);
+    *peak = r + abytes(sizeof(float) * 3 * n) + abytes(n) + abytes(sizeof(ushort4) * n) + lanczos_bytes(s);
 }
 
 // Host analysis of the mask: face-connected components (breadth-first), the
@@ -368,101 +380,56 @@ static double tridiag_eig(const std::vector<double> &a, const std::vector<double
 }
 
 // Interval [lmin, lmax] of the eigenvalues of D^-1 A (A the elliptic operator,
-// D its diagonal as the sweeps use it) for the Chebyshev semi-iteration: 40
-// Lanczos steps on D^-1/2 A D^-1/2 over the coupled tissue voxels, the null
-// space (D^1/2 times each component's indicator) projected out, A applied by
-// the library's own operator kernel; the smallest Ritz value is scaled by 0.8
-// (Ritz values approach it from above) and the largest by 1.05.
+// D its diagonal as the sweeps use it) for the Chebyshev semi-iteration:
+// kLanczosSteps steps of the Lanczos process for D^-1 A in the D inner product
+// (where it is self-adjoint; the same tridiagonal as symmetric Lanczos on
+// D^-1/2 A D^-1/2), all on the device -- A applied by the library's operator
+// kernel, FP64 inner products, the null space (constants on each component)
+// D-orthogonally projected out at every step.  The host reads the tridiagonal
+// once; the smallest Ritz value is scaled by 0.8 (Ritz values approach it from
+// above) and the largest by 1.05.  v, vprev, w, t: n values each; lz: the
+// scalars, then two partial sums per reduction chunk.
 template <typename real>
-ep_status estimate_cheb_interval(ep_sim *s, real *u_dev, real *out_dev)
+ep_status estimate_cheb_interval(ep_sim *s, real *v, real *vprev, real *w, real *t, double *lz)
 {
-    const HostPlan &P = s->plan;
-    const long long n = s->n;
-    const size_t nt = P.order.size();
+    const long long n = s->n, nt = s->n_tissue;
+    if (nt == 0 || s->nchunk == 0) return fail(s, EP_EINVAL, "Chebyshev interval: no tissue");
     cudaStream_t st = s->stream;
-    std::vector<ushort4> rec(n);
-    CK(cudaMemcpyAsync(rec.data(), s->rec, sizeof(ushort4) * n, cudaMemcpyDeviceToHost, st));
-    CK(cudaStreamSynchronize(st));
-    const double C = 1.0 / (8.0 * s->d.dx_mm * s->d.dx_mm);
-    std::vector<double> sc(nt);   // D^-1/2 per tissue voxel (0 for voxels with an empty row)
-    for (size_t i = 0; i < nt; ++i) {
-        __half h;
-        std::memcpy(&h, &rec[P.order[i]].w, sizeof(h));
-        const double inv_dhat = (double)__half2float(h);
-        sc[i] = inv_dhat > 0.0 ? std::sqrt(inv_dhat / C) : 0.0;
-    }
-    // null space: per component, D^1/2 on its coupled voxels, normalised
-    std::vector<double> nullv(nt, 0.0);
-    {
-        size_t pos = 0;
-        for (long long cnt : P.comp_count) {
-            double nn = 0.0;
-            for (size_t i = pos; i < pos + (size_t)cnt; ++i) {
-                nullv[i] = sc[i] > 0.0 ? 1.0 / sc[i] : 0.0;
-                nn += nullv[i] * nullv[i];
-            }
-            nn = std::sqrt(nn);
-            for (size_t i = pos; i < pos + (size_t)cnt; ++i) nullv[i] = nn > 0.0 ? nullv[i] / nn : 0.0;
-            pos += (size_t)cnt;
-        }
-    }
-    auto project = [&](std::vector<double> &v) {
-        size_t pos = 0;
-        for (long long cnt : P.comp_count) {
-            double d = 0.0;
-            for (size_t i = pos; i < pos + (size_t)cnt; ++i) d += v[i] * nullv[i];
-            for (size_t i = pos; i < pos + (size_t)cnt; ++i) v[i] -= d * nullv[i];
-            pos += (size_t)cnt;
-        }
-    };
-    auto norm = [](const std::vector<double> &v) {
-        double t = 0.0;
-        for (double x : v) t += x * x;
-        return std::sqrt(t);
-    };
-    std::vector<double> v(nt), vprev(nt, 0.0), w(nt);
-    uint64_t seed = 0x9E3779B97F4A7C15ull;   // fixed start vector (splitmix64)
-    for (size_t i = 0; i < nt; ++i) {
-        seed += 0x9E3779B97F4A7C15ull;
-        uint64_t z = seed;
-        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
-        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
-        z ^= z >> 31;
-        v[i] = sc[i] > 0.0 ? ((double)(z >> 11) * 0x1.0p-53 - 0.5) : 0.0;
-    }
-    project(v);
-    double nv = norm(v);
-    if (nv == 0.0) return fail(s, EP_EINVAL, "Chebyshev interval: no coupled tissue voxels");
-    for (double &x : v) x /= nv;
+    Inst<real> I = make_inst<real>(s);
+    I.partials = lz + kLanczosScalars;
     const double sT = s->p.sig_iT + s->p.sig_eT, sL = s->p.sig_iL + s->p.sig_eL;
     ApplyIO<real> io;
-    io.u = u_dev;
-    io.out = out_dev;
+    io.u = v;
+    io.out = t;
     io.sT = (real)sT;
     io.dS = (real)(sL - sT);
-    const Inst<real> I = make_inst<real>(s);
-    std::vector<real> hu(n, real(0)), hout(n);
-    std::vector<double> alpha, beta(1, 0.0);
-    for (int j = 0; j < 40; ++j) {
-        for (size_t i = 0; i < nt; ++i) hu[P.order[i]] = (real)(sc[i] * v[i]);
-        CK(cudaMemcpyAsync(u_dev, hu.data(), sizeof(real) * n, cudaMemcpyHostToDevice, st));
-        k_stencil<real, M_APPLY><<<stencil_blocks(s), kThreads, 0, st>>>(I, io);
-        CK(cudaGetLastError());
-        CK(cudaMemcpyAsync(hout.data(), out_dev, sizeof(real) * n, cudaMemcpyDeviceToHost, st));
-        CK(cudaStreamSynchronize(st));
-        for (size_t i = 0; i < nt; ++i) w[i] = sc[i] * (double)hout[P.order[i]] - beta.back() * vprev[i];
-        double a = 0.0;
-        for (size_t i = 0; i < nt; ++i) a += w[i] * v[i];
-        for (size_t i = 0; i < nt; ++i) w[i] -= a * v[i];
-        project(w);
-        alpha.push_back(a);
-        const double b = norm(w);
-        if (!(b > 1e-12 * std::fabs(a))) break;   // invariant subspace: the Ritz values are exact
-        beta.push_back(b);
-        vprev.swap(v);
-        for (size_t i = 0; i < nt; ++i) v[i] = w[i] / b;
+    const int gt = grid_for(nt, kRedThreads), gc = s->nchunk, gs = stencil_blocks(s);
+    CK(cudaMemsetAsync(lz, 0, sizeof(double) * kLanczosScalars, st));
+    k_fill<real><<<grid_for(n, 256), 256, 0, st>>>(v, n, real(0));
+    k_fill<real><<<grid_for(n, 256), 256, 0, st>>>(vprev, n, real(0));
+    k_lz_start<real><<<gt, kRedThreads, 0, st>>>(I, nt, w);
+    k_lz_proj<real><<<gc, kRedThreads, 0, st>>>(I, v, w, lz, 0);
+    k_lz_norm<real><<<gc, kRedThreads, 0, st>>>(I, w, lz, -1);
+    k_lz_next<real><<<gt, kRedThreads, 0, st>>>(I, nt, v, vprev, w, lz);
+    for (int j = 0; j < kLanczosSteps; ++j) {
+        k_stencil<real, M_APPLY><<<gs, kThreads, 0, st>>>(I, io);
+        k_lz_w<real><<<gc, kRedThreads, 0, st>>>(I, t, v, vprev, w, lz);
+        k_lz_proj<real><<<gc, kRedThreads, 0, st>>>(I, v, w, lz, 1);
+        k_lz_norm<real><<<gc, kRedThreads, 0, st>>>(I, w, lz, j);
+        k_lz_next<real><<<gt, kRedThreads, 0, st>>>(I, nt, v, vprev, w, lz);
     }
-    beta.resize(alpha.size());   // beta[i] couples rows i-1 and i
+    CK(cudaGetLastError());
+    std::vector<double> h(kLanczosScalars);
+    CK(cudaMemcpyAsync(h.data(), lz, sizeof(double) * kLanczosScalars, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (h[2] == 0.0 && h[3] == 0.0) return fail(s, EP_EINVAL, "Chebyshev interval: no coupled tissue voxels");
+    std::vector<double> alpha, beta(1, 0.0);   // beta[i] couples rows i-1 and i
+    for (int j = 0; j < kLanczosSteps; ++j) {
+        const double a = h[2 + 2 * j], b = h[3 + 2 * j];
+        alpha.push_back(a);
+        if (!(b > 1e-12 * std::fabs(a))) break;   // invariant subspace: the Ritz values are exact
+        if (j + 1 < kLanczosSteps) beta.push_back(b);
+    }
     const double tmin = tridiag_eig(alpha, beta, 0), tmax = tridiag_eig(alpha, beta, 1);
     if (!(tmin > 0.0) || !(tmax > tmin)) return fail(s, EP_EINVAL, "Chebyshev interval: estimate failed");
     s->cheb_lmin = 0.8 * tmin;
@@ -535,6 +502,8 @@ ep_status setup_typed(ep_sim *s)
     void *tmp_fib = dalloc(s, sizeof(float) * 3 * n);
     void *tmp_mask = dalloc(s, n);
     void *tmp_rec = dalloc(s, sizeof(ushort4) * n);
+    void *tmp_lz = lanczos_bytes(s) ? dalloc(s, lanczos_bytes(s)) : nullptr;
+    if (lanczos_bytes(s) && !tmp_lz) return fail(s, EP_ENOMEM, "device allocation failed");
     const void *all[] = {s->rec, s->v[0], s->v[1], s->w[0], s->w[1], s->x[0], s->x[1], s->b, s->tact, s->segs,
                          s->idx, s->chunks, s->comp_chunk0, s->comp_count, s->means, s->partials, s->ctl,
                          tmp_fib, tmp_mask, tmp_rec};
@@ -565,6 +534,17 @@ ep_status setup_typed(ep_sim *s)
         k_fill<real><<<grid_for(n, 256), 256, 0, st>>>((real *)s->ie_x, n, real(0));
         CK(cudaGetLastError());
     }
+    if (s->p.solver == EP_SOLVER_CHEBYSHEV && s->d.model == EP_BI) {
+        if (s->p.cheb_lmin > 0.0) {
+            s->cheb_lmin = s->p.cheb_lmin;
+            s->cheb_lmax = s->p.cheb_lmax;
+        } else {   // the state buffers serve as the Lanczos vectors before the rest state is written
+            CK(cudaMemsetAsync(s->ctl, 0, sizeof(Ctl), st));   // the reductions' arrival counter
+            ep_status es = estimate_cheb_interval<real>(s, (real *)s->v[0], (real *)s->v[1], (real *)s->w[0],
+                                                        (real *)s->w[1], (double *)tmp_lz);
+            if (es != EP_OK) return es;
+        }
+    }
     // rest state
     for (int i = 0; i < 2; ++i) {
         k_fill<real><<<grid_for(n, 256), 256, 0, st>>>((real *)s->v[i], n, real(0));
@@ -576,17 +556,9 @@ ep_status setup_typed(ep_sim *s)
     CK(cudaGetLastError());
     CK(cudaMemsetAsync(s->ctl, 0, sizeof(Ctl), st));
     CK(cudaStreamSynchronize(st));
-    if (s->p.solver == EP_SOLVER_CHEBYSHEV && s->d.model == EP_BI) {
-        if (s->p.cheb_lmin > 0.0) {
-            s->cheb_lmin = s->p.cheb_lmin;
-            s->cheb_lmax = s->p.cheb_lmax;
-        } else {   // staging buffers serve as the operator's input and output
-            ep_status es = estimate_cheb_interval<real>(s, (real *)tmp_fib, (real *)tmp_rec);
-            if (es != EP_OK) return es;
-        }
-    }
     // free the set-up temporaries
-    for (void *t : {tmp_fib, tmp_mask, tmp_rec}) {
+    for (void *t : {tmp_fib, tmp_mask, tmp_rec, tmp_lz}) {
+        if (!t) continue;
         auto it = std::find(s->allocs.begin(), s->allocs.end(), t);
         if (it != s->allocs.end()) {
             if (s->d.dev_alloc && s->d.dev_free) s->d.dev_free(t, s->d.alloc_ctx);

@@ -342,6 +342,150 @@ __global__ void __launch_bounds__(kRedThreads) k_ie_finish(Inst<real> I)
     if (blockIdx.x == 0 && threadIdx.x == 0) ctl->ie_total += iters;
 }
 
+// ---------------------------------------------------------------------------
+// Lanczos process for the spectrum of D^-1 A (Chebyshev interval at set-up),
+// in the D inner product <x, y> = sum D x y, where D^-1 A is self-adjoint;
+// D_q = C / (1/Dhat_q) from the fp16 record, voxels with an empty row left
+// out.  One CTA per tissue chunk; FP64 partials (two per chunk in k_lz_proj);
+// the item that completes a launch finishes it.  Scalars: lz[0] alpha, lz[1] beta of the current step,
+// lz[2 + 2j] alpha_j, lz[3 + 2j] beta_{j+1}.
+// ---------------------------------------------------------------------------
+template <typename real>
+__device__ __forceinline__ double lz_diag(const Inst<real> &I, int q)
+{
+    const float h = h2f(I.rec[q].w);
+    return h > 0.0f ? (double)I.C / (double)h : 0.0;
+}
+
+// w = D^-1 t - beta vprev (t = A v); alpha = <w, v>_D
+template <typename real>
+__global__ void __launch_bounds__(kRedThreads) k_lz_w(Inst<real> I, const real *t, const real *v, const real *vprev,
+                                                     real *w, double *lz)
+{
+    __shared__ RedSmem sm;
+    const Chunk ch = I.chunks[blockIdx.x];
+    const double beta = lz[1];
+    double sa = 0.0;
+    for (int i = ch.start + threadIdx.x; i < ch.end; i += kRedThreads) {
+        const int q = I.idx[i];
+        const double d = lz_diag(I, q);
+        const double wq = d > 0.0 ? (double)t[q] / d - beta * (double)vprev[q] : 0.0;
+        w[q] = (real)wq;
+        sa += d * wq * (double)v[q];
+    }
+    sa = block_sum<kRedThreads>(sa, sm.sred);
+    if (threadIdx.x == 0) I.partials[blockIdx.x] = sa;
+    if (!arrive_last(I.ctl, gridDim.x, &sm.sflag)) return;
+    double tsum = 0.0;
+    for (int i = threadIdx.x; i < (int)gridDim.x; i += kRedThreads) tsum += ((volatile double *)I.partials)[i];
+    tsum = block_sum<kRedThreads>(tsum, sm.sred);
+    if (threadIdx.x == 0) {
+        I.ctl->arrive = 0;
+        lz[0] = tsum;
+        __threadfence();
+    }
+}
+
+// w -= alpha v; per component the D-weighted mean of w (the null-space
+// coefficient: the constants of each component span the null space) into means[c]
+template <typename real>
+__global__ void __launch_bounds__(kRedThreads) k_lz_proj(Inst<real> I, const real *v, real *w, const double *lz,
+                                                        int use_alpha)
+{
+    __shared__ RedSmem sm;
+    const Chunk ch = I.chunks[blockIdx.x];
+    const double alpha = use_alpha ? lz[0] : 0.0;
+    double sn = 0.0, sd = 0.0;
+    for (int i = ch.start + threadIdx.x; i < ch.end; i += kRedThreads) {
+        const int q = I.idx[i];
+        const double d = lz_diag(I, q);
+        const double wq = (double)w[q] - alpha * (double)v[q];
+        w[q] = (real)wq;
+        sn += d * wq;
+        sd += d;
+    }
+    sn = block_sum<kRedThreads>(sn, sm.sred);
+    const double dsum = block_sum<kRedThreads>(sd, sm.sred);
+    if (threadIdx.x == 0) {
+        I.partials[2 * blockIdx.x] = sn;
+        I.partials[2 * blockIdx.x + 1] = dsum;
+    }
+    if (!arrive_last(I.ctl, gridDim.x, &sm.sflag)) return;
+    for (int c = threadIdx.x; c < I.ncomp; c += kRedThreads) {
+        double tn = 0.0, td = 0.0;
+        for (int i = I.comp_chunk0[c]; i < I.comp_chunk0[c + 1]; ++i) {
+            tn += ((volatile double *)I.partials)[2 * i];
+            td += ((volatile double *)I.partials)[2 * i + 1];
+        }
+        I.means[c] = td > 0.0 ? tn / td : 0.0;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        I.ctl->arrive = 0;
+        __threadfence();
+    }
+}
+
+// w -= means[comp] on the coupled voxels; beta' = ||w||_D; records alpha_j, beta_{j+1}
+template <typename real>
+__global__ void __launch_bounds__(kRedThreads) k_lz_norm(Inst<real> I, real *w, double *lz, int j)
+{
+    __shared__ RedSmem sm;
+    const Chunk ch = I.chunks[blockIdx.x];
+    const double m = I.means[ch.comp];
+    double s2 = 0.0;
+    for (int i = ch.start + threadIdx.x; i < ch.end; i += kRedThreads) {
+        const int q = I.idx[i];
+        const double d = lz_diag(I, q);
+        const double wq = d > 0.0 ? (double)w[q] - m : 0.0;
+        w[q] = (real)wq;
+        s2 += d * wq * wq;
+    }
+    s2 = block_sum<kRedThreads>(s2, sm.sred);
+    if (threadIdx.x == 0) I.partials[blockIdx.x] = s2;
+    if (!arrive_last(I.ctl, gridDim.x, &sm.sflag)) return;
+    double t = 0.0;
+    for (int i = threadIdx.x; i < (int)gridDim.x; i += kRedThreads) t += ((volatile double *)I.partials)[i];
+    t = block_sum<kRedThreads>(t, sm.sred);
+    if (threadIdx.x == 0) {
+        I.ctl->arrive = 0;
+        lz[1] = sqrt(t);
+        if (j >= 0) {
+            lz[2 + 2 * j] = lz[0];
+            lz[3 + 2 * j] = lz[1];
+        }
+        __threadfence();
+    }
+}
+
+// vprev = v; v = w / beta (the next Lanczos vector)
+template <typename real>
+__global__ void __launch_bounds__(kRedThreads) k_lz_next(Inst<real> I, long long nt, real *v, real *vprev,
+                                                        const real *w, const double *lz)
+{
+    const double inv = lz[1] > 0.0 ? 1.0 / lz[1] : 0.0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nt; i += (long long)gridDim.x * blockDim.x) {
+        const int q = I.idx[i];
+        vprev[q] = v[q];
+        v[q] = (real)((double)w[q] * inv);
+    }
+}
+
+// Start vector on the coupled tissue voxels: splitmix64 of the voxel index,
+// uniform in [-1/2, 1/2).
+template <typename real>
+__global__ void __launch_bounds__(kRedThreads) k_lz_start(Inst<real> I, long long nt, real *w)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nt; i += (long long)gridDim.x * blockDim.x) {
+        const int q = I.idx[i];
+        unsigned long long z = 0x9E3779B97F4A7C15ull * (unsigned long long)(q + 1);
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        z ^= z >> 31;
+        w[q] = lz_diag(I, q) > 0.0 ? (real)((double)(z >> 11) * 0x1.0p-53 - 0.5) : real(0);
+    }
+}
+
 // v_e <- x_final - means[comp] (written to x0, the warm start of the next solve).
 template <typename real>
 __device__ __forceinline__ void project_item(const Inst<real> &I, int item)

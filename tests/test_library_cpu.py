@@ -127,6 +127,24 @@ def test_footprint_is_planned_on_the_host(lib):
     s.close()
 
 
+def test_footprint_counts_the_interval_estimate(lib):
+    """A Chebyshev bidomain handle without a given interval estimates it at
+    set-up: the peak adds the Lanczos scalars (82 doubles) and two partial sums
+    per reduction chunk; with the interval given, or for damped Jacobi, nothing."""
+    import workloads as W
+    c = W.random_case(4, 17, 12, 10, model=W.BI)
+    peaks = {}
+    for key, solver, lmin, lmax in (("jac", 0, 0.0, 0.0), ("est", 1, 0.0, 0.0), ("given", 1, 0.01, 4.0)):
+        c.params.solver, c.params.cheb_lmin, c.params.cheb_lmax = solver, lmin, lmax
+        s = ep.sim_from_case(c, use_torch=False)
+        peaks[key] = s.footprint()
+        s.close()
+    (rj, pj), (re_, pe), (rg, pg) = peaks["jac"], peaks["est"], peaks["given"]
+    assert rj == re_ == rg and pj == pg
+    extra = pe - pj
+    assert extra >= 8 * 82 + 16 and (extra - 8 * 82) % 16 == 0
+
+
 def test_server_needs_a_device(lib):
     """Without a GPU the server cannot start and says so (no host fallback)."""
     import torch
