@@ -42,7 +42,8 @@ def build(force: bool = False) -> str:
 
 class _Grid(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
-                ("dx", ctypes.c_double), ("mask", ctypes.c_void_p), ("fib", ctypes.c_void_p)]
+                ("dx", ctypes.c_double), ("mask", ctypes.c_void_p), ("fib", ctypes.c_void_p),
+                ("torso", ctypes.c_void_p), ("sig_o", ctypes.c_double)]
 
 
 class _Params(ctypes.Structure):
@@ -51,7 +52,7 @@ class _Params(ctypes.Structure):
                  "sig_iL", "sig_iT", "sig_eL", "sig_eT", "lam", "K", "dt", "omega", "rel_tol")] + \
                [("check_every", ctypes.c_int), ("max_iter", ctypes.c_int), ("model", ctypes.c_int),
                 ("diffusion", ctypes.c_int), ("solver", ctypes.c_int),
-                ("cheb_lmin", ctypes.c_double), ("cheb_lmax", ctypes.c_double)]
+                ("cheb_lmin", ctypes.c_double), ("cheb_lmax", ctypes.c_double), ("sig_o", ctypes.c_double)]
 
 
 class _Stim(ctypes.Structure):
@@ -84,6 +85,8 @@ def lib():
                                 ctypes.POINTER(_Stim), ip]
         L.og_create.restype = vp
         L.og_destroy.argtypes = [vp]
+        L.og_set_torso.argtypes = [vp, vp]
+        L.og_set_torso.restype = ip
         L.og_set_state.argtypes = [vp, vp, vp, vp, ctypes.c_long]
         L.og_get_state.argtypes = [vp, vp, vp, vp, vp, ctypes.POINTER(ctypes.c_long)]
         L.og_step.argtypes = [vp, ctypes.POINTER(ip), ctypes.POINTER(dp)]
@@ -106,18 +109,36 @@ def _ptr(a: np.ndarray) -> int:
 
 
 class Grid:
-    """Holds contiguous FP64 copies of a mask and fibre field."""
+    """Holds contiguous FP64 copies of a mask and fibre field, and optionally a
+    conducting torso (voxels outside the tissue, conductivity sig_o I) that
+    joins the domain of the operator."""
 
-    def __init__(self, nx: int, ny: int, nz: int, dx: float, mask, fib):
+    def __init__(self, nx: int, ny: int, nz: int, dx: float, mask, fib, torso=None, sig_o: float = 0.0):
         self.nx, self.ny, self.nz, self.dx = nx, ny, nz, float(dx)
         self.mask = np.ascontiguousarray(np.asarray(mask).reshape(-1), dtype=np.uint8)
         self.fib = np.ascontiguousarray(np.asarray(fib, dtype=np.float64).reshape(-1))
         assert self.mask.size == nx * ny * nz and self.fib.size == 3 * nx * ny * nz
-        self._g = _Grid(nx, ny, nz, self.dx, _ptr(self.mask), _ptr(self.fib))
+        self.torso = None
+        tp = None
+        if torso is not None:
+            self.torso = np.ascontiguousarray((np.asarray(torso).reshape(-1) != 0) & (self.mask == 0), dtype=np.uint8)
+            tp = _ptr(self.torso)
+        self._g = _Grid(nx, ny, nz, self.dx, _ptr(self.mask), _ptr(self.fib), tp, float(sig_o))
 
     @classmethod
     def from_case(cls, case) -> "Grid":
+        """The tissue grid of a case (torso left out: the intracellular operator)."""
         return cls(case.nx, case.ny, case.nz, case.dx, case.mask, case.fib)
+
+    @classmethod
+    def elliptic_from_case(cls, case) -> "Grid":
+        """The domain of the case's elliptic equation: tissue plus its torso, if any."""
+        return cls(case.nx, case.ny, case.nz, case.dx, case.mask, case.fib, case.torso, case.params.sig_o)
+
+    def domain(self) -> np.ndarray:
+        """Boolean membership of every voxel in the operator's domain."""
+        d = self.mask != 0
+        return d | (self.torso != 0) if self.torso is not None else d
 
     @property
     def n(self) -> int:
@@ -174,7 +195,8 @@ def _params_struct(p, model: int) -> _Params:
                    p.sig_iL, p.sig_iT, p.sig_eL, p.sig_eT, p.lam, p.K, p.dt, p.omega,
                    p.rel_tol, int(p.check_every), int(p.max_iter), int(model),
                    int(getattr(p, "diffusion", 0)), int(getattr(p, "solver", 0)),
-                   float(getattr(p, "cheb_lmin", 0.0)), float(getattr(p, "cheb_lmax", 0.0)))
+                   float(getattr(p, "cheb_lmin", 0.0)), float(getattr(p, "cheb_lmax", 0.0)),
+                   float(getattr(p, "sig_o", 0.0)))
 
 
 class Sim:
@@ -195,6 +217,10 @@ class Sim:
         self._h = lib().og_create(case.nx, case.ny, case.nz, float(case.dx),
                                   _ptr(self.grid.mask), _ptr(self.grid.fib),
                                   ctypes.byref(self._p), st, len(case.stimuli))
+        self._torso = None
+        if getattr(case, "torso", None) is not None:
+            self._torso = np.ascontiguousarray(np.asarray(case.torso).reshape(-1), dtype=np.uint8)
+            lib().og_set_torso(self._h, _ptr(self._torso))
         self.last_iters = 0
         self.last_relres = 0.0
 
@@ -255,3 +281,21 @@ def num_threads() -> int:
 def vm_mV(v):
     """Transmembrane potential in mV from dimensionless v (V_m = 100 v - 80)."""
     return 100.0 * np.asarray(v) - 80.0
+
+
+def electrode_potentials(case, ve) -> np.ndarray:
+    """Potentials (mV, V_e = 100 v_e) at the case's three electrodes RA, LA, LL."""
+    ve = np.asarray(ve).reshape(-1)
+    return np.array([100.0 * ve[i + case.nx * (j + case.ny * k)] for (i, j, k) in case.electrodes])
+
+
+def ecg_leads(phi) -> np.ndarray:
+    """The six limb leads from the electrode potentials (RA, LA, LL) (Sec.
+    "Electrocardiogram"): I = LA - RA, II = LL - RA, III = LL - LA, and the
+    augmented leads aVR, aVL, aVF, each one electrode minus the mean of the
+    other two.  phi: (..., 3); returns (..., 6) in the order I, II, III, aVR,
+    aVL, aVF."""
+    phi = np.asarray(phi, dtype=np.float64)
+    ra, la, ll = phi[..., 0], phi[..., 1], phi[..., 2]
+    return np.stack([la - ra, ll - ra, ll - la,
+                     ra - 0.5 * (la + ll), la - 0.5 * (ra + ll), ll - 0.5 * (ra + la)], axis=-1)

@@ -38,6 +38,14 @@
  *    Eq. iejac1 with A = -L (L approximates -div Sigma grad):
  *      monodomain  (I + a L_i) v+ = v*,             a = dt/K lambda/(1+lambda)
  *      bidomain    (I + a L_i) v+ = v* - a L_i ve^n, a = dt/K   (ve lagged to step n)
+ *  - Torso (Eq. bidomain1, lines 3-5): an optional set of conducting voxels
+ *    around the tissue with isotropic conductivity sig_o.  The extracellular
+ *    potential extends into it: the elliptic operator acts on tissue + torso
+ *    with Sigma_j = Sigma_i + Sigma_e on tissue voxels and sig_o I on torso
+ *    voxels (the same vertex averaging), which makes v_e continuous and the
+ *    extracellular current continuous across the tissue surface, and no-flux
+ *    on the outer surface of the torso; the intracellular operator and the
+ *    membrane state stay on the tissue.
  *  - Elliptic solve by damped Jacobi, Eq. dampjac1, from the previous ve,
  *    stopping when ||b - A x||_2 <= tol ||b||_2 (checked every m sweeps), then
  *    the reference potential is fixed by subtracting the mean over every
@@ -65,11 +73,18 @@ static long og_idx(const og_grid *g, int i, int j, int k)
     return (long)i + (long)g->nx * ((long)j + (long)g->ny * (long)k);
 }
 
+/* Voxel q belongs to the domain of the operator: tissue, or torso when the
+ * grid carries one. */
+static int og_in(const og_grid *g, long q)
+{
+    return g->mask[q] != 0 || (g->torso && g->torso[q] != 0);
+}
+
 static int og_tissue(const og_grid *g, int i, int j, int k)
 {
     if (i < 0 || j < 0 || k < 0 || i >= g->nx || j >= g->ny || k >= g->nz)
         return 0;
-    return g->mask[og_idx(g, i, j, k)] != 0;
+    return og_in(g, og_idx(g, i, j, k));
 }
 
 /* Offsets of the two voxels of pair number p (0..3) along axis a, inside the
@@ -89,7 +104,8 @@ static void og_pair(int I, int J, int K, int a, int p, int lo[3], int hi[3])
 }
 
 /* Vertex data: per axis the number of valid pairs, and the block tensor
- * S_p = (1/8) sum_{tissue j in block} Sigma_j. */
+ * S_p = (1/8) sum_{domain voxels j in block} Sigma_j, with Sigma_j the fibre
+ * tensor on tissue voxels and sig_o I on torso voxels. */
 static void og_vertex_tensor(const og_grid *g, int I, int J, int K, double sL, double sT,
                              double S[3][3])
 {
@@ -103,6 +119,11 @@ static void og_vertex_tensor(const og_grid *g, int I, int J, int K, double sL, d
                 int i = I - 1 + s, j = J - 1 + t, k = K - 1 + u;
                 if (!og_tissue(g, i, j, k))
                     continue;
+                if (!g->mask[og_idx(g, i, j, k)]) {   /* torso voxel */
+                    for (a = 0; a < 3; a++)
+                        S[a][a] += g->sig_o;
+                    continue;
+                }
                 const double *f = g->fib + 3 * og_idx(g, i, j, k);
                 for (a = 0; a < 3; a++)
                     for (b = 0; b < 3; b++)
@@ -237,7 +258,8 @@ void og_diag_L(const og_grid *g, double sL, double sT, double *diag)
     }
 }
 
-/* Face-connected (6-neighbour) components of the tissue; comp[q] = -1 off tissue. */
+/* Face-connected (6-neighbour) components of the domain (tissue, and torso if
+ * present); comp[q] = -1 outside. */
 int og_components(const og_grid *g, int *comp)
 {
     long n = (long)g->nx * g->ny * g->nz, q, head, tail;
@@ -246,7 +268,7 @@ int og_components(const og_grid *g, int *comp)
     for (q = 0; q < n; q++)
         comp[q] = -1;
     for (q = 0; q < n; q++) {
-        if (!g->mask[q] || comp[q] >= 0)
+        if (!og_in(g, q) || comp[q] >= 0)
             continue;
         head = tail = 0;
         queue[tail++] = q;
@@ -301,7 +323,7 @@ double og_default_omega(double sL, double sT)
     return w > 1.0 ? 1.0 : w;
 }
 
-/* Damped Jacobi (Eq. dampjac1) for A x = b on the tissue, A = L_{sL,sT}:
+/* Damped Jacobi (Eq. dampjac1) for A x = b on the domain, A = L_{sL,sT}:
  *   r^k = b - A x^k ;  x^{k+1} = x^k + omega D^{-1} r^k   (x_q kept where D_q = 0).
  * At k = 0, m, 2m, ... the relative residual ||r^k|| / ||b|| is formed; when it
  * is <= tol the sweep that used r^k is the last one.  Stops with status 1
@@ -315,7 +337,7 @@ int og_jacobi(const og_grid *g, double sL, double sT, const double *b, double *x
     double nb = 0.0, nr = 0.0;
     int k = 0, status = 1;
     for (q = 0; q < n; q++)
-        if (g->mask[q])
+        if (og_in(g, q))
             nb += b[q] * b[q];
     nb = sqrt(nb);
     *relres = 0.0;
@@ -336,7 +358,7 @@ int og_jacobi(const og_grid *g, double sL, double sT, const double *b, double *x
         if (check)
             nr = 0.0;
         for (q = 0; q < n; q++) {
-            if (!g->mask[q])
+            if (!og_in(g, q))
                 continue;
             double r = b[q] - Ax[q];
             if (check)
@@ -377,13 +399,13 @@ int og_ie_jacobi(const og_grid *g, double sL, double sT, double alpha, const dou
     double nf = 0.0, nr = 0.0;
     int k = 0, status = 1;
     for (q = 0; q < n; q++)
-        if (g->mask[q])
+        if (og_in(g, q))
             nf += f[q] * f[q];
     nf = sqrt(nf);
     *relres = 0.0;
     if (nf == 0.0) {
         for (q = 0; q < n; q++)
-            if (g->mask[q])
+            if (og_in(g, q))
                 x[q] = 0.0;
         *iters = 0;
         free(diag);
@@ -400,7 +422,7 @@ int og_ie_jacobi(const og_grid *g, double sL, double sT, double alpha, const dou
         if (check)
             nr = 0.0;
         for (q = 0; q < n; q++) {
-            if (!g->mask[q])
+            if (!og_in(g, q))
                 continue;
             if (check) {
                 double r = f[q] - (x[q] + alpha * Lx[q]);
@@ -410,7 +432,7 @@ int og_ie_jacobi(const og_grid *g, double sL, double sT, double alpha, const dou
             xn[q] = (f[q] - alpha * (Lx[q] - diag[q] * x[q])) / (1.0 + alpha * diag[q]);
         }
         for (q = 0; q < n; q++)
-            if (g->mask[q])
+            if (og_in(g, q))
                 x[q] = xn[q];
         if (check) {
             *relres = sqrt(nr) / nf;
@@ -451,7 +473,7 @@ int og_chebyshev(const og_grid *g, double sL, double sT, const double *b, double
     int k = 0, status = 1;
     for (q = 0; q < n; q++) {
         prev[q] = x[q];
-        if (g->mask[q])
+        if (og_in(g, q))
             nb += b[q] * b[q];
     }
     nb = sqrt(nb);
@@ -479,7 +501,7 @@ int og_chebyshev(const og_grid *g, double sL, double sT, const double *b, double
         if (check)
             nr = 0.0;
         for (q = 0; q < n; q++) {
-            if (!g->mask[q])
+            if (!og_in(g, q))
                 continue;
             double r = b[q] - Ax[q];
             if (check)
@@ -510,7 +532,9 @@ int og_chebyshev(const og_grid *g, double sL, double sT, const double *b, double
 /* ------------------------------------------------------------------------ */
 
 struct og_sim {
-    og_grid g;
+    og_grid g;                  /* tissue: membrane state and the intracellular operator */
+    og_grid ge;                 /* domain of the elliptic equation: tissue, plus the torso if set */
+    unsigned char *torso;       /* NULL without a torso */
     unsigned char *mask;
     double *fib;
     og_params p;
@@ -542,6 +566,9 @@ og_sim *og_create(int nx, int ny, int nz, double dx, const unsigned char *mask,
     s->g.dx = dx;
     s->g.mask = s->mask;
     s->g.fib = s->fib;
+    s->g.torso = NULL;
+    s->g.sig_o = 0.0;
+    s->ge = s->g;
     s->p = *p;
     s->nstim = nstim;
     s->stim = (og_stim *)malloc(sizeof(og_stim) * (size_t)(nstim > 0 ? nstim : 1));
@@ -570,6 +597,7 @@ void og_destroy(og_sim *s)
         return;
     free(s->mask);
     free(s->fib);
+    free(s->torso);
     free(s->stim);
     free(s->comp);
     free(s->v);
@@ -583,18 +611,37 @@ void og_destroy(og_sim *s)
     free(s);
 }
 
+/* Conducting torso around the tissue (voxels with torso[q] != 0 that are not
+ * tissue), conductivity p->sig_o.  The elliptic equation, its null space
+ * and v_e then live on tissue + torso.  Returns the number of domain
+ * components. */
+int og_set_torso(og_sim *s, const unsigned char *torso)
+{
+    long q;
+    if (!s->torso)
+        s->torso = (unsigned char *)malloc((size_t)s->n);
+    for (q = 0; q < s->n; q++)
+        s->torso[q] = (torso[q] != 0 && !s->mask[q]) ? 1 : 0;
+    s->ge = s->g;
+    s->ge.torso = s->torso;
+    s->ge.sig_o = s->p.sig_o;
+    s->ncomp = og_components(&s->ge, s->comp);
+    return s->ncomp;
+}
+
+/* v, w are taken on the tissue, ve on the domain of the elliptic equation. */
 void og_set_state(og_sim *s, const double *v, const double *w, const double *ve, long step)
 {
     long q;
     for (q = 0; q < s->n; q++) {
+        if (ve && og_in(&s->ge, q))
+            s->ve[q] = ve[q];
         if (!s->mask[q])
             continue;
         if (v)
             s->v[q] = v[q];
         if (w)
             s->w[q] = w[q];
-        if (ve)
-            s->ve[q] = ve[q];
     }
     s->step = step;
 }
@@ -696,17 +743,19 @@ int og_step(og_sim *s, int *iters, double *relres)
         s->v[q] = v1;
     }
 
-    /* 3. elliptic: (L_i + L_e) ve = -L_i v+, zero mean per component */
+    /* 3. elliptic: (L_i + L_e) ve = -L_i v+ (plus sig_o on the torso, where the
+     *    right-hand side is 0), zero mean per component of the domain */
     if (p->model == OG_BI) {
+        const og_grid *ge = &s->ge;
         og_apply_L(g, p->sig_iL, p->sig_iT, s->v, s->b);
         for (q = 0; q < n; q++)
             s->b[q] = s->mask[q] ? -s->b[q] : 0.0;
         og_project(n, s->ncomp, s->comp, s->b);
         if (p->solver == OG_CHEBYSHEV)
-            status = og_chebyshev(g, p->sig_iL + p->sig_eL, p->sig_iT + p->sig_eT, s->b, s->ve, p->cheb_lmin,
+            status = og_chebyshev(ge, p->sig_iL + p->sig_eL, p->sig_iT + p->sig_eT, s->b, s->ve, p->cheb_lmin,
                                   p->cheb_lmax, p->rel_tol, p->check_every, p->max_iter, iters, relres);
         else
-            status = og_jacobi(g, p->sig_iL + p->sig_eL, p->sig_iT + p->sig_eT, s->b, s->ve,
+            status = og_jacobi(ge, p->sig_iL + p->sig_eL, p->sig_iT + p->sig_eT, s->b, s->ve,
                                p->omega, p->rel_tol, p->check_every, p->max_iter, iters, relres);
         og_project(n, s->ncomp, s->comp, s->ve);
         s->total_iters += *iters;

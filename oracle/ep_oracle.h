@@ -17,6 +17,8 @@ typedef struct {
     double dx;                  /* mm */
     const unsigned char *mask;  /* n, 1 = tissue */
     const double *fib;          /* 3n, (fx, fy, fz) per voxel; unit or zero */
+    const unsigned char *torso; /* NULL, or n: 1 = conducting torso (bath) voxel outside the tissue */
+    double sig_o;               /* isotropic torso conductivity (mS/mm) */
 } og_grid;
 
 typedef struct {
@@ -27,6 +29,7 @@ typedef struct {
     int diffusion;              /* OG_EXPLICIT or OG_IMPLICIT (Eq. iejac1) */
     int solver;                 /* elliptic solve: OG_JACOBI (Eq. dampjac1) or OG_CHEBYSHEV */
     double cheb_lmin, cheb_lmax;   /* spectral interval of D^-1 A for OG_CHEBYSHEV */
+    double sig_o;               /* torso conductivity, used once og_set_torso is called */
 } og_params;
 
 #define OG_JACOBI 0
@@ -56,6 +59,7 @@ int og_chebyshev(const og_grid *g, double sL, double sT, const double *b, double
 og_sim *og_create(int nx, int ny, int nz, double dx, const unsigned char *mask,
                   const double *fib, const og_params *p, const og_stim *stim, int nstim);
 void og_destroy(og_sim *s);
+int og_set_torso(og_sim *s, const unsigned char *torso);
 void og_set_state(og_sim *s, const double *v, const double *w, const double *ve, long step);
 void og_get_state(const og_sim *s, double *v, double *w, double *ve, double *tact, long *step);
 int og_step(og_sim *s, int *iters, double *relres);

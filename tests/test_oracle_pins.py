@@ -145,12 +145,14 @@ def _dense(g, sL, sT):
     return A, t
 
 
-def _assemble_independent(c, sL, sT):
+def _assemble_independent(c, sL, sT, torso=None, sig_o=0.0):
     """Independent sparse assembly of G'^T S G' (scipy), enumerating vertex
-    blocks and their valid voxel pairs directly."""
+    blocks and their valid voxel pairs directly.  With a torso, its voxels
+    join the domain with the tensor sig_o I."""
     import scipy.sparse as sp
     nx, ny, nz, dx = c.nx, c.ny, c.nz, c.dx
-    m = c.mask.astype(bool)
+    heart = c.mask.astype(bool)
+    m = heart if torso is None else heart | (np.asarray(torso).reshape(heart.shape) > 0)
     f = c.fib.astype(np.float64)
     t_idx = -np.ones(m.shape, int)
     t_idx[m] = np.arange(m.sum())
@@ -163,7 +165,10 @@ def _assemble_independent(c, sL, sT):
                        if 0 <= i < nx and 0 <= j < ny and 0 <= k < nz and m[k, j, i]]
                 S = np.zeros((3, 3))
                 for (k, j, i) in blk:
-                    S += sT * np.eye(3) + (sL - sT) * np.outer(f[k, j, i], f[k, j, i])
+                    if heart[k, j, i]:
+                        S += sT * np.eye(3) + (sL - sT) * np.outer(f[k, j, i], f[k, j, i])
+                    else:
+                        S += sig_o * np.eye(3)
                 S /= 8.0
                 for a in range(3):
                     pairs = []

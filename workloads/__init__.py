@@ -78,6 +78,7 @@ class Params:
     solver: int = 0           # elliptic solve: 0 damped Jacobi (Eq. dampjac1), 1 Chebyshev-accelerated Jacobi
     cheb_lmin: float = 0.0    # spectral interval of D^-1 A for the Chebyshev solver (<= 0: estimated)
     cheb_lmax: float = 0.0
+    sig_o: float = 0.0        # isotropic torso conductivity (mS/mm), used when the case has a torso
 
 
 @dataclasses.dataclass
@@ -94,6 +95,8 @@ class Case:
     model: int = BI
     precision: int = FP32
     steps: int = 100
+    torso: Optional[np.ndarray] = None      # uint8 (nz, ny, nx): conducting torso voxels outside the tissue
+    electrodes: Optional[List[Tuple[int, int, int]]] = None   # (i, j, k) of RA, LA, LL
 
     @property
     def n(self) -> int:
@@ -366,5 +369,36 @@ def random_state(seed: int, case: Case):
     w = rng.uniform(0.2, 1.0, size=v.shape)
     ve = 0.1 * rng.standard_normal(v.shape)
     t = case.mask > 0
+    d = t if case.torso is None else t | (case.torso > 0)   # v_e lives on tissue + torso
     return (np.where(t, v, 0.0).reshape(-1), np.where(t, w, 1.0).reshape(-1),
-            np.where(t, ve, 0.0).reshape(-1))
+            np.where(d, ve, 0.0).reshape(-1))
+
+
+def corner_electrodes(nx: int, ny: int, nz: int) -> List[Tuple[int, int, int]]:
+    """RA, LA, LL at corners of the box: the arms at the top (high z) on either
+    side in y, the leg at the bottom corner diametrically opposite RA."""
+    return [(0, ny - 1, nz - 1), (0, 0, nz - 1), (nx - 1, 0, 0)]
+
+
+def with_torso(case: Case, sig_o: float = 1.0, pad: int = 0, fill: Optional[float] = None,
+               seed: int = 0) -> Case:
+    """The case's tissue inside a conducting torso of isotropic conductivity
+    sig_o (mS/mm): the grid grows by `pad` voxels on every side and every
+    non-tissue voxel of the box is torso (or, with `fill`, a random fraction of
+    them, for tests).  Electrodes RA, LA, LL at corners of the box."""
+    nx, ny, nz = case.nx + 2 * pad, case.ny + 2 * pad, case.nz + 2 * pad
+    mask = np.zeros((nz, ny, nx), np.uint8)
+    fib = np.zeros((nz, ny, nx, 3), np.float32)
+    sl = (slice(pad, pad + case.nz), slice(pad, pad + case.ny), slice(pad, pad + case.nx))
+    mask[sl] = case.mask
+    fib[sl] = case.fib
+    torso = (mask == 0).astype(np.uint8)
+    if fill is not None:
+        rng = np.random.default_rng(seed + 104729)
+        torso &= (rng.random(torso.shape) < fill).astype(np.uint8)
+    p = dataclasses.replace(case.params, sig_o=sig_o)
+    stims = [Stimulus(tuple(a + pad for a in st.lo), tuple(a + pad for a in st.hi), st.t_start, st.dur, st.amp)
+             for st in case.stimuli]
+    return Case(case.name + f"_torso{pad}", nx, ny, nz, case.dx, mask, fib, p, stims, model=case.model,
+                precision=case.precision, steps=case.steps, torso=torso,
+                electrodes=corner_electrodes(nx, ny, nz))
