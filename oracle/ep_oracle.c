@@ -40,12 +40,17 @@
  *      bidomain    (I + a L_i) v+ = v* - a L_i ve^n, a = dt/K   (ve lagged to step n)
  *  - Torso (Eq. bidomain1, lines 3-5): an optional set of conducting voxels
  *    around the tissue with isotropic conductivity sig_o.  The extracellular
- *    potential extends into it: the elliptic operator acts on tissue + torso
- *    with Sigma_j = Sigma_i + Sigma_e on tissue voxels and sig_o I on torso
- *    voxels (the same vertex averaging), which makes v_e continuous and the
- *    extracellular current continuous across the tissue surface, and no-flux
- *    on the outer surface of the torso; the intracellular operator and the
- *    membrane state stay on the tissue.
+ *    potential extends into it, and the elliptic operator on tissue + torso
+ *    is the sum of two vertex operators: the tissue's (pairs of tissue
+ *    voxels, Sigma_i + Sigma_e of the tissue voxels of the block) and the
+ *    torso's (pairs of any two domain voxels, sig_o I times the fraction of
+ *    torso voxels in the block).  The torso term carries the current across
+ *    the heart surface and through the torso; no current leaves the torso's
+ *    outer surface; both terms conserve charge.  Keeping the tissue term on
+ *    tissue pairs makes the operator dominate the intracellular one, which
+ *    the explicit split needs to stay stable (one vertex average over both
+ *    media does not, and the step diverges).  The intracellular operator and
+ *    the membrane state stay on the tissue.
  *  - Elliptic solve by damped Jacobi, Eq. dampjac1, from the previous ve,
  *    stopping when ||b - A x||_2 <= tol ||b||_2 (checked every m sweeps), then
  *    the reference potential is fixed by subtracting the mean over every
@@ -87,6 +92,19 @@ static int og_tissue(const og_grid *g, int i, int j, int k)
     return og_in(g, og_idx(g, i, j, k));
 }
 
+/* The operator is a sum of vertex terms in two parts.  OG_TISSUE: pairs of
+ * tissue voxels, tensor from the tissue voxels of the block (the operator of
+ * the thesis).  OG_TORSO (grids with a torso): pairs of domain voxels, tensor
+ * sig_o I from the torso voxels of the block. */
+enum { OG_TISSUE = 0, OG_TORSO = 1 };
+
+static int og_member(const og_grid *g, int part, int i, int j, int k)
+{
+    if (i < 0 || j < 0 || k < 0 || i >= g->nx || j >= g->ny || k >= g->nz)
+        return 0;
+    return part == OG_TISSUE ? g->mask[og_idx(g, i, j, k)] != 0 : og_in(g, og_idx(g, i, j, k));
+}
+
 /* Offsets of the two voxels of pair number p (0..3) along axis a, inside the
  * 2x2x2 block of vertex (I,J,K).  The block voxels are (I-1+s, J-1+t, K-1+u)
  * with s,t,u in {0,1}; along axis a the pair is (lo: offset 0, hi: offset 1)
@@ -103,10 +121,9 @@ static void og_pair(int I, int J, int K, int a, int p, int lo[3], int hi[3])
     hi[a] += 1;
 }
 
-/* Vertex data: per axis the number of valid pairs, and the block tensor
- * S_p = (1/8) sum_{domain voxels j in block} Sigma_j, with Sigma_j the fibre
- * tensor on tissue voxels and sig_o I on torso voxels. */
-static void og_vertex_tensor(const og_grid *g, int I, int J, int K, double sL, double sT,
+/* Block tensor of a part: OG_TISSUE S_p = (1/8) sum_{tissue j in block} Sigma_j;
+ * OG_TORSO S_p = (1/8) (torso voxels in block) sig_o I. */
+static void og_vertex_tensor(const og_grid *g, int part, int I, int J, int K, double sL, double sT,
                              double S[3][3])
 {
     int a, b, s, t, u;
@@ -117,14 +134,16 @@ static void og_vertex_tensor(const og_grid *g, int I, int J, int K, double sL, d
         for (t = 0; t < 2; t++)
             for (s = 0; s < 2; s++) {
                 int i = I - 1 + s, j = J - 1 + t, k = K - 1 + u;
-                if (!og_tissue(g, i, j, k))
+                if (!og_member(g, part, i, j, k))
                     continue;
-                if (!g->mask[og_idx(g, i, j, k)]) {   /* torso voxel */
-                    for (a = 0; a < 3; a++)
-                        S[a][a] += g->sig_o;
+                long q = og_idx(g, i, j, k);
+                if (part == OG_TORSO) {
+                    if (!g->mask[q])
+                        for (a = 0; a < 3; a++)
+                            S[a][a] += g->sig_o;
                     continue;
                 }
-                const double *f = g->fib + 3 * og_idx(g, i, j, k);
+                const double *f = g->fib + 3 * q;
                 for (a = 0; a < 3; a++)
                     for (b = 0; b < 3; b++)
                         S[a][b] += (a == b ? sT : 0.0) + (sL - sT) * f[a] * f[b];
@@ -134,20 +153,20 @@ static void og_vertex_tensor(const og_grid *g, int I, int J, int K, double sL, d
             S[a][b] *= 0.125;
 }
 
-static int og_count_pairs(const og_grid *g, int I, int J, int K, int a)
+static int og_count_pairs(const og_grid *g, int part, int I, int J, int K, int a)
 {
     int p, n = 0, lo[3], hi[3];
     for (p = 0; p < 4; p++) {
         og_pair(I, J, K, a, p, lo, hi);
-        if (og_tissue(g, lo[0], lo[1], lo[2]) && og_tissue(g, hi[0], hi[1], hi[2]))
+        if (og_member(g, part, lo[0], lo[1], lo[2]) && og_member(g, part, hi[0], hi[1], hi[2]))
             n++;
     }
     return n;
 }
 
-/* Contribution of vertex (I,J,K) to out = L u:  g = G'_p u, F = S_p g,
- * out += G'_p^T F. */
-static void og_vertex_apply(const og_grid *g, int I, int J, int K, double sL, double sT,
+/* Contribution of one part of vertex (I,J,K) to out = L u:  g = G'_p u,
+ * F = S_p g, out += G'_p^T F. */
+static void og_vertex_apply(const og_grid *g, int part, int I, int J, int K, double sL, double sT,
                             const double *u, double *out)
 {
     double S[3][3], grad[3], F[3];
@@ -157,7 +176,7 @@ static void og_vertex_apply(const og_grid *g, int I, int J, int K, double sL, do
         np[a] = 0;
         for (p = 0; p < 4; p++) {
             og_pair(I, J, K, a, p, lo, hi);
-            if (og_tissue(g, lo[0], lo[1], lo[2]) && og_tissue(g, hi[0], hi[1], hi[2])) {
+            if (og_member(g, part, lo[0], lo[1], lo[2]) && og_member(g, part, hi[0], hi[1], hi[2])) {
                 sum += u[og_idx(g, hi[0], hi[1], hi[2])] - u[og_idx(g, lo[0], lo[1], lo[2])];
                 np[a]++;
             }
@@ -166,7 +185,7 @@ static void og_vertex_apply(const og_grid *g, int I, int J, int K, double sL, do
     }
     if (!np[0] && !np[1] && !np[2])
         return;
-    og_vertex_tensor(g, I, J, K, sL, sT, S);
+    og_vertex_tensor(g, part, I, J, K, sL, sT, S);
     for (a = 0; a < 3; a++) {
         F[a] = 0.0;
         for (b = 0; b < 3; b++)
@@ -178,7 +197,7 @@ static void og_vertex_apply(const og_grid *g, int I, int J, int K, double sL, do
         double wgt = F[a] / (np[a] * g->dx);
         for (p = 0; p < 4; p++) {
             og_pair(I, J, K, a, p, lo, hi);
-            if (og_tissue(g, lo[0], lo[1], lo[2]) && og_tissue(g, hi[0], hi[1], hi[2])) {
+            if (og_member(g, part, lo[0], lo[1], lo[2]) && og_member(g, part, hi[0], hi[1], hi[2])) {
                 out[og_idx(g, hi[0], hi[1], hi[2])] += wgt;
                 out[og_idx(g, lo[0], lo[1], lo[2])] -= wgt;
             }
@@ -186,32 +205,32 @@ static void og_vertex_apply(const og_grid *g, int I, int J, int K, double sL, do
     }
 }
 
-/* Contribution of vertex (I,J,K) to the diagonal of L: for every tissue voxel q
- * of the block, c = d g_p / d u_q and diag_q += c^T S_p c. */
-static void og_vertex_diag(const og_grid *g, int I, int J, int K, double sL, double sT,
+/* Contribution of one part of vertex (I,J,K) to the diagonal of L: for every
+ * member voxel q of the block, c = d g_p / d u_q and diag_q += c^T S_p c. */
+static void og_vertex_diag(const og_grid *g, int part, int I, int J, int K, double sL, double sT,
                            double *diag)
 {
     double S[3][3];
     int np[3], a, b, s, t, u;
     for (a = 0; a < 3; a++)
-        np[a] = og_count_pairs(g, I, J, K, a);
+        np[a] = og_count_pairs(g, part, I, J, K, a);
     if (!np[0] && !np[1] && !np[2])
         return;
-    og_vertex_tensor(g, I, J, K, sL, sT, S);
+    og_vertex_tensor(g, part, I, J, K, sL, sT, S);
     for (u = 0; u < 2; u++)
         for (t = 0; t < 2; t++)
             for (s = 0; s < 2; s++) {
                 int q[3] = {I - 1 + s, J - 1 + t, K - 1 + u};
                 int off[3] = {s, t, u};
                 double c[3], acc = 0.0;
-                if (!og_tissue(g, q[0], q[1], q[2]))
+                if (!og_member(g, part, q[0], q[1], q[2]))
                     continue;
                 for (a = 0; a < 3; a++) {
                     /* partner of q along a inside the block */
                     int r[3] = {q[0], q[1], q[2]};
                     r[a] += off[a] ? -1 : 1;
                     c[a] = 0.0;
-                    if (np[a] && og_tissue(g, r[0], r[1], r[2]))
+                    if (np[a] && og_member(g, part, r[0], r[1], r[2]))
                         c[a] = (off[a] ? 1.0 : -1.0) / (np[a] * g->dx);
                 }
                 for (a = 0; a < 3; a++)
@@ -235,8 +254,11 @@ void og_apply_L(const og_grid *g, double sL, double sT, const double *u, double 
         for (K = color; K <= g->nz; K += 2) {
             int I, J;
             for (J = 0; J <= g->ny; J++)
-                for (I = 0; I <= g->nx; I++)
-                    og_vertex_apply(g, I, J, K, sL, sT, u, out);
+                for (I = 0; I <= g->nx; I++) {
+                    og_vertex_apply(g, OG_TISSUE, I, J, K, sL, sT, u, out);
+                    if (g->torso)
+                        og_vertex_apply(g, OG_TORSO, I, J, K, sL, sT, u, out);
+                }
         }
     }
 }
@@ -252,8 +274,11 @@ void og_diag_L(const og_grid *g, double sL, double sT, double *diag)
         for (K = color; K <= g->nz; K += 2) {
             int I, J;
             for (J = 0; J <= g->ny; J++)
-                for (I = 0; I <= g->nx; I++)
-                    og_vertex_diag(g, I, J, K, sL, sT, diag);
+                for (I = 0; I <= g->nx; I++) {
+                    og_vertex_diag(g, OG_TISSUE, I, J, K, sL, sT, diag);
+                    if (g->torso)
+                        og_vertex_diag(g, OG_TORSO, I, J, K, sL, sT, diag);
+                }
         }
     }
 }

@@ -145,14 +145,18 @@ def _dense(g, sL, sT):
     return A, t
 
 
-def _assemble_independent(c, sL, sT, torso=None, sig_o=0.0):
+def _assemble_independent(c, sL, sT, torso=None, sig_o=0.0, part="tissue"):
     """Independent sparse assembly of G'^T S G' (scipy), enumerating vertex
-    blocks and their valid voxel pairs directly.  With a torso, its voxels
-    join the domain with the tensor sig_o I."""
+    blocks and their valid voxel pairs directly.  With a torso the matrix
+    spans tissue + torso voxels, and part selects the term: "tissue" (pairs
+    of tissue voxels, tensor from the tissue voxels of the block) or "torso"
+    (pairs of any two domain voxels, tensor sig_o I per torso voxel of the
+    block)."""
     import scipy.sparse as sp
     nx, ny, nz, dx = c.nx, c.ny, c.nz, c.dx
     heart = c.mask.astype(bool)
     m = heart if torso is None else heart | (np.asarray(torso).reshape(heart.shape) > 0)
+    member = heart if part == "tissue" else m
     f = c.fib.astype(np.float64)
     t_idx = -np.ones(m.shape, int)
     t_idx[m] = np.arange(m.sum())
@@ -162,12 +166,12 @@ def _assemble_independent(c, sL, sT, torso=None, sig_o=0.0):
         for J in range(ny + 1):
             for I in range(nx + 1):
                 blk = [(k, j, i) for k in (K - 1, K) for j in (J - 1, J) for i in (I - 1, I)
-                       if 0 <= i < nx and 0 <= j < ny and 0 <= k < nz and m[k, j, i]]
+                       if 0 <= i < nx and 0 <= j < ny and 0 <= k < nz and member[k, j, i]]
                 S = np.zeros((3, 3))
                 for (k, j, i) in blk:
-                    if heart[k, j, i]:
+                    if part == "tissue":
                         S += sT * np.eye(3) + (sL - sT) * np.outer(f[k, j, i], f[k, j, i])
-                    else:
+                    elif not heart[k, j, i]:
                         S += sig_o * np.eye(3)
                 S /= 8.0
                 for a in range(3):
@@ -176,7 +180,7 @@ def _assemble_independent(c, sL, sT, torso=None, sig_o=0.0):
                         hi = [i, j, k]
                         hi[a] += 1
                         hi_in_block = (hi[0] == I and a == 0) or (hi[1] == J and a == 1) or (hi[2] == K and a == 2)
-                        if hi_in_block and hi[0] < nx and hi[1] < ny and hi[2] < nz and m[hi[2], hi[1], hi[0]]:
+                        if hi_in_block and hi[0] < nx and hi[1] < ny and hi[2] < nz and member[hi[2], hi[1], hi[0]]:
                             pairs.append((t_idx[k, j, i], t_idx[hi[2], hi[1], hi[0]]))
                     for lo_q, hi_q in pairs:
                         rows += [r + a, r + a]

@@ -2,11 +2,12 @@
 potential continues into a passive conductor around the heart) and of the
 ECG lead formulas (Sec. "Electrocardiogram").
 
-The torso operator is checked against an independent dense assembly, against
-the plain operator it must reduce to when the torso conducts like zero-fibre
-tissue, and against the layered closed form (an insulated torso layer takes
+The torso operator is checked against an independent dense assembly of its
+two terms, against the plain operator it reduces to without tissue, against
+the domination of the intracellular operator that keeps the explicit split
+stable, and against the layered closed form (an insulated torso layer takes
 the potential of the tissue surface it touches); the step against charge
-conservation and the rest state."""
+conservation, the rest state and boundedness."""
 import numpy as np
 import pytest
 
@@ -25,18 +26,29 @@ def _dense_domain(g, sL, sT):
     return A, t
 
 
+def _dense_domain_part(g, sL, sT, idx):
+    A = np.zeros((len(idx), len(idx)))
+    for col, q in enumerate(idx):
+        e = np.zeros(g.n)
+        e[q] = 1.0
+        A[:, col] = g.apply_L(sL, sT, e)[idx]
+    return A
+
+
 @pytest.mark.parametrize("seed", [51, 52])
 def test_torso_operator_matches_independent_assembly(seed):
-    """Applying the oracle to unit vectors on tissue + torso gives the
-    independently assembled G'^T S G' with sig_o I on the torso voxels; the
-    matrix is symmetric PSD with zero row sums, and its diagonal is the
-    oracle's Jacobi diagonal."""
+    """Applying the oracle to unit vectors on tissue + torso gives the sum of
+    the independently assembled tissue term (tissue pairs, fibre tensors) and
+    torso term (domain pairs, sig_o I per torso voxel); the matrix is
+    symmetric PSD with zero row sums, and its diagonal is the oracle's Jacobi
+    diagonal."""
     c = W.with_torso(W.random_case(seed, 5, 4, 4, fill=0.5), sig_o=0.7, fill=0.8, seed=seed)
     g = oracle.Grid.elliptic_from_case(c)
     sL, sT = 0.4, 0.15
     A, t = _dense_domain(g, sL, sT)
     assert len(t) > c.n_tissue   # the torso joined the domain
-    B = _assemble_independent(c, sL, sT, torso=c.torso, sig_o=0.7)
+    B = _assemble_independent(c, sL, sT, torso=c.torso, sig_o=0.7, part="tissue") + \
+        _assemble_independent(c, sL, sT, torso=c.torso, sig_o=0.7, part="torso")
     np.testing.assert_allclose(A, B, rtol=1e-12, atol=1e-12)
     np.testing.assert_allclose(A, A.T, rtol=0, atol=1e-12)
     np.testing.assert_allclose(A.sum(axis=1), 0.0, atol=1e-12)
@@ -44,22 +56,39 @@ def test_torso_operator_matches_independent_assembly(seed):
     np.testing.assert_allclose(g.diag_L(sL, sT)[t], np.diag(A), rtol=1e-13, atol=1e-13)
 
 
-def test_torso_conducting_like_isotropic_tissue_is_the_plain_operator():
-    """Zero fibres make the tissue tensor sT I; a torso with sig_o = sT is then
-    indistinguishable from tissue, so the operator equals the plain one on the
-    union mask, bit for bit (the same sums in the same order)."""
+def test_torso_without_tissue_is_the_plain_isotropic_operator():
+    """With no tissue voxel the torso term alone remains: the plain operator
+    of the torso voxels with sigma_L = sigma_T = sig_o and zero fibres, bit for
+    bit (the same sums in the same order)."""
     base = W.random_case(53, 9, 8, 7, fill=0.5)
-    base.fib[...] = 0.0
-    c = W.with_torso(base, sig_o=0.15, fill=0.7, seed=53)
-    g = oracle.Grid.elliptic_from_case(c)
-    union = oracle.Grid(c.nx, c.ny, c.nz, c.dx, (c.mask > 0) | (c.torso > 0), np.zeros(3 * c.n))
+    c = W.with_torso(base, sig_o=0.35, fill=0.7, seed=53)
+    empty = np.zeros(c.n, np.uint8)
+    g = oracle.Grid(c.nx, c.ny, c.nz, c.dx, empty, np.zeros(3 * c.n), c.torso, 0.35)
+    plain = oracle.Grid(c.nx, c.ny, c.nz, c.dx, c.torso, np.zeros(3 * c.n))
     rng = np.random.default_rng(53)
     u = rng.standard_normal(c.n)
-    np.testing.assert_array_equal(g.apply_L(0.4, 0.15, u), union.apply_L(0.4, 0.15, u))
-    np.testing.assert_array_equal(g.diag_L(0.4, 0.15), union.diag_L(0.4, 0.15))
+    np.testing.assert_array_equal(g.apply_L(0.4, 0.15, u), plain.apply_L(0.35, 0.35, u))
+    np.testing.assert_array_equal(g.diag_L(0.4, 0.15), plain.diag_L(0.35, 0.35))
     nc, comp = g.components()
-    nc2, comp2 = union.components()
+    nc2, comp2 = plain.components()
     assert nc == nc2 and np.array_equal(comp, comp2)
+
+
+@pytest.mark.parametrize("seed", [54, 55])
+def test_torso_operator_dominates_the_intracellular_one(seed):
+    """A - L_i >= 0 on tissue + torso (L_i extended by zero), hence the
+    operator of the explicit split, L_i - L_i A^+ L_i, is PSD and bounded by
+    L_i: the bidomain step with a torso is as stable as the plain one."""
+    c = W.with_torso(W.random_case(seed, 7, 6, 6, fill=0.5), sig_o=1.0, fill=0.9, seed=seed)
+    p = c.params
+    ge, gh = oracle.Grid.elliptic_from_case(c), oracle.Grid.from_case(c)
+    idx = np.nonzero(ge.domain())[0]
+    A = _dense_domain_part(ge, p.sig_iL + p.sig_eL, p.sig_iT + p.sig_eT, idx)
+    Li = _dense_domain_part(gh, p.sig_iL, p.sig_iT, idx)
+    assert np.linalg.eigvalsh(A - Li).min() > -1e-12
+    M = Li - Li @ np.linalg.pinv(A, rcond=1e-12) @ Li
+    ev = np.linalg.eigvalsh(0.5 * (M + M.T))
+    assert ev.min() > -1e-9 and ev.max() <= np.linalg.eigvalsh(Li).max() * (1 + 1e-9)
 
 
 def _layered(sig_o):

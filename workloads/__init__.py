@@ -273,6 +273,15 @@ def config2(seed: int = 0, unequal: bool = False, n: int = 256) -> Case:
                 _fp16_exact(f), p, [stim], model=BI, precision=FP32, steps=20000)
 
 
+def ecg_case(n: int = 256, sig_o: float = 1.0, seed: int = 0) -> Case:
+    """The config 2 heart in its n^3 box, every other voxel of the box a
+    conducting torso of conductivity sig_o (mS/mm), electrodes RA, LA, LL at
+    corners of the box (the ECG set-up of Sec. "Electrocardiogram")."""
+    c = with_torso(config2(seed=seed, n=n), sig_o=sig_o)
+    c.name = f"ecg_biv{n}_sigo{sig_o:g}"
+    return c
+
+
 def sampled_shell(rng: np.random.Generator, n: int, steps: int, name: str) -> Case:
     """One instance of the batched / served workloads: shell scaled by n/128
     from config 1, sampled conductivities, stimulus at a random tissue voxel."""
@@ -393,12 +402,14 @@ def with_torso(case: Case, sig_o: float = 1.0, pad: int = 0, fill: Optional[floa
     mask[sl] = case.mask
     fib[sl] = case.fib
     torso = (mask == 0).astype(np.uint8)
+    electrodes = corner_electrodes(nx, ny, nz)
     if fill is not None:
         rng = np.random.default_rng(seed + 104729)
         torso &= (rng.random(torso.shape) < fill).astype(np.uint8)
+        for (i, j, k) in electrodes:   # the electrodes stay on the domain
+            torso[k, j, i] = 0 if mask[k, j, i] else 1
     p = dataclasses.replace(case.params, sig_o=sig_o)
     stims = [Stimulus(tuple(a + pad for a in st.lo), tuple(a + pad for a in st.hi), st.t_start, st.dur, st.amp)
              for st in case.stimuli]
     return Case(case.name + f"_torso{pad}", nx, ny, nz, case.dx, mask, fib, p, stims, model=case.model,
-                precision=case.precision, steps=case.steps, torso=torso,
-                electrodes=corner_electrodes(nx, ny, nz))
+                precision=case.precision, steps=case.steps, torso=torso, electrodes=electrodes)
