@@ -43,12 +43,14 @@ def _args():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["config2", "config0", "config1", "config3", "config4", "slab"],
+    ap.add_argument("--workload", choices=["config2", "config0", "config1", "config3", "config4", "slab", "ecg"],
                     default="config2")
     ap.add_argument("--model", choices=["mono", "bi"], default="mono", help="slab: model")
     ap.add_argument("--slab-n", type=int, default=512, help="slab: voxels per side")
-    ap.add_argument("--solver", choices=["jacobi", "chebyshev"], default="jacobi",
-                    help="elliptic solve: the paper's damped Jacobi, or Chebyshev-accelerated Jacobi")
+    ap.add_argument("--solver", choices=["jacobi", "chebyshev"], default=None,
+                    help="elliptic solve: the paper's damped Jacobi, or Chebyshev-accelerated Jacobi "
+                         "(default: jacobi; chebyshev for ecg)")
+    ap.add_argument("--sig-o", type=float, default=1.0, help="ecg: torso conductivity (mS/mm)")
     ap.add_argument("--diffusion", choices=["explicit", "implicit"], default="explicit",
                     help="parabolic step: explicit Euler, or implicit Euler solved by Jacobi (Eq. iejac1)")
     ap.add_argument("--instances", type=int, default=64, help="config3: number of instances")
@@ -65,8 +67,8 @@ def _args():
     return ap.parse_args()
 
 
-def _workload(name, model="mono", slab_n=512, diffusion="explicit", solver="jacobi"):
-    c, desc = _workload_case(name, model, slab_n)
+def _workload(name, model="mono", slab_n=512, diffusion="explicit", solver=None, sig_o=1.0):
+    c, desc = _workload_case(name, model, slab_n, sig_o)
     if diffusion == "implicit":
         c.params.diffusion = 1
         desc += "; implicit-Euler diffusion (Jacobi, Eq. iejac1)"
@@ -76,8 +78,14 @@ def _workload(name, model="mono", slab_n=512, diffusion="explicit", solver="jaco
     return c, desc
 
 
-def _workload_case(name, model, slab_n):
+def _workload_case(name, model, slab_n, sig_o=1.0):
     import workloads as W
+    if name == "ecg":
+        c = W.ecg_case(sig_o=sig_o)
+        desc = (f"ecg: config2 heart (bidomain FP32, 256^3 biventricular, 20.3% tissue) in a torso filling the rest "
+                f"of the box (sig_o {sig_o:g} mS/mm), ECG electrodes RA, LA, LL at box corners; the elliptic "
+                f"solve spans all 16.8M voxels")
+        return c, desc
     if name == "slab":
         bi = model == "bi"
         c = W.slab(slab_n, W.BI if bi else W.MONO, unequal=bi)
@@ -238,13 +246,16 @@ def oracle_sample(case, sweeps_per_step, n_samples=1):
 
 def _oracle_case(a, case):
     """The case the oracle is timed on: the workload itself, except for the
-    slab above 256^3, whose bounded sample is a 256^3 slab of the same
-    construction (the rate is per tissue voxel)."""
+    slab above 256^3 and the ECG workload, whose bounded samples are the same
+    construction at 256^3 and 128^3 (the rate is per tissue voxel)."""
     if a.workload == "slab" and a.slab_n > 256:
         import workloads as W
         oc = W.slab(256, case.model, unequal=case.model == 1)
         oc.params.diffusion = case.params.diffusion
         return oc
+    if a.workload == "ecg":   # the same construction at 128^3 (the oracle's sweep spans the whole box)
+        import workloads as W
+        return W.ecg_case(n=128, sig_o=case.params.sig_o)
     return case
 
 
@@ -252,7 +263,7 @@ def run_reference(a):
     world, rank, local = _dist()
     if rank != 0:
         return
-    case, desc = _workload(a.workload, a.model, a.slab_n, a.diffusion, a.solver)
+    case, desc = _workload(a.workload, a.model, a.slab_n, a.diffusion, a.solver, a.sig_o)
     M = case.n_tissue
     k_ref = a.ref_sweeps_per_step or DEFAULT_REF_SWEEPS_PER_STEP
     times = []
@@ -264,7 +275,7 @@ def run_reference(a):
             times.append(info["step_s"])
     tot = sum(times)
     value = oc.n_tissue * a.steps / tot   # tissue voxel-steps/s of the sampled case
-    what = "a 256^3 slab of the same construction" if oc is not case else "the workload"
+    what = f"the same construction at {oc.nx}^3" if oc is not case else "the workload"
     sample = (f"per step: one oracle step of {what} with the Jacobi solve capped at "
               f"{REF_SAMPLE_SWEEPS[0]} and {REF_SAMPLE_SWEEPS[1]} sweeps (fixed {info['fixed_s']:.2f} s, "
               f"{info['per_sweep_s']:.3f} s/sweep), extrapolated to {k_ref:.0f} sweeps per step")
@@ -291,7 +302,7 @@ def run_ours(a):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     epbuild.build()
-    case, desc = _workload(a.workload, a.model, a.slab_n, a.diffusion, a.solver)
+    case, desc = _workload(a.workload, a.model, a.slab_n, a.diffusion, a.solver, a.sig_o)
     M = case.n_tissue
     mono = case.model == 0
     stream = torch.cuda.Stream()
@@ -303,6 +314,12 @@ def run_ours(a):
     sim.set_params(case.params)
     for s in case.stimuli:
         sim.add_stimulus(s.lo, s.hi, s.t_start, s.dur, s.amp)
+    torso = case.torso is not None
+    if torso:
+        sim.set_torso(case.torso, case.params.sig_o)
+    ecg = case.electrodes is not None and case.model == 1
+    if ecg:   # room for the warm-up, the timed window and its end-to-end replay
+        sim.set_ecg(case.electrodes, a.warmup + 2 * a.steps + 1)
     if a.solver == "chebyshev":   # the oracle baseline runs the same semi-iteration on the same interval
         info = sim.info()
         case.params.cheb_lmin, case.params.cheb_lmax = info.cheb_lmin, info.cheb_lmax
@@ -311,6 +328,7 @@ def run_ours(a):
     for _ in range(a.warmup):
         sim.step(1, allow_noconv=True)
     torch.cuda.synchronize()
+    n_dom = sim.info().n_domain   # voxels of the elliptic sweeps (tissue + torso)
     # snapshot of the state that starts the timed window (the e2e leg replays the same steps)
     nb = sim.state_bytes()
     blobs = [torch.empty(nb, dtype=torch.uint8, pin_memory=True).numpy() for _ in range(2)]
@@ -364,22 +382,34 @@ def run_ours(a):
     else:
         sweep_s = prof.sweep_ms / 1e3
         launch_s = sweep_s / max(prof.sweeps, 1)
-        alg_bytes = BYTES_PER_SWEEP_VOXEL * M
-        kname, share = "k_stencil<float,M_JAC> (damped Jacobi sweep)", sweep_s / total_s
+        alg_bytes = BYTES_PER_SWEEP_VOXEL * n_dom   # over tissue + torso when a torso is set
+        kname = ("k_stencil<float,M_JAC_BATH> (elliptic sweep over tissue + torso)" if torso else
+                 "k_stencil<float,M_JAC> (damped Jacobi sweep)")
+        if a.solver == "chebyshev":
+            kname += ", Chebyshev-accelerated"
+        share = sweep_s / total_s
     achieved = alg_bytes / launch_s / 1e9 if launch_s > 0 else 0.0
     stem = (f"ie_sweep_slab{a.slab_n}_mono" if mono and implicit else
             f"fused_step_slab{a.slab_n}_mono" if mono else
             f"jacobi_sweep_slab{a.slab_n}_bi" if a.workload == "slab" else f"jacobi_sweep_{a.workload}")
+    if torso:
+        stem = f"elliptic_sweep_{a.workload}"
     tpv = _traffic_record(stem)
     roofline = {"bound": "hbm", "kernel": kname,
                 "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": (tpv * M) if tpv is not None else None,
+                "traffic": (tpv * (n_dom if not mono else M)) if tpv is not None else None,
                 "algorithmic_bytes_per_launch": alg_bytes, "avg_launch_us": launch_s * 1e6,
                 "kernel_share_of_step": share if world == 1 else None, "peak_source": peak_src}
 
     # end to end through the C ABI with host buffers: the same steps as the timed
     # window, each step's state in from pinned host memory and its new state out
     e2e = None
+    ecg_trace = None
+    if ecg:   # the samples of the warm-up and the timed window
+        t_ms, phi, lead = sim.read_ecg()
+        ecg_trace = {"t_ms": [round(float(x), 4) for x in t_ms],
+                     "lead_I_mV": [round(float(x), 5) for x in lead[:, 0]],
+                     "lead_II_mV": [round(float(x), 5) for x in lead[:, 1]]}
     if not a.no_e2e:
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -387,10 +417,12 @@ def run_ours(a):
             sim.write_state(blobs[i & 1])
             sim.step(1, allow_noconv=True)
             sim.read_state(blobs[(i + 1) & 1])
+            if ecg:
+                sim.read_ecg(8)   # this step's electrode potentials and leads
         torch.cuda.synchronize()
         e2e_s = time.perf_counter() - t0
         e2e = {"value": M * a.steps / e2e_s, "unit": "tissue voxel-steps/s", "h2d_bytes_per_step": int(nb),
-               "d2h_bytes_per_step": int(nb)}
+               "d2h_bytes_per_step": int(nb) + (24 if ecg else 0)}
 
     cpu = None
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
@@ -399,7 +431,7 @@ def run_ours(a):
         info = oracle_sample(oc, k)
         cpu = {"value": oc.n_tissue / info["step_s"], "unit": "tissue voxel-steps/s", "cores": info["cores"],
                "kind": "oracle",
-               "sample": (f"one oracle step of {'a 256^3 slab of the same construction' if oc is not case else 'this workload'} with the Jacobi solve capped at {REF_SAMPLE_SWEEPS[0]} "
+               "sample": (f"one oracle step of {f'the same construction at {oc.nx}^3' if oc is not case else 'this workload'} with the Jacobi solve capped at {REF_SAMPLE_SWEEPS[0]} "
                           f"and {REF_SAMPLE_SWEEPS[1]} sweeps (fixed {info['fixed_s']:.2f} s + "
                           f"{info['per_sweep_s']:.3f} s/sweep, {info['sample_s']:.1f} s of CPU work), extrapolated "
                           f"to the {k:.0f} sweeps per step of the timed GPU steps")}
@@ -415,7 +447,8 @@ def run_ours(a):
                            "sweeps_per_step": iters, "step_status": statuses,
                            "implicit_sweeps_per_step": ie_iters if a.diffusion == "implicit" else None,
                            "l2": "flushed between timed steps (256 MB write)",
-                           "parallelism": f"replicas x{world}"},
+                           "parallelism": f"replicas x{world}",
+                           "elliptic_voxels": n_dom, "ecg": ecg_trace},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": int(prof.sweep_launches + prof.other_launches),
                 "clocks": clk}
@@ -607,6 +640,8 @@ def run_served(a):
 
 def main():
     a = _args()
+    if a.solver is None:
+        a.solver = "chebyshev" if a.workload == "ecg" else "jacobi"
     if a.workload == "config3" and a.impl == "ours":
         run_batched(a)
         return

@@ -131,6 +131,8 @@ typedef struct {
     double omega;            /* damping in use */
     size_t device_bytes;     /* device memory held by the handle */
     double cheb_lmin, cheb_lmax;   /* Chebyshev interval in use (0 for the Jacobi solver) */
+    long long n_domain;      /* voxels of the elliptic equation: tissue, plus the torso if set */
+    int n_segments_elliptic; /* work items of the elliptic sweeps (n_segments without a torso) */
 } ep_info;
 
 typedef struct ep_sim ep_sim;
@@ -188,6 +190,50 @@ ep_status ep_apply_operator(ep_sim *s, double sig_L, double sig_T,
                             const double *u_host, double *out_host, size_t n);
 
 ep_status ep_get_info(ep_sim *s, ep_info *info);
+
+/* Conducting torso around the heart (Eq. bidomain1, lines 3-5; Sec.
+ * "Electrocardiogram": the extracellular potential spreads into the
+ * surrounding body, whose conductivity is a free parameter).  torso: n bytes,
+ * non-zero = a torso voxel; voxels that are also tissue stay tissue.  sig_o:
+ * the torso's isotropic conductivity (mS/mm, finite and > 0).  The elliptic
+ * equation then acts on tissue + torso, with Sigma_i + Sigma_e on the tissue
+ * and sig_o I on the torso under the same vertex averaging, so v_e and the
+ * extracellular current are continuous across the heart surface and no
+ * current leaves the outer surface of the torso; the right-hand side
+ * -L_i v and the membrane state stay on the tissue, and the reference
+ * potential is zero mean per face-connected component of tissue + torso.
+ * Bidomain with explicit diffusion only (EP_EINVAL at set-up otherwise);
+ * not for the batched or served forms.  An all-zero torso removes it.
+ * Valid only before set-up (EP_ESTATE). */
+ep_status ep_set_torso(ep_sim *s, const uint8_t *torso, size_t n, double sig_o);
+
+/* ECG (Sec. "Electrocardiogram"): three electrode voxels (i, j, k) of the
+ * right arm, left arm and left leg, in that order (9 ints), on tissue or
+ * torso (checked at set-up, EP_EINVAL).  After every step's elliptic solve
+ * the device records the three potentials; capacity is the number of samples
+ * it holds between ep_read_ecg calls, and a step that would exceed it returns
+ * EP_EBUSY without running.  capacity 0 switches the ECG off.  Bidomain only;
+ * valid only before set-up (EP_ESTATE). */
+ep_status ep_set_ecg(ep_sim *s, const int electrodes[9], int capacity);
+
+typedef struct {
+    double t_ms;             /* time at the end of the step */
+    double phi_mV[3];        /* electrode potentials RA, LA, LL: 100 v_e */
+    double lead_mV[6];       /* I = LA - RA, II = LL - RA, III = LL - LA, aVR = RA - (LA + LL)/2,
+                                aVL = LA - (RA + LL)/2, aVF = LL - (RA + LA)/2 */
+} ep_ecg_sample;
+
+/* Moves the samples recorded since the last call into out (oldest first) and
+ * empties the record; *n_out = their number.  max_samples below that number
+ * gives EP_EINVAL with the number in *n_out and nothing moved.  Synchronises
+ * the handle's stream. */
+ep_status ep_read_ecg(ep_sim *s, ep_ecg_sample *out, int max_samples, int *n_out);
+
+/* Apply the elliptic operator of the handle (L_i + L_e, plus the torso's
+ * sig_o I if set) to a host field u (n doubles), writing n doubles (zero
+ * outside tissue + torso), with the same kernel as the solve's sweeps.
+ * Diagnostic. */
+ep_status ep_apply_elliptic(ep_sim *s, const double *u_host, double *out_host, size_t n);
 
 /* Same as ep_step, but the call allocates no device memory.  (The paper has
  * no counterpart; this serves embedding code.)  Some callers cannot allocate

@@ -35,7 +35,8 @@ EXPORTS = ["ep_create", "ep_set_mask", "ep_set_fibres", "ep_set_params", "ep_add
            "ep_batch_slot_stats", "ep_batch_autotune", "ep_batch_get_info", "ep_batch_last_error",
            "ep_batch_destroy", "ep_footprint", "ep_batch_set_schedule", "ep_server_create", "ep_server_submit",
            "ep_server_cancel", "ep_server_collect", "ep_server_drain", "ep_server_get_stats", "ep_server_now",
-           "ep_server_last_error", "ep_server_destroy"]
+           "ep_server_last_error", "ep_server_destroy", "ep_set_torso", "ep_set_ecg", "ep_read_ecg",
+           "ep_apply_elliptic"]
 
 _ALLOC_T = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
 _FREE_T = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
@@ -64,7 +65,12 @@ class StepStats(ctypes.Structure):
 class Info(ctypes.Structure):
     _fields_ = [("n_voxels", ctypes.c_longlong), ("n_tissue", ctypes.c_longlong), ("n_components", ctypes.c_int),
                 ("n_segments", ctypes.c_int), ("omega", ctypes.c_double), ("device_bytes", ctypes.c_size_t),
-                ("cheb_lmin", ctypes.c_double), ("cheb_lmax", ctypes.c_double)]
+                ("cheb_lmin", ctypes.c_double), ("cheb_lmax", ctypes.c_double),
+                ("n_domain", ctypes.c_longlong), ("n_segments_elliptic", ctypes.c_int)]
+
+
+class EcgSample(ctypes.Structure):
+    _fields_ = [("t_ms", ctypes.c_double), ("phi_mV", ctypes.c_double * 3), ("lead_mV", ctypes.c_double * 6)]
 
 
 class Profile(ctypes.Structure):
@@ -136,6 +142,10 @@ def load(path: str = LIB_PATH):
         "ep_write_state": ([vp, vp, sz], ip),
         "ep_apply_operator": ([vp, dp, dp, vp, vp, sz], ip),
         "ep_get_info": ([vp, ctypes.POINTER(Info)], ip),
+        "ep_set_torso": ([vp, vp, sz, dp], ip),
+        "ep_set_ecg": ([vp, ctypes.POINTER(ctypes.c_int * 9), ip], ip),
+        "ep_read_ecg": ([vp, vp, ip, ctypes.POINTER(ip)], ip),
+        "ep_apply_elliptic": ([vp, vp, vp, sz], ip),
         "ep_profile_enable": ([vp, ip], ip),
         "ep_get_profile": ([vp, ctypes.POINTER(Profile)], ip),
         "ep_last_error": ([vp], ctypes.c_char_p),
@@ -309,6 +319,36 @@ class Sim:
                                               self.n), "ep_apply_operator")
         return out
 
+    def apply_elliptic(self, u) -> np.ndarray:
+        """ep_apply_elliptic: the elliptic operator (with the torso, if set) applied to u."""
+        u = _f64(u, self.n)
+        out = np.empty(self.n, np.float64)
+        self._check(self._L.ep_apply_elliptic(self._h, u.ctypes.data, out.ctypes.data, self.n), "ep_apply_elliptic")
+        return out
+
+    def set_torso(self, torso, sig_o: float):
+        t = np.ascontiguousarray(np.asarray(torso, dtype=np.uint8).reshape(-1))
+        self._check(self._L.ep_set_torso(self._h, t.ctypes.data, t.size, float(sig_o)), "ep_set_torso")
+
+    def set_ecg(self, electrodes, capacity: int):
+        """electrodes: (i, j, k) of RA, LA, LL (None with capacity 0 switches the ECG off)."""
+        if electrodes is None:
+            self._check(self._L.ep_set_ecg(self._h, None, int(capacity)), "ep_set_ecg")
+            return
+        e = (ctypes.c_int * 9)(*[int(a) for ijk in electrodes for a in ijk])
+        self._check(self._L.ep_set_ecg(self._h, ctypes.byref(e), int(capacity)), "ep_set_ecg")
+
+    def read_ecg(self, max_samples: int = 1 << 16):
+        """Samples since the last read: (t_ms (m,), phi_mV (m, 3), lead_mV (m, 6))."""
+        buf = (EcgSample * max(1, int(max_samples)))()
+        n = ctypes.c_int(0)
+        self._check(self._L.ep_read_ecg(self._h, buf, int(max_samples), ctypes.byref(n)), "ep_read_ecg")
+        m = n.value
+        t = np.array([buf[i].t_ms for i in range(m)])
+        phi = np.array([list(buf[i].phi_mV) for i in range(m)]).reshape(m, 3)
+        lead = np.array([list(buf[i].lead_mV) for i in range(m)]).reshape(m, 6)
+        return t, phi, lead
+
     def footprint(self):
         """(resident, peak) device bytes, planned on the host (ep_footprint)."""
         r, p = ctypes.c_size_t(), ctypes.c_size_t()
@@ -481,8 +521,14 @@ class Server:
             pass
 
 
-def sim_from_case(case, use_torch: bool = True, model: Optional[int] = None, precision: Optional[int] = None) -> Sim:
-    """Create a handle from a ``workloads.Case`` (mask, fibres, parameters, stimuli)."""
+def _is_bi(case, model: Optional[int]) -> bool:
+    return (case.model if model is None else model) == EP_BI
+
+
+def sim_from_case(case, use_torch: bool = True, model: Optional[int] = None, precision: Optional[int] = None,
+                  ecg_capacity: int = 4096) -> Sim:
+    """Create a handle from a ``workloads.Case`` (mask, fibres, parameters,
+    stimuli; the torso and the ECG electrodes if the case has them)."""
     s = Sim(case.nx, case.ny, case.nz, case.dx, case.model if model is None else model,
             case.precision if precision is None else precision, use_torch=use_torch)
     s.set_mask(case.mask_flat())
@@ -490,4 +536,8 @@ def sim_from_case(case, use_torch: bool = True, model: Optional[int] = None, pre
     s.set_params(case.params)
     for st in case.stimuli:
         s.add_stimulus(st.lo, st.hi, st.t_start, st.dur, st.amp)
+    if getattr(case, "torso", None) is not None:
+        s.set_torso(case.torso, case.params.sig_o)
+    if getattr(case, "electrodes", None) is not None and _is_bi(case, model):
+        s.set_ecg(case.electrodes, ecg_capacity)
     return s

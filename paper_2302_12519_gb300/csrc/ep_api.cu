@@ -48,16 +48,18 @@ struct StimDef {
 }  // namespace
 
 // Host-side layout of a handle, computed from the mask alone (before any
-// device memory exists): tissue voxels sorted by face-connected component,
-// reduction chunks, and the z-march work items.
+// device memory exists): the voxels of the elliptic domain (the tissue, plus
+// the torso if one is set) sorted by face-connected component, reduction
+// chunks, and the z-march work items of the tissue and of the domain.
 struct HostPlan {
     bool done = false;
-    std::vector<int> order;             // tissue voxels, sorted by component then index
+    std::vector<int> order;             // domain voxels, sorted by component then index
     std::vector<long long> comp_count;  // voxels per component
     std::vector<Chunk> chunks;
     std::vector<int> comp_chunk0;       // first chunk of each component (+ end)
     std::vector<Seg> segs;              // work items at the handle's z-planes per item
     std::vector<Seg> segs_z[4];         // work items at kZLens[i] planes per item (set-up picks one)
+    std::vector<Seg> segs_e, segs_e_z[4];   // the same over the domain (torso handles only)
 };
 
 constexpr int kZLens[4] = {8, 16, 24, 32};
@@ -73,12 +75,18 @@ struct ep_sim {
     bool have_mask = false, have_params = false;
     ep_params p{};
     std::vector<StimDef> stims;
+    std::vector<uint8_t> torso;  // conducting torso voxels outside the tissue (empty: none)
+    double sig_o = 0.0;          // its conductivity (mS/mm)
+    int ecg_q[3] = {-1, -1, -1}; // electrode voxels RA, LA, LL (-1: no ECG)
+    long long ecg_cap = 0;       // samples the device record holds between reads
     HostPlan plan;
     size_t fp_resident = 0, fp_peak = 0;   // device bytes after / during set-up (from the plan)
     bool ready = false;
     // derived layout
     long long n_tissue = 0;
+    long long n_domain = 0;      // voxels of the elliptic equation (tissue + torso)
     int ncomp = 0, nseg = 0, nchunk = 0;
+    int nseg_e = 0;              // work items of the elliptic sweeps (nseg without a torso)
     int zseg = kZSeg;            // z-planes per stencil work item
     long long max_items = 0;     // segment capacity of the segs / partials buffers
     double omega = 0.0;
@@ -88,6 +96,11 @@ struct ep_sim {
     std::vector<void *> allocs;
     size_t dev_bytes = 0;
     ushort4 *rec = nullptr;
+    ushort4 *rec_e = nullptr;    // records of the elliptic domain (rec without a torso)
+    Seg *segs_e = nullptr;       // work items of the elliptic sweeps (segs without a torso)
+    double *ecg = nullptr;       // ECG record: 3 potentials per sample
+    long long ecg_n = 0;         // samples recorded since the last read
+    double ecg_t0 = 0.0;         // time of the first of them (ms)
     void *v[2] = {nullptr, nullptr}, *w[2] = {nullptr, nullptr}, *x[2] = {nullptr, nullptr};
     void *b = nullptr, *tact = nullptr;
     Seg *segs = nullptr;
@@ -266,8 +279,12 @@ void footprint(const ep_sim *s, size_t rb, size_t *resident, size_t *peak)
     r += abytes(sizeof(long long) * P.comp_count.size()) + abytes(sizeof(double) * (size_t)s->ncomp);
     r += abytes(sizeof(double) * (size_t)std::max<long long>(s->max_items, s->nchunk)) + abytes(sizeof(Ctl));
     if (s->have_params && s->p.diffusion == EP_IMPLICIT) r += 2 * abytes(rb * n);   // second iterate, 1/(1 + a D)
+    const bool torso = !s->torso.empty();
+    if (torso) r += abytes(sizeof(ushort4) * n) + abytes(sizeof(Seg) * (size_t)s->max_items);   // domain records, items
+    if (s->ecg_q[0] >= 0) r += abytes(sizeof(double) * 3 * (size_t)s->ecg_cap);
     *resident = r;
-    *peak = r + abytes(sizeof(float) * 3 * n) + abytes(n) + abytes(sizeof(ushort4) * n) + lanczos_bytes(s);
+    *peak = r + abytes(sizeof(float) * 3 * n) + abytes(n) + abytes(sizeof(ushort4) * n) + lanczos_bytes(s) +
+            (torso ? abytes(n) : 0);
 }
 
 // Host analysis of the mask: face-connected components (breadth-first), the
@@ -282,7 +299,13 @@ ep_status plan_layout(ep_sim *s)
     if (!s->have_mask) return fail(s, EP_ESTATE, "ep_set_mask must be called first");
     const int nx = s->d.nx, ny = s->d.ny, nz = s->d.nz;
     const long long n = s->n;
-    const uint8_t *m = s->mask.data();
+    const bool torso = !s->torso.empty();
+    std::vector<uint8_t> dom;   // elliptic domain: tissue or torso
+    if (torso) {
+        dom.resize(n);
+        for (long long q = 0; q < n; ++q) dom[q] = (s->mask[q] || s->torso[q]) ? 1 : 0;
+    }
+    const uint8_t *m = torso ? dom.data() : s->mask.data();
     HostPlan &P = s->plan;
     std::vector<int> comp(n, -1);
     P.order.clear();
@@ -314,7 +337,8 @@ ep_status plan_layout(ep_sim *s)
         P.comp_count.push_back((long long)queue.size());
         ++nc;
     }
-    if (P.order.empty()) return fail(s, EP_EINVAL, "mask has no tissue voxel");
+    const long long n_heart = std::count_if(s->mask.begin(), s->mask.end(), [](uint8_t c) { return c != 0; });
+    if (n_heart == 0) return fail(s, EP_EINVAL, "mask has no tissue voxel");
     P.chunks.clear();
     P.comp_chunk0.assign(nc + 1, 0);
     long long pos = 0;
@@ -327,17 +351,25 @@ ep_status plan_layout(ep_sim *s)
     }
     P.comp_chunk0[nc] = (int)P.chunks.size();
     long long most = 0;
+    const uint8_t *mh = s->mask.data();   // the membrane kernels' items cover the tissue
     for (int i = 0; i < 4; ++i) {
-        P.segs_z[i] = build_segments(m, nx, ny, nz, kZLens[i]);
+        P.segs_z[i] = build_segments(mh, nx, ny, nz, kZLens[i]);
         most = std::max<long long>(most, (long long)P.segs_z[i].size());
+        if (torso) {
+            P.segs_e_z[i] = build_segments(m, nx, ny, nz, kZLens[i]);
+            most = std::max<long long>(most, (long long)P.segs_e_z[i].size());
+        }
     }
-    P.segs = build_segments(m, nx, ny, nz, s->zseg);
-    s->n_tissue = (long long)P.order.size();
+    P.segs = build_segments(mh, nx, ny, nz, s->zseg);
+    if (torso) P.segs_e = build_segments(m, nx, ny, nz, s->zseg);
+    s->n_tissue = n_heart;
+    s->n_domain = (long long)P.order.size();
     s->ncomp = nc;
     s->nchunk = (int)P.chunks.size();
     s->nseg = (int)P.segs.size();
+    s->nseg_e = torso ? (int)P.segs_e.size() : s->nseg;
     // capacity of the item buffers: the largest item count of the z-lengths set-up and the batch use
-    s->max_items = std::max<long long>(most, s->nseg);
+    s->max_items = std::max<long long>(most, std::max(s->nseg, s->nseg_e));
     footprint(s, s->d.precision == EP_FP64 ? sizeof(double) : sizeof(float), &s->fp_resident, &s->fp_peak);
     P.done = true;
     return EP_OK;
@@ -346,6 +378,8 @@ ep_status plan_layout(ep_sim *s)
 
 template <typename real>
 Inst<real> make_inst(const ep_sim *s);
+template <typename real>
+Inst<real> make_elliptic_inst(const ep_sim *s);
 int stencil_blocks(const ep_sim *s);
 
 // Extreme eigenvalues of the symmetric tridiagonal (a, b) by Sturm bisection:
@@ -392,10 +426,10 @@ static double tridiag_eig(const std::vector<double> &a, const std::vector<double
 template <typename real>
 ep_status estimate_cheb_interval(ep_sim *s, real *v, real *vprev, real *w, real *t, double *lz)
 {
-    const long long n = s->n, nt = s->n_tissue;
+    const long long n = s->n, nt = s->n_domain;
     if (nt == 0 || s->nchunk == 0) return fail(s, EP_EINVAL, "Chebyshev interval: no tissue");
     cudaStream_t st = s->stream;
-    Inst<real> I = make_inst<real>(s);
+    Inst<real> I = make_elliptic_inst<real>(s);   // the domain's records (diagonal) and work items
     I.partials = lz + kLanczosScalars;
     const double sT = s->p.sig_iT + s->p.sig_eT, sL = s->p.sig_iL + s->p.sig_eL;
     ApplyIO<real> io;
@@ -403,7 +437,8 @@ ep_status estimate_cheb_interval(ep_sim *s, real *v, real *vprev, real *w, real 
     io.out = t;
     io.sT = (real)sT;
     io.dS = (real)(sL - sT);
-    const int gt = grid_for(nt, kRedThreads), gc = s->nchunk, gs = stencil_blocks(s);
+    const int gt = grid_for(nt, kRedThreads), gc = s->nchunk, gs = std::max(1, I.nseg);
+    const bool torso = !s->torso.empty();
     CK(cudaMemsetAsync(lz, 0, sizeof(double) * kLanczosScalars, st));
     k_fill<real><<<grid_for(n, 256), 256, 0, st>>>(v, n, real(0));
     k_fill<real><<<grid_for(n, 256), 256, 0, st>>>(vprev, n, real(0));
@@ -412,7 +447,8 @@ ep_status estimate_cheb_interval(ep_sim *s, real *v, real *vprev, real *w, real 
     k_lz_norm<real><<<gc, kRedThreads, 0, st>>>(I, w, lz, -1);
     k_lz_next<real><<<gt, kRedThreads, 0, st>>>(I, nt, v, vprev, w, lz);
     for (int j = 0; j < kLanczosSteps; ++j) {
-        k_stencil<real, M_APPLY><<<gs, kThreads, 0, st>>>(I, io);
+        if (torso) k_stencil<real, M_APPLY_BATH><<<gs, kThreads, 0, st>>>(I, io);
+        else k_stencil<real, M_APPLY><<<gs, kThreads, 0, st>>>(I, io);
         k_lz_w<real><<<gc, kRedThreads, 0, st>>>(I, t, v, vprev, w, lz);
         k_lz_proj<real><<<gc, kRedThreads, 0, st>>>(I, v, w, lz, 1);
         k_lz_norm<real><<<gc, kRedThreads, 0, st>>>(I, w, lz, j);
@@ -454,14 +490,17 @@ ep_status setup_typed(ep_sim *s)
         CK(cudaGetDevice(&dev));
         CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
         const long long wave = (long long)nsm * kMinBlocks;
+        const bool tor = !s->torso.empty();   // with a torso the elliptic sweeps over the domain dominate
         int pick = 0;   // index into kZLens
         for (int i = 3; i >= 1; --i)
-            if ((long long)s->plan.segs_z[i].size() >= (kZLens[i] == 16 ? wave : 2 * wave)) {
+            if ((long long)(tor ? s->plan.segs_e_z[i] : s->plan.segs_z[i]).size() >= (kZLens[i] == 16 ? wave : 2 * wave)) {
                 pick = i;
                 break;
             }
         s->plan.segs = s->plan.segs_z[pick];
         s->nseg = (int)s->plan.segs.size();
+        if (tor) s->plan.segs_e = s->plan.segs_e_z[pick];
+        s->nseg_e = tor ? (int)s->plan.segs_e.size() : s->nseg;
         s->zseg = kZLens[pick];
     }
     const HostPlan &P = s->plan;
@@ -474,6 +513,7 @@ ep_status setup_typed(ep_sim *s)
     footprint(s, sizeof(real), &s->fp_resident, &s->fp_peak);   // the parameters are known now
     const size_t want_resident = s->fp_resident, want_peak = s->fp_peak;
     const bool ie = s->p.diffusion == EP_IMPLICIT;
+    const bool torso = !s->torso.empty();
 
     // device buffers
     const size_t rb = sizeof(real);
@@ -499,11 +539,24 @@ ep_status setup_typed(ep_sim *s)
         s->ie_inv = dalloc(s, rb * n);
         if (!s->ie_x || !s->ie_inv) return fail(s, EP_ENOMEM, "device allocation failed");
     }
+    s->rec_e = s->rec;
+    s->segs_e = s->segs;
+    if (torso) {
+        s->rec_e = (ushort4 *)dalloc(s, sizeof(ushort4) * n);
+        s->segs_e = (Seg *)dalloc(s, sizeof(Seg) * (size_t)s->max_items);
+        if (!s->rec_e || !s->segs_e) return fail(s, EP_ENOMEM, "device allocation failed");
+    }
+    if (s->ecg_q[0] >= 0) {
+        s->ecg = (double *)dalloc(s, sizeof(double) * 3 * (size_t)s->ecg_cap);
+        if (!s->ecg) return fail(s, EP_ENOMEM, "device allocation failed");
+    }
     void *tmp_fib = dalloc(s, sizeof(float) * 3 * n);
     void *tmp_mask = dalloc(s, n);
     void *tmp_rec = dalloc(s, sizeof(ushort4) * n);
     void *tmp_lz = lanczos_bytes(s) ? dalloc(s, lanczos_bytes(s)) : nullptr;
     if (lanczos_bytes(s) && !tmp_lz) return fail(s, EP_ENOMEM, "device allocation failed");
+    void *tmp_torso = torso ? dalloc(s, n) : nullptr;
+    if (torso && !tmp_torso) return fail(s, EP_ENOMEM, "device allocation failed");
     const void *all[] = {s->rec, s->v[0], s->v[1], s->w[0], s->w[1], s->x[0], s->x[1], s->b, s->tact, s->segs,
                          s->idx, s->chunks, s->comp_chunk0, s->comp_count, s->means, s->partials, s->ctl,
                          tmp_fib, tmp_mask, tmp_rec};
@@ -520,11 +573,20 @@ ep_status setup_typed(ep_sim *s)
     if (s->fib.empty()) CK(cudaMemsetAsync(tmp_fib, 0, sizeof(float) * 3 * n, st));
     else CK(cudaMemcpyAsync(tmp_fib, s->fib.data(), sizeof(float) * 3 * n, cudaMemcpyHostToDevice, st));
     k_build_records<<<grid_for(n, 256), 256, 0, st>>>(nx, ny, nz, (const float *)tmp_fib, (const uint8_t *)tmp_mask,
-                                                      (ushort4 *)tmp_rec);
+                                                      nullptr, (ushort4 *)tmp_rec);
     // Jacobi diagonal of the elliptic operator L_i + L_e (conductivities add)
     const double sL = s->p.sig_iL + s->p.sig_eL, sT = s->p.sig_iT + s->p.sig_eT;
-    k_build_diag<<<grid_for(n, 128), 128, 0, st>>>(nx, ny, nz, sT, sL - sT, (const ushort4 *)tmp_rec, s->rec);
+    k_build_diag<<<grid_for(n, 128), 128, 0, st>>>(nx, ny, nz, sT, sL - sT, 0.0, (const ushort4 *)tmp_rec, s->rec);
     CK(cudaGetLastError());
+    if (torso) {   // the domain's records: torso voxels tagged, the diagonal with the torso term
+        CK(cudaMemcpyAsync(tmp_torso, s->torso.data(), n, cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync(s->segs_e, s->plan.segs_e.data(), sizeof(Seg) * s->plan.segs_e.size(), cudaMemcpyHostToDevice, st));
+        k_build_records<<<grid_for(n, 256), 256, 0, st>>>(nx, ny, nz, (const float *)tmp_fib, (const uint8_t *)tmp_mask,
+                                                          (const uint8_t *)tmp_torso, (ushort4 *)tmp_rec);
+        k_build_diag<<<grid_for(n, 128), 128, 0, st>>>(nx, ny, nz, sT, sL - sT, s->sig_o, (const ushort4 *)tmp_rec,
+                                                       s->rec_e);
+        CK(cudaGetLastError());
+    }
     if (ie) {   // implicit diffusion: 1 / (1 + a D_i) for the intracellular operator, second iterate
         const double C = 1.0 / (8.0 * s->d.dx_mm * s->d.dx_mm);
         const double fac = s->d.model == EP_MONO ? s->p.lambda / (1.0 + s->p.lambda) : 1.0;
@@ -557,7 +619,7 @@ ep_status setup_typed(ep_sim *s)
     CK(cudaMemsetAsync(s->ctl, 0, sizeof(Ctl), st));
     CK(cudaStreamSynchronize(st));
     // free the set-up temporaries
-    for (void *t : {tmp_fib, tmp_mask, tmp_rec, tmp_lz}) {
+    for (void *t : {tmp_fib, tmp_mask, tmp_rec, tmp_lz, tmp_torso}) {
         if (!t) continue;
         auto it = std::find(s->allocs.begin(), s->allocs.end(), t);
         if (it != s->allocs.end()) {
@@ -573,13 +635,27 @@ ep_status setup_typed(ep_sim *s)
     s->plan.chunks = std::vector<Chunk>();
     s->plan.comp_chunk0 = std::vector<int>();
     s->plan.segs = std::vector<Seg>();
+    s->plan.segs_e = std::vector<Seg>();
     for (auto &v : s->plan.segs_z) v = std::vector<Seg>();
+    for (auto &v : s->plan.segs_e_z) v = std::vector<Seg>();
     CK(cudaMallocHost((void **)&s->ctl_host, 2 * sizeof(Ctl)));
     std::memset(s->ctl_host, 0, 2 * sizeof(Ctl));
     CK(cudaEventCreateWithFlags(&s->ev[0], cudaEventDisableTiming));
     CK(cudaEventCreateWithFlags(&s->ev[1], cudaEventDisableTiming));
 
     return EP_OK;
+}
+
+// Descriptor of the elliptic sweeps: the work items and records of the domain
+// (tissue + torso); the tissue descriptor without a torso.
+template <typename real>
+Inst<real> make_elliptic_inst(const ep_sim *s)
+{
+    Inst<real> I = make_inst<real>(s);
+    I.segs = s->segs_e;
+    I.nseg = s->nseg_e;
+    I.rec = s->rec_e;
+    return I;
 }
 
 // Descriptor of this handle for the kernels.
@@ -640,6 +716,9 @@ Inst<real> make_inst(const ep_sim *s)
         I.cheb_rho = rho;
         I.cheb_theta = std::acosh(1.0 / rho);
     }
+    I.torso = s->torso.empty() ? 0 : 1;
+    I.pad4 = 0;
+    I.sig_o = (real)(s->torso.empty() ? 0.0 : s->sig_o);
     I.dt = (real)s->p.dt_ms;
     I.inv_tin = (real)(1.0 / s->p.tau_in);
     I.inv_tout = (real)(1.0 / s->p.tau_out);
@@ -671,17 +750,17 @@ ApplyIO<real> no_io()
     return io;
 }
 
-// A CUDA graph of kSweepChunk sweep launches of one solve (MODE = M_JAC or M_IE).
+// A CUDA graph of kSweepChunk sweep launches of one solve (MODE = M_JAC,
+// M_JAC_BATH or M_IE) with descriptor I (one CTA per work item of I).
 template <typename real, int MODE>
-ep_status build_sweep_graph(ep_sim *s, cudaGraphExec_t *out)
+ep_status build_sweep_graph(ep_sim *s, const Inst<real> &I, cudaGraphExec_t *out)
 {
     if (*out) return EP_OK;
-    const Inst<real> I = make_inst<real>(s);
     const ApplyIO<real> io = no_io<real>();
     cudaGraph_t g = nullptr;
     CK(cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeThreadLocal));
     for (int i = 0; i < kSweepChunk; ++i)
-        k_stencil<real, MODE><<<stencil_blocks(s), kThreads, 0, s->stream>>>(I, io);
+        k_stencil<real, MODE><<<std::max(1, I.nseg), kThreads, 0, s->stream>>>(I, io);
     cudaError_t e = cudaStreamEndCapture(s->stream, &g);
     if (e != cudaSuccess) return fail(s, EP_ECUDA, std::string("sweep graph capture: ") + cudaGetErrorString(e));
     e = cudaGraphInstantiate(out, g, 0);
@@ -703,7 +782,7 @@ ep_status run_sweeps(ep_sim *s, const Inst<real> &I, cudaGraphExec_t *graph, lon
     cudaStream_t st = s->stream;
     const ApplyIO<real> io = no_io<real>();
     if (!s->noalloc_call) {
-        ep_status gs = build_sweep_graph<real, MODE>(s, graph);
+        ep_status gs = build_sweep_graph<real, MODE>(s, I, graph);
         if (gs != EP_OK) return gs;
     }
     const long long limit = (long long)s->p.max_iter + 1;
@@ -714,7 +793,7 @@ ep_status run_sweeps(ep_sim *s, const Inst<real> &I, cudaGraphExec_t *graph, lon
             queued += kSweepChunk;
         } else {
             const long long stop = std::min(limit, queued + (long long)kSweepChunk);
-            for (; queued < stop; ++queued) k_stencil<real, MODE><<<stencil_blocks(s), kThreads, 0, st>>>(I, io);
+            for (; queued < stop; ++queued) k_stencil<real, MODE><<<std::max(1, I.nseg), kThreads, 0, st>>>(I, io);
             CK(cudaGetLastError());
         }
         CK(cudaMemcpyAsync(&s->ctl_host[c & 1], s->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
@@ -748,6 +827,16 @@ ep_status ensure_ready(ep_sim *s)
             return fail(s, EP_ECUDA, std::string("cudaStreamCreate: ") + cudaGetErrorString(e));
         }
         s->own_stream = true;
+    }
+    if (!s->torso.empty() && (s->d.model != EP_BI || s->p.diffusion != EP_EXPLICIT))
+        return fail(s, EP_EINVAL, "a torso needs the bidomain model with explicit diffusion");
+    if (s->ecg_q[0] >= 0) {
+        if (s->d.model != EP_BI) return fail(s, EP_EINVAL, "the ECG needs the bidomain model (it reads v_e)");
+        for (int e = 0; e < 3; ++e) {
+            const int q = s->ecg_q[e];
+            if (!s->mask[q] && (s->torso.empty() || !s->torso[q]))
+                return fail(s, EP_EINVAL, "ECG electrodes must lie on tissue or torso voxels");
+        }
     }
     const double sL = s->p.sig_iL + s->p.sig_eL, sT = s->p.sig_iT + s->p.sig_eT;
     s->omega = s->p.jacobi_omega > 0.0 ? s->p.jacobi_omega : std::min(1.0, 1.8 * (sL + 2.0 * sT) / (8.0 * sL));
@@ -784,7 +873,13 @@ ep_status solve_elliptic(ep_sim *s, const Inst<real> &I, int &iters, double &rel
     // sweeps, queued in graph chunks, one chunk of look-ahead
     if (s->prof_on) CK(cudaEventRecord(s->pev[2], st));
     long long queued = 0;
-    ep_status rs = run_sweeps<real, M_JAC>(s, I, &s->sweep_graph, &queued);
+    ep_status rs = EP_OK;
+    if (s->torso.empty()) {
+        rs = run_sweeps<real, M_JAC>(s, I, &s->sweep_graph, &queued);
+    } else {   // tissue + torso: the domain's items and records
+        const Inst<real> Ie = make_elliptic_inst<real>(s);
+        rs = run_sweeps<real, M_JAC_BATH>(s, Ie, &s->sweep_graph, &queued);
+    }
     if (rs != EP_OK) return rs;
     if (s->prof_on) {
         CK(cudaEventRecord(s->pev[3], st));
@@ -794,6 +889,11 @@ ep_status solve_elliptic(ep_sim *s, const Inst<real> &I, int &iters, double &rel
     // reference potential: subtract each component's mean of the final iterate
     k_comp_mean<real><<<s->nchunk, kRedThreads, 0, st>>>(I, (int)RED_X_FINAL);
     k_project<real><<<s->nchunk, kRedThreads, 0, st>>>(I);
+    if (s->ecg_q[0] >= 0) {   // electrode potentials of this step
+        k_ecg_record<real><<<1, 32, 0, st>>>(I.x0, s->ecg_q[0], s->ecg_q[1], s->ecg_q[2], s->ecg, s->ecg_n);
+        if (s->ecg_n == 0) s->ecg_t0 = (double)(s->step + 1) * s->p.dt_ms;
+        ++s->ecg_n;
+    }
     CK(cudaGetLastError());
     CK(cudaMemcpyAsync(&s->ctl_host[0], s->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
@@ -929,10 +1029,14 @@ ep_status set_state_typed(ep_sim *s, const double *v, const double *w, const dou
     const double *src[3] = {v, w, ve};
     void *dst[3] = {s->v[s->step & 1], s->w[s->step & 1], s->x[0]};
     const double rest[3] = {0.0, 1.0, 0.0};
+    const bool torso = !s->torso.empty();
     std::vector<real> h(s->n);
     for (int f = 0; f < 3; ++f) {
         if (!src[f]) continue;
-        for (long long q = 0; q < s->n; ++q) h[q] = (real)(s->mask[q] ? src[f][q] : rest[f]);
+        for (long long q = 0; q < s->n; ++q) {   // v, w on the tissue; v_e on tissue + torso
+            const bool in = s->mask[q] || (f == 2 && torso && s->torso[q]);
+            h[q] = (real)(in ? src[f][q] : rest[f]);
+        }
         CK(cudaMemcpyAsync(dst[f], h.data(), sizeof(real) * s->n, cudaMemcpyHostToDevice, s->stream));
         CK(cudaStreamSynchronize(s->stream));
     }
@@ -1056,6 +1160,8 @@ ep_status ep_step(ep_sim *s, int n_steps, ep_step_stats *stats)
     if (n_steps < 0) return fail(s, EP_EINVAL, "n_steps must be >= 0");
     ep_status st = ensure_ready(s);
     if (st != EP_OK) return st;
+    if (s->ecg_q[0] >= 0 && s->ecg_n + n_steps > s->ecg_cap)
+        return fail(s, EP_EBUSY, "the ECG record would overflow: read it with ep_read_ecg first");
     return s->d.precision == EP_FP64 ? step_typed<double>(s, n_steps, stats) : step_typed<float>(s, n_steps, stats);
 }
 
@@ -1163,7 +1269,112 @@ ep_status ep_get_info(ep_sim *s, ep_info *info)
     info->cheb_lmin = s->cheb_lmin;
     info->cheb_lmax = s->cheb_lmax;
     info->device_bytes = s->dev_bytes;
+    info->n_domain = s->n_domain;
+    info->n_segments_elliptic = s->nseg_e;
     return EP_OK;
+}
+
+ep_status ep_set_torso(ep_sim *s, const uint8_t *torso, size_t n, double sig_o)
+{
+    if (!s) return EP_EINVAL;
+    if (s->ready) return fail(s, EP_ESTATE, "the torso can only be set before the first step");
+    if (!torso || (long long)n != s->n) return fail(s, EP_EINVAL, "torso must hold nx*ny*nz bytes");
+    if (!(sig_o > 0.0) || !std::isfinite(sig_o)) return fail(s, EP_EINVAL, "sig_o must be finite and > 0");
+    s->torso.assign(torso, torso + n);
+    bool any = false;
+    for (auto &c : s->torso) {
+        c = c ? 1 : 0;
+        any = any || c;
+    }
+    if (!any) s->torso.clear();   // an empty torso is no torso
+    s->sig_o = sig_o;
+    s->plan = HostPlan();         // the domain changed
+    return EP_OK;
+}
+
+ep_status ep_set_ecg(ep_sim *s, const int electrodes[9], int capacity)
+{
+    if (!s) return EP_EINVAL;
+    if (s->ready) return fail(s, EP_ESTATE, "the ECG can only be set up before the first step");
+    if (capacity == 0) {
+        s->ecg_q[0] = s->ecg_q[1] = s->ecg_q[2] = -1;
+        s->ecg_cap = 0;
+        return EP_OK;
+    }
+    if (!electrodes || capacity < 0) return fail(s, EP_EINVAL, "electrodes must be given and capacity >= 0");
+    int q[3];
+    for (int e = 0; e < 3; ++e) {
+        const int i = electrodes[3 * e], j = electrodes[3 * e + 1], k = electrodes[3 * e + 2];
+        if (i < 0 || j < 0 || k < 0 || i >= s->d.nx || j >= s->d.ny || k >= s->d.nz)
+            return fail(s, EP_EINVAL, "electrode outside the grid");
+        q[e] = i + s->d.nx * (j + s->d.ny * k);
+    }
+    for (int e = 0; e < 3; ++e) s->ecg_q[e] = q[e];
+    s->ecg_cap = capacity;
+    s->ecg_n = 0;
+    return EP_OK;
+}
+
+ep_status ep_read_ecg(ep_sim *s, ep_ecg_sample *out, int max_samples, int *n_out)
+{
+    if (!s || !n_out) return EP_EINVAL;
+    *n_out = 0;
+    if (s->ecg_q[0] < 0) return fail(s, EP_EINVAL, "no ECG set up (ep_set_ecg)");
+    if (!s->ready || s->ecg_n == 0) return EP_OK;
+    if (!out || max_samples < s->ecg_n) {
+        *n_out = (int)s->ecg_n;
+        return fail(s, EP_EINVAL, "max_samples is below the samples recorded (returned in *n_out)");
+    }
+    std::vector<double> h(3 * (size_t)s->ecg_n);
+    CK(cudaMemcpyAsync(h.data(), s->ecg, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, s->stream));
+    CK(cudaStreamSynchronize(s->stream));
+    for (long long i = 0; i < s->ecg_n; ++i) {
+        ep_ecg_sample &o = out[i];
+        o.t_ms = s->ecg_t0 + (double)i * s->p.dt_ms;
+        const double ra = 100.0 * h[3 * i], la = 100.0 * h[3 * i + 1], ll = 100.0 * h[3 * i + 2];
+        o.phi_mV[0] = ra;
+        o.phi_mV[1] = la;
+        o.phi_mV[2] = ll;
+        // limb leads (Sec. "Electrocardiogram"): Einthoven's I, II, III and the augmented leads
+        o.lead_mV[0] = la - ra;
+        o.lead_mV[1] = ll - ra;
+        o.lead_mV[2] = ll - la;
+        o.lead_mV[3] = ra - 0.5 * (la + ll);
+        o.lead_mV[4] = la - 0.5 * (ra + ll);
+        o.lead_mV[5] = ll - 0.5 * (ra + la);
+    }
+    *n_out = (int)s->ecg_n;
+    s->ecg_n = 0;
+    return EP_OK;
+}
+
+ep_status ep_apply_elliptic(ep_sim *s, const double *u_host, double *out_host, size_t n)
+{
+    if (!s) return EP_EINVAL;
+    if (!u_host || !out_host || (long long)n != s->n) return fail(s, EP_EINVAL, "fields must hold nx*ny*nz doubles");
+    ep_status st = ensure_ready(s);
+    if (st != EP_OK) return st;
+    auto run = [&](auto tag) -> ep_status {   // b and x[1] are scratch between steps
+        using real = decltype(tag);
+        std::vector<real> h(s->n);
+        for (long long q = 0; q < s->n; ++q) h[q] = (real)u_host[q];
+        CK(cudaMemcpyAsync(s->b, h.data(), sizeof(real) * s->n, cudaMemcpyHostToDevice, s->stream));
+        k_fill<real><<<grid_for(s->n, 256), 256, 0, s->stream>>>((real *)s->x[1], s->n, real(0));
+        const Inst<real> I = make_elliptic_inst<real>(s);
+        ApplyIO<real> io;
+        io.u = (const real *)s->b;
+        io.out = (real *)s->x[1];
+        io.sT = (real)(s->p.sig_iT + s->p.sig_eT);
+        io.dS = (real)(s->p.sig_iL + s->p.sig_eL - s->p.sig_iT - s->p.sig_eT);
+        if (s->torso.empty()) k_stencil<real, M_APPLY><<<std::max(1, I.nseg), kThreads, 0, s->stream>>>(I, io);
+        else k_stencil<real, M_APPLY_BATH><<<std::max(1, I.nseg), kThreads, 0, s->stream>>>(I, io);
+        CK(cudaGetLastError());
+        CK(cudaMemcpyAsync(h.data(), s->x[1], sizeof(real) * s->n, cudaMemcpyDeviceToHost, s->stream));
+        CK(cudaStreamSynchronize(s->stream));
+        for (long long q = 0; q < s->n; ++q) out_host[q] = (double)h[q];
+        return EP_OK;
+    };
+    return s->d.precision == EP_FP64 ? run(double(0)) : run(float(0));
 }
 
 ep_status ep_footprint(ep_sim *s, size_t *resident_bytes, size_t *peak_bytes)
@@ -1259,7 +1470,9 @@ ep_status ep_step_noalloc(ep_sim *s, int n_steps, ep_step_stats *stats)
     if (!s->ready)
         return fail(s, EP_ESTATE, "ep_step_noalloc needs a handle that is already set up (call ep_step, "
                                   "ep_set_state or ep_get_info once first): set-up allocates device memory");
-    if (stencil_blocks(s) > kNoAllocMaxPartials || s->nchunk > kNoAllocMaxPartials)
+    if (s->ecg_q[0] >= 0 && s->ecg_n + n_steps > s->ecg_cap)
+        return fail(s, EP_EBUSY, "the ECG record would overflow: read it with ep_read_ecg first");
+    if (std::max(stencil_blocks(s), s->nseg_e) > kNoAllocMaxPartials || s->nchunk > kNoAllocMaxPartials)
         return fail(s, EP_EINVAL, "grid too large for ep_step_noalloc: more than 32768 stencil work items or "
                                   "reduction chunks (use ep_step)");
     if (s->ncomp > kNoAllocMaxComponents)
@@ -1683,6 +1896,8 @@ ep_status ep_batch_add(ep_batch *b, ep_sim *s, int *slot)
     if (s->d.precision != EP_FP32) return bfail(b, EP_EINVAL, "batched members must be FP32 handles");
     if (s->have_params && s->p.diffusion != EP_EXPLICIT)
         return bfail(b, EP_EINVAL, "implicit-diffusion handles are stepped by ep_step only");
+    if (!s->torso.empty() || s->ecg_q[0] >= 0)
+        return bfail(b, EP_EINVAL, "torso and ECG handles are stepped by ep_step only");
     if (b->model >= 0 && s->d.model != b->model)
         return bfail(b, EP_EINVAL, "batched members must share the model (monodomain or bidomain)");
     for (ep_sim *t : b->slot)
@@ -2240,6 +2455,8 @@ ep_status ep_server_submit(ep_server *v, ep_sim *sim, int n_steps, double releas
     if (sim->d.precision != EP_FP32) return sfail(v, EP_EINVAL, "served requests must be FP32 handles");
     if (sim->have_params && sim->p.diffusion != EP_EXPLICIT)
         return sfail(v, EP_EINVAL, "implicit-diffusion handles are stepped by ep_step only");
+    if (!sim->torso.empty() || sim->ecg_q[0] >= 0)
+        return sfail(v, EP_EINVAL, "torso and ECG handles are stepped by ep_step only");
     if (!sim->have_mask || !sim->have_params) return sfail(v, EP_ESTATE, "a request needs its mask and parameters set");
     std::lock_guard<std::mutex> lk(v->mu);
     if (v->stop) return sfail(v, EP_ESTATE, "server is shutting down");

@@ -10,9 +10,13 @@ namespace gbep {
 // from global memory (8x redundant, used once at setup or for checking).
 // ---------------------------------------------------------------------------
 
-// Static data of vertex (I, J, K): valid-pair counts, nT and M = sum f f^T.
+// Static data of vertex (I, J, K): tissue flags T, valid tissue-pair counts,
+// nT and M = sum f f^T over the tissue voxels; with torso records also the
+// domain flags Td (tissue or torso), domain-pair counts cntd and the torso
+// voxel count nB.
 __device__ inline void vertex_static(int nx, int ny, int nz, const ushort4 *rec, int I, int J, int K,
-                                     int cnt[3], int &nT, double M[6], bool T[2][2][2])
+                                     int cnt[3], int &nT, double M[6], bool T[2][2][2], int cntd[3], int &nB,
+                                     bool Td[2][2][2])
 {
     double f[2][2][2][3];
     for (int u = 0; u < 2; ++u)
@@ -20,22 +24,24 @@ __device__ inline void vertex_static(int nx, int ny, int nz, const ushort4 *rec,
             for (int s = 0; s < 2; ++s) {
                 const int i = I - 1 + s, j = J - 1 + t, k = K - 1 + u;
                 bool in = i >= 0 && j >= 0 && k >= 0 && i < nx && j < ny && k < nz;
-                T[u][t][s] = false;
+                T[u][t][s] = Td[u][t][s] = false;
                 f[u][t][s][0] = f[u][t][s][1] = f[u][t][s][2] = 0.0;
                 if (in) {
                     const ushort4 r = rec[(long long)i + (long long)nx * ((long long)j + (long long)ny * k)];
                     if (rec_tissue(r)) {
-                        T[u][t][s] = true;
+                        Td[u][t][s] = true;
+                        T[u][t][s] = !rec_bath(r);
                         f[u][t][s][0] = h2f(r.x); f[u][t][s][1] = h2f(r.y); f[u][t][s][2] = h2f(r.z);
                     }
                 }
             }
-    nT = 0;
+    nT = nB = 0;
     for (int i = 0; i < 6; ++i) M[i] = 0.0;
-    cnt[0] = cnt[1] = cnt[2] = 0;
+    cnt[0] = cnt[1] = cnt[2] = cntd[0] = cntd[1] = cntd[2] = 0;
     for (int u = 0; u < 2; ++u)
         for (int t = 0; t < 2; ++t)
             for (int s = 0; s < 2; ++s) {
+                if (Td[u][t][s] && !T[u][t][s]) ++nB;
                 if (!T[u][t][s]) continue;
                 const double *g = f[u][t][s];
                 ++nT;
@@ -47,13 +53,19 @@ __device__ inline void vertex_static(int nx, int ny, int nz, const ushort4 *rec,
             cnt[0] += T[o2][o1][0] && T[o2][o1][1];
             cnt[1] += T[o2][0][o1] && T[o2][1][o1];
             cnt[2] += T[0][o2][o1] && T[1][o2][o1];
+            cntd[0] += Td[o2][o1][0] && Td[o2][o1][1];
+            cntd[1] += Td[o2][0][o1] && Td[o2][1][o1];
+            cntd[2] += Td[0][o2][o1] && Td[1][o2][o1];
         }
 }
 
 // Dhat_q = sum over the 8 vertices of q of c^T Shat c, c_a = +-T(partner) r_a,
 // Shat = nT sT I + dS M; D_q = Dhat_q / (8 dx^2).  Writes the fp16 record.
+// With a torso (nullable), its voxels outside the tissue get the record
+// (-0, 0, 0, .): in the domain, zero fibre, tagged; a tissue fibre lane that
+// rounds to -0 is stored as +0 so that the tag stays unique.
 __global__ void k_build_records(int nx, int ny, int nz, const float *fib, const uint8_t *mask,
-                                ushort4 *rec)
+                                const uint8_t *torso, ushort4 *rec)
 {
     const long long n = (long long)nx * ny * nz;
     for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
@@ -62,7 +74,12 @@ __global__ void k_build_records(int nx, int ny, int nz, const float *fib, const 
             r.x = __half_as_ushort(__float2half_rn(fib[3 * q + 0]));
             r.y = __half_as_ushort(__float2half_rn(fib[3 * q + 1]));
             r.z = __half_as_ushort(__float2half_rn(fib[3 * q + 2]));
+            if (r.x == kBathTag) r.x = 0;
             r.w = 0;   // 1/Dhat filled by k_build_diag
+        } else if (torso && torso[q]) {
+            r.x = kBathTag;
+            r.y = r.z = 0;
+            r.w = 0;
         } else {
             r.x = r.y = r.z = 0;
             r.w = kNonTissue;
@@ -71,36 +88,47 @@ __global__ void k_build_records(int nx, int ny, int nz, const float *fib, const 
     }
 }
 
-// Dhat of tissue voxel (i, j, k) for the operator with sigma_T = sT and
-// sigma_L - sigma_T = dS: the diagonal of L is C Dhat, C = 1 / (8 dx^2).
+// Dhat of voxel (i, j, k) for the operator with sigma_T = sT and
+// sigma_L - sigma_T = dS (tissue term, tissue voxels), plus with so > 0 the
+// torso term so nB I over domain pairs (torso records): the diagonal of L is
+// C Dhat, C = 1 / (8 dx^2).
 __device__ inline double diag_hat(int nx, int ny, int nz, const ushort4 *rec, int i, int j, int k, double sT,
-                                  double dS)
+                                  double dS, double so)
 {
     double D = 0.0;
     for (int u = 0; u < 2; ++u)
         for (int t = 0; t < 2; ++t)
             for (int s = 0; s < 2; ++s) {
-                int cnt[3], nT;
+                int cnt[3], cntd[3], nT, nB;
                 double M[6];
-                bool T[2][2][2];
-                vertex_static(nx, ny, nz, rec, i + s, j + t, k + u, cnt, nT, M, T);
+                bool T[2][2][2], Td[2][2][2];
+                vertex_static(nx, ny, nz, rec, i + s, j + t, k + u, cnt, nT, M, T, cntd, nB, Td);
                 // q sits at block offset (1-s, 1-t, 1-u); partner along a flips that offset
                 const int os = 1 - s, ot = 1 - t, ou = 1 - u;
-                double c[3];
-                c[0] = T[ou][ot][1 - os] && cnt[0] ? (os ? 1.0 : -1.0) / cnt[0] : 0.0;
-                c[1] = T[ou][1 - ot][os] && cnt[1] ? (ot ? 1.0 : -1.0) / cnt[1] : 0.0;
-                c[2] = T[1 - ou][ot][os] && cnt[2] ? (ou ? 1.0 : -1.0) / cnt[2] : 0.0;
-                const double iso = sT * nT;
-                const double S[3][3] = {{iso + dS * M[0], dS * M[3], dS * M[4]},
-                                        {dS * M[3], iso + dS * M[1], dS * M[5]},
-                                        {dS * M[4], dS * M[5], iso + dS * M[2]}};
-                for (int x = 0; x < 3; ++x)
-                    for (int y = 0; y < 3; ++y) D += c[x] * S[x][y] * c[y];
+                if (T[ou][ot][os]) {
+                    double c[3];
+                    c[0] = T[ou][ot][1 - os] && cnt[0] ? (os ? 1.0 : -1.0) / cnt[0] : 0.0;
+                    c[1] = T[ou][1 - ot][os] && cnt[1] ? (ot ? 1.0 : -1.0) / cnt[1] : 0.0;
+                    c[2] = T[1 - ou][ot][os] && cnt[2] ? (ou ? 1.0 : -1.0) / cnt[2] : 0.0;
+                    const double iso = sT * nT;
+                    const double S[3][3] = {{iso + dS * M[0], dS * M[3], dS * M[4]},
+                                            {dS * M[3], iso + dS * M[1], dS * M[5]},
+                                            {dS * M[4], dS * M[5], iso + dS * M[2]}};
+                    for (int x = 0; x < 3; ++x)
+                        for (int y = 0; y < 3; ++y) D += c[x] * S[x][y] * c[y];
+                }
+                if (so > 0.0 && nB > 0) {
+                    double c2 = 0.0;
+                    if (Td[ou][ot][1 - os] && cntd[0]) c2 += 1.0 / ((double)cntd[0] * cntd[0]);
+                    if (Td[ou][1 - ot][os] && cntd[1]) c2 += 1.0 / ((double)cntd[1] * cntd[1]);
+                    if (Td[1 - ou][ot][os] && cntd[2]) c2 += 1.0 / ((double)cntd[2] * cntd[2]);
+                    D += so * nB * c2;
+                }
             }
     return D;
 }
 
-__global__ void k_build_diag(int nx, int ny, int nz, double sT, double dS, const ushort4 *rec,
+__global__ void k_build_diag(int nx, int ny, int nz, double sT, double dS, double so, const ushort4 *rec,
                              ushort4 *rec_out)
 {
     const long long n = (long long)nx * ny * nz;
@@ -108,7 +136,7 @@ __global__ void k_build_diag(int nx, int ny, int nz, double sT, double dS, const
         ushort4 r = rec[q];
         if (!rec_tissue(r)) { rec_out[q] = r; continue; }
         const int i = (int)(q % nx), j = (int)((q / nx) % ny), k = (int)(q / ((long long)nx * ny));
-        const double D = diag_hat(nx, ny, nz, rec, i, j, k, sT, dS);
+        const double D = diag_hat(nx, ny, nz, rec, i, j, k, sT, dS, so);
         r.w = D > 0.0 ? __half_as_ushort(__float2half_rn((float)(1.0 / D))) : (unsigned short)0;
         rec_out[q] = r;
     }
@@ -124,60 +152,9 @@ __global__ void k_build_ie_diag(int nx, int ny, int nz, double sT, double dS, do
     for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
         if (!rec_tissue(rec[q])) { inv[q] = real(0); continue; }
         const int i = (int)(q % nx), j = (int)((q / nx) % ny), k = (int)(q / ((long long)nx * ny));
-        inv[q] = (real)(1.0 / (1.0 + aC * diag_hat(nx, ny, nz, rec, i, j, k, sT, dS)));
+        inv[q] = (real)(1.0 / (1.0 + aC * diag_hat(nx, ny, nz, rec, i, j, k, sT, dS, 0.0)));
     }
 }
-
-// Diagnostic: L u by visiting the 8 vertices of each voxel (independent of
-// the z-march kernel's data movement).
-template <typename real>
-__global__ void k_apply_simple(int nx, int ny, int nz, const ushort4 *rec, const real *u, double sT, double dS,
-                               double C, real *out)
-{
-    const long long n = (long long)nx * ny * nz;
-    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
-        if (!rec_tissue(rec[q])) { out[q] = 0; continue; }
-        const int i = (int)(q % nx), j = (int)((q / nx) % ny), k = (int)(q / ((long long)nx * ny));
-        double acc = 0.0;
-        for (int uu = 0; uu < 2; ++uu)
-            for (int t = 0; t < 2; ++t)
-                for (int s = 0; s < 2; ++s) {
-                    const int I = i + s, J = j + t, K = k + uu;
-                    int cnt[3], nT;
-                    double M[6];
-                    bool T[2][2][2];
-                    vertex_static(nx, ny, nz, rec, I, J, K, cnt, nT, M, T);
-                    double val[2][2][2];
-                    for (int a2 = 0; a2 < 2; ++a2)
-                        for (int b2 = 0; b2 < 2; ++b2)
-                            for (int c2 = 0; c2 < 2; ++c2) {
-                                const int ii = I - 1 + c2, jj = J - 1 + b2, kk = K - 1 + a2;
-                                val[a2][b2][c2] = T[a2][b2][c2] ? (double)u[(long long)ii + (long long)nx * ((long long)jj + (long long)ny * kk)] : 0.0;
-                            }
-                    double g[3] = {0, 0, 0};
-                    for (int o1 = 0; o1 < 2; ++o1)
-                        for (int o2 = 0; o2 < 2; ++o2) {
-                            if (T[o2][o1][0] && T[o2][o1][1]) g[0] += val[o2][o1][1] - val[o2][o1][0];
-                            if (T[o2][0][o1] && T[o2][1][o1]) g[1] += val[o2][1][o1] - val[o2][0][o1];
-                            if (T[0][o2][o1] && T[1][o2][o1]) g[2] += val[1][o2][o1] - val[0][o2][o1];
-                        }
-                    double r3[3];
-                    for (int a3 = 0; a3 < 3; ++a3) r3[a3] = cnt[a3] ? 1.0 / cnt[a3] : 0.0;
-                    const double h[3] = {g[0] * r3[0], g[1] * r3[1], g[2] * r3[2]};
-                    const double iso = sT * nT;
-                    double F[3];
-                    F[0] = r3[0] * (iso * h[0] + dS * (M[0] * h[0] + M[3] * h[1] + M[4] * h[2]));
-                    F[1] = r3[1] * (iso * h[1] + dS * (M[3] * h[0] + M[1] * h[1] + M[5] * h[2]));
-                    F[2] = r3[2] * (iso * h[2] + dS * (M[4] * h[0] + M[5] * h[1] + M[2] * h[2]));
-                    const int os = 1 - s, ot = 1 - t, ou = 1 - uu;
-                    if (T[ou][ot][1 - os]) acc += (os ? 1.0 : -1.0) * F[0];
-                    if (T[ou][1 - ot][os]) acc += (ot ? 1.0 : -1.0) * F[1];
-                    if (T[1 - ou][ot][os]) acc += (ou ? 1.0 : -1.0) * F[2];
-                }
-        out[q] = (real)(C * acc);
-    }
-}
-
 
 // ---------------------------------------------------------------------------
 // Per-component reductions over the component-sorted tissue index list.
@@ -200,8 +177,12 @@ __device__ __forceinline__ void comp_mean_item(const Inst<real> &I, int field, i
     Ctl *ctl = I.ctl;
     const real *x = field == RED_B ? I.b : ((ctl->iters & 1) ? I.x1 : I.x0);
     const Chunk ch = I.chunks[item];
+    const bool rhs_torso = field == RED_B && I.torso;   // b is 0 on the torso (stale values there are skipped)
     double s = 0.0;
-    for (int i = ch.start + threadIdx.x; i < ch.end; i += kRedThreads) s += (double)x[I.idx[i]];
+    for (int i = ch.start + threadIdx.x; i < ch.end; i += kRedThreads) {
+        const int q = I.idx[i];
+        if (!rhs_torso || rec_tissue(I.rec[q])) s += (double)x[q];
+    }
     s = block_sum<kRedThreads>(s, sm.sred);
     if (threadIdx.x == 0) I.partials[item] = s;
     if (!arrive_last(ctl, nitems, &sm.sflag)) return;
@@ -217,7 +198,8 @@ __device__ __forceinline__ void comp_mean_item(const Inst<real> &I, int field, i
     }
 }
 
-// b <- b - means[comp] on the tissue; the item that completes the launch forms
+// b <- b - means[comp] on the domain (with a torso, b counts as 0 on its voxels:
+// the right-hand side -L_i v lives on the tissue); the item that completes the launch forms
 // ||b||^2 and starts a new elliptic solve in the control block.
 template <typename real>
 __device__ __forceinline__ void comp_subtract_item(const Inst<real> &I, int item, int nitems, RedSmem &sm)
@@ -228,7 +210,8 @@ __device__ __forceinline__ void comp_subtract_item(const Inst<real> &I, int item
     double s = 0.0;
     for (int i = ch.start + threadIdx.x; i < ch.end; i += kRedThreads) {
         const int q = I.idx[i];
-        const real v = (real)((double)I.b[q] - m);
+        const double bq = (I.torso && !rec_tissue(I.rec[q])) ? 0.0 : (double)I.b[q];   // 0 on the torso
+        const real v = (real)(bq - m);
         I.b[q] = v;
         s += (double)v * (double)v;
     }
@@ -484,6 +467,15 @@ __global__ void __launch_bounds__(kRedThreads) k_lz_start(Inst<real> I, long lon
         z ^= z >> 31;
         w[q] = lz_diag(I, q) > 0.0 ? (real)((double)(z >> 11) * 0x1.0p-53 - 0.5) : real(0);
     }
+}
+
+// ECG (Sec. "Electrocardiogram"): the potentials at the three electrode voxels
+// (RA, LA, LL) after the solve, appended to the record as sample `slot`.
+template <typename real>
+__global__ void k_ecg_record(const real *ve, int q0, int q1, int q2, double *rec, long long slot)
+{
+    const int t = threadIdx.x;
+    if (t < 3) rec[3 * slot + t] = (double)ve[t == 0 ? q0 : (t == 1 ? q1 : q2)];
 }
 
 // v_e <- x_final - means[comp] (written to x0, the warm start of the next solve).

@@ -25,17 +25,27 @@ constexpr int kTileX = 30;                  // output voxels per row (lanes 1..3
 constexpr int kMaxStim = 8;
 constexpr unsigned kFull = 0xffffffffu;
 constexpr unsigned short kNonTissue = 0xBC00u;  // fp16 -1.0: record lane 3 of a non-tissue voxel
+constexpr unsigned short kBathTag = 0x8000u;    // fp16 -0.0 in lane 0: a torso voxel of the elliptic records
 constexpr int kRedThreads = 256;            // reduction kernels
 constexpr int kChunk = 2048;                // tissue voxels per reduction chunk
 
 // M_IE_RHS: reaction plus f = v* - a L_i ve of the implicit bidomain step;
-// M_IE: one Jacobi sweep of (I + a L_i) x = f (Eq. iejac1).
-enum Mode { M_APPLY = 0, M_RHS = 1, M_PAR_MONO = 2, M_PAR_BI = 3, M_JAC = 4, M_IE_RHS = 5, M_IE = 6 };
+// M_IE: one Jacobi sweep of (I + a L_i) x = f (Eq. iejac1);
+// M_JAC_BATH, M_APPLY_BATH: the elliptic sweep and operator over tissue + a
+// conducting torso (Eq. bidomain1, lines 3-5): the tissue term (pairs of
+// tissue voxels, fibre tensors) plus the torso term (pairs of any two domain
+// voxels, sig_o I per torso voxel of the vertex block).
+enum Mode { M_APPLY = 0, M_RHS = 1, M_PAR_MONO = 2, M_PAR_BI = 3, M_JAC = 4, M_IE_RHS = 5, M_IE = 6, M_JAC_BATH = 7,
+            M_APPLY_BATH = 8 };
 enum Diffusion { DIFF_EXPLICIT = 0, DIFF_IMPLICIT = 1 };
 
 // Modes that run a solve sweep (Jacobi of the elliptic or the implicit parabolic system).
 template <int MODE>
-constexpr bool kSweep = MODE == M_JAC || MODE == M_IE;
+constexpr bool kJac = MODE == M_JAC || MODE == M_JAC_BATH;
+template <int MODE>
+constexpr bool kTwoTerm = MODE == M_JAC_BATH || MODE == M_APPLY_BATH;
+template <int MODE>
+constexpr bool kSweep = kJac<MODE> || MODE == M_IE;
 enum Model { MODEL_MONO = 0, MODEL_BI = 1 };
 
 // One stencil work item: voxel columns x in [x0, x0 + 30), rows
@@ -120,6 +130,11 @@ struct Inst {
     int solver, pad3;
     real cheb_tau_c;
     double cheb_rho, cheb_theta;
+    // conducting torso: the elliptic descriptor's records tag torso voxels (kBathTag), and
+    // sig_o is the torso term's conductivity; in the tissue descriptor the reductions of the
+    // elliptic right-hand side count torso voxels as 0
+    int torso, pad4;
+    real sig_o;
 };
 
 // Weight of sweep k of the Chebyshev semi-iteration: w = 1 for k = 0, else
@@ -136,6 +151,8 @@ __device__ __forceinline__ float h2f(unsigned short b) { return __half2float(__u
 __device__ __forceinline__ bool rec_tissue(const ushort4 &r) { return (r.w & 0x8000u) == 0; }
 // The same record as two packed 32-bit words: (fx | fy << 16, fz | w << 16).
 __device__ __forceinline__ bool rec_tissue(const uint2 &r) { return (int)r.y >= 0; }
+__device__ __forceinline__ bool rec_bath(const ushort4 &r) { return r.x == kBathTag; }
+__device__ __forceinline__ bool rec_bath(const uint2 &r) { return (r.x & 0xFFFFu) == kBathTag; }
 __device__ __forceinline__ float2 lo_hi_f(unsigned w) { return __half22float2(*reinterpret_cast<const __half2 *>(&w)); }
 
 // Mitchell-Schaeffer explicit Euler (Eqs. ms1, ms2; closing branch -w/tau_close).

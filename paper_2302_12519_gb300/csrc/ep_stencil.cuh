@@ -33,6 +33,13 @@
 // The same item body serves the single-instance kernels (descriptor passed by
 // value) and the batched persistent kernels (descriptor read from a device
 // table, items of all instances packed in one list).
+//
+// With a conducting torso (M_JAC_BATH, M_APPLY_BATH) the records cover tissue
+// + torso, torso voxels tagged, and every vertex carries two terms: the one
+// above over tissue pairs, and Fo_a = ro_a^2 sig_o nB go_a over the pairs of
+// any two domain voxels (go_a their summed differences, ro_a = 1 / their
+// count, nB the torso voxels of the block).  Each term is scattered with its
+// own pair flags.
 #pragma once
 
 #include "ep_common.cuh"
@@ -50,7 +57,8 @@ __device__ __forceinline__ float rcp_count<float>(float n)
     return n > 0.5f ? __fdividef(1.0f, n) : 0.0f;   // n in {1, 2, 3, 4}
 }
 
-// Diagnostic operand for M_APPLY: out = L_{sL,sT} u.
+// Operand of M_APPLY (out = L_{sL,sT} u) and M_APPLY_BATH (the same plus the
+// torso term of the descriptor's sig_o).
 template <typename real>
 struct ApplyIO {
     const real *u;
@@ -67,6 +75,7 @@ struct Op {
     real *out, *wout, *tact;        // stores (PAR: v, w, t_act; RHS: b; APPLY: out; JAC, IE: next iterate;
     real *out2;                     //         IE_RHS: f, w, and v* in out2)
     real sT, dS, C, coef;
+    real so;           // torso conductivity of the torso term (two-term modes)
     double tn, dt_d;
     int nz;
     int cheb;          // Jacobi sweep accelerated by the Chebyshev semi-iteration
@@ -97,6 +106,19 @@ struct St {
     real tYm;                    // tissue of voxel (x, lo - 1) in this plane
     real tzm;                    // tissue of voxel (x, lo) in the plane below
     real e0, e1, e2;             // output voxel (x, lo): JAC b, 1/Dhat ; PAR v*, w+, v
+    // torso term (two-term modes): the same over domain voxels (tissue or torso)
+    real dLo, dHi, dLoL, dHiL;   // domain 0/1
+    real nB;                     // torso voxels of the four voxels of this plane
+    real sxd, cxd, syd, cyd;     // masked differences over domain pairs and their counts
+    real FBo[3], FAo[3];         // torso-term vertex fluxes
+    real dYm, dzm;               // domain flags of (x, lo - 1) here and of (x, lo) below
+};
+
+// Vertex-flux exchange of the torso term between warps (the row's tissue and
+// domain flags travel together in sT as t + d).
+template <typename real>
+struct TorsoSmem {
+    real sFo[2][3][kWarps][32];
 };
 
 template <typename real, int MODE>
@@ -113,7 +135,8 @@ __device__ __forceinline__ void load_plane(const Op<real> &o, int k, bool lo_in,
         L.uLo = __ldg(o.src + q);
         if (MODE == M_PAR_MONO || MODE == M_PAR_BI || MODE == M_IE_RHS) L.wLo = __ldg(o.w + q);
         if (MODE == M_PAR_BI || MODE == M_IE_RHS) L.veLo = __ldg(o.ve + q);
-        if (MODE == M_JAC) L.bLo = __ldg(o.b + q);
+        if (kJac<MODE>) L.bLo = __ldg(o.b + q);
+        if (kJac<MODE> && o.cheb) L.iLo = o.out[q];   // x_{k-1}: this thread overwrites it one plane later
     }
     if (kin && hi_in) {
         const int q = qhi + k * plane;
@@ -137,10 +160,13 @@ template <typename real, int MODE>
 __device__ __forceinline__ void plane_step(const Inst<real> &I, const Op<real> &o, const Lane &g, int k,
                                            bool do_vertex, bool do_output, const St<real> &P, St<real> &C,
                                            const Ld<real, MODE> &L, real (*sF)[3][kWarps][32],
-                                           real (*sT)[kWarps][32], bool check, float &acc)
+                                           real (*sT)[kWarps][32], TorsoSmem<real> *ts, bool check, float &acc)
 {
+    constexpr bool TT = kTwoTerm<MODE>;
     // ---- decode the two voxels of the lane ----
-    const bool tlo = rec_tissue(L.rLo), thi = rec_tissue(L.rHi);
+    const bool dlo = rec_tissue(L.rLo), dhi = rec_tissue(L.rHi);   // in the records' domain
+    const bool tlo = TT ? dlo && !rec_bath(L.rLo) : dlo;           // tissue
+    const bool thi = TT ? dhi && !rec_bath(L.rHi) : dhi;
     const float2 alo = lo_hi_f(L.rLo.x), blo = lo_hi_f(L.rLo.y), ahi = lo_hi_f(L.rHi.x), bhi = lo_hi_f(L.rHi.y);
     const real flo0 = (real)alo.x, flo1 = (real)alo.y, flo2 = (real)blo.x;
     const real fhi0 = (real)ahi.x, fhi1 = (real)ahi.y, fhi2 = (real)bhi.x;
@@ -159,9 +185,9 @@ __device__ __forceinline__ void plane_step(const Inst<real> &I, const Op<real> &
         }
         C.e0 = vs; C.e1 = wn; C.e2 = L.uLo;
     } else {
-        ulo = tlo ? L.uLo : real(0);
-        uhi = thi ? L.uHi : real(0);
-        if (MODE == M_JAC) { C.e0 = L.bLo; C.e1 = (real)blo.y; C.e2 = L.iLo; }
+        ulo = dlo ? L.uLo : real(0);
+        uhi = dhi ? L.uHi : real(0);
+        if (kJac<MODE>) { C.e0 = L.bLo; C.e1 = (real)blo.y; C.e2 = L.iLo; }
         if (MODE == M_IE) { C.e0 = L.bLo; C.e1 = L.iLo; }
     }
     C.uLo = ulo;
@@ -191,6 +217,20 @@ __device__ __forceinline__ void plane_step(const Inst<real> &I, const Op<real> &
     const real cyo = C.tLo * C.tHi, cyl = C.tLoL * C.tHiL;
     C.sy = cyo * (uhi - ulo) + cyl * (C.uHiL - C.uLoL);
     C.cy = cyo + cyl;
+    if constexpr (TT) {   // the same over domain pairs
+        C.dLo = dlo ? real(1) : real(0);
+        C.dHi = dhi ? real(1) : real(0);
+        C.dLoL = __shfl_up_sync(kFull, C.dLo, 1);
+        C.dHiL = __shfl_up_sync(kFull, C.dHi, 1);
+        C.dzm = P.dLo;
+        C.nB = ((C.dLo + C.dHi) + (C.dLoL + C.dHiL)) - C.nT;
+        const real dxlo = C.dLo * C.dLoL, dxhi = C.dHi * C.dHiL;
+        C.sxd = dxlo * (ulo - C.uLoL) + dxhi * (uhi - C.uHiL);
+        C.cxd = dxlo + dxhi;
+        const real dyo = C.dLo * C.dHi, dyl = C.dLoL * C.dHiL;
+        C.syd = dyo * (uhi - ulo) + dyl * (C.uHiL - C.uLoL);
+        C.cyd = dyo + dyl;
+    }
 
     // ---- vertex (x - 1/2, lo + 1/2, k - 1/2) ----
     real F0 = real(0), F1 = real(0), F2 = real(0);
@@ -210,12 +250,31 @@ __device__ __forceinline__ void plane_step(const Inst<real> &I, const Op<real> &
         F1 = ry * (iso * hy + o.dS * (M3 * hx + M1 * hy + M5 * hz));
         F2 = rz * (iso * hz + o.dS * (M4 * hx + M5 * hy + M2 * hz));
     }
+    real Fo0 = real(0), Fo1 = real(0), Fo2 = real(0);
+    if constexpr (TT) {
+        if (do_vertex) {
+            const real dzlo = P.dLo * C.dLo, dzhi = P.dHi * C.dHi, dzlol = P.dLoL * C.dLoL, dzhil = P.dHiL * C.dHiL;
+            const real gzd = dzlo * (ulo - P.uLo) + dzhi * (uhi - P.uHi) + dzlol * (C.uLoL - P.uLoL) +
+                             dzhil * (C.uHiL - P.uHiL);
+            const real rxd = rcp_count(P.cxd + C.cxd), ryd = rcp_count(P.cyd + C.cyd),
+                       rzd = rcp_count((dzlo + dzhi) + (dzlol + dzhil));
+            const real ko = o.so * (P.nB + C.nB);
+            Fo0 = rxd * rxd * ko * (P.sxd + C.sxd);
+            Fo1 = ryd * ryd * ko * (P.syd + C.syd);
+            Fo2 = rzd * rzd * ko * gzd;
+        }
+    }
     // ---- exchange vertex rows between warps (buffer by plane parity) ----
     const int par = k & 1;
     sF[par][0][g.wid][g.lane] = F0;
     sF[par][1][g.wid][g.lane] = F1;
     sF[par][2][g.wid][g.lane] = F2;
-    sT[par][g.wid][g.lane] = C.tLo;
+    sT[par][g.wid][g.lane] = TT ? C.tLo + C.dLo : C.tLo;
+    if constexpr (TT) {
+        ts->sFo[par][0][g.wid][g.lane] = Fo0;
+        ts->sFo[par][1][g.wid][g.lane] = Fo1;
+        ts->sFo[par][2][g.wid][g.lane] = Fo2;
+    }
     __syncthreads();
     C.FB[0] = F0; C.FB[1] = F1; C.FB[2] = F2;
     if (g.wid >= 1) {
@@ -223,8 +282,22 @@ __device__ __forceinline__ void plane_step(const Inst<real> &I, const Op<real> &
         C.FA[1] = sF[par][1][g.wid - 1][g.lane];
         C.FA[2] = sF[par][2][g.wid - 1][g.lane];
         C.tYm = sT[par][g.wid - 1][g.lane];
+        if constexpr (TT) {   // unpack t + d (t <= d)
+            C.dYm = C.tYm > real(0.5) ? real(1) : real(0);
+            C.tYm = C.tYm > real(1.5) ? real(1) : real(0);
+        }
     } else {
         C.FA[0] = C.FA[1] = C.FA[2] = C.tYm = real(0);
+    }
+    if constexpr (TT) {
+        C.FBo[0] = Fo0; C.FBo[1] = Fo1; C.FBo[2] = Fo2;
+        if (g.wid >= 1) {
+            C.FAo[0] = ts->sFo[par][0][g.wid - 1][g.lane];
+            C.FAo[1] = ts->sFo[par][1][g.wid - 1][g.lane];
+            C.FAo[2] = ts->sFo[par][2][g.wid - 1][g.lane];
+        } else {
+            C.FAo[0] = C.FAo[1] = C.FAo[2] = C.dYm = real(0);
+        }
     }
 
     // ---- output voxel (x, lo, k - 1) ----
@@ -238,15 +311,30 @@ __device__ __forceinline__ void plane_step(const Inst<real> &I, const Op<real> &
         const real phzm = pszP + __shfl_down_sync(kFull, pszP, 1);
         const real phzp = pszC + __shfl_down_sync(kFull, pszC, 1);
         const real tR = __shfl_down_sync(kFull, P.tLo, 1);
-        if (g.out_lane && P.tLo != real(0)) {
-            const real s = P.tLoL * phxm - tR * phxp + P.tYm * phym - P.tHi * phyp + P.tzm * phzm - C.tLo * phzp;
+        real so_sum = real(0), own = P.tLo;
+        if constexpr (TT) {   // torso term, scattered with the domain flags
+            const real qxm = (P.FAo[0] + C.FAo[0]) + (P.FBo[0] + C.FBo[0]);
+            const real qxp = __shfl_down_sync(kFull, qxm, 1);
+            const real qyA = P.FAo[1] + C.FAo[1], qyB = P.FBo[1] + C.FBo[1];
+            const real qym = qyA + __shfl_down_sync(kFull, qyA, 1);
+            const real qyp = qyB + __shfl_down_sync(kFull, qyB, 1);
+            const real qzP = P.FAo[2] + P.FBo[2], qzC = C.FAo[2] + C.FBo[2];
+            const real qzm = qzP + __shfl_down_sync(kFull, qzP, 1);
+            const real qzp = qzC + __shfl_down_sync(kFull, qzC, 1);
+            const real dR = __shfl_down_sync(kFull, P.dLo, 1);
+            so_sum = P.dLoL * qxm - dR * qxp + P.dYm * qym - P.dHi * qyp + P.dzm * qzm - C.dLo * qzp;
+            own = P.dLo;
+        }
+        if (g.out_lane && own != real(0)) {
+            real s = P.tLoL * phxm - tR * phxp + P.tYm * phym - P.tHi * phyp + P.tzm * phzm - C.tLo * phzp;
+            if constexpr (TT) s = P.tLo * s + so_sum;   // the tissue term acts on tissue voxels only
             const real Lu = o.C * s;
             const int q = g.qlo + (k - 1) * g.plane;
-            if (MODE == M_APPLY) {
+            if (MODE == M_APPLY || MODE == M_APPLY_BATH) {
                 o.out[q] = Lu;
             } else if (MODE == M_RHS) {
                 o.out[q] = -Lu;
-            } else if (MODE == M_JAC) {
+            } else if (kJac<MODE>) {
                 const real r = P.e0 - Lu;
                 const real basic = P.uLo + o.coef * P.e1 * r;
                 if (o.cheb) {   // x_{k+1} = w (basic - x_{k-1}) + x_{k-1}; x_{k-1} came through the ring
@@ -288,7 +376,8 @@ __device__ __forceinline__ void zero_state(St<real> &S)
     for (int j = 0; j < 6; ++j) S.Y[j] = real(0);
     S.sx = S.cx = S.sy = S.cy = S.tYm = S.tzm = S.e0 = S.e1 = S.e2 = real(0);
 #pragma unroll
-    for (int j = 0; j < 3; ++j) S.FB[j] = S.FA[j] = real(0);
+    for (int j = 0; j < 3; ++j) S.FB[j] = S.FA[j] = S.FBo[j] = S.FAo[j] = real(0);
+    S.dLo = S.dHi = S.dLoL = S.dHiL = S.nB = S.sxd = S.cxd = S.syd = S.cyd = S.dYm = S.dzm = real(0);
 }
 
 // The Jacobi sweep and the monodomain step stage their loads through a
@@ -296,8 +385,11 @@ __device__ __forceinline__ void zero_state(St<real> &S)
 // each thread reads back only what it copied itself, so the ring needs no
 // barrier, and the prefetched planes hold no registers.  The other modes run
 // once per step and prefetch one plane into registers.
-template <int MODE>
-constexpr bool kRinged = MODE == M_JAC || MODE == M_IE || MODE == M_PAR_MONO;
+// (The FP64 torso sweep prefetches into registers: its ring would not fit in
+// 48 KB of static shared memory next to both terms' flux exchange.)
+template <typename real, int MODE>
+constexpr bool kRinged = (kJac<MODE> || MODE == M_IE || MODE == M_PAR_MONO) &&
+                         !(kTwoTerm<MODE> && sizeof(real) == 8);
 
 template <typename real, int MODE>
 struct Ring {
@@ -310,6 +402,8 @@ struct Ring {
 };
 struct NoRing {};
 
+struct NoTorso {};
+
 template <typename real, int MODE>
 struct StencilSmem {
     real sF[2][3][kWarps][32];
@@ -317,7 +411,8 @@ struct StencilSmem {
     double sred[kWarps];
     double cheb_w;   // Chebyshev weight of the sweep, formed by one thread (FP64 is slow here)
     int sflag;
-    typename std::conditional<kRinged<MODE>, Ring<real, MODE>, NoRing>::type ring;
+    typename std::conditional<kRinged<real, MODE>, Ring<real, MODE>, NoRing>::type ring;
+    typename std::conditional<kTwoTerm<MODE>, TorsoSmem<real>, NoTorso>::type tor;
 };
 
 template <int BYTES>
@@ -345,12 +440,12 @@ __device__ __forceinline__ void ring_issue(const Op<real> &o, Ring<real, MODE> &
         cp_async_n<sizeof(real)>(&R.x[slot][0][t], (MODE == M_PAR_MONO ? o.w : o.b) + q);
         if (MODE == M_IE) cp_async_n<sizeof(real)>(&R.x[slot][1][t], o.inv + q);
         // x_{k-1} sits where this thread will write x_{k+1} of this voxel, one plane later
-        if (MODE == M_JAC && o.cheb) cp_async_n<sizeof(real)>(&R.x[slot][1][t], o.out + q);
+        if (kJac<MODE> && o.cheb) cp_async_n<sizeof(real)>(&R.x[slot][1][t], o.out + q);
     } else {
         R.rec[slot][0][t] = make_uint2(0u, (unsigned)kNonTissue << 16);
         R.u[slot][0][t] = real(0);
         R.x[slot][0][t] = MODE == M_PAR_MONO ? real(1) : real(0);
-        if (MODE == M_IE || MODE == M_JAC) R.x[slot][1][t] = real(0);
+        if (MODE == M_IE || kJac<MODE>) R.x[slot][1][t] = real(0);
     }
     if (kin && hi_in) {
         const int q = qhi + k * plane;
@@ -372,7 +467,7 @@ __device__ __forceinline__ void ring_read(const Ring<real, MODE> &R, int slot, L
     L.rHi = R.rec[slot][1][t];
     L.uLo = R.u[slot][0][t];
     L.uHi = R.u[slot][1][t];
-    if (MODE == M_JAC || MODE == M_IE) {
+    if (kJac<MODE> || MODE == M_IE) {
         L.bLo = R.x[slot][0][t];
         L.iLo = (MODE == M_IE || o_cheb) ? R.x[slot][1][t] : real(0);
         L.wLo = L.wHi = real(1);
@@ -389,7 +484,8 @@ template <typename real, int MODE, int S>
 __device__ __forceinline__ void ring_plane(const Inst<real> &I, const Op<real> &o, const Lane &g, int k, int kbeg,
                                            int kend, bool lo_in, bool hi_in, int qhi, Ring<real, MODE> &R,
                                            const St<real> &P, St<real> &Cn, Ld<real, MODE> &L,
-                                           real (*sF)[3][kWarps][32], real (*sT)[kWarps][32], bool check, float &acc)
+                                           real (*sF)[3][kWarps][32], real (*sT)[kWarps][32], TorsoSmem<real> *ts,
+                                           bool check, float &acc)
 {
     constexpr int D = Ring<real, MODE>::D;
     constexpr int slot = S % D, next = (S + D - 1) % D;
@@ -397,7 +493,7 @@ __device__ __forceinline__ void ring_plane(const Inst<real> &I, const Op<real> &
     cp_async_commit();
     cp_async_wait<D - 1>();
     ring_read<real, MODE>(R, slot, L, o.cheb != 0);
-    plane_step<real, MODE>(I, o, g, k, k > kbeg, k > kbeg + 1, P, Cn, L, sF, sT, check, acc);
+    plane_step<real, MODE>(I, o, g, k, k > kbeg, k > kbeg + 1, P, Cn, L, sF, sT, ts, check, acc);
 }
 
 // One work item (segment) of one instance.  item / nitems: index of this item
@@ -409,6 +505,8 @@ __device__ __forceinline__ void stencil_item(const Inst<real> &I, int seg_index,
 {
     real(*sF)[3][kWarps][32] = reinterpret_cast<real(*)[3][kWarps][32]>(&sm.sF[0][0][0][0]);
     real(*sT)[kWarps][32] = reinterpret_cast<real(*)[kWarps][32]>(&sm.sT[0][0][0]);
+    TorsoSmem<real> *ts = nullptr;
+    if constexpr (kTwoTerm<MODE>) ts = &sm.tor;
     Ctl *ctl = I.ctl;
 
     Op<real> o;
@@ -419,11 +517,12 @@ __device__ __forceinline__ void stencil_item(const Inst<real> &I, int seg_index,
     o.out = o.wout = o.tact = o.out2 = nullptr;
     o.cheb = 0;
     o.cheb_w = real(1);
+    o.so = I.sig_o;
     o.tn = 0.0;
     o.dt_d = I.dt_d;
     int sweep = 0;
     bool check = false;
-    const long long step = (MODE == M_APPLY) ? 0 : ctl->step;
+    const long long step = (MODE == M_APPLY || MODE == M_APPLY_BATH) ? 0 : ctl->step;
     const int cur = (int)(step & 1);
     if (kSweep<MODE>) {
         sweep = (int)(*(volatile unsigned long long *)&ctl->jarrive / (unsigned long long)nitems);
@@ -436,7 +535,7 @@ __device__ __forceinline__ void stencil_item(const Inst<real> &I, int seg_index,
             }
             return;
         }
-        if (MODE == M_JAC) {
+        if (kJac<MODE>) {
             o.src = (sweep & 1) ? I.x1 : I.x0;
             o.out = (sweep & 1) ? I.x0 : I.x1;
             o.sT = I.sTie; o.dS = I.dSie; o.coef = I.coef_jac;
@@ -470,7 +569,7 @@ __device__ __forceinline__ void stencil_item(const Inst<real> &I, int seg_index,
         o.src = I.v[cur ^ 1];        // v of step n + 1 (the step counter moves at the end of the step)
         o.out = I.b;
         o.sT = I.sTi; o.dS = I.dSi; o.coef = real(0);
-    } else if (MODE == M_APPLY) {
+    } else if (MODE == M_APPLY || MODE == M_APPLY_BATH) {
         o.src = io->u;
         o.out = io->out;
         o.sT = io->sT; o.dS = io->dS; o.coef = real(0);
@@ -505,7 +604,7 @@ __device__ __forceinline__ void stencil_item(const Inst<real> &I, int seg_index,
     zero_state(S1);
     Ld<real, MODE> L0, L1;
     const int kbeg = sg.k0 - 1, kend = sg.k1;
-    if constexpr (kRinged<MODE>) {
+    if constexpr (kRinged<real, MODE>) {
         // planes staged D - 1 ahead through the shared-memory ring; the loop is
         // unrolled by 4 so that every ring slot is a compile-time constant
         constexpr int D = Ring<real, MODE>::D;
@@ -516,13 +615,13 @@ __device__ __forceinline__ void stencil_item(const Inst<real> &I, int seg_index,
             cp_async_commit();
         }
         for (int k = kbeg;;) {
-            ring_plane<real, MODE, 0>(I, o, g, k, kbeg, kend, lo_in, hi_in, qhi, R, S1, S0, L0, sF, sT, check, acc);
+            ring_plane<real, MODE, 0>(I, o, g, k, kbeg, kend, lo_in, hi_in, qhi, R, S1, S0, L0, sF, sT, ts, check, acc);
             if (++k > kend) break;
-            ring_plane<real, MODE, 1>(I, o, g, k, kbeg, kend, lo_in, hi_in, qhi, R, S0, S1, L1, sF, sT, check, acc);
+            ring_plane<real, MODE, 1>(I, o, g, k, kbeg, kend, lo_in, hi_in, qhi, R, S0, S1, L1, sF, sT, ts, check, acc);
             if (++k > kend) break;
-            ring_plane<real, MODE, 2>(I, o, g, k, kbeg, kend, lo_in, hi_in, qhi, R, S1, S0, L0, sF, sT, check, acc);
+            ring_plane<real, MODE, 2>(I, o, g, k, kbeg, kend, lo_in, hi_in, qhi, R, S1, S0, L0, sF, sT, ts, check, acc);
             if (++k > kend) break;
-            ring_plane<real, MODE, 3>(I, o, g, k, kbeg, kend, lo_in, hi_in, qhi, R, S0, S1, L1, sF, sT, check, acc);
+            ring_plane<real, MODE, 3>(I, o, g, k, kbeg, kend, lo_in, hi_in, qhi, R, S0, S1, L1, sF, sT, ts, check, acc);
             if (++k > kend) break;
         }
         cp_async_wait<0>();
@@ -531,10 +630,10 @@ __device__ __forceinline__ void stencil_item(const Inst<real> &I, int seg_index,
         // two planes per iteration; the state records swap roles
         for (int k = kbeg;;) {
             if (k + 1 <= kend) load_plane<real, MODE>(o, k + 1, lo_in, hi_in, g.qlo, qhi, g.plane, L1);
-            plane_step<real, MODE>(I, o, g, k, k > kbeg, k > kbeg + 1, S1, S0, L0, sF, sT, check, acc);
+            plane_step<real, MODE>(I, o, g, k, k > kbeg, k > kbeg + 1, S1, S0, L0, sF, sT, ts, check, acc);
             if (++k > kend) break;
             if (k + 1 <= kend) load_plane<real, MODE>(o, k + 1, lo_in, hi_in, g.qlo, qhi, g.plane, L0);
-            plane_step<real, MODE>(I, o, g, k, k > kbeg, k > kbeg + 1, S0, S1, L1, sF, sT, check, acc);
+            plane_step<real, MODE>(I, o, g, k, k > kbeg, k > kbeg + 1, S0, S1, L1, sF, sT, ts, check, acc);
             if (++k > kend) break;
         }
     }
@@ -578,9 +677,10 @@ __device__ __forceinline__ void stencil_item(const Inst<real> &I, int seg_index,
     }
 }
 
-// Single instance: one CTA per segment.
+// Single instance: one CTA per segment.  The two-term modes keep both terms'
+// vertex state and run two CTAs an SM.
 template <typename real, int MODE>
-__global__ void __launch_bounds__(kThreads, kMinBlocks) k_stencil(Inst<real> I, ApplyIO<real> io)
+__global__ void __launch_bounds__(kThreads, kTwoTerm<MODE> ? 2 : kMinBlocks) k_stencil(Inst<real> I, ApplyIO<real> io)
 {
     __shared__ StencilSmem<real, MODE> sm;
     if (kSweep<MODE> && I.ctl->done) return;   // converged earlier: queued sweeps are no-ops

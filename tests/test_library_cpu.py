@@ -145,6 +145,38 @@ def test_footprint_counts_the_interval_estimate(lib):
     assert extra >= 8 * 82 + 16 and (extra - 8 * 82) % 16 == 0
 
 
+def test_torso_and_ecg_are_validated_and_planned_on_the_host(lib):
+    """ep_set_torso / ep_set_ecg check their arguments without a device; a
+    torso adds the domain's records (8 bytes a voxel) and work items to the
+    resident bytes and its staging (1 byte a voxel) to the peak; an ECG adds its
+    record (3 doubles a sample)."""
+    import workloads as W
+    c = W.with_torso(W.random_case(5, 12, 10, 9), sig_o=0.8, pad=1)
+    plain = ep.sim_from_case(W.with_torso(W.random_case(5, 12, 10, 9), sig_o=0.8, pad=1), use_torch=False)
+    plain.set_torso(np.zeros(c.n, np.uint8), 1.0)   # an all-zero torso is no torso
+    plain.set_ecg(None, 0)
+    s = ep.sim_from_case(c, use_torch=False, ecg_capacity=100)
+    (r0, p0), (r1, p1) = plain.footprint(), s.footprint()
+    assert p0 - r0 == 21 * c.n and p1 - r1 == 22 * c.n
+    assert r1 - r0 >= 8 * c.n + 3 * 8 * 100
+    for bad in (0.0, -1.0, float("nan"), float("inf")):
+        with pytest.raises(ep.EPError) as e:
+            s.set_torso(c.torso, bad)
+        assert e.value.status == ep.EP_EINVAL
+    with pytest.raises(ep.EPError) as e:
+        s.set_torso(np.zeros(7, np.uint8), 1.0)
+    assert e.value.status == ep.EP_EINVAL
+    for el in ([(0, 0, 0), (0, 0, 0), (c.nx, 0, 0)], [(-1, 0, 0), (0, 0, 0), (0, 0, 0)]):
+        with pytest.raises(ep.EPError) as e:
+            s.set_ecg(el, 10)
+        assert e.value.status == ep.EP_EINVAL
+    with pytest.raises(ep.EPError) as e:
+        s.set_ecg([(0, 0, 0)] * 3, -1)
+    assert e.value.status == ep.EP_EINVAL
+    s.close()
+    plain.close()
+
+
 def test_server_needs_a_device(lib):
     """Without a GPU the server cannot start and says so (no host fallback)."""
     import torch
