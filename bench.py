@@ -31,6 +31,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 BYTES_PER_SWEEP_VOXEL = 19      # x 4 + b 4 + x' 4 + fibre 6 + mask 1 (algorithmic, per tissue voxel)
+BYTES_PER_CHEB_SWEEP_VOXEL = 23  # the same plus x_{k-1} 4 (the Chebyshev semi-iteration's second operand)
 BYTES_PER_MONO_VOXEL = 23       # fused monodomain step: v, w read 8 + written 8 + fibre 6 + mask 1
 BYTES_PER_IE_SWEEP_VOXEL = 23   # implicit sweep: x, f, 1/(1 + a D) read 12 + fibre 6 + mask 1 + x' written 4
 REF_SAMPLE_SWEEPS = (8, 64)     # oracle sweeps timed per sample step (two caps -> per-sweep cost)
@@ -132,7 +133,8 @@ def _traffic_record(stem):
                 rec[k.strip()] = v.strip().strip("`")
         if rec.get("kernel_source_sha256_16") != _kernel_hash():
             return None
-        return float(rec["dram_bytes_per_tissue_voxel"])
+        # per voxel the kernel sweeps: tissue voxels, or tissue + torso voxels for a torso sweep
+        return float(rec.get("dram_bytes_per_domain_voxel", rec.get("dram_bytes_per_tissue_voxel")))
     except Exception:
         return None
 
@@ -382,7 +384,8 @@ def run_ours(a):
     else:
         sweep_s = prof.sweep_ms / 1e3
         launch_s = sweep_s / max(prof.sweeps, 1)
-        alg_bytes = BYTES_PER_SWEEP_VOXEL * n_dom   # over tissue + torso when a torso is set
+        per_voxel = BYTES_PER_CHEB_SWEEP_VOXEL if a.solver == "chebyshev" else BYTES_PER_SWEEP_VOXEL
+        alg_bytes = per_voxel * n_dom   # over tissue + torso when a torso is set
         kname = ("k_stencil<float,M_JAC_BATH> (elliptic sweep over tissue + torso)" if torso else
                  "k_stencil<float,M_JAC> (damped Jacobi sweep)")
         if a.solver == "chebyshev":
