@@ -55,6 +55,16 @@ class _Params(ctypes.Structure):
                 ("cheb_lmin", ctypes.c_double), ("cheb_lmax", ctypes.c_double), ("sig_o", ctypes.c_double)]
 
 
+class _SdfNode(ctypes.Structure):
+    _fields_ = [("op", ctypes.c_int), ("a", ctypes.c_float), ("b", ctypes.c_float), ("c", ctypes.c_float),
+                ("centre", ctypes.c_float * 3), ("rot", ctypes.c_float * 9)]
+
+
+class _SdfRegion(ctypes.Structure):
+    _fields_ = [("first", ctypes.c_int), ("count", ctypes.c_int), ("kind", ctypes.c_int),
+                ("axis", ctypes.c_float * 3), ("scale", ctypes.c_float)]
+
+
 class _Stim(ctypes.Structure):
     _fields_ = [("lo", ctypes.c_int * 3), ("hi", ctypes.c_int * 3),
                 ("t_start", ctypes.c_double), ("dur", ctypes.c_double), ("amp", ctypes.c_double)]
@@ -100,6 +110,11 @@ def lib():
         L.og_ie_total_iters.argtypes = [vp]
         L.og_ie_total_iters.restype = ctypes.c_long
         L.og_num_threads.restype = ip
+        L.og_sdf_eval.argtypes = [ctypes.POINTER(_SdfNode), ip, ctypes.POINTER(ctypes.c_float * 3)]
+        L.og_sdf_eval.restype = ctypes.c_float
+        L.og_sdf_encode.argtypes = [ctypes.POINTER(_SdfNode), ctypes.POINTER(_SdfRegion), ip, ip, ip, ip,
+                                    ctypes.c_float, ctypes.POINTER(ctypes.c_float * 3), dp, vp, vp, vp, vp]
+        L.og_sdf_encode.restype = ip
         _lib = L
     return _lib
 
@@ -299,3 +314,39 @@ def ecg_leads(phi) -> np.ndarray:
     ra, la, ll = phi[..., 0], phi[..., 1], phi[..., 2]
     return np.stack([la - ra, ll - ra, ll - la,
                      ra - 0.5 * (la + ll), la - 0.5 * (ra + ll), ll - 0.5 * (ra + la)], axis=-1)
+
+
+def _sdf_nodes(nodes):
+    N = (_SdfNode * len(nodes))()
+    for i, nd in enumerate(nodes):
+        N[i].op, N[i].a, N[i].b, N[i].c = int(nd.op), float(nd.a), float(nd.b), float(nd.c)
+        N[i].centre[:] = [float(v) for v in nd.centre]
+        N[i].rot[:] = [float(v) for v in nd.rot]
+    return N
+
+
+def sdf_eval(nodes, x) -> float:
+    """Value (FP32) of a postfix SDF program at the point x (mm)."""
+    N = _sdf_nodes(nodes)
+    p = (ctypes.c_float * 3)(*[float(v) for v in x])
+    return float(lib().og_sdf_eval(N, len(nodes), ctypes.byref(p)))
+
+
+def sdf_encode(nodes, regions, nx, ny, nz, dx, origin, helix_rad):
+    """Two-pass encoding of a scene (Sec. "Geometry", "Encoding"): per voxel
+    label, tissue mask and fibre (FP64), per vertex class; tissue count."""
+    N = _sdf_nodes(nodes)
+    R = (_SdfRegion * len(regions))()
+    for i, rg in enumerate(regions):
+        R[i].first, R[i].count, R[i].kind = int(rg.first), int(rg.count), int(rg.kind)
+        R[i].axis[:] = [float(v) for v in rg.axis]
+        R[i].scale = float(rg.scale)
+    n = nx * ny * nz
+    label = np.zeros(n, np.uint8)
+    mask = np.zeros(n, np.uint8)
+    fib = np.zeros(3 * n)
+    vert = np.zeros((nx + 1) * (ny + 1) * (nz + 1), np.uint8)
+    org = (ctypes.c_float * 3)(*[float(v) for v in origin])
+    cnt = lib().og_sdf_encode(N, R, len(regions), nx, ny, nz, float(dx), ctypes.byref(org), float(helix_rad),
+                              _ptr(label), _ptr(mask), _ptr(fib), _ptr(vert))
+    return {"label": label, "mask": mask, "fibres": fib, "vertices": vert, "n_tissue": cnt}

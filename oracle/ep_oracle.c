@@ -802,6 +802,158 @@ int og_run(og_sim *s, int nsteps, int *last_iters, double *last_relres)
     return st;
 }
 
+/* ------------------------------------------------------------------------ */
+/* geometry: signed distance functions and their two-pass encoding          */
+/* ------------------------------------------------------------------------ */
+
+/* Sec. "Geometry", subsections "Primitives" and "Encoding".  All arithmetic
+ * that decides an integer (inside or outside) is FP32, as in the thesis'
+ * kernels, one rounded operation at a time (the file is built without
+ * contraction): translate, rotate (row by row, left to right), then the
+ * primitive's formula:
+ *   cuboid     max_i(|p_i / r_i|) - 1             (a box in the max norm)
+ *   ellipsoid  |p / r|_2 - 1
+ *   cylinder   max(|p_xy| - r, |p_z| - h)
+ *   cone       max(|p_xy| - slope p_z - r, |p_z| - h)
+ * and the set algebra union = min, intersection = max, S1 minus S2 =
+ * max(s1, -s2), hollow = |s| - t.  The smoothed minimum is read as the
+ * quadratic blend min(a, b) - h^2 k / 4, h = max(k - |a - b|, 0) / k (the
+ * thesis shows it for several k without a formula). */
+static float og_sdf_prim(const og_sdf_node *nd, const float x[3])
+{
+    float d[3], p[3];
+    int i;
+    for (i = 0; i < 3; i++)
+        d[i] = x[i] - nd->centre[i];
+    for (i = 0; i < 3; i++) {
+        float t0 = nd->rot[3 * i] * d[0];
+        float t1 = nd->rot[3 * i + 1] * d[1];
+        float t2 = nd->rot[3 * i + 2] * d[2];
+        p[i] = (t0 + t1) + t2;
+    }
+    switch (nd->op) {
+    case OG_SDF_CUBOID: {
+        float q0 = fabsf(p[0] / nd->a), q1 = fabsf(p[1] / nd->b), q2 = fabsf(p[2] / nd->c);
+        return fmaxf(q0 - 1.0f, fmaxf(q1 - 1.0f, q2 - 1.0f));
+    }
+    case OG_SDF_ELLIPSOID: {
+        float q0 = p[0] / nd->a, q1 = p[1] / nd->b, q2 = p[2] / nd->c;
+        float s0 = q0 * q0, s1 = q1 * q1, s2 = q2 * q2;
+        return sqrtf((s0 + s1) + s2) - 1.0f;
+    }
+    case OG_SDF_CYLINDER: {
+        float s0 = p[0] * p[0], s1 = p[1] * p[1];
+        return fmaxf(sqrtf(s0 + s1) - nd->a, fabsf(p[2]) - nd->b);
+    }
+    default: { /* OG_SDF_CONE */
+        float s0 = p[0] * p[0], s1 = p[1] * p[1];
+        float lean = nd->c * p[2];
+        return fmaxf((sqrtf(s0 + s1) - lean) - nd->a, fabsf(p[2]) - nd->b);
+    }
+    }
+}
+
+float og_sdf_eval(const og_sdf_node *nodes, int count, const float x[3])
+{
+    float st[32];
+    int sp = 0, i;
+    for (i = 0; i < count; i++) {
+        const og_sdf_node *nd = &nodes[i];
+        if (nd->op < OG_SDF_UNION) {
+            st[sp++] = og_sdf_prim(nd, x);
+        } else if (nd->op == OG_SDF_HOLLOW) {
+            st[sp - 1] = fabsf(st[sp - 1]) - nd->a;
+        } else {
+            float b = st[--sp], a = st[--sp], r;
+            if (nd->op == OG_SDF_UNION)
+                r = fminf(a, b);
+            else if (nd->op == OG_SDF_INTERSECT)
+                r = fmaxf(a, b);
+            else if (nd->op == OG_SDF_SUBTRACT)
+                r = fmaxf(a, -b);
+            else { /* OG_SDF_SMOOTH_UNION */
+                float k = nd->a;
+                float h = fmaxf(k - fabsf(a - b), 0.0f) / k;
+                float hh = h * h;
+                float hk = hh * k;
+                r = fminf(a, b) - hk * 0.25f;
+            }
+            st[sp++] = r;
+        }
+    }
+    return st[0];
+}
+
+/* Volume pass: every voxel takes the kind of the last region whose SDF is
+ * negative at its centre (0 = none); tissue = myocardium or fast fibre.
+ * Fibres (FP64): myocardium follows Sec. "Fibre Directions" -- the horizontal
+ * unit vector orthogonal to the position vector p (from the scene origin),
+ * h = (-p_y, p_x, 0) / |p_xy|, rotated by helix_rad about p:
+ * f = cos(a) h + sin(a) (p / |p|) x h (h is orthogonal to p); zero where p is
+ * vertical.  Fast fibre: scale * axis.  Vertex pass: a vertex is 1 (solid)
+ * when every voxel incident to it is tissue, 0 (fluid) when none is, 2
+ * (surface) otherwise; only voxels inside the grid count.  Returns the number
+ * of tissue voxels. */
+int og_sdf_encode(const og_sdf_node *nodes, const og_sdf_region *regions, int n_regions, int nx, int ny, int nz,
+                  float dx, const float origin[3], double helix_rad, unsigned char *label, unsigned char *mask,
+                  double *fib, unsigned char *vclass)
+{
+    long q, n = (long)nx * ny * nz;
+    int count = 0;
+    const double ca = cos(helix_rad), sa = sin(helix_rad);
+    for (q = 0; q < n; q++) {
+        int i = (int)(q % nx), j = (int)((q / nx) % ny), k = (int)(q / ((long)nx * ny)), r;
+        float x[3];
+        float ci[3] = {(float)i + 0.5f, (float)j + 0.5f, (float)k + 0.5f};
+        int c;
+        for (c = 0; c < 3; c++)
+            x[c] = origin[c] + ci[c] * dx;
+        int last = -1;
+        for (r = 0; r < n_regions; r++)
+            if (og_sdf_eval(nodes + regions[r].first, regions[r].count, x) < 0.0f)
+                last = r;
+        int kind = last >= 0 ? regions[last].kind : 0;
+        label[q] = (unsigned char)kind;
+        mask[q] = (kind == OG_REGION_MYOCARDIUM || kind == OG_REGION_FAST) ? 1 : 0;
+        fib[3 * q] = fib[3 * q + 1] = fib[3 * q + 2] = 0.0;
+        if (kind == OG_REGION_MYOCARDIUM) {
+            double px = x[0], py = x[1], pz = x[2];
+            double hl = sqrt(px * px + py * py), pl = sqrt(px * px + py * py + pz * pz);
+            if (hl > 0.0) {
+                double h[3] = {-py / hl, px / hl, 0.0};
+                double u[3] = {px / pl, py / pl, pz / pl};
+                double w[3] = {u[1] * h[2] - u[2] * h[1], u[2] * h[0] - u[0] * h[2], u[0] * h[1] - u[1] * h[0]};
+                for (c = 0; c < 3; c++)
+                    fib[3 * q + c] = ca * h[c] + sa * w[c];
+            }
+        } else if (kind == OG_REGION_FAST) {
+            for (c = 0; c < 3; c++)
+                fib[3 * q + c] = (double)regions[last].scale * (double)regions[last].axis[c];
+        }
+        count += mask[q];
+    }
+    if (vclass) {
+        int I, J, K;
+        for (K = 0; K <= nz; K++)
+            for (J = 0; J <= ny; J++)
+                for (I = 0; I <= nx; I++) {
+                    int in = 0, tis = 0, s, t, u;
+                    for (u = 0; u < 2; u++)
+                        for (t = 0; t < 2; t++)
+                            for (s = 0; s < 2; s++) {
+                                int i = I - 1 + s, j = J - 1 + t, k = K - 1 + u;
+                                if (i < 0 || j < 0 || k < 0 || i >= nx || j >= ny || k >= nz)
+                                    continue;
+                                in++;
+                                tis += mask[(long)i + (long)nx * ((long)j + (long)ny * k)];
+                            }
+                    vclass[(long)I + (long)(nx + 1) * ((long)J + (long)(ny + 1) * K)] =
+                        (unsigned char)(tis == 0 ? 0 : (tis == in ? 1 : 2));
+                }
+    }
+    return count;
+}
+
 int og_num_threads(void)
 {
 #ifdef _OPENMP

@@ -69,6 +69,41 @@ long og_total_iters(const og_sim *s);
 long og_ie_total_iters(const og_sim *s);
 int og_num_threads(void);
 
+/* Geometry by signed distance functions (Sec. "Geometry"): a postfix program
+ * of nodes.  Primitives push their value at the point, operators pop their
+ * operands and push the result. */
+#define OG_SDF_CUBOID 0          /* a, b, c: half-extents */
+#define OG_SDF_ELLIPSOID 1       /* a, b, c: semi-axes */
+#define OG_SDF_CYLINDER 2        /* a: radius, b: half-height (axis z) */
+#define OG_SDF_CONE 3            /* a: radius at z = 0, b: half-height, c: radius slope (axis z) */
+#define OG_SDF_UNION 10
+#define OG_SDF_INTERSECT 11
+#define OG_SDF_SUBTRACT 12       /* first minus second */
+#define OG_SDF_HOLLOW 13         /* |s| - a */
+#define OG_SDF_SMOOTH_UNION 14   /* smoothed minimum with width a */
+
+typedef struct {
+    int op;
+    float a, b, c;
+    float centre[3];             /* mm, scene frame */
+    float rot[9];                /* row-major: local = rot (x - centre) */
+} og_sdf_node;
+
+#define OG_REGION_MYOCARDIUM 1   /* tissue, helical fibres */
+#define OG_REGION_FAST 2         /* tissue, fibre = scale * axis */
+#define OG_REGION_INSULATOR 3    /* not tissue (zero conductivity) */
+
+typedef struct {
+    int first, count, kind;      /* its program: nodes [first, first + count) */
+    float axis[3];
+    float scale;
+} og_sdf_region;
+
+float og_sdf_eval(const og_sdf_node *nodes, int count, const float x[3]);
+int og_sdf_encode(const og_sdf_node *nodes, const og_sdf_region *regions, int n_regions, int nx, int ny, int nz,
+                  float dx, const float origin[3], double helix_rad, unsigned char *label, unsigned char *mask,
+                  double *fib, unsigned char *vclass);
+
 #ifdef __cplusplus
 }
 #endif

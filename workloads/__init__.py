@@ -413,3 +413,147 @@ def with_torso(case: Case, sig_o: float = 1.0, pad: int = 0, fill: Optional[floa
              for st in case.stimuli]
     return Case(case.name + f"_torso{pad}", nx, ny, nz, case.dx, mask, fib, p, stims, model=case.model,
                 precision=case.precision, steps=case.steps, torso=torso, electrodes=electrodes)
+
+
+# ---------------------------------------------------------------------------
+# Signed-distance scenes (inputs of the geometry encoder; the SDF arithmetic
+# itself lives in the encoder and in the oracle, not here)
+# ---------------------------------------------------------------------------
+SDF_CUBOID, SDF_ELLIPSOID, SDF_CYLINDER, SDF_CONE = 0, 1, 2, 3
+SDF_UNION, SDF_INTERSECT, SDF_SUBTRACT, SDF_HOLLOW, SDF_SMOOTH_UNION = 10, 11, 12, 13, 14
+REGION_MYOCARDIUM, REGION_FAST, REGION_INSULATOR = 1, 2, 3
+IDENTITY9 = (1.0, 0.0, 0.0, 0.0, 1.0, 0.0, 0.0, 0.0, 1.0)
+
+
+@dataclasses.dataclass
+class SdfNode:
+    op: int
+    a: float = 0.0
+    b: float = 0.0
+    c: float = 0.0
+    centre: Tuple[float, float, float] = (0.0, 0.0, 0.0)
+    rot: Tuple[float, ...] = IDENTITY9
+
+
+@dataclasses.dataclass
+class SdfRegion:
+    first: int
+    count: int
+    kind: int
+    axis: Tuple[float, float, float] = (0.0, 0.0, 1.0)
+    scale: float = 1.0
+
+
+@dataclasses.dataclass
+class SdfScene:
+    nodes: List[SdfNode]
+    regions: List[SdfRegion]
+    nx: int
+    ny: int
+    nz: int
+    dx: float
+    origin: Tuple[float, float, float]
+    helix_rad: float = 0.4 * math.pi
+
+
+def rotation(axis: Tuple[float, float, float], angle: float) -> Tuple[float, ...]:
+    """Row-major matrix of the rotation by -angle about axis (it maps scene
+    coordinates into a frame turned by +angle)."""
+    a = np.asarray(axis, np.float64)
+    a = a / np.linalg.norm(a)
+    K = np.array([[0, -a[2], a[1]], [a[2], 0, -a[0]], [-a[1], a[0], 0]])
+    R = np.eye(3) + math.sin(angle) * K + (1 - math.cos(angle)) * K @ K
+    return tuple(float(v) for v in R.T.reshape(-1))
+
+
+class _Prog:
+    """Builds postfix programs region by region."""
+
+    def __init__(self):
+        self.nodes: List[SdfNode] = []
+        self.regions: List[SdfRegion] = []
+        self._start = 0
+
+    def push(self, op, a=0.0, b=0.0, c=0.0, centre=(0.0, 0.0, 0.0), rot=IDENTITY9):
+        self.nodes.append(SdfNode(op, a, b, c, tuple(centre), tuple(rot)))
+        return self
+
+    def region(self, kind, axis=(0.0, 0.0, 1.0), scale=1.0):
+        self.regions.append(SdfRegion(self._start, len(self.nodes) - self._start, kind, tuple(axis), scale))
+        self._start = len(self.nodes)
+        return self
+
+
+def schematic_heart(n: int = 128, size_mm: float = 128.0, wall: float = 0.12, fast_gain: float = 2.0,
+                    sig_L: float = 0.20, sig_T: float = 0.05) -> SdfScene:
+    """The thesis' schematic whole heart (Sec. "Myocardium", "Fibre
+    Directions"), sizes read off its figures (the text gives none), in mm
+    with the origin at the centre of an n^3 box of side size_mm:
+    - myocardium: the hollow union of two half-spheres above the origin
+      (atria) and two half-ellipsoids below it (ventricles), plus the
+      intra-ventricular septum, a vertical elliptic disc; the shells are
+      `wall` thick in the primitives' normalised units;
+    - the horizontal septum, an elliptic disc at the origin, is an insulator
+      (zero conductivity), so is each hollow elliptic cone of the mitral and
+      tricuspid valves that pierce it, and each hollow vertical vessel on top;
+    - a vertical fast fibre (Purkinje) through the centre with `fast_gain`
+      times the longitudinal conductivity, the only path from atria to
+      ventricles."""
+    P = _Prog()
+    lv, rv = (14.0, 0.0, 0.0), (-16.0, 4.0, 0.0)
+    up = (0.0, 0.0, 40.0)       # half-space z > 0: a cuboid above the origin
+    down = (0.0, 0.0, -60.0)
+    # myocardium: ((LA u RA) n up) u ((LV u RV) n down), hollowed, plus the septum disc
+    P.push(SDF_ELLIPSOID, 26.0, 26.0, 26.0, (lv[0], lv[1], 0.0)).push(SDF_ELLIPSOID, 22.0, 22.0, 22.0, (rv[0], rv[1], 0.0))
+    P.push(SDF_UNION).push(SDF_CUBOID, 60.0, 60.0, 40.0, up).push(SDF_INTERSECT)
+    P.push(SDF_ELLIPSOID, 26.0, 26.0, 52.0, (lv[0], lv[1], 0.0)).push(SDF_ELLIPSOID, 22.0, 24.0, 46.0, (rv[0], rv[1], 0.0))
+    P.push(SDF_UNION).push(SDF_CUBOID, 60.0, 60.0, 60.0, down).push(SDF_INTERSECT)
+    P.push(SDF_UNION).push(SDF_HOLLOW, wall)
+    P.push(SDF_ELLIPSOID, 3.0, 20.0, 40.0, (-1.0, 2.0, -20.0)).push(SDF_UNION)
+    P.region(REGION_MYOCARDIUM)
+    # horizontal septum: a thin elliptic disc across the whole heart
+    P.push(SDF_ELLIPSOID, 48.0, 36.0, 2.0, (0.0, 2.0, 0.0)).region(REGION_INSULATOR)
+    # valves: hollow elliptic cones through the septum; vessels: hollow cylinders above
+    P.push(SDF_CONE, 7.0, 6.0, -0.3, (lv[0], lv[1] + 6.0, 0.0)).push(SDF_HOLLOW, 1.0)
+    P.push(SDF_CONE, 6.0, 6.0, -0.3, (rv[0], rv[1] + 6.0, 0.0)).push(SDF_HOLLOW, 1.0).push(SDF_UNION)
+    P.region(REGION_INSULATOR)
+    P.push(SDF_CYLINDER, 6.0, 12.0, 0.0, (lv[0] - 6.0, 0.0, 40.0)).push(SDF_HOLLOW, 1.5)
+    P.push(SDF_CYLINDER, 5.0, 12.0, 0.0, (rv[0] + 4.0, rv[1], 38.0)).push(SDF_HOLLOW, 1.5).push(SDF_UNION)
+    P.region(REGION_INSULATOR)
+    # fast fibre: vertical cylinder from the atria to the apex region
+    scale = math.sqrt((fast_gain * sig_L - sig_T) / (sig_L - sig_T))
+    P.push(SDF_CYLINDER, 1.6, 30.0, 0.0, (0.0, 2.0, -6.0)).region(REGION_FAST, (0.0, 0.0, 1.0), scale)
+    dx = size_mm / n
+    return SdfScene(P.nodes, P.regions, n, n, n, dx, (-size_mm / 2, -size_mm / 2, -size_mm / 2))
+
+
+def random_scene(seed: int, n: int = 24, size_mm: float = 24.0) -> SdfScene:
+    """A random scene for tests: every primitive and operator, rotations,
+    three regions of each kind in turn."""
+    rng = np.random.default_rng(seed)
+    P = _Prog()
+
+    def prim():
+        op = int(rng.integers(0, 4))
+        c = tuple(float(v) for v in rng.uniform(-size_mm / 4, size_mm / 4, 3))
+        rot = rotation(tuple(rng.standard_normal(3)), float(rng.uniform(0, math.pi)))
+        if op in (SDF_CUBOID, SDF_ELLIPSOID):
+            a, b, cc = (float(v) for v in rng.uniform(2.0, size_mm / 3, 3))
+        elif op == SDF_CYLINDER:
+            a, b, cc = float(rng.uniform(1.5, size_mm / 4)), float(rng.uniform(2.0, size_mm / 3)), 0.0
+        else:
+            a, b, cc = float(rng.uniform(1.5, size_mm / 4)), float(rng.uniform(2.0, size_mm / 3)), float(rng.uniform(-0.5, 0.5))
+        P.push(op, a, b, cc, c, rot)
+
+    for kind in (REGION_MYOCARDIUM, REGION_INSULATOR, REGION_FAST):
+        prim()
+        for _ in range(int(rng.integers(1, 4))):
+            prim()
+            op = int(rng.choice([SDF_UNION, SDF_INTERSECT, SDF_SUBTRACT, SDF_SMOOTH_UNION]))
+            P.push(op, float(rng.uniform(0.5, 3.0)) if op == SDF_SMOOTH_UNION else 0.0)
+        if rng.random() < 0.5:
+            P.push(SDF_HOLLOW, float(rng.uniform(0.1, 2.0)))
+        ax = rng.standard_normal(3)
+        P.region(kind, tuple(float(v) for v in ax / np.linalg.norm(ax)), float(rng.uniform(1.0, 1.6)))
+    dx = size_mm / n
+    return SdfScene(P.nodes, P.regions, n, n + 3, n - 2, dx, (-size_mm / 2, -size_mm / 2 - 1.0, -size_mm / 2 + 1.0))
