@@ -16,6 +16,7 @@ data-path collective), value = all ranks' voxel-steps / max rank time.
 from __future__ import annotations
 
 import argparse
+import ctypes
 import hashlib
 import json
 import os
@@ -44,8 +45,9 @@ def _args():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["config2", "config0", "config1", "config3", "config4", "slab", "ecg"],
-                    default="config2")
+    ap.add_argument("--workload", choices=["config2", "config0", "config1", "config3", "config4", "slab", "ecg",
+                                           "sdf"], default="config2")
+    ap.add_argument("--sdf-n", type=int, default=512, help="sdf: voxels per side of the schematic heart's box")
     ap.add_argument("--model", choices=["mono", "bi"], default="mono", help="slab: model")
     ap.add_argument("--slab-n", type=int, default=512, help="slab: voxels per side")
     ap.add_argument("--solver", choices=["jacobi", "chebyshev"], default=None,
@@ -550,6 +552,116 @@ def _pct(x, q):
     return float(np.percentile(np.asarray(x, float), q)) if len(x) else None
 
 
+# FP32 operations per node of a scene program, counted from the formulas (a
+# division or square root counts as one): translate 3, rotate 15, then the
+# primitive; operators as written.
+SDF_PRIM_OPS = {0: 18 + 11, 1: 18 + 10, 2: 18 + 8, 3: 18 + 10}
+SDF_OP_OPS = {10: 1, 11: 1, 12: 2, 13: 2, 14: 7}
+SDF_VOXEL_OPS = 9 + 30   # centre coordinates; the fibre rule (upper bound)
+
+
+def _sdf_ops_per_voxel(scene):
+    return SDF_VOXEL_OPS + sum(SDF_PRIM_OPS.get(nd.op, SDF_OP_OPS.get(nd.op, 0)) for nd in scene.nodes)
+
+
+def run_sdf(a):
+    """NEXT-4: the geometry encoder on the schematic heart.  value = voxels
+    encoded per second by the two device passes (outputs resident in HBM);
+    e2e = the same through ep_sdf_encode with host outputs."""
+    import torch
+    import paper_2302_12519_gb300 as ep
+    import workloads as W
+    from paper_2302_12519_gb300 import build as epbuild
+    world, rank, local = _dist()
+    torch.cuda.set_device(local)
+    epbuild.build()
+    L = ep.load()
+    sc = W.schematic_heart(a.sdf_n)
+    n = sc.nx * sc.ny * sc.nz
+    nv = (sc.nx + 1) * (sc.ny + 1) * (sc.nz + 1)
+    dev = torch.device("cuda", local)
+    d_nodes = torch.empty(len(sc.nodes) * ctypes.sizeof(ep.SdfNode), dtype=torch.uint8, device=dev)
+    d_reg = torch.empty(len(sc.regions) * ctypes.sizeof(ep.SdfRegion), dtype=torch.uint8, device=dev)
+    d_label = torch.empty(n, dtype=torch.uint8, device=dev)
+    d_mask = torch.empty(n, dtype=torch.uint8, device=dev)
+    d_fib = torch.empty(3 * n, dtype=torch.float32, device=dev)
+    d_vert = torch.empty(nv, dtype=torch.uint8, device=dev)
+    d_cnt = torch.zeros(1, dtype=torch.int64, device=dev)
+    N = (ep.SdfNode * len(sc.nodes))()
+    for i, nd in enumerate(sc.nodes):
+        N[i].op, N[i].a, N[i].b, N[i].c = nd.op, nd.a, nd.b, nd.c
+        N[i].centre[:] = list(nd.centre)
+        N[i].rot[:] = list(nd.rot)
+    R = (ep.SdfRegion * len(sc.regions))()
+    for i, rg in enumerate(sc.regions):
+        R[i].first, R[i].count, R[i].kind, R[i].scale = rg.first, rg.count, rg.kind, rg.scale
+        R[i].axis[:] = list(rg.axis)
+    org = (ctypes.c_float * 3)(*sc.origin)
+    stream = torch.cuda.Stream()
+
+    def once():
+        st = L.ep_sdf_encode_device(N, len(sc.nodes), R, len(sc.regions), sc.nx, sc.ny, sc.nz, sc.dx,
+                                    ctypes.byref(org), sc.helix_rad, d_nodes.data_ptr(), d_reg.data_ptr(),
+                                    d_label.data_ptr(), d_mask.data_ptr(), d_fib.data_ptr(), d_vert.data_ptr(),
+                                    d_cnt.data_ptr(), stream.cuda_stream)
+        if st != 0:
+            raise RuntimeError(L.ep_sdf_last_error().decode())
+
+    for _ in range(a.warmup):
+        once()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    ms = []
+    for _ in range(a.steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        once()
+        e1.record(stream)
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    clk = clocks.stop()
+    total_s = sum(ms) / 1e3
+    n_tissue = int(d_cnt.item())
+    ops = _sdf_ops_per_voxel(sc)
+    peaks = _peaks()
+    mhz = float(peaks["sm_max_mhz"]) if peaks else 2070.0
+    peak = 152 * 128 * mhz * 1e6 / 1e9   # FP32 lanes x clock, one operation per lane per cycle (GOP/s)
+    achieved = ops * n * a.steps / total_s / 1e9
+    e2e = None
+    if not a.no_e2e:
+        t0 = time.perf_counter()
+        for _ in range(a.steps):
+            ep.sdf_encode(sc.nodes, sc.regions, sc.nx, sc.ny, sc.nz, sc.dx, sc.origin, sc.helix_rad)
+        e2e_s = time.perf_counter() - t0
+        e2e = {"value": n * a.steps / e2e_s, "unit": "voxels/s", "h2d_bytes_per_step":
+               len(sc.nodes) * ctypes.sizeof(ep.SdfNode) + len(sc.regions) * ctypes.sizeof(ep.SdfRegion),
+               "d2h_bytes_per_step": 2 * n + 12 * n + nv + 8}
+    cpu = None
+    if not a.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        m = 128   # bounded sample: the same scene at 128^3
+        small = W.schematic_heart(m)
+        t0 = time.perf_counter()
+        oracle.sdf_encode(small.nodes, small.regions, m, m, m, small.dx, small.origin, small.helix_rad)
+        cs = time.perf_counter() - t0
+        cpu = {"value": m ** 3 / cs, "unit": "voxels/s", "cores": 1, "kind": "oracle",
+               "sample": f"the oracle's two passes over the same scene at {m}^3 ({cs:.2f} s, one thread)"}
+    line = {"metric": "voxels encoded/sec", "value": n * a.steps / total_s, "unit": "voxels/s", "n_gpus": 1,
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1e3 * total_s / a.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"sdf: the schematic heart (NEXT-4) encoded on a {a.sdf_n}^3 grid, "
+                                   f"{len(sc.nodes)} nodes in {len(sc.regions)} regions; volume + vertex passes",
+                       "tissue_voxels": n_tissue, "l2": "outputs larger than L2 (1.9 GB written per step at 512^3)"},
+            "roofline": {"bound": "alu", "kernel": "k_sdf_volume + k_sdf_vertex", "achieved": achieved,
+                         "peak": peak, "unit": "GOP/s", "frac": achieved / peak, "traffic": None,
+                         "fp32_ops_per_voxel": ops,
+                         "peak_source": "152 SMs x 128 FP32 lanes x max SM clock (one operation per lane per cycle)"},
+            "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": 2 * a.steps, "clocks": clk}
+    print(json.dumps(line), flush=True)
+
+
 def run_served(a):
     """config4: Poisson arrivals of bidomain requests of uneven size, served
     with continuous batching under a device-memory budget (ep_server), against
@@ -650,6 +762,13 @@ def main():
         return
     if a.workload == "config4" and a.impl == "ours":
         run_served(a)
+        return
+    if a.workload == "sdf":
+        if a.impl == "ours":
+            run_sdf(a)
+        else:
+            print(json.dumps({"impl": "reference", "unavailable": "the sdf line is a set-up kernel; its oracle "
+                                                                  "timing is the cpu_baseline of the ours line"}))
         return
     if a.impl == "reference":
         run_reference(a)

@@ -144,9 +144,14 @@ ep_status ep_create(const ep_grid_desc *desc, ep_sim **out);
 /* Tissue mask, n = nx*ny*nz bytes, non-zero = myocardium.  Required. */
 ep_status ep_set_mask(ep_sim *s, const uint8_t *mask, size_t n);
 
-/* Fibre field, 3n floats (fx, fy, fz) per voxel, unit length or zero (zero
- * gives Sigma = sigma_T I, Sec. "Fibre Directions").  Stored as IEEE half
- * precision.  Optional (default zero fibres). */
+/* Fibre field, 3n floats (fx, fy, fz) per voxel: unit length, or zero
+ * (Sigma = sigma_T I, Sec. "Fibre Directions"), or longer than 1 for a
+ * fast-conducting fibre (Sigma = sigma_T I + (sigma_L - sigma_T) f f^T,
+ * Eq. sigma1, so |f|^2 = (g sigma_L - sigma_T) / (sigma_L - sigma_T) gives
+ * the longitudinal conductivity g sigma_L; such voxels may need a smaller
+ * jacobi_omega than the default).  Components finite and at most 4 in
+ * magnitude (EP_EINVAL).  Stored as IEEE half precision.  Optional (default
+ * zero fibres). */
 ep_status ep_set_fibres(ep_sim *s, const float *f, size_t n3);
 
 /* Model parameters.  Required.  Values are validated (EP_EINVAL). */

@@ -36,7 +36,7 @@ EXPORTS = ["ep_create", "ep_set_mask", "ep_set_fibres", "ep_set_params", "ep_add
            "ep_batch_destroy", "ep_footprint", "ep_batch_set_schedule", "ep_server_create", "ep_server_submit",
            "ep_server_cancel", "ep_server_collect", "ep_server_drain", "ep_server_get_stats", "ep_server_now",
            "ep_server_last_error", "ep_server_destroy", "ep_set_torso", "ep_set_ecg", "ep_read_ecg",
-           "ep_apply_elliptic"]
+           "ep_apply_elliptic", "ep_sdf_encode", "ep_sdf_encode_device", "ep_sdf_last_error"]
 
 _ALLOC_T = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
 _FREE_T = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
@@ -67,6 +67,16 @@ class Info(ctypes.Structure):
                 ("n_segments", ctypes.c_int), ("omega", ctypes.c_double), ("device_bytes", ctypes.c_size_t),
                 ("cheb_lmin", ctypes.c_double), ("cheb_lmax", ctypes.c_double),
                 ("n_domain", ctypes.c_longlong), ("n_segments_elliptic", ctypes.c_int)]
+
+
+class SdfNode(ctypes.Structure):
+    _fields_ = [("op", ctypes.c_int), ("a", ctypes.c_float), ("b", ctypes.c_float), ("c", ctypes.c_float),
+                ("centre", ctypes.c_float * 3), ("rot", ctypes.c_float * 9)]
+
+
+class SdfRegion(ctypes.Structure):
+    _fields_ = [("first", ctypes.c_int), ("count", ctypes.c_int), ("kind", ctypes.c_int),
+                ("axis", ctypes.c_float * 3), ("scale", ctypes.c_float)]
 
 
 class EcgSample(ctypes.Structure):
@@ -146,6 +156,13 @@ def load(path: str = LIB_PATH):
         "ep_set_ecg": ([vp, ctypes.POINTER(ctypes.c_int * 9), ip], ip),
         "ep_read_ecg": ([vp, vp, ip, ctypes.POINTER(ip)], ip),
         "ep_apply_elliptic": ([vp, vp, vp, sz], ip),
+        "ep_sdf_encode": ([ctypes.POINTER(SdfNode), ip, ctypes.POINTER(SdfRegion), ip, ip, ip, ip, ctypes.c_float,
+                           ctypes.POINTER(ctypes.c_float * 3), dp, vp, vp, vp, vp, ctypes.POINTER(ctypes.c_longlong),
+                           vp], ip),
+        "ep_sdf_encode_device": ([ctypes.POINTER(SdfNode), ip, ctypes.POINTER(SdfRegion), ip, ip, ip, ip,
+                                  ctypes.c_float, ctypes.POINTER(ctypes.c_float * 3), dp, vp, vp, vp, vp, vp, vp,
+                                  vp, vp], ip),
+        "ep_sdf_last_error": ([], ctypes.c_char_p),
         "ep_profile_enable": ([vp, ip], ip),
         "ep_get_profile": ([vp, ctypes.POINTER(Profile)], ip),
         "ep_last_error": ([vp], ctypes.c_char_p),
@@ -519,6 +536,38 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+def sdf_encode(nodes, regions, nx: int, ny: int, nz: int, dx_mm: float, origin_mm, helix_rad: float,
+               want_vertices: bool = True, stream: Optional[int] = None):
+    """ep_sdf_encode.  nodes: sequence of objects with op, a, b, c, centre (3),
+    rot (9); regions: objects with first, count, kind, axis (3), scale.
+    Returns a dict of label, mask (uint8, n), fibres (float32, 3n), vertices
+    (uint8, (nx+1)(ny+1)(nz+1)) and n_tissue."""
+    L = load()
+    N = (SdfNode * len(nodes))()
+    for i, nd in enumerate(nodes):
+        N[i].op, N[i].a, N[i].b, N[i].c = int(nd.op), float(nd.a), float(nd.b), float(nd.c)
+        N[i].centre[:] = [float(v) for v in nd.centre]
+        N[i].rot[:] = [float(v) for v in nd.rot]
+    R = (SdfRegion * len(regions))()
+    for i, rg in enumerate(regions):
+        R[i].first, R[i].count, R[i].kind = int(rg.first), int(rg.count), int(rg.kind)
+        R[i].axis[:] = [float(v) for v in rg.axis]
+        R[i].scale = float(rg.scale)
+    n = nx * ny * nz
+    label = np.empty(n, np.uint8)
+    mask = np.empty(n, np.uint8)
+    fib = np.empty(3 * n, np.float32)
+    vert = np.empty((nx + 1) * (ny + 1) * (nz + 1), np.uint8) if want_vertices else None
+    cnt = ctypes.c_longlong(0)
+    org = (ctypes.c_float * 3)(*[float(v) for v in origin_mm])
+    st = L.ep_sdf_encode(N, len(nodes), R, len(regions), nx, ny, nz, float(dx_mm), ctypes.byref(org),
+                         float(helix_rad), label.ctypes.data, mask.ctypes.data, fib.ctypes.data,
+                         None if vert is None else vert.ctypes.data, ctypes.byref(cnt), stream)
+    if st != EP_OK:
+        raise EPError(st, f"ep_sdf_encode: {L.ep_sdf_last_error().decode()}")
+    return {"label": label, "mask": mask, "fibres": fib, "vertices": vert, "n_tissue": cnt.value}
 
 
 def _is_bi(case, model: Optional[int]) -> bool:

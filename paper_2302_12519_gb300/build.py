@@ -12,9 +12,9 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libep.so")
-SOURCES = [os.path.join(CSRC, "ep_api.cu")]
+SOURCES = [os.path.join(CSRC, "ep_api.cu"), os.path.join(CSRC, "ep_sdf.cu")]
 HEADERS = [os.path.join(CSRC, h) for h in ("ep_kernels.cuh", "ep_common.cuh", "ep_stencil.cuh", "ep_aux.cuh")]
-DEPS = SOURCES + HEADERS + [os.path.join(ROOT, "include", "ep.h")]
+DEPS = SOURCES + HEADERS + [os.path.join(ROOT, "include", h) for h in ("ep.h", "ep_sdf.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -39,7 +39,7 @@ def build(force: bool = False, ptxas_verbose: bool = False, defines=None, out: s
     if out is None and not defines and not force and not needs_build():
         return LIB
     tmp = target + f".tmp{os.getpid()}"
-    cmd = [nvcc(), *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-shared",
+    cmd = [nvcc(), *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-shared", "--threads", "2",
            "-I", os.path.join(ROOT, "include"), "-o", tmp, *SOURCES]
     for k, v in (defines or {}).items():
         cmd.insert(1, f"-D{k}={v}")

@@ -1097,7 +1097,7 @@ ep_status ep_set_fibres(ep_sim *s, const float *f, size_t n3)
     if (s->ready) return fail(s, EP_ESTATE, "fibres can only be set before the first step");
     if (!f || (long long)n3 != 3 * s->n) return fail(s, EP_EINVAL, "fibres must hold 3*nx*ny*nz floats");
     for (size_t i = 0; i < n3; ++i)
-        if (!std::isfinite(f[i]) || std::fabs(f[i]) > 1.0001f) return fail(s, EP_EINVAL, "fibre components must be finite and unit or zero");
+        if (!std::isfinite(f[i]) || std::fabs(f[i]) > 4.0f) return fail(s, EP_EINVAL, "fibre components must be finite and at most 4 in magnitude");
     s->fib.assign(f, f + n3);
     return EP_OK;
 }

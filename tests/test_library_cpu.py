@@ -1,5 +1,5 @@
 """Host-side checks of the C ABI that need no GPU: the library builds, loads,
-exports every function include/ep.h declares, and validates arguments
+exports every function include/*.h declares, and validates arguments
 before touching the device."""
 import ctypes
 import os
@@ -21,7 +21,8 @@ def lib():
 
 
 def _declared():
-    txt = open(os.path.join(ROOT, "include", "ep.h")).read()
+    txt = "".join(open(os.path.join(ROOT, "include", h)).read()
+                  for h in sorted(os.listdir(os.path.join(ROOT, "include"))) if h.endswith(".h"))
     txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
     names = set(re.findall(r"\b(ep_[a-z_]+)\s*\(", txt))
     return sorted(names)
@@ -59,7 +60,10 @@ def test_setters_validate_before_any_device_work(lib):
         s.set_mask(np.ones(n - 1, np.uint8))
     assert e.value.status == ep.EP_EINVAL
     with pytest.raises(ep.EPError):
-        s.set_fibres(np.full(3 * n, 2.0, np.float32))
+        s.set_fibres(np.full(3 * n, 4.5, np.float32))
+    with pytest.raises(ep.EPError):
+        s.set_fibres(np.full(3 * n, np.nan, np.float32))
+    s.set_fibres(np.full(3 * n, 1.5, np.float32))   # a fast-conducting fibre is longer than 1
     p = W.Params()
     p.sig_iT = -1.0
     with pytest.raises(ep.EPError) as e:
@@ -175,6 +179,33 @@ def test_torso_and_ecg_are_validated_and_planned_on_the_host(lib):
     assert e.value.status == ep.EP_EINVAL
     s.close()
     plain.close()
+
+
+def test_sdf_encoder_validates_the_program_without_a_device(lib):
+    """ep_sdf_encode checks programs, regions and the grid before it touches
+    the device."""
+    import workloads as W
+    E = W.SdfNode(W.SDF_ELLIPSOID, 2.0, 2.0, 2.0)
+    bad = [
+        ([W.SdfNode(W.SDF_UNION)], [W.SdfRegion(0, 1, W.REGION_MYOCARDIUM)]),            # no operands
+        ([E, E], [W.SdfRegion(0, 2, W.REGION_MYOCARDIUM)]),                                # two values left
+        ([W.SdfNode(99)], [W.SdfRegion(0, 1, W.REGION_MYOCARDIUM)]),                      # unknown op
+        ([W.SdfNode(W.SDF_ELLIPSOID, 0.0, 1.0, 1.0)], [W.SdfRegion(0, 1, W.REGION_MYOCARDIUM)]),   # zero size
+        ([E], [W.SdfRegion(0, 2, W.REGION_MYOCARDIUM)]),                                   # range past the nodes
+        ([E], [W.SdfRegion(0, 1, 7)]),                                                     # unknown kind
+        ([E, E, W.SdfNode(W.SDF_SMOOTH_UNION, 0.0)], [W.SdfRegion(0, 3, W.REGION_MYOCARDIUM)]),   # zero width
+    ]
+    for nodes, regions in bad:
+        with pytest.raises(ep.EPError) as e:
+            ep.sdf_encode(nodes, regions, 4, 4, 4, 1.0, (0.0, 0.0, 0.0), 0.0)
+        assert e.value.status == ep.EP_EINVAL
+    deep = [E] * 33 + [W.SdfNode(W.SDF_UNION)] * 32
+    with pytest.raises(ep.EPError) as e:
+        ep.sdf_encode(deep, [W.SdfRegion(0, len(deep), W.REGION_MYOCARDIUM)], 4, 4, 4, 1.0, (0, 0, 0), 0.0)
+    assert e.value.status == ep.EP_EINVAL
+    with pytest.raises(ep.EPError) as e:
+        ep.sdf_encode([E], [W.SdfRegion(0, 1, W.REGION_MYOCARDIUM)], 0, 4, 4, 1.0, (0, 0, 0), 0.0)
+    assert e.value.status == ep.EP_EINVAL
 
 
 def test_server_needs_a_device(lib):
