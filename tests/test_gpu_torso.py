@@ -180,3 +180,45 @@ def test_chebyshev_interval_with_torso_brackets_the_spectrum():
     info = ep.sim_from_case(c).info()
     assert hi * 0.999 <= info.cheb_lmax <= hi * 1.1
     assert 0.5 * lo <= info.cheb_lmin <= 1.0 * lo
+
+
+def test_chebyshev_fp64_with_torso_matches_oracle():
+    """FP64 Chebyshev semi-iteration over tissue + torso on an interval both
+    sides share: the same iterates to the same stop rule."""
+    c = _torso_case(66, (11, 9, 8), fill=0.9, rel_tol=1e-11, check_every=5)
+    c.params.max_iter = 200000
+    c.params.solver = 1
+    s0 = ep.sim_from_case(c, precision=ep.EP_FP64)
+    info = s0.info()
+    s0.close()
+    c.params.cheb_lmin, c.params.cheb_lmax = info.cheb_lmin, info.cheb_lmax
+    s = ep.sim_from_case(c, precision=ep.EP_FP64)
+    o = oracle.Sim(c)
+    v, w, ve = W.random_state(66, c)
+    s.set_state(v, w, ve, 0)
+    o.set_state(v, w, ve, 0)
+    for _ in range(2):
+        stats = s.step(1)
+        assert o.step() == 0 and stats.converged == 1
+    st = o.state()
+    np.testing.assert_allclose(s.read(ep.EP_V), st["v"], rtol=0, atol=1e-10)
+    np.testing.assert_allclose(s.read(ep.EP_VE), st["ve"], rtol=0, atol=1e-7)
+
+
+def test_noalloc_step_with_torso_and_ecg_equals_step():
+    """ep_step_noalloc on a torso handle (its own sweep items, the ECG record)
+    gives the states and samples of ep_step."""
+    c = _heart_in_box(n=16, pad=2, steps=6)
+    a = ep.sim_from_case(c, ecg_capacity=8)
+    b = ep.sim_from_case(c, ecg_capacity=8)
+    a.info()
+    b.info()
+    for _ in range(3):
+        a.step(2, allow_noconv=True)
+        b.step_noalloc(2, allow_noconv=True)
+    np.testing.assert_array_equal(a.read(ep.EP_V), b.read(ep.EP_V))
+    np.testing.assert_array_equal(a.read(ep.EP_VE), b.read(ep.EP_VE))
+    ta, pa, _ = a.read_ecg()
+    tb, pb, _ = b.read_ecg()
+    np.testing.assert_array_equal(ta, tb)
+    np.testing.assert_array_equal(pa, pb)
