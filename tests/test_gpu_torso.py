@@ -222,3 +222,32 @@ def test_noalloc_step_with_torso_and_ecg_equals_step():
     tb, pb, _ = b.read_ecg()
     np.testing.assert_array_equal(ta, tb)
     np.testing.assert_array_equal(pa, pb)
+
+
+def test_ecg_workload_fullsize_operator_and_capped_step():
+    """The bench's ECG workload at full size (256^3, torso over the whole
+    box): the two-term operator against the oracle's, and one step with a
+    capped damped-Jacobi solve whose final residual, recomputed by the oracle
+    in FP64 over tissue + torso, matches the one the GPU reported."""
+    c = W.ecg_case()
+    p = c.params
+    p.max_iter = 4000
+    sL, sT = p.sig_iL + p.sig_eL, p.sig_iT + p.sig_eT
+    ge, gh = oracle.Grid.elliptic_from_case(c), oracle.Grid.from_case(c)
+    dom = ge.domain()
+    s = ep.sim_from_case(c)
+    rng = np.random.default_rng(67)
+    u = rng.standard_normal(c.n) * dom
+    ref = ge.apply_L(sL, sT, u)
+    np.testing.assert_allclose(s.apply_elliptic(u), ref, rtol=0, atol=2e-6 * np.abs(ref).max())
+    v, w, ve = W.random_state(67, c)
+    s.set_state(v, w, ve, 10)
+    stats = s.step(1, allow_noconv=True)
+    assert stats.iters > 0
+    vg, xg = s.read(ep.EP_V), s.read(ep.EP_VE)
+    b = -gh.apply_L(p.sig_iL, p.sig_iT, vg)
+    b[c.mask.reshape(-1) == 0] = 0.0
+    b[dom] -= b[dom].mean()          # one component: the whole box
+    r = b - ge.apply_L(sL, sT, xg)
+    rr = np.linalg.norm(r[dom]) / np.linalg.norm(b[dom])
+    assert abs(rr - stats.rel_res) <= 0.05 * stats.rel_res + 1e-5, (rr, stats.rel_res)
