@@ -874,11 +874,14 @@ ep_status solve_elliptic(ep_sim *s, const Inst<real> &I, int &iters, double &rel
     if (s->prof_on) CK(cudaEventRecord(s->pev[2], st));
     long long queued = 0;
     ep_status rs = EP_OK;
+    const bool cheb = I.solver == 1;   // the sweep instance matches the handle's solver
     if (s->torso.empty()) {
-        rs = run_sweeps<real, M_JAC>(s, I, &s->sweep_graph, &queued);
+        rs = cheb ? run_sweeps<real, M_JAC_CHEB>(s, I, &s->sweep_graph, &queued)
+                  : run_sweeps<real, M_JAC>(s, I, &s->sweep_graph, &queued);
     } else {   // tissue + torso: the domain's items and records
         const Inst<real> Ie = make_elliptic_inst<real>(s);
-        rs = run_sweeps<real, M_JAC_BATH>(s, Ie, &s->sweep_graph, &queued);
+        rs = cheb ? run_sweeps<real, M_JAC_BATH_CHEB>(s, Ie, &s->sweep_graph, &queued)
+                  : run_sweeps<real, M_JAC_BATH>(s, Ie, &s->sweep_graph, &queued);
     }
     if (rs != EP_OK) return rs;
     if (s->prof_on) {
@@ -1576,6 +1579,7 @@ struct ep_batch {
         long long seg0, nseg;     // range of its stencil items in d_seg
         std::vector<int> solo;    // rows swept in their own launches
         long long packed_items;   // items of the other rows (packed sweep launches)
+        bool cheb;                // its members' solver: Chebyshev-accelerated (else damped Jacobi)
     };
     std::vector<Group> groups;
     std::vector<Ctl> last;         // per table row, after the last step
@@ -1639,6 +1643,12 @@ ep_status rebuild_tables(ep_batch *b)
     b->order.clear();
     for (int i = 0; i < b->max_inst; ++i)
         if (b->slot[i]) b->order.push_back(i);
+    // damped-Jacobi members first, then Chebyshev ones: a group holds one solver (its sweep instance)
+    auto is_cheb = [&](int slot) {   // as Inst::solver: the Chebyshev solver with its interval known
+        const ep_sim *m = b->slot[slot];
+        return m->p.solver == EP_SOLVER_CHEBYSHEV && m->cheb_lmax > 0.0;
+    };
+    std::stable_sort(b->order.begin(), b->order.end(), [&](int x, int y) { return !is_cheb(x) && is_cheb(y); });
     b->ninst = (int)b->order.size();
     std::vector<Inst<float>> insts;
     std::vector<BItem> segs, chunks;
@@ -1653,12 +1663,14 @@ ep_status rebuild_tables(ep_batch *b)
     for (int r = 0; r < b->ninst;) {
         int r1 = r;
         size_t bytes = 0;
+        const bool cheb = is_cheb(b->order[r]);
         do {
             bytes += 20 * (size_t)b->slot[b->order[r1]]->n;
             ++r1;
-        } while (r1 < b->ninst && (b->group_bytes == 0 ||
-                                   bytes + 20 * (size_t)b->slot[b->order[r1]]->n <= b->group_bytes));
+        } while (r1 < b->ninst && is_cheb(b->order[r1]) == cheb &&
+                 (b->group_bytes == 0 || bytes + 20 * (size_t)b->slot[b->order[r1]]->n <= b->group_bytes));
         ep_batch::Group g;
+        g.cheb = cheb;
         g.inst0 = r;
         g.inst1 = r1;
         g.seg0 = (long long)segs.size();
@@ -1805,15 +1817,19 @@ ep_status build_batch_graph(ep_batch *b)
                 cudaStream_t a = b->aux[j];
                 CKB(cudaStreamWaitEvent(a, b->ev_fork, 0));
                 const Inst<float> I = make_inst<float>(b->slot[b->order[gr.solo[j]]]);
-                for (int i = 0; i < spc; ++i)
-                    k_stencil<float, M_JAC><<<I.nseg, kThreads, 0, a>>>(I, no_io<float>());
+                for (int i = 0; i < spc; ++i) {
+                    if (gr.cheb) k_stencil<float, M_JAC_CHEB><<<I.nseg, kThreads, 0, a>>>(I, no_io<float>());
+                    else k_stencil<float, M_JAC><<<I.nseg, kThreads, 0, a>>>(I, no_io<float>());
+                }
                 CKB(cudaEventRecord(b->ev_join[j], a));
             }
             // the other members: packed sweeps over the unfinished ones
             if (gr.packed_items > 0)
-                for (int i = 0; i < spc; ++i)
-                    k_stencil_active<float, M_JAC><<<grid_of(gr.packed_items, 1 << 30), kThreads, 0, b->side>>>(
-                        gi_inst, b->d_act, gn);
+                for (int i = 0; i < spc; ++i) {
+                    const int gp = grid_of(gr.packed_items, 1 << 30);
+                    if (gr.cheb) k_stencil_active<float, M_JAC_CHEB><<<gp, kThreads, 0, b->side>>>(gi_inst, b->d_act, gn);
+                    else k_stencil_active<float, M_JAC><<<gp, kThreads, 0, b->side>>>(gi_inst, b->d_act, gn);
+                }
             for (int j = 0; j < nsolo; ++j) CKB(cudaStreamWaitEvent(b->side, b->ev_join[j], 0));
             k_active_list<float><<<1, kActThreads, 0, b->side>>>(gi_inst, gi_packed, gn, b->d_act, b->d_counts,
                                                                  hg[gi]);
@@ -2038,10 +2054,13 @@ ep_status ep_batch_autotune(ep_batch *b, int trial_sweeps)
             double ms_total = 0.0;
             for (const ep_batch::Group &gr : b->groups) {
                 const int gs = grid_of(gr.nseg, 1 << 30);
-                k_stencil_batch<float, M_JAC><<<gs, kThreads, 0, s0>>>(b->d_inst, b->d_seg + gr.seg0);
+                auto sweep = [&]() {
+                    if (gr.cheb) k_stencil_batch<float, M_JAC_CHEB><<<gs, kThreads, 0, s0>>>(b->d_inst, b->d_seg + gr.seg0);
+                    else k_stencil_batch<float, M_JAC><<<gs, kThreads, 0, s0>>>(b->d_inst, b->d_seg + gr.seg0);
+                };
+                sweep();
                 CKB(cudaEventRecord(e0, s0));
-                for (int i = 0; i < trial_sweeps; ++i)
-                    k_stencil_batch<float, M_JAC><<<gs, kThreads, 0, s0>>>(b->d_inst, b->d_seg + gr.seg0);
+                for (int i = 0; i < trial_sweeps; ++i) sweep();
                 CKB(cudaEventRecord(e1, s0));
                 CKB(cudaEventSynchronize(e1));
                 float ms = 0.f;

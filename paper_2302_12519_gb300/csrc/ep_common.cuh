@@ -35,15 +35,19 @@ constexpr int kChunk = 2048;                // tissue voxels per reduction chunk
 // conducting torso (Eq. bidomain1, lines 3-5): the tissue term (pairs of
 // tissue voxels, fibre tensors) plus the torso term (pairs of any two domain
 // voxels, sig_o I per torso voxel of the vertex block).
+// M_JAC_CHEB, M_JAC_BATH_CHEB: the same sweeps accelerated by the Chebyshev
+// semi-iteration (separate instances, so the plain sweeps carry none of it).
 enum Mode { M_APPLY = 0, M_RHS = 1, M_PAR_MONO = 2, M_PAR_BI = 3, M_JAC = 4, M_IE_RHS = 5, M_IE = 6, M_JAC_BATH = 7,
-            M_APPLY_BATH = 8 };
+            M_APPLY_BATH = 8, M_JAC_CHEB = 9, M_JAC_BATH_CHEB = 10 };
 enum Diffusion { DIFF_EXPLICIT = 0, DIFF_IMPLICIT = 1 };
 
 // Modes that run a solve sweep (Jacobi of the elliptic or the implicit parabolic system).
 template <int MODE>
-constexpr bool kJac = MODE == M_JAC || MODE == M_JAC_BATH;
+constexpr bool kCheb = MODE == M_JAC_CHEB || MODE == M_JAC_BATH_CHEB;
 template <int MODE>
-constexpr bool kTwoTerm = MODE == M_JAC_BATH || MODE == M_APPLY_BATH;
+constexpr bool kJac = MODE == M_JAC || MODE == M_JAC_BATH || kCheb<MODE>;
+template <int MODE>
+constexpr bool kTwoTerm = MODE == M_JAC_BATH || MODE == M_APPLY_BATH || MODE == M_JAC_BATH_CHEB;
 template <int MODE>
 constexpr bool kSweep = kJac<MODE> || MODE == M_IE;
 enum Model { MODEL_MONO = 0, MODEL_BI = 1 };

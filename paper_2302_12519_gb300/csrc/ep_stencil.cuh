@@ -136,7 +136,7 @@ __device__ __forceinline__ void load_plane(const Op<real> &o, int k, bool lo_in,
         if (MODE == M_PAR_MONO || MODE == M_PAR_BI || MODE == M_IE_RHS) L.wLo = __ldg(o.w + q);
         if (MODE == M_PAR_BI || MODE == M_IE_RHS) L.veLo = __ldg(o.ve + q);
         if (kJac<MODE>) L.bLo = __ldg(o.b + q);
-        if (kJac<MODE> && o.cheb) L.iLo = o.out[q];   // x_{k-1}: this thread overwrites it one plane later
+        if (kCheb<MODE> && o.cheb) L.iLo = o.out[q];   // x_{k-1}: this thread overwrites it one plane later
     }
     if (kin && hi_in) {
         const int q = qhi + k * plane;
@@ -337,7 +337,7 @@ __device__ __forceinline__ void plane_step(const Inst<real> &I, const Op<real> &
             } else if (kJac<MODE>) {
                 const real r = P.e0 - Lu;
                 const real basic = P.uLo + o.coef * P.e1 * r;
-                if (o.cheb) {   // x_{k+1} = w (basic - x_{k-1}) + x_{k-1}; x_{k-1} came through the ring
+                if (kCheb<MODE> && o.cheb) {   // x_{k+1} = w (basic - x_{k-1}) + x_{k-1}; x_{k-1} came through the ring
                     const real prev = P.e2;
                     o.out[q] = o.cheb_w * (basic - prev) + prev;
                 } else {
@@ -440,12 +440,12 @@ __device__ __forceinline__ void ring_issue(const Op<real> &o, Ring<real, MODE> &
         cp_async_n<sizeof(real)>(&R.x[slot][0][t], (MODE == M_PAR_MONO ? o.w : o.b) + q);
         if (MODE == M_IE) cp_async_n<sizeof(real)>(&R.x[slot][1][t], o.inv + q);
         // x_{k-1} sits where this thread will write x_{k+1} of this voxel, one plane later
-        if (kJac<MODE> && o.cheb) cp_async_n<sizeof(real)>(&R.x[slot][1][t], o.out + q);
+        if (kCheb<MODE> && o.cheb) cp_async_n<sizeof(real)>(&R.x[slot][1][t], o.out + q);
     } else {
         R.rec[slot][0][t] = make_uint2(0u, (unsigned)kNonTissue << 16);
         R.u[slot][0][t] = real(0);
         R.x[slot][0][t] = MODE == M_PAR_MONO ? real(1) : real(0);
-        if (MODE == M_IE || kJac<MODE>) R.x[slot][1][t] = real(0);
+        if (MODE == M_IE || kCheb<MODE>) R.x[slot][1][t] = real(0);
     }
     if (kin && hi_in) {
         const int q = qhi + k * plane;
@@ -469,7 +469,7 @@ __device__ __forceinline__ void ring_read(const Ring<real, MODE> &R, int slot, L
     L.uHi = R.u[slot][1][t];
     if (kJac<MODE> || MODE == M_IE) {
         L.bLo = R.x[slot][0][t];
-        L.iLo = (MODE == M_IE || o_cheb) ? R.x[slot][1][t] : real(0);
+        L.iLo = (MODE == M_IE || (kCheb<MODE> && o_cheb)) ? R.x[slot][1][t] : real(0);
         L.wLo = L.wHi = real(1);
     } else {
         L.bLo = real(0);
@@ -539,7 +539,7 @@ __device__ __forceinline__ void stencil_item(const Inst<real> &I, int seg_index,
             o.src = (sweep & 1) ? I.x1 : I.x0;
             o.out = (sweep & 1) ? I.x0 : I.x1;
             o.sT = I.sTie; o.dS = I.dSie; o.coef = I.coef_jac;
-            if (I.solver == 1) {
+            if (kCheb<MODE>) {   // the launch matches the descriptor's solver (host)
                 o.coef = I.cheb_tau_c;
                 if (sweep > 0) {   // sweep 0 is the basic step itself
                     if (threadIdx.x == 0) sm.cheb_w = cheb_weight(sweep, I.cheb_rho, I.cheb_theta);
@@ -711,7 +711,7 @@ k_stencil_batch(const Inst<real> *insts, const BItem *items)
     __shared__ StencilSmem<real, MODE> sm;
     __shared__ Inst<real> sI;
     const BItem it = items[blockIdx.x];
-    if (MODE == M_JAC && *(volatile int *)&insts[it.inst].ctl->done) return;
+    if (kJac<MODE> && *(volatile int *)&insts[it.inst].ctl->done) return;
     const Inst<real> &I = stage_inst(insts + it.inst, sI);
     stencil_item<real, MODE>(I, it.item, it.item, it.nitems, nullptr, sm);
 }
@@ -740,7 +740,7 @@ k_stencil_active(const Inst<real> *insts, const ActRec *act, int n)
     __syncthreads();
     if (sk < 0) return;
     const ActRec r = act[sk];
-    if (MODE == M_JAC && *(volatile int *)&r.ctl->done) return;   // converged at a check in this loop pass
+    if (kJac<MODE> && *(volatile int *)&r.ctl->done) return;   // converged at a check in this loop pass
     const Inst<real> &I = stage_inst(insts + r.inst, sI);
     const int item = i - r.cum;
     stencil_item<real, MODE>(I, item, item, I.nseg, nullptr, sm);
