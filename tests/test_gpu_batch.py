@@ -123,3 +123,25 @@ def test_autotune_keeps_results_within_tolerance():
         np.testing.assert_allclose(s_mix.read(ep.EP_VM_MV), s_alone.read(ep.EP_VM_MV), rtol=0, atol=0.5)
         np.testing.assert_allclose(s_mix.read(ep.EP_W), s_alone.read(ep.EP_W), rtol=0, atol=1e-4)
     b.close()
+
+
+def test_mixed_solvers_same_alone_and_in_the_mix():
+    """Damped-Jacobi and Chebyshev members in one batch: the table keeps each
+    group to one solver (its own sweep kernel instance), interleaved slots
+    included, and every member matches its standalone run bit for bit."""
+    cases = _cases(W.BI)
+    for i, c in enumerate(cases):
+        c.params.solver = 1 if i % 2 else 0
+    alone = _handles(cases, seed0=500)
+    for s in alone:
+        s.step(3, allow_noconv=True)
+    mixed = _handles(cases, seed0=500)
+    b = ep.Batch(len(cases))
+    slots = [b.add(s) for s in mixed]
+    assert b.info().groups >= 2
+    b.step(3, allow_noconv=True)
+    for s_alone, s_mix, slot in zip(alone, mixed, slots):
+        assert b.slot_stats(slot).step == 6
+        for f in FIELDS:
+            np.testing.assert_array_equal(s_mix.read(f), s_alone.read(f))
+    b.close()
