@@ -54,6 +54,8 @@ def _args():
                     help="elliptic solve: the paper's damped Jacobi, or Chebyshev-accelerated Jacobi "
                          "(default: jacobi; chebyshev for ecg)")
     ap.add_argument("--sig-o", type=float, default=1.0, help="ecg: torso conductivity (mS/mm)")
+    ap.add_argument("--omega", type=float, default=None,
+                    help="Jacobi damping: > 0 that value, 0 the bound rule, < 0 estimated from the spectrum")
     ap.add_argument("--diffusion", choices=["explicit", "implicit"], default="explicit",
                     help="parabolic step: explicit Euler, or implicit Euler solved by Jacobi (Eq. iejac1)")
     ap.add_argument("--instances", type=int, default=64, help="config3: number of instances")
@@ -70,8 +72,12 @@ def _args():
     return ap.parse_args()
 
 
-def _workload(name, model="mono", slab_n=512, diffusion="explicit", solver=None, sig_o=1.0):
+def _workload(name, model="mono", slab_n=512, diffusion="explicit", solver=None, sig_o=1.0, omega=None):
     c, desc = _workload_case(name, model, slab_n, sig_o)
+    if omega is not None:
+        c.params.omega = omega
+        if omega < 0:
+            desc += "; damping estimated from the spectrum of D^-1 A (omega = 1.9 / lmax)"
     if diffusion == "implicit":
         c.params.diffusion = 1
         desc += "; implicit-Euler diffusion (Jacobi, Eq. iejac1)"
@@ -267,7 +273,7 @@ def run_reference(a):
     world, rank, local = _dist()
     if rank != 0:
         return
-    case, desc = _workload(a.workload, a.model, a.slab_n, a.diffusion, a.solver, a.sig_o)
+    case, desc = _workload(a.workload, a.model, a.slab_n, a.diffusion, a.solver, a.sig_o, a.omega)
     M = case.n_tissue
     k_ref = a.ref_sweeps_per_step or DEFAULT_REF_SWEEPS_PER_STEP
     times = []
@@ -306,7 +312,7 @@ def run_ours(a):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     epbuild.build()
-    case, desc = _workload(a.workload, a.model, a.slab_n, a.diffusion, a.solver, a.sig_o)
+    case, desc = _workload(a.workload, a.model, a.slab_n, a.diffusion, a.solver, a.sig_o, a.omega)
     M = case.n_tissue
     mono = case.model == 0
     stream = torch.cuda.Stream()

@@ -88,8 +88,13 @@ typedef struct {
     double lambda;        /* monodomain ratio (Eq. monodomain1) */
     double K;             /* chi_m * C_m, > 0 */
     double dt_ms;         /* time step, > 0 */
-    double jacobi_omega;  /* damping of Eq. dampjac1; <= 0 selects 1.8 / (8 sL / (sL + 2 sT))
-                             for the elliptic operator's sL = sig_iL + sig_eL, sT = sig_iT + sig_eT */
+    double jacobi_omega;  /* damping of Eq. dampjac1 (the thesis requires damping but gives no value):
+                             > 0: that value, < 2;
+                             0: 1.8 / (8 sL / (sL + 2 sT)), the Fourier bound of a uniform tensor, for
+                             the elliptic operator's sL = sig_iL + sig_eL, sT = sig_iT + sig_eT;
+                             < 0: estimated at set-up (bidomain): min(1, 1.9 / lmax), lmax the
+                             largest eigenvalue of D^-1 A from the Lanczos estimate scaled by 1.05
+                             (or cheb_lmax when given).  The value in use: ep_get_info's omega. */
     double rel_tol;       /* stop when ||b - A x||_2 <= rel_tol ||b||_2 */
     int check_every;      /* residual check interval in sweeps, >= 1 (both solves) */
     int max_iter;         /* sweep cap per solve, >= 1 (both solves) */
@@ -130,7 +135,8 @@ typedef struct {
     int n_segments;          /* z-march work items of the stencil kernels */
     double omega;            /* damping in use */
     size_t device_bytes;     /* device memory held by the handle */
-    double cheb_lmin, cheb_lmax;   /* Chebyshev interval in use (0 for the Jacobi solver) */
+    double cheb_lmin, cheb_lmax;   /* interval of D^-1 A in use: the Chebyshev solver's, or the estimate behind
+                                      an estimated jacobi_omega; 0 when neither needs one */
     long long n_domain;      /* voxels of the elliptic equation: tissue, plus the torso if set */
     int n_segments_elliptic; /* work items of the elliptic sweeps (n_segments without a torso) */
 } ep_info;

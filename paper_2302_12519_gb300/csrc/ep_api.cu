@@ -183,7 +183,7 @@ bool params_ok(const ep_params &p, std::string &why)
     if (!pos(p.sig_iL) || !pos(p.sig_iT) || !pos(p.sig_eL) || !pos(p.sig_eT)) { why = "conductivities must be > 0"; return false; }
     if (!std::isfinite(p.lambda) || p.lambda <= 0.0) { why = "lambda must be > 0"; return false; }
     if (!pos(p.K) || !pos(p.dt_ms)) { why = "K and dt_ms must be > 0"; return false; }
-    if (!std::isfinite(p.jacobi_omega) || p.jacobi_omega >= 2.0) { why = "jacobi_omega must be < 2 (<= 0 selects the default)"; return false; }
+    if (!std::isfinite(p.jacobi_omega) || p.jacobi_omega >= 2.0) { why = "jacobi_omega must be < 2 (0: the bound rule, < 0: estimated)"; return false; }
     if (!std::isfinite(p.rel_tol) || p.rel_tol < 0.0) { why = "rel_tol must be >= 0"; return false; }
     if (p.check_every < 1 || p.max_iter < 1) { why = "check_every and max_iter must be >= 1"; return false; }
     if (p.diffusion != EP_EXPLICIT && p.diffusion != EP_IMPLICIT) { why = "diffusion must be EP_EXPLICIT or EP_IMPLICIT"; return false; }
@@ -265,7 +265,8 @@ constexpr int kLanczosScalars = 2 + 2 * kLanczosSteps;   // alpha, beta of the c
 // sums per reduction chunk.
 size_t lanczos_bytes(const ep_sim *s)
 {
-    if (!s->have_params || s->p.solver != EP_SOLVER_CHEBYSHEV || s->d.model != EP_BI || s->p.cheb_lmin > 0.0) return 0;
+    if (!s->have_params || s->d.model != EP_BI || s->p.cheb_lmin > 0.0) return 0;
+    if (s->p.solver != EP_SOLVER_CHEBYSHEV && !(s->p.jacobi_omega < 0.0)) return 0;   // no spectrum needed
     return sizeof(double) * ((size_t)kLanczosScalars + 2 * (size_t)s->nchunk);
 }
 
@@ -596,7 +597,8 @@ ep_status setup_typed(ep_sim *s)
         k_fill<real><<<grid_for(n, 256), 256, 0, st>>>((real *)s->ie_x, n, real(0));
         CK(cudaGetLastError());
     }
-    if (s->p.solver == EP_SOLVER_CHEBYSHEV && s->d.model == EP_BI) {
+    // the spectrum of D^-1 A: for the Chebyshev solver, and for damped Jacobi with estimated damping
+    if ((s->p.solver == EP_SOLVER_CHEBYSHEV || s->p.jacobi_omega < 0.0) && s->d.model == EP_BI) {
         if (s->p.cheb_lmin > 0.0) {
             s->cheb_lmin = s->p.cheb_lmin;
             s->cheb_lmax = s->p.cheb_lmax;
@@ -606,6 +608,9 @@ ep_status setup_typed(ep_sim *s)
                                                         (real *)s->w[1], (double *)tmp_lz);
             if (es != EP_OK) return es;
         }
+        // estimated damping: omega lambda_max = 1.9 / 1.05 on the largest Ritz value (below 2 with room
+        // for the estimate's error), the fastest contraction of the slow modes that stays stable
+        if (s->p.jacobi_omega < 0.0) s->omega = std::min(1.0, 1.9 / s->cheb_lmax);
     }
     // rest state
     for (int i = 0; i < 2; ++i) {

@@ -104,3 +104,29 @@ def test_chebyshev_interval_is_validated():
     with pytest.raises(ep.EPError) as e:
         ep.sim_from_case(c)
     assert e.value.status == ep.EP_EINVAL
+
+
+def test_estimated_jacobi_damping_is_stable_and_matches_oracle():
+    """jacobi_omega < 0: damping from the set-up spectrum estimate,
+    omega = 1.9 / lmax.  It keeps omega lambda_max(D^-1 A) below 2 on the
+    dense spectrum, and with that omega the FP64 damped Jacobi solve equals the
+    oracle's."""
+    c = W.random_case(44, 13, 9, 8, model=W.BI, rel_tol=1e-11, check_every=5)
+    c.params.max_iter = 400000
+    c.params.omega = -1.0
+    lo, hi = _dense_interval(c)
+    s = ep.sim_from_case(c, precision=ep.EP_FP64)
+    info = s.info()
+    assert info.omega == pytest.approx(min(1.0, 1.9 / info.cheb_lmax), rel=1e-15)
+    assert info.omega * hi < 2.0
+    c.params.omega = info.omega
+    o = oracle.Sim(c)
+    v, w, ve = W.random_state(44, c)
+    s.set_state(v, w, ve, 0)
+    o.set_state(v, w, ve, 0)
+    for _ in range(2):
+        stats = s.step(1)
+        assert o.step() == 0 and stats.converged == 1 and stats.iters == o.last_iters
+    st = o.state()
+    np.testing.assert_allclose(s.read(ep.EP_V), st["v"], rtol=0, atol=1e-10)
+    np.testing.assert_allclose(s.read(ep.EP_VE), st["ve"], rtol=0, atol=1e-7)

@@ -147,6 +147,11 @@ def test_footprint_counts_the_interval_estimate(lib):
     assert rj == re_ == rg and pj == pg
     extra = pe - pj
     assert extra >= 8 * 82 + 16 and (extra - 8 * 82) % 16 == 0
+    # damped Jacobi with estimated damping runs the same estimate
+    c.params.solver, c.params.cheb_lmin, c.params.cheb_lmax, c.params.omega = 0, 0.0, 0.0, -1.0
+    s = ep.sim_from_case(c, use_torch=False)
+    assert s.footprint() == (re_, pe)
+    s.close()
 
 
 def test_torso_and_ecg_are_validated_and_planned_on_the_host(lib):
