@@ -394,8 +394,9 @@ def run_ours(a):
         launch_s = sweep_s / max(prof.sweeps, 1)
         per_voxel = BYTES_PER_CHEB_SWEEP_VOXEL if a.solver == "chebyshev" else BYTES_PER_SWEEP_VOXEL
         alg_bytes = per_voxel * n_dom   # over tissue + torso when a torso is set
-        kname = ("k_stencil<float,M_JAC_BATH> (elliptic sweep over tissue + torso)" if torso else
-                 "k_stencil<float,M_JAC> (damped Jacobi sweep)")
+        kname = ("k_stencil<float,M_JAC(_CHEB)> over the torso items away from the tissue + "
+                 "k_stencil<float,M_JAC_BATH(_CHEB)> over the rest (one elliptic sweep over tissue + torso)"
+                 if torso else "k_stencil<float,M_JAC> (damped Jacobi sweep)")
         if a.solver == "chebyshev":
             kname += ", Chebyshev-accelerated"
         share = sweep_s / total_s

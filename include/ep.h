@@ -139,6 +139,8 @@ typedef struct {
                                       an estimated jacobi_omega; 0 when neither needs one */
     long long n_domain;      /* voxels of the elliptic equation: tissue, plus the torso if set */
     int n_segments_elliptic; /* work items of the elliptic sweeps (n_segments without a torso) */
+    int n_segments_far;      /* of those, items whose voxels and halo hold no tissue (swept by the
+                                single-term kernel: there the operator is the torso's alone) */
 } ep_info;
 
 typedef struct ep_sim ep_sim;

@@ -66,7 +66,8 @@ class Info(ctypes.Structure):
     _fields_ = [("n_voxels", ctypes.c_longlong), ("n_tissue", ctypes.c_longlong), ("n_components", ctypes.c_int),
                 ("n_segments", ctypes.c_int), ("omega", ctypes.c_double), ("device_bytes", ctypes.c_size_t),
                 ("cheb_lmin", ctypes.c_double), ("cheb_lmax", ctypes.c_double),
-                ("n_domain", ctypes.c_longlong), ("n_segments_elliptic", ctypes.c_int)]
+                ("n_domain", ctypes.c_longlong), ("n_segments_elliptic", ctypes.c_int),
+                ("n_segments_far", ctypes.c_int)]
 
 
 class SdfNode(ctypes.Structure):

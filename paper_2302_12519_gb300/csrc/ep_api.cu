@@ -87,6 +87,7 @@ struct ep_sim {
     long long n_domain = 0;      // voxels of the elliptic equation (tissue + torso)
     int ncomp = 0, nseg = 0, nchunk = 0;
     int nseg_e = 0;              // work items of the elliptic sweeps (nseg without a torso)
+    int nseg_far = 0;            // the first of them, whose cells and halo hold no tissue
     int zseg = kZSeg;            // z-planes per stencil work item
     long long max_items = 0;     // segment capacity of the segs / partials buffers
     double omega = 0.0;
@@ -203,6 +204,28 @@ bool params_ok(const ep_params &p, std::string &why)
 // ones holding tissue.  The items partition the tissue voxels.  Placing the
 // windows on the tissue, rather than on a fixed 30-column lattice, spends
 // about 12 % fewer thread slots on the shell geometries.
+// Torso handles: moves the work items whose voxels and one-voxel halo hold no
+// tissue (the reach of their stencil) to the front, keeping the order within
+// each class; returns their number.  There the elliptic operator is the torso
+// term alone, which the single-term kernel computes with sigma = sig_o I.
+int partition_far(std::vector<Seg> &segs, const uint8_t *heart, int nx, int ny, int nz)
+{
+    auto far = [&](const Seg &g) {
+        const int xa = std::max(0, g.x0 - 1), xb = std::min(nx, g.x0 + kTileX + 1);
+        const int ya = std::max(0, g.by * kTileY - 1), yb = std::min(ny, g.by * kTileY + kTileY + 1);
+        const int za = std::max(0, g.k0 - 1), zb = std::min(nz, g.k1 + 1);
+        for (int k = za; k < zb; ++k)
+            for (int j = ya; j < yb; ++j) {
+                const uint8_t *row = heart + (long long)nx * (j + (long long)ny * k);
+                for (int i = xa; i < xb; ++i)
+                    if (row[i]) return false;
+            }
+        return true;
+    };
+    auto mid = std::stable_partition(segs.begin(), segs.end(), far);
+    return (int)(mid - segs.begin());
+}
+
 std::vector<Seg> build_segments(const uint8_t *m, int nx, int ny, int nz, int zseg)
 {
     std::vector<Seg> segs;
@@ -502,6 +525,7 @@ ep_status setup_typed(ep_sim *s)
         s->nseg = (int)s->plan.segs.size();
         if (tor) s->plan.segs_e = s->plan.segs_e_z[pick];
         s->nseg_e = tor ? (int)s->plan.segs_e.size() : s->nseg;
+        s->nseg_far = tor ? partition_far(s->plan.segs_e, s->mask.data(), s->d.nx, s->d.ny, s->d.nz) : 0;
         s->zseg = kZLens[pick];
     }
     const HostPlan &P = s->plan;
@@ -755,17 +779,36 @@ ApplyIO<real> no_io()
     return io;
 }
 
-// A CUDA graph of kSweepChunk sweep launches of one solve (MODE = M_JAC,
-// M_JAC_BATH or M_IE) with descriptor I (one CTA per work item of I).
+// One sweep of a solve on stream q: a sweep kernel over descriptor I (one CTA
+// per work item of I), or, for a torso handle whose items split, the
+// single-term kernel over the items far from the tissue and the two-term one
+// over the rest.
 template <typename real, int MODE>
-ep_status build_sweep_graph(ep_sim *s, const Inst<real> &I, cudaGraphExec_t *out)
+struct OneSweep {
+    Inst<real> I;
+    void operator()(cudaStream_t q) const
+    {
+        k_stencil<real, MODE><<<std::max(1, I.nseg), kThreads, 0, q>>>(I, no_io<real>());
+    }
+};
+template <typename real, int MODE_FAR, int MODE_NEAR>
+struct SplitSweep {
+    Inst<real> far, near;   // far.nseg or near.nseg may be 0
+    void operator()(cudaStream_t q) const
+    {
+        if (far.nseg > 0) k_stencil<real, MODE_FAR><<<far.nseg, kThreads, 0, q>>>(far, no_io<real>());
+        if (near.nseg > 0) k_stencil<real, MODE_NEAR><<<near.nseg, kThreads, 0, q>>>(near, no_io<real>());
+    }
+};
+
+// A CUDA graph of kSweepChunk sweeps of one solve.
+template <typename Sweep>
+ep_status build_sweep_graph(ep_sim *s, const Sweep &sweep, cudaGraphExec_t *out)
 {
     if (*out) return EP_OK;
-    const ApplyIO<real> io = no_io<real>();
     cudaGraph_t g = nullptr;
     CK(cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeThreadLocal));
-    for (int i = 0; i < kSweepChunk; ++i)
-        k_stencil<real, MODE><<<std::max(1, I.nseg), kThreads, 0, s->stream>>>(I, io);
+    for (int i = 0; i < kSweepChunk; ++i) sweep(s->stream);
     cudaError_t e = cudaStreamEndCapture(s->stream, &g);
     if (e != cudaSuccess) return fail(s, EP_ECUDA, std::string("sweep graph capture: ") + cudaGetErrorString(e));
     e = cudaGraphInstantiate(out, g, 0);
@@ -781,13 +824,12 @@ ep_status build_sweep_graph(ep_sim *s, const Inst<real> &I, cudaGraphExec_t *out
 // the host reads the control block one chunk behind, so the GPU never waits
 // for it.  At most max_iter sweeps do work; launch max_iter + 1 marks a capped
 // solve done.  Returns the launches queued in *queued_out.
-template <typename real, int MODE>
-ep_status run_sweeps(ep_sim *s, const Inst<real> &I, cudaGraphExec_t *graph, long long *queued_out)
+template <typename Sweep>
+ep_status run_sweeps(ep_sim *s, const Sweep &sweep, cudaGraphExec_t *graph, long long *queued_out)
 {
     cudaStream_t st = s->stream;
-    const ApplyIO<real> io = no_io<real>();
     if (!s->noalloc_call) {
-        ep_status gs = build_sweep_graph<real, MODE>(s, I, graph);
+        ep_status gs = build_sweep_graph(s, sweep, graph);
         if (gs != EP_OK) return gs;
     }
     const long long limit = (long long)s->p.max_iter + 1;
@@ -798,7 +840,7 @@ ep_status run_sweeps(ep_sim *s, const Inst<real> &I, cudaGraphExec_t *graph, lon
             queued += kSweepChunk;
         } else {
             const long long stop = std::min(limit, queued + (long long)kSweepChunk);
-            for (; queued < stop; ++queued) k_stencil<real, MODE><<<std::max(1, I.nseg), kThreads, 0, st>>>(I, io);
+            for (; queued < stop; ++queued) sweep(st);
             CK(cudaGetLastError());
         }
         CK(cudaMemcpyAsync(&s->ctl_host[c & 1], s->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
@@ -881,12 +923,20 @@ ep_status solve_elliptic(ep_sim *s, const Inst<real> &I, int &iters, double &rel
     ep_status rs = EP_OK;
     const bool cheb = I.solver == 1;   // the sweep instance matches the handle's solver
     if (s->torso.empty()) {
-        rs = cheb ? run_sweeps<real, M_JAC_CHEB>(s, I, &s->sweep_graph, &queued)
-                  : run_sweeps<real, M_JAC>(s, I, &s->sweep_graph, &queued);
-    } else {   // tissue + torso: the domain's items and records
+        rs = cheb ? run_sweeps(s, OneSweep<real, M_JAC_CHEB>{I}, &s->sweep_graph, &queued)
+                  : run_sweeps(s, OneSweep<real, M_JAC>{I}, &s->sweep_graph, &queued);
+    } else {   // tissue + torso: the domain's items and records, split by distance from the tissue
         const Inst<real> Ie = make_elliptic_inst<real>(s);
-        rs = cheb ? run_sweeps<real, M_JAC_BATH_CHEB>(s, Ie, &s->sweep_graph, &queued)
-                  : run_sweeps<real, M_JAC_BATH>(s, Ie, &s->sweep_graph, &queued);
+        Inst<real> far = Ie, near = Ie;
+        far.nseg = s->nseg_far;                 // items far from the tissue come first
+        far.nitems_all = near.nitems_all = s->nseg_e;
+        far.sTie = (real)s->sig_o;              // there the operator is the torso term alone:
+        far.dSie = real(0);                     // the plain one with sigma = sig_o I
+        near.segs = s->segs_e + s->nseg_far;
+        near.nseg = s->nseg_e - s->nseg_far;
+        near.item0 = s->nseg_far;
+        rs = cheb ? run_sweeps(s, SplitSweep<real, M_JAC_CHEB, M_JAC_BATH_CHEB>{far, near}, &s->sweep_graph, &queued)
+                  : run_sweeps(s, SplitSweep<real, M_JAC, M_JAC_BATH>{far, near}, &s->sweep_graph, &queued);
     }
     if (rs != EP_OK) return rs;
     if (s->prof_on) {
@@ -947,7 +997,7 @@ ep_status step_typed(ep_sim *s, int n_steps, ep_step_stats *stats)
             CK(cudaGetLastError());
             if (s->prof_on) CK(cudaEventRecord(s->pev[4], st));
             long long queued = 0;
-            ep_status e = run_sweeps<real, M_IE>(s, I, &s->ie_graph, &queued);
+            ep_status e = run_sweeps(s, OneSweep<real, M_IE>{I}, &s->ie_graph, &queued);
             if (e != EP_OK) return e;
             if (s->prof_on) {
                 CK(cudaEventRecord(s->pev[5], st));
@@ -1279,6 +1329,7 @@ ep_status ep_get_info(ep_sim *s, ep_info *info)
     info->device_bytes = s->dev_bytes;
     info->n_domain = s->n_domain;
     info->n_segments_elliptic = s->nseg_e;
+    info->n_segments_far = s->nseg_far;
     return EP_OK;
 }
 

@@ -139,6 +139,10 @@ struct Inst {
     // elliptic right-hand side count torso voxels as 0
     int torso, pad4;
     real sig_o;
+    // a sweep split over two launches (torso handles: items far from the tissue run the
+    // single-term kernel): this launch's first item among the sweep's items, and their count
+    // (0: the launch is the whole sweep)
+    int item0, nitems_all;
 };
 
 // Weight of sweep k of the Chebyshev semi-iteration: w = 1 for k = 0, else

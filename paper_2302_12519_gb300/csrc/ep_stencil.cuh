@@ -684,7 +684,8 @@ __global__ void __launch_bounds__(kThreads, kTwoTerm<MODE> ? 2 : kMinBlocks) k_s
 {
     __shared__ StencilSmem<real, MODE> sm;
     if (kSweep<MODE> && I.ctl->done) return;   // converged earlier: queued sweeps are no-ops
-    stencil_item<real, MODE>(I, blockIdx.x, blockIdx.x, gridDim.x, &io, sm);
+    const int nitems = I.nitems_all > 0 ? I.nitems_all : (int)gridDim.x;
+    stencil_item<real, MODE>(I, blockIdx.x, I.item0 + (int)blockIdx.x, nitems, &io, sm);
 }
 
 // Copies a member's descriptor into shared memory (read there, like the

@@ -251,3 +251,32 @@ def test_ecg_workload_fullsize_operator_and_capped_step():
     r = b - ge.apply_L(sL, sT, xg)
     rr = np.linalg.norm(r[dom]) / np.linalg.norm(b[dom])
     assert abs(rr - stats.rel_res) <= 0.05 * stats.rel_res + 1e-5, (rr, stats.rel_res)
+
+
+def test_far_items_single_term_sweep_matches_oracle():
+    """A small heart padded by a thick torso: the items whose stencil reach holds
+    no tissue run the single-term kernel (sigma = sig_o I), the rest the two-term
+    one.  The FP64 solve to 1e-11 (Chebyshev, the oracle on the GPU's interval)
+    equals the oracle's.  (Unconverged iterates are not compared: the library's
+    Jacobi diagonal is stored in fp16, which changes the iterates but not the
+    solution.)"""
+    base = W.random_case(68, 8, 8, 8, fill=0.7, rel_tol=1e-11, check_every=5)
+    c = W.with_torso(base, sig_o=0.9, pad=12)
+    c.params.max_iter = 400000
+    c.params.solver = 1
+    s0 = ep.sim_from_case(c, precision=ep.EP_FP64)
+    info = s0.info()
+    s0.close()
+    assert 0 < info.n_segments_far < info.n_segments_elliptic
+    c.params.cheb_lmin, c.params.cheb_lmax = info.cheb_lmin, info.cheb_lmax
+    s = ep.sim_from_case(c, precision=ep.EP_FP64)
+    o = oracle.Sim(c)
+    v, w, ve = W.random_state(68, c)
+    s.set_state(v, w, ve, 0)
+    o.set_state(v, w, ve, 0)
+    for _ in range(2):
+        stats = s.step(1)
+        assert o.step() == 0 and stats.converged == 1
+    st = o.state()
+    np.testing.assert_allclose(s.read(ep.EP_V), st["v"], rtol=0, atol=1e-10)
+    np.testing.assert_allclose(s.read(ep.EP_VE), st["ve"], rtol=0, atol=1e-7)
