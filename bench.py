@@ -594,15 +594,7 @@ def run_sdf(a):
     d_fib = torch.empty(3 * n, dtype=torch.float32, device=dev)
     d_vert = torch.empty(nv, dtype=torch.uint8, device=dev)
     d_cnt = torch.zeros(1, dtype=torch.int64, device=dev)
-    N = (ep.SdfNode * len(sc.nodes))()
-    for i, nd in enumerate(sc.nodes):
-        N[i].op, N[i].a, N[i].b, N[i].c = nd.op, nd.a, nd.b, nd.c
-        N[i].centre[:] = list(nd.centre)
-        N[i].rot[:] = list(nd.rot)
-    R = (ep.SdfRegion * len(sc.regions))()
-    for i, rg in enumerate(sc.regions):
-        R[i].first, R[i].count, R[i].kind, R[i].scale = rg.first, rg.count, rg.kind, rg.scale
-        R[i].axis[:] = list(rg.axis)
+    N, R = ep.sdf_tables(sc.nodes, sc.regions)
     org = (ctypes.c_float * 3)(*sc.origin)
     stream = torch.cuda.Stream()
 

@@ -539,13 +539,9 @@ class Server:
             pass
 
 
-def sdf_encode(nodes, regions, nx: int, ny: int, nz: int, dx_mm: float, origin_mm, helix_rad: float,
-               want_vertices: bool = True, stream: Optional[int] = None):
-    """ep_sdf_encode.  nodes: sequence of objects with op, a, b, c, centre (3),
-    rot (9); regions: objects with first, count, kind, axis (3), scale.
-    Returns a dict of label, mask (uint8, n), fibres (float32, 3n), vertices
-    (uint8, (nx+1)(ny+1)(nz+1)) and n_tissue."""
-    L = load()
+def sdf_tables(nodes, regions):
+    """ctypes arrays of ep_sdf_node / ep_sdf_region from node and region
+    objects (op, a, b, c, centre, rot / first, count, kind, axis, scale)."""
     N = (SdfNode * len(nodes))()
     for i, nd in enumerate(nodes):
         N[i].op, N[i].a, N[i].b, N[i].c = int(nd.op), float(nd.a), float(nd.b), float(nd.c)
@@ -556,6 +552,17 @@ def sdf_encode(nodes, regions, nx: int, ny: int, nz: int, dx_mm: float, origin_m
         R[i].first, R[i].count, R[i].kind = int(rg.first), int(rg.count), int(rg.kind)
         R[i].axis[:] = [float(v) for v in rg.axis]
         R[i].scale = float(rg.scale)
+    return N, R
+
+
+def sdf_encode(nodes, regions, nx: int, ny: int, nz: int, dx_mm: float, origin_mm, helix_rad: float,
+               want_vertices: bool = True, stream: Optional[int] = None):
+    """ep_sdf_encode.  nodes: sequence of objects with op, a, b, c, centre (3),
+    rot (9); regions: objects with first, count, kind, axis (3), scale.
+    Returns a dict of label, mask (uint8, n), fibres (float32, 3n), vertices
+    (uint8, (nx+1)(ny+1)(nz+1)) and n_tissue."""
+    L = load()
+    N, R = sdf_tables(nodes, regions)
     n = nx * ny * nz
     label = np.empty(n, np.uint8)
     mask = np.empty(n, np.uint8)
