@@ -213,6 +213,24 @@ def test_sdf_encoder_validates_the_program_without_a_device(lib):
     assert e.value.status == ep.EP_EINVAL
 
 
+def test_ecg_calls_validate_on_the_host(lib):
+    """Without an ECG set up, ep_read_ecg is EP_EINVAL and reports no samples;
+    capacity 0 switches a set-up ECG off again (no record in the footprint)."""
+    import workloads as W
+    c = W.random_case(6, 10, 9, 8)
+    s = ep.sim_from_case(c, use_torch=False)
+    n = ctypes.c_int(7)
+    assert lib.ep_read_ecg(s._h, None, 0, ctypes.byref(n)) == ep.EP_EINVAL and n.value == 0
+    r0 = s.footprint()
+    s.set_ecg([(0, 0, 0), (1, 1, 1), (2, 2, 2)], 50)
+    r1 = s.footprint()
+    assert r1[0] == r0[0] + 3 * 8 * 50
+    s.set_ecg(None, 0)
+    assert s.footprint() == r0
+    assert lib.ep_read_ecg(s._h, None, 0, ctypes.byref(n)) == ep.EP_EINVAL
+    s.close()
+
+
 def test_server_needs_a_device(lib):
     """Without a GPU the server cannot start and says so (no host fallback)."""
     import torch
