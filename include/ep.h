@@ -263,8 +263,11 @@ ep_status ep_apply_elliptic(ep_sim *s, const double *u_host, double *out_host, s
  * 32768 stencil work items (ep_info.n_segments) and 32768 reduction chunks
  * (2048 tissue voxels each), at most 4096 tissue components; larger problems
  * get EP_EINVAL with a message.  The first call on a device looks up the
- * array's device address (cudaGetSymbolAddress) with that device current;
- * make that first call before any stream capture.  All calls on a device
+ * array's device address (cudaGetSymbolAddress) with that device current,
+ * and looks it up again when the device's context has changed since (after
+ * a cudaDeviceReset the handle itself must be created anew: its device
+ * memory went with the old context); make that first call before any stream
+ * capture.  All calls on a device
  * share the one array and each call clears it first: calls whose work
  * overlaps on the GPU (several handles on concurrent streams) race on it,
  * so run them one after another.  Sweeps are launched one by one, without

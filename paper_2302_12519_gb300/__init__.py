@@ -197,9 +197,9 @@ def load(path: str = LIB_PATH):
     return L
 
 
-def _torch_hooks():
-    """Device allocator callbacks backed by torch's caching allocator, and the
-    current torch stream.  Returns (alloc, free, stream) or None."""
+def torch_allocator():
+    """(alloc(nbytes) -> pointer, free(pointer)) backed by torch's caching
+    allocator on the current device and stream, or None without a GPU."""
     try:
         import torch
     except Exception:
@@ -209,11 +209,34 @@ def _torch_hooks():
     dev = torch.cuda.current_device()
     stream = torch.cuda.current_stream(dev)
 
-    def _alloc(nbytes, ctx):
+    def alloc(nbytes):
         return int(torch.cuda.caching_allocator_alloc(int(nbytes), dev, stream))
 
-    def _free(ptr, ctx):
+    def free(ptr):
         torch.cuda.caching_allocator_delete(int(ptr))
+
+    return alloc, free
+
+
+def _torch_hooks(allocator=None):
+    """Device allocator callbacks for ep_grid_desc (from `allocator`, a pair of
+    Python callables alloc(nbytes) -> pointer (0 = failure) and free(pointer),
+    else torch's caching allocator) and the current torch stream.  Returns
+    (alloc, free, stream) or None."""
+    try:
+        import torch
+    except Exception:
+        return None
+    if not torch.cuda.is_available():
+        return None
+    alloc, free = allocator if allocator is not None else torch_allocator()
+    stream = torch.cuda.current_stream(torch.cuda.current_device())
+
+    def _alloc(nbytes, ctx):
+        return int(alloc(int(nbytes)) or 0)
+
+    def _free(ptr, ctx):
+        free(int(ptr))
 
     return _ALLOC_T(_alloc), _FREE_T(_free), int(stream.cuda_stream)
 
@@ -229,14 +252,16 @@ class Sim:
     """One simulation handle (ep_sim).  Mirrors the C ABI one call per method."""
 
     def __init__(self, nx: int, ny: int, nz: int, dx_mm: float, model: int = EP_BI, precision: int = EP_FP32,
-                 use_torch: bool = True, stream: Optional[int] = None):
+                 use_torch: bool = True, stream: Optional[int] = None, allocator=None):
+        """allocator: optional (alloc(nbytes) -> pointer, free(pointer)) used for
+        the handle's device memory instead of torch's caching allocator."""
         L = load()
         self._L = L
         self.nx, self.ny, self.nz = int(nx), int(ny), int(nz)
         self.n = self.nx * self.ny * self.nz
         d = GridDesc()
         d.nx, d.ny, d.nz, d.dx_mm, d.model, d.precision = self.nx, self.ny, self.nz, float(dx_mm), int(model), int(precision)
-        self._hooks = _torch_hooks() if use_torch else None
+        self._hooks = _torch_hooks(allocator) if use_torch else None
         if self._hooks is not None:
             d.dev_alloc, d.dev_free = self._hooks[0], self._hooks[1]
             d.cuda_stream = self._hooks[2] if stream is None else stream
@@ -583,11 +608,11 @@ def _is_bi(case, model: Optional[int]) -> bool:
 
 
 def sim_from_case(case, use_torch: bool = True, model: Optional[int] = None, precision: Optional[int] = None,
-                  ecg_capacity: int = 4096) -> Sim:
+                  ecg_capacity: int = 4096, allocator=None) -> Sim:
     """Create a handle from a ``workloads.Case`` (mask, fibres, parameters,
     stimuli; the torso and the ECG electrodes if the case has them)."""
     s = Sim(case.nx, case.ny, case.nz, case.dx, case.model if model is None else model,
-            case.precision if precision is None else precision, use_torch=use_torch)
+            case.precision if precision is None else precision, use_torch=use_torch, allocator=allocator)
     s.set_mask(case.mask_flat())
     s.set_fibres(case.fib_flat())
     s.set_params(case.params)

@@ -22,7 +22,10 @@
 #include <new>
 #include <string>
 #include <thread>
+#include <utility>
 #include <vector>
+
+#include <cuda.h>
 
 #include "../../include/ep.h"
 #include "ep_kernels.cuh"
@@ -96,8 +99,8 @@ struct ep_sim {
     // device memory
     std::vector<void *> allocs;
     size_t dev_bytes = 0;
-    ushort4 *rec = nullptr;
-    ushort4 *rec_e = nullptr;    // records of the elliptic domain (rec without a torso)
+    float4 *rec = nullptr;
+    float4 *rec_e = nullptr;    // records of the elliptic domain (rec without a torso)
     Seg *segs_e = nullptr;       // work items of the elliptic sweeps (segs without a torso)
     double *ecg = nullptr;       // ECG record: 3 potentials per sample
     long long ecg_n = 0;         // samples recorded since the last read
@@ -297,17 +300,17 @@ void footprint(const ep_sim *s, size_t rb, size_t *resident, size_t *peak)
 {
     const HostPlan &P = s->plan;
     const size_t n = (size_t)s->n;
-    size_t r = abytes(sizeof(ushort4) * n) + 8 * abytes(rb * n);
+    size_t r = abytes(sizeof(float4) * n) + 8 * abytes(rb * n);
     r += abytes(sizeof(Seg) * (size_t)s->max_items) + abytes(sizeof(int) * P.order.size());
     r += abytes(sizeof(Chunk) * P.chunks.size()) + abytes(sizeof(int) * P.comp_chunk0.size());
     r += abytes(sizeof(long long) * P.comp_count.size()) + abytes(sizeof(double) * (size_t)s->ncomp);
     r += abytes(sizeof(double) * (size_t)std::max<long long>(s->max_items, s->nchunk)) + abytes(sizeof(Ctl));
     if (s->have_params && s->p.diffusion == EP_IMPLICIT) r += 2 * abytes(rb * n);   // second iterate, 1/(1 + a D)
     const bool torso = !s->torso.empty();
-    if (torso) r += abytes(sizeof(ushort4) * n) + abytes(sizeof(Seg) * (size_t)s->max_items);   // domain records, items
+    if (torso) r += abytes(sizeof(float4) * n) + abytes(sizeof(Seg) * (size_t)s->max_items);   // domain records, items
     if (s->ecg_q[0] >= 0) r += abytes(sizeof(double) * 3 * (size_t)s->ecg_cap);
     *resident = r;
-    *peak = r + abytes(sizeof(float) * 3 * n) + abytes(n) + abytes(sizeof(ushort4) * n) + lanczos_bytes(s) +
+    *peak = r + abytes(sizeof(float) * 3 * n) + abytes(n) + abytes(sizeof(float4) * n) + lanczos_bytes(s) +
             (torso ? abytes(n) : 0);
 }
 
@@ -471,8 +474,8 @@ ep_status estimate_cheb_interval(ep_sim *s, real *v, real *vprev, real *w, real 
     k_lz_norm<real><<<gc, kRedThreads, 0, st>>>(I, w, lz, -1);
     k_lz_next<real><<<gt, kRedThreads, 0, st>>>(I, nt, v, vprev, w, lz);
     for (int j = 0; j < kLanczosSteps; ++j) {
-        if (torso) k_stencil<real, M_APPLY_BATH><<<gs, kThreads, 0, st>>>(I, io);
-        else k_stencil<real, M_APPLY><<<gs, kThreads, 0, st>>>(I, io);
+        if (torso) k_stencil<real, M_APPLY_BATH><<<gs, kThreads, kSmemBytes<real, M_APPLY_BATH>, st>>>(I, io);
+        else k_stencil<real, M_APPLY><<<gs, kThreads, kSmemBytes<real, M_APPLY>, st>>>(I, io);
         k_lz_w<real><<<gc, kRedThreads, 0, st>>>(I, t, v, vprev, w, lz);
         k_lz_proj<real><<<gc, kRedThreads, 0, st>>>(I, v, w, lz, 1);
         k_lz_norm<real><<<gc, kRedThreads, 0, st>>>(I, w, lz, j);
@@ -543,7 +546,7 @@ ep_status setup_typed(ep_sim *s)
     // device buffers
     const size_t rb = sizeof(real);
     s->rsz = rb;
-    s->rec = (ushort4 *)dalloc(s, sizeof(ushort4) * n);
+    s->rec = (float4 *)dalloc(s, sizeof(float4) * n);
     for (int i = 0; i < 2; ++i) {
         s->v[i] = dalloc(s, rb * n);
         s->w[i] = dalloc(s, rb * n);
@@ -567,7 +570,7 @@ ep_status setup_typed(ep_sim *s)
     s->rec_e = s->rec;
     s->segs_e = s->segs;
     if (torso) {
-        s->rec_e = (ushort4 *)dalloc(s, sizeof(ushort4) * n);
+        s->rec_e = (float4 *)dalloc(s, sizeof(float4) * n);
         s->segs_e = (Seg *)dalloc(s, sizeof(Seg) * (size_t)s->max_items);
         if (!s->rec_e || !s->segs_e) return fail(s, EP_ENOMEM, "device allocation failed");
     }
@@ -577,7 +580,7 @@ ep_status setup_typed(ep_sim *s)
     }
     void *tmp_fib = dalloc(s, sizeof(float) * 3 * n);
     void *tmp_mask = dalloc(s, n);
-    void *tmp_rec = dalloc(s, sizeof(ushort4) * n);
+    void *tmp_rec = dalloc(s, sizeof(float4) * n);
     void *tmp_lz = lanczos_bytes(s) ? dalloc(s, lanczos_bytes(s)) : nullptr;
     if (lanczos_bytes(s) && !tmp_lz) return fail(s, EP_ENOMEM, "device allocation failed");
     void *tmp_torso = torso ? dalloc(s, n) : nullptr;
@@ -598,17 +601,17 @@ ep_status setup_typed(ep_sim *s)
     if (s->fib.empty()) CK(cudaMemsetAsync(tmp_fib, 0, sizeof(float) * 3 * n, st));
     else CK(cudaMemcpyAsync(tmp_fib, s->fib.data(), sizeof(float) * 3 * n, cudaMemcpyHostToDevice, st));
     k_build_records<<<grid_for(n, 256), 256, 0, st>>>(nx, ny, nz, (const float *)tmp_fib, (const uint8_t *)tmp_mask,
-                                                      nullptr, (ushort4 *)tmp_rec);
+                                                      nullptr, (float4 *)tmp_rec);
     // Jacobi diagonal of the elliptic operator L_i + L_e (conductivities add)
     const double sL = s->p.sig_iL + s->p.sig_eL, sT = s->p.sig_iT + s->p.sig_eT;
-    k_build_diag<<<grid_for(n, 128), 128, 0, st>>>(nx, ny, nz, sT, sL - sT, 0.0, (const ushort4 *)tmp_rec, s->rec);
+    k_build_diag<<<grid_for(n, 128), 128, 0, st>>>(nx, ny, nz, sT, sL - sT, 0.0, (const float4 *)tmp_rec, s->rec);
     CK(cudaGetLastError());
     if (torso) {   // the domain's records: torso voxels tagged, the diagonal with the torso term
         CK(cudaMemcpyAsync(tmp_torso, s->torso.data(), n, cudaMemcpyHostToDevice, st));
         CK(cudaMemcpyAsync(s->segs_e, s->plan.segs_e.data(), sizeof(Seg) * s->plan.segs_e.size(), cudaMemcpyHostToDevice, st));
         k_build_records<<<grid_for(n, 256), 256, 0, st>>>(nx, ny, nz, (const float *)tmp_fib, (const uint8_t *)tmp_mask,
-                                                          (const uint8_t *)tmp_torso, (ushort4 *)tmp_rec);
-        k_build_diag<<<grid_for(n, 128), 128, 0, st>>>(nx, ny, nz, sT, sL - sT, s->sig_o, (const ushort4 *)tmp_rec,
+                                                          (const uint8_t *)tmp_torso, (float4 *)tmp_rec);
+        k_build_diag<<<grid_for(n, 128), 128, 0, st>>>(nx, ny, nz, sT, sL - sT, s->sig_o, (const float4 *)tmp_rec,
                                                        s->rec_e);
         CK(cudaGetLastError());
     }
@@ -788,7 +791,7 @@ struct OneSweep {
     Inst<real> I;
     void operator()(cudaStream_t q) const
     {
-        k_stencil<real, MODE><<<std::max(1, I.nseg), kThreads, 0, q>>>(I, no_io<real>());
+        k_stencil<real, MODE><<<std::max(1, I.nseg), kThreads, kSmemBytes<real, MODE>, q>>>(I, no_io<real>());
     }
 };
 template <typename real, int MODE_FAR, int MODE_NEAR>
@@ -796,8 +799,8 @@ struct SplitSweep {
     Inst<real> far, near;   // far.nseg or near.nseg may be 0
     void operator()(cudaStream_t q) const
     {
-        if (far.nseg > 0) k_stencil<real, MODE_FAR><<<far.nseg, kThreads, 0, q>>>(far, no_io<real>());
-        if (near.nseg > 0) k_stencil<real, MODE_NEAR><<<near.nseg, kThreads, 0, q>>>(near, no_io<real>());
+        if (far.nseg > 0) k_stencil<real, MODE_FAR><<<far.nseg, kThreads, kSmemBytes<real, MODE_FAR>, q>>>(far, no_io<real>());
+        if (near.nseg > 0) k_stencil<real, MODE_NEAR><<<near.nseg, kThreads, kSmemBytes<real, MODE_NEAR>, q>>>(near, no_io<real>());
     }
 };
 
@@ -860,6 +863,61 @@ ep_status run_sweeps(ep_sim *s, const Sweep &sweep, cudaGraphExec_t *graph, long
 
 }  // namespace
 
+namespace {
+
+template <typename F>
+cudaError_t allow_smem(F *fn, size_t bytes)
+{
+    return cudaFuncSetAttribute(reinterpret_cast<const void *>(fn), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)bytes);
+}
+
+template <typename real, int... MODES>
+cudaError_t allow_stencil(std::integer_sequence<int, MODES...>)
+{
+    cudaError_t e = cudaSuccess;
+    ((e = e == cudaSuccess ? allow_smem(k_stencil<real, MODES>, kSmemBytes<real, MODES>) : e), ...);
+    return e;
+}
+
+template <int... MODES>
+cudaError_t allow_stencil_batch(std::integer_sequence<int, MODES...>)
+{
+    cudaError_t e = cudaSuccess;
+    ((e = e == cudaSuccess ? allow_smem(k_stencil_batch<float, MODES>, kSmemBytes<float, MODES>) : e), ...);
+    return e;
+}
+
+template <int... MODES>
+cudaError_t allow_stencil_active(std::integer_sequence<int, MODES...>)
+{
+    cudaError_t e = cudaSuccess;
+    ((e = e == cudaSuccess ? allow_smem(k_stencil_active<float, MODES>, kSmemBytes<float, MODES>) : e), ...);
+    return e;
+}
+
+}  // namespace
+
+// The stencil kernels take their shared memory dynamically (with the cp.async
+// rings and fp32 records several exceed the 48 KB of static shared memory):
+// raise every instance's limit on the current device.  Idempotent; called at
+// every set-up, so it follows the device (and context) the handle runs on.
+ep_status configure_kernels(ep_sim *s)
+{
+    using Modes = std::integer_sequence<int, M_APPLY, M_RHS, M_PAR_MONO, M_PAR_BI, M_JAC, M_IE_RHS, M_IE, M_JAC_BATH,
+                                        M_APPLY_BATH, M_JAC_CHEB, M_JAC_BATH_CHEB>;
+    cudaError_t e = allow_stencil<float>(Modes{});
+    if (e == cudaSuccess) e = allow_stencil<double>(Modes{});
+    if (e == cudaSuccess)
+        e = allow_stencil_batch(std::integer_sequence<int, M_PAR_MONO, M_PAR_BI, M_RHS, M_JAC, M_JAC_CHEB>{});
+    if (e == cudaSuccess) e = allow_stencil_active(std::integer_sequence<int, M_JAC, M_JAC_CHEB>{});
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(s, EP_ECUDA, std::string("cudaFuncSetAttribute(shared memory): ") + cudaGetErrorString(e));
+    }
+    return EP_OK;
+}
+
 ep_status ensure_ready(ep_sim *s)
 {
     if (s->ready) return EP_OK;
@@ -887,6 +945,8 @@ ep_status ensure_ready(ep_sim *s)
     }
     const double sL = s->p.sig_iL + s->p.sig_eL, sT = s->p.sig_iT + s->p.sig_eT;
     s->omega = s->p.jacobi_omega > 0.0 ? s->p.jacobi_omega : std::min(1.0, 1.8 * (sL + 2.0 * sT) / (8.0 * sL));
+    ep_status cs = configure_kernels(s);
+    if (cs != EP_OK) return cs;
     ep_status st = s->d.precision == EP_FP64 ? setup_typed<double>(s) : setup_typed<float>(s);
     if (st != EP_OK) {
         dfree_all(s);
@@ -913,7 +973,7 @@ ep_status solve_elliptic(ep_sim *s, const Inst<real> &I, int &iters, double &rel
     cudaStream_t st = s->stream;
     const ApplyIO<real> io = no_io<real>();
     // b = -L_i v, zero mean per component, ||b|| and a fresh solve in ctl
-    k_stencil<real, M_RHS><<<stencil_blocks(s), kThreads, 0, st>>>(I, io);
+    k_stencil<real, M_RHS><<<stencil_blocks(s), kThreads, kSmemBytes<real, M_RHS>, st>>>(I, io);
     k_comp_mean<real><<<s->nchunk, kRedThreads, 0, st>>>(I, (int)RED_B);
     k_comp_subtract<real><<<s->nchunk, kRedThreads, 0, st>>>(I);
     CK(cudaGetLastError());
@@ -980,9 +1040,12 @@ ep_status step_typed(ep_sim *s, int n_steps, ep_step_stats *stats)
     const Inst<real> I = make_inst<real>(s);
     const ApplyIO<real> io = no_io<real>();
     const bool ie = s->p.diffusion == EP_IMPLICIT;
-    {   // the non-convergence flag of this call starts clear
-        const int zero = 0;
-        CK(cudaMemcpyAsync((char *)s->ctl + offsetof(Ctl, noconv), &zero, sizeof(int), cudaMemcpyHostToDevice, st));
+    {   // the flags of this call (non-finite, diverged, not converged) start clear
+        static_assert(offsetof(Ctl, diverged) == offsetof(Ctl, nonfinite) + sizeof(int) &&
+                          offsetof(Ctl, noconv) == offsetof(Ctl, diverged) + sizeof(int),
+                      "the call's flags are adjacent");
+        const int zero[3] = {0, 0, 0};
+        CK(cudaMemcpyAsync((char *)s->ctl + offsetof(Ctl, nonfinite), zero, sizeof(zero), cudaMemcpyHostToDevice, st));
     }
     for (int it = 0; it < n_steps; ++it) {
         const double sweep_ms0 = s->prof.sweep_ms;
@@ -992,7 +1055,7 @@ ep_status step_typed(ep_sim *s, int n_steps, ep_step_stats *stats)
             // from v* to rel_tol, then the final iterate, activation times and the flags
             const int gt = grid_for(s->n_tissue, kRedThreads);
             if (s->d.model == EP_MONO) k_ie_react<real><<<gt, kRedThreads, 0, st>>>(I);
-            else k_stencil<real, M_IE_RHS><<<stencil_blocks(s), kThreads, 0, st>>>(I, io);
+            else k_stencil<real, M_IE_RHS><<<stencil_blocks(s), kThreads, kSmemBytes<real, M_IE_RHS>, st>>>(I, io);
             k_ie_start<real><<<s->nchunk, kRedThreads, 0, st>>>(I);
             CK(cudaGetLastError());
             if (s->prof_on) CK(cudaEventRecord(s->pev[4], st));
@@ -1006,8 +1069,8 @@ ep_status step_typed(ep_sim *s, int n_steps, ep_step_stats *stats)
             k_ie_finish<real><<<gt, kRedThreads, 0, st>>>(I);
         } else {
             // reaction + diffusion: reads v, w of step n (buffer n & 1), writes buffer (n + 1) & 1
-            if (s->d.model == EP_MONO) k_stencil<real, M_PAR_MONO><<<stencil_blocks(s), kThreads, 0, st>>>(I, io);
-            else k_stencil<real, M_PAR_BI><<<stencil_blocks(s), kThreads, 0, st>>>(I, io);
+            if (s->d.model == EP_MONO) k_stencil<real, M_PAR_MONO><<<stencil_blocks(s), kThreads, kSmemBytes<real, M_PAR_MONO>, st>>>(I, io);
+            else k_stencil<real, M_PAR_BI><<<stencil_blocks(s), kThreads, kSmemBytes<real, M_PAR_BI>, st>>>(I, io);
         }
         CK(cudaGetLastError());
         if (s->d.model == EP_BI) {
@@ -1304,7 +1367,7 @@ ep_status ep_apply_operator(ep_sim *s, double sig_L, double sig_T, const double 
         io.out = (real *)s->x[1];
         io.sT = (real)sig_T;
         io.dS = (real)(sig_L - sig_T);
-        k_stencil<real, M_APPLY><<<stencil_blocks(s), kThreads, 0, s->stream>>>(I, io);
+        k_stencil<real, M_APPLY><<<stencil_blocks(s), kThreads, kSmemBytes<real, M_APPLY>, s->stream>>>(I, io);
         CK(cudaGetLastError());
         CK(cudaMemcpyAsync(h.data(), s->x[1], sizeof(real) * s->n, cudaMemcpyDeviceToHost, s->stream));
         CK(cudaStreamSynchronize(s->stream));
@@ -1425,8 +1488,8 @@ ep_status ep_apply_elliptic(ep_sim *s, const double *u_host, double *out_host, s
         io.out = (real *)s->x[1];
         io.sT = (real)(s->p.sig_iT + s->p.sig_eT);
         io.dS = (real)(s->p.sig_iL + s->p.sig_eL - s->p.sig_iT - s->p.sig_eT);
-        if (s->torso.empty()) k_stencil<real, M_APPLY><<<std::max(1, I.nseg), kThreads, 0, s->stream>>>(I, io);
-        else k_stencil<real, M_APPLY_BATH><<<std::max(1, I.nseg), kThreads, 0, s->stream>>>(I, io);
+        if (s->torso.empty()) k_stencil<real, M_APPLY><<<std::max(1, I.nseg), kThreads, kSmemBytes<real, M_APPLY>, s->stream>>>(I, io);
+        else k_stencil<real, M_APPLY_BATH><<<std::max(1, I.nseg), kThreads, kSmemBytes<real, M_APPLY_BATH>, s->stream>>>(I, io);
         CK(cudaGetLastError());
         CK(cudaMemcpyAsync(h.data(), s->x[1], sizeof(real) * s->n, cudaMemcpyDeviceToHost, s->stream));
         CK(cudaStreamSynchronize(s->stream));
@@ -1487,7 +1550,45 @@ constexpr size_t kNoAllocBytes =
 static_assert(sizeof(Ctl) <= kNoAllocCtlBytes, "control block must fit its slot");
 constexpr int kNoAllocMaxDevices = 256;
 std::mutex g_noalloc_mu;
-void *g_noalloc_addr[kNoAllocMaxDevices] = {};
+struct NoAllocAddr {
+    unsigned long long ctx = 0;   // context the address belongs to (0: unknown)
+    void *addr = nullptr;
+};
+NoAllocAddr g_noalloc_addr[kNoAllocMaxDevices];
+
+// Identity of the calling thread's current CUDA context, through the runtime's
+// driver entry points (cuCtxGetCurrent, cuCtxGetId); 0 if it cannot be told.
+// A context that is torn down and recreated (a device reset) gets a new
+// identity, and with it a new address of the library's device arrays.
+unsigned long long current_context_id()
+{
+    using GetCurrent = CUresult(CUDAAPI *)(CUcontext *);
+    using GetId = CUresult(CUDAAPI *)(CUcontext, unsigned long long *);
+    static const GetCurrent get_current = [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 4000, cudaEnableDefault, &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess) {
+            cudaGetLastError();
+            p = nullptr;
+        }
+        return reinterpret_cast<GetCurrent>(p);
+    }();
+    static const GetId get_id = [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess) {
+            cudaGetLastError();
+            p = nullptr;
+        }
+        return reinterpret_cast<GetId>(p);
+    }();
+    CUcontext c = nullptr;
+    unsigned long long id = 0;
+    if (!get_current || !get_id || get_current(&c) != CUDA_SUCCESS || !c || get_id(c, &id) != CUDA_SUCCESS) return 0;
+    return id;
+}
 }  // namespace
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
@@ -1495,7 +1596,9 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 namespace {
 // Device address of the static scratch on the current device.  In host code
 // the array's name is only a stand-in, so the address is looked up once per
-// device (with that device current) and cached.
+// device and context (with that device current) and cached; a new context on
+// the device (after a reset) looks it up again.  Without a context identity
+// it is looked up on every call (the lookup allocates nothing).
 ep_status noalloc_scratch(ep_sim *s, unsigned char **out)
 {
     int dev = 0;
@@ -1505,17 +1608,20 @@ ep_status noalloc_scratch(ep_sim *s, unsigned char **out)
         return fail(s, EP_ECUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
     }
     if (dev < 0 || dev >= kNoAllocMaxDevices) return fail(s, EP_EINVAL, "device ordinal out of range");
+    const unsigned long long ctx = current_context_id();
     std::lock_guard<std::mutex> lock(g_noalloc_mu);
-    if (!g_noalloc_addr[dev]) {
+    NoAllocAddr &slot = g_noalloc_addr[dev];
+    if (!slot.addr || ctx == 0 || slot.ctx != ctx) {
         void *p = nullptr;
         e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
         if (e != cudaSuccess || !p) {
             cudaGetLastError();
             return fail(s, EP_ECUDA, std::string("cudaGetSymbolAddress(scratch): ") + cudaGetErrorString(e));
         }
-        g_noalloc_addr[dev] = p;
+        slot.addr = p;
+        slot.ctx = ctx;
     }
-    *out = (unsigned char *)g_noalloc_addr[dev];
+    *out = (unsigned char *)slot.addr;
     return EP_OK;
 }
 }  // namespace
@@ -1828,10 +1934,10 @@ ep_status build_batch_graph(ep_batch *b)
         for (int gi = 0; gi < ngroups; ++gi) CKB(cudaGraphConditionalHandleCreate(&hg[gi], body, 1, 0));
 
     CKB(cudaStreamBeginCaptureToGraph(st, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
-    if (b->model == EP_MONO) k_stencil_batch<float, M_PAR_MONO><<<gs, kThreads, 0, st>>>(b->d_inst, b->d_seg);
-    else k_stencil_batch<float, M_PAR_BI><<<gs, kThreads, 0, st>>>(b->d_inst, b->d_seg);
+    if (b->model == EP_MONO) k_stencil_batch<float, M_PAR_MONO><<<gs, kThreads, kSmemBytes<float, M_PAR_MONO>, st>>>(b->d_inst, b->d_seg);
+    else k_stencil_batch<float, M_PAR_BI><<<gs, kThreads, kSmemBytes<float, M_PAR_BI>, st>>>(b->d_inst, b->d_seg);
     if (b->model == EP_BI) {
-        k_stencil_batch<float, M_RHS><<<gs, kThreads, 0, st>>>(b->d_inst, b->d_seg);
+        k_stencil_batch<float, M_RHS><<<gs, kThreads, kSmemBytes<float, M_RHS>, st>>>(b->d_inst, b->d_seg);
         k_comp_mean_batch<float><<<gc, kRedThreads, 0, st>>>(b->d_inst, b->d_chunk, nc, (int)RED_B);
         k_comp_subtract_batch<float><<<gc, kRedThreads, 0, st>>>(b->d_inst, b->d_chunk, nc);
         for (int gi = 0; gi < ngroups; ++gi) {
@@ -1874,8 +1980,8 @@ ep_status build_batch_graph(ep_batch *b)
                 CKB(cudaStreamWaitEvent(a, b->ev_fork, 0));
                 const Inst<float> I = make_inst<float>(b->slot[b->order[gr.solo[j]]]);
                 for (int i = 0; i < spc; ++i) {
-                    if (gr.cheb) k_stencil<float, M_JAC_CHEB><<<I.nseg, kThreads, 0, a>>>(I, no_io<float>());
-                    else k_stencil<float, M_JAC><<<I.nseg, kThreads, 0, a>>>(I, no_io<float>());
+                    if (gr.cheb) k_stencil<float, M_JAC_CHEB><<<I.nseg, kThreads, kSmemBytes<float, M_JAC_CHEB>, a>>>(I, no_io<float>());
+                    else k_stencil<float, M_JAC><<<I.nseg, kThreads, kSmemBytes<float, M_JAC>, a>>>(I, no_io<float>());
                 }
                 CKB(cudaEventRecord(b->ev_join[j], a));
             }
@@ -1883,8 +1989,8 @@ ep_status build_batch_graph(ep_batch *b)
             if (gr.packed_items > 0)
                 for (int i = 0; i < spc; ++i) {
                     const int gp = grid_of(gr.packed_items, 1 << 30);
-                    if (gr.cheb) k_stencil_active<float, M_JAC_CHEB><<<gp, kThreads, 0, b->side>>>(gi_inst, b->d_act, gn);
-                    else k_stencil_active<float, M_JAC><<<gp, kThreads, 0, b->side>>>(gi_inst, b->d_act, gn);
+                    if (gr.cheb) k_stencil_active<float, M_JAC_CHEB><<<gp, kThreads, kSmemBytes<float, M_JAC_CHEB>, b->side>>>(gi_inst, b->d_act, gn);
+                    else k_stencil_active<float, M_JAC><<<gp, kThreads, kSmemBytes<float, M_JAC>, b->side>>>(gi_inst, b->d_act, gn);
                 }
             for (int j = 0; j < nsolo; ++j) CKB(cudaStreamWaitEvent(b->side, b->ev_join[j], 0));
             k_active_list<float><<<1, kActThreads, 0, b->side>>>(gi_inst, gi_packed, gn, b->d_act, b->d_counts,
@@ -2022,9 +2128,9 @@ ep_status ep_batch_step(ep_batch *b, int n_steps)
     for (int r = 0; r < b->ninst; ++r) {
         ep_sim *s = b->slot[b->order[r]];
         CKB(cudaStreamSynchronize(s->stream));
-        // flags of this call start clear
-        const int zero = 0;
-        CKB(cudaMemcpyAsync((char *)s->ctl + offsetof(Ctl, noconv), &zero, sizeof(int), cudaMemcpyHostToDevice, s0));
+        // flags of this call (non-finite, diverged, not converged) start clear
+        const int zero[3] = {0, 0, 0};
+        CKB(cudaMemcpyAsync((char *)s->ctl + offsetof(Ctl, nonfinite), zero, sizeof(zero), cudaMemcpyHostToDevice, s0));
     }
     const long long n = n_steps;
     CKB(cudaMemcpyAsync(b->d_steps_left, &n, sizeof(n), cudaMemcpyHostToDevice, s0));
@@ -2111,8 +2217,8 @@ ep_status ep_batch_autotune(ep_batch *b, int trial_sweeps)
             for (const ep_batch::Group &gr : b->groups) {
                 const int gs = grid_of(gr.nseg, 1 << 30);
                 auto sweep = [&]() {
-                    if (gr.cheb) k_stencil_batch<float, M_JAC_CHEB><<<gs, kThreads, 0, s0>>>(b->d_inst, b->d_seg + gr.seg0);
-                    else k_stencil_batch<float, M_JAC><<<gs, kThreads, 0, s0>>>(b->d_inst, b->d_seg + gr.seg0);
+                    if (gr.cheb) k_stencil_batch<float, M_JAC_CHEB><<<gs, kThreads, kSmemBytes<float, M_JAC_CHEB>, s0>>>(b->d_inst, b->d_seg + gr.seg0);
+                    else k_stencil_batch<float, M_JAC><<<gs, kThreads, kSmemBytes<float, M_JAC>, s0>>>(b->d_inst, b->d_seg + gr.seg0);
                 };
                 sweep();
                 CKB(cudaEventRecord(e0, s0));

@@ -14,7 +14,7 @@ namespace gbep {
 // nT and M = sum f f^T over the tissue voxels; with torso records also the
 // domain flags Td (tissue or torso), domain-pair counts cntd and the torso
 // voxel count nB.
-__device__ inline void vertex_static(int nx, int ny, int nz, const ushort4 *rec, int I, int J, int K,
+__device__ inline void vertex_static(int nx, int ny, int nz, const float4 *rec, int I, int J, int K,
                                      int cnt[3], int &nT, double M[6], bool T[2][2][2], int cntd[3], int &nB,
                                      bool Td[2][2][2])
 {
@@ -27,11 +27,11 @@ __device__ inline void vertex_static(int nx, int ny, int nz, const ushort4 *rec,
                 T[u][t][s] = Td[u][t][s] = false;
                 f[u][t][s][0] = f[u][t][s][1] = f[u][t][s][2] = 0.0;
                 if (in) {
-                    const ushort4 r = rec[(long long)i + (long long)nx * ((long long)j + (long long)ny * k)];
+                    const float4 r = rec[(long long)i + (long long)nx * ((long long)j + (long long)ny * k)];
                     if (rec_tissue(r)) {
                         Td[u][t][s] = true;
                         T[u][t][s] = !rec_bath(r);
-                        f[u][t][s][0] = h2f(r.x); f[u][t][s][1] = h2f(r.y); f[u][t][s][2] = h2f(r.z);
+                        f[u][t][s][0] = r.x; f[u][t][s][1] = r.y; f[u][t][s][2] = r.z;
                     }
                 }
             }
@@ -59,40 +59,42 @@ __device__ inline void vertex_static(int nx, int ny, int nz, const ushort4 *rec,
         }
 }
 
-// Dhat_q = sum over the 8 vertices of q of c^T Shat c, c_a = +-T(partner) r_a,
-// Shat = nT sT I + dS M; D_q = Dhat_q / (8 dx^2).  Writes the fp16 record.
-// With a torso (nullable), its voxels outside the tissue get the record
-// (-0, 0, 0, .): in the domain, zero fibre, tagged; a tissue fibre lane that
-// rounds to -0 is stored as +0 so that the tag stays unique.
+// The fp32 record of every voxel: the caller's fibre (fx, fy, fz) on the tissue,
+// lane 3 filled by k_build_diag, -1 there off the records' domain.  With a torso
+// (nullable), its voxels outside the tissue get the record (-0, 0, 0, .): in the
+// domain, zero fibre, tagged; a tissue fibre lane 0 of -0 is stored as +0 so that
+// the tag stays unique.
 __global__ void k_build_records(int nx, int ny, int nz, const float *fib, const uint8_t *mask,
-                                const uint8_t *torso, ushort4 *rec)
+                                const uint8_t *torso, float4 *rec)
 {
     const long long n = (long long)nx * ny * nz;
     for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
-        ushort4 r;
+        float4 r;
         if (mask[q]) {
-            r.x = __half_as_ushort(__float2half_rn(fib[3 * q + 0]));
-            r.y = __half_as_ushort(__float2half_rn(fib[3 * q + 1]));
-            r.z = __half_as_ushort(__float2half_rn(fib[3 * q + 2]));
-            if (r.x == kBathTag) r.x = 0;
-            r.w = 0;   // 1/Dhat filled by k_build_diag
+            r.x = fib[3 * q + 0];
+            r.y = fib[3 * q + 1];
+            r.z = fib[3 * q + 2];
+            if (__float_as_uint(r.x) == kBathTag) r.x = 0.0f;
+            r.w = 0.0f;   // 1/Dhat filled by k_build_diag
         } else if (torso && torso[q]) {
-            r.x = kBathTag;
-            r.y = r.z = 0;
-            r.w = 0;
+            r.x = __uint_as_float(kBathTag);
+            r.y = r.z = 0.0f;
+            r.w = 0.0f;
         } else {
-            r.x = r.y = r.z = 0;
-            r.w = kNonTissue;
+            r.x = r.y = r.z = 0.0f;
+            r.w = kNonTissueW;
         }
         rec[q] = r;
     }
 }
 
+// Dhat_q = sum over the 8 vertices of q of c^T Shat c, c_a = +-T(partner) r_a,
+// Shat = nT sT I + dS M; D_q = Dhat_q / (8 dx^2).
 // Dhat of voxel (i, j, k) for the operator with sigma_T = sT and
 // sigma_L - sigma_T = dS (tissue term, tissue voxels), plus with so > 0 the
 // torso term so nB I over domain pairs (torso records): the diagonal of L is
 // C Dhat, C = 1 / (8 dx^2).
-__device__ inline double diag_hat(int nx, int ny, int nz, const ushort4 *rec, int i, int j, int k, double sT,
+__device__ inline double diag_hat(int nx, int ny, int nz, const float4 *rec, int i, int j, int k, double sT,
                                   double dS, double so)
 {
     double D = 0.0;
@@ -128,16 +130,16 @@ __device__ inline double diag_hat(int nx, int ny, int nz, const ushort4 *rec, in
     return D;
 }
 
-__global__ void k_build_diag(int nx, int ny, int nz, double sT, double dS, double so, const ushort4 *rec,
-                             ushort4 *rec_out)
+__global__ void k_build_diag(int nx, int ny, int nz, double sT, double dS, double so, const float4 *rec,
+                             float4 *rec_out)
 {
     const long long n = (long long)nx * ny * nz;
     for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
-        ushort4 r = rec[q];
+        float4 r = rec[q];
         if (!rec_tissue(r)) { rec_out[q] = r; continue; }
         const int i = (int)(q % nx), j = (int)((q / nx) % ny), k = (int)(q / ((long long)nx * ny));
         const double D = diag_hat(nx, ny, nz, rec, i, j, k, sT, dS, so);
-        r.w = D > 0.0 ? __half_as_ushort(__float2half_rn((float)(1.0 / D))) : (unsigned short)0;
+        r.w = D > 0.0 ? (float)(1.0 / D) : 0.0f;
         rec_out[q] = r;
     }
 }
@@ -145,7 +147,7 @@ __global__ void k_build_diag(int nx, int ny, int nz, double sT, double dS, doubl
 // Implicit-Euler Jacobi (Eq. iejac1): inv_q = 1 / (1 + a C Dhat_q) for the
 // intracellular operator on the tissue, 0 elsewhere.
 template <typename real>
-__global__ void k_build_ie_diag(int nx, int ny, int nz, double sT, double dS, double aC, const ushort4 *rec,
+__global__ void k_build_ie_diag(int nx, int ny, int nz, double sT, double dS, double aC, const float4 *rec,
                                 real *inv)
 {
     const long long n = (long long)nx * ny * nz;
@@ -328,7 +330,7 @@ __global__ void __launch_bounds__(kRedThreads) k_ie_finish(Inst<real> I)
 // ---------------------------------------------------------------------------
 // Lanczos process for the spectrum of D^-1 A (Chebyshev interval at set-up),
 // in the D inner product <x, y> = sum D x y, where D^-1 A is self-adjoint;
-// D_q = C / (1/Dhat_q) from the fp16 record, voxels with an empty row left
+// D_q = C / (1/Dhat_q) from the fp32 record, voxels with an empty row left
 // out.  One CTA per tissue chunk; FP64 partials (two per chunk in k_lz_proj);
 // the item that completes a launch finishes it.  Scalars: lz[0] alpha, lz[1] beta of the current step,
 // lz[2 + 2j] alpha_j, lz[3 + 2j] beta_{j+1}.
@@ -336,7 +338,7 @@ __global__ void __launch_bounds__(kRedThreads) k_ie_finish(Inst<real> I)
 template <typename real>
 __device__ __forceinline__ double lz_diag(const Inst<real> &I, int q)
 {
-    const float h = h2f(I.rec[q].w);
+    const float h = I.rec[q].w;
     return h > 0.0f ? (double)I.C / (double)h : 0.0;
 }
 

@@ -3,7 +3,6 @@
 // block, the Mitchell-Schaeffer update and a fixed-order block reduction.
 #pragma once
 
-#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -24,8 +23,8 @@ constexpr int kMinBlocks = EP_MIN_BLOCKS;   // occupancy hint for the stencil ke
 constexpr int kTileX = 30;                  // output voxels per row (lanes 1..30)
 constexpr int kMaxStim = 8;
 constexpr unsigned kFull = 0xffffffffu;
-constexpr unsigned short kNonTissue = 0xBC00u;  // fp16 -1.0: record lane 3 of a non-tissue voxel
-constexpr unsigned short kBathTag = 0x8000u;    // fp16 -0.0 in lane 0: a torso voxel of the elliptic records
+constexpr float kNonTissueW = -1.0f;           // record lane 3 of a voxel outside the records' domain
+constexpr unsigned kBathTag = 0x80000000u;      // -0.0f in lane 0: a torso voxel of the elliptic records
 constexpr int kRedThreads = 256;            // reduction kernels
 constexpr int kChunk = 2048;                // tissue voxels per reduction chunk
 
@@ -104,7 +103,7 @@ struct Inst {
     int nseg, nchunk, ncomp, check_every;
     int max_iter, pad;
     const Seg *segs;
-    const ushort4 *rec;   // (fx, fy, fz, 1/Dhat) in fp16; lane 3 = -1 off the tissue
+    const float4 *rec;    // (fx, fy, fz, 1/Dhat) in fp32; lane 3 = -1 off the records' domain
     real *v[2], *w[2];    // state, buffer = step & 1
     real *x0, *x1;        // elliptic iterates; x0 holds v_e between steps
     real *b;              // elliptic right-hand side
@@ -155,13 +154,9 @@ __device__ __forceinline__ double cheb_weight(int k, double rho, double theta)
     return (2.0 / rho) * exp(-theta) * (1.0 + a) / (1.0 + a * exp(-2.0 * theta));
 }
 
-__device__ __forceinline__ float h2f(unsigned short b) { return __half2float(__ushort_as_half(b)); }
-__device__ __forceinline__ bool rec_tissue(const ushort4 &r) { return (r.w & 0x8000u) == 0; }
-// The same record as two packed 32-bit words: (fx | fy << 16, fz | w << 16).
-__device__ __forceinline__ bool rec_tissue(const uint2 &r) { return (int)r.y >= 0; }
-__device__ __forceinline__ bool rec_bath(const ushort4 &r) { return r.x == kBathTag; }
-__device__ __forceinline__ bool rec_bath(const uint2 &r) { return (r.x & 0xFFFFu) == kBathTag; }
-__device__ __forceinline__ float2 lo_hi_f(unsigned w) { return __half22float2(*reinterpret_cast<const __half2 *>(&w)); }
+// A record is in its domain (tissue, or tissue + torso) when the sign bit of lane 3 is clear.
+__device__ __forceinline__ bool rec_tissue(const float4 &r) { return __float_as_int(r.w) >= 0; }
+__device__ __forceinline__ bool rec_bath(const float4 &r) { return __float_as_uint(r.x) == kBathTag; }
 
 // Mitchell-Schaeffer explicit Euler (Eqs. ms1, ms2; closing branch -w/tau_close).
 template <typename real>

@@ -27,8 +27,10 @@
 // shuffle.  The plane loop is unrolled by two with two state records that
 // swap roles, so nothing is copied between planes, and the loads of plane
 // k + 1 are issued before plane k is processed.  The conductivity sums are
-// rebuilt from the fp16 fibres on every pass: on this GPU recomputing them
-// costs less than streaming precomputed FP32 coefficients.
+// rebuilt from the fp32 fibre records on every pass: on this GPU recomputing
+// them costs less than streaming precomputed per-vertex FP32 coefficients
+// (24 bytes a vertex; measured 67.7 against 72.4 us a sweep on the 256^3
+// biventricular workload, the coefficient tiles brought in by TMA).
 //
 // The same item body serves the single-instance kernels (descriptor passed by
 // value) and the batched persistent kernels (descriptor read from a device
@@ -69,7 +71,7 @@ struct ApplyIO {
 // Per-item constants and pointers, resolved once at the start of an item.
 template <typename real>
 struct Op {
-    const ushort4 *rec;
+    const float4 *rec;
     const real *src, *w, *ve, *b;   // loads
     const real *inv;                // implicit sweep: 1 / (1 + a D_i)
     real *out, *wout, *tact;        // stores (PAR: v, w, t_act; RHS: b; APPLY: out; JAC, IE: next iterate;
@@ -85,7 +87,7 @@ struct Op {
 // Loads of one plane for a lane's two voxel rows (lo = y0 + w - 1, hi = y0 + w).
 template <typename real, int MODE>
 struct Ld {
-    uint2 rLo, rHi;    // fp16 records as packed words
+    float4 rLo, rHi;   // fp32 records
     real uLo, uHi;
     real wLo, wHi;     // PAR
     real veLo, veHi;   // PAR_BI
@@ -126,12 +128,12 @@ __device__ __forceinline__ void load_plane(const Op<real> &o, int k, bool lo_in,
                                            int plane, Ld<real, MODE> &L)
 {
     const bool kin = (unsigned)k < (unsigned)o.nz;
-    L.rLo = L.rHi = make_uint2(0u, (unsigned)kNonTissue << 16);
+    L.rLo = L.rHi = make_float4(0.f, 0.f, 0.f, kNonTissueW);
     L.uLo = L.uHi = L.veLo = L.veHi = L.bLo = L.iLo = real(0);
     L.wLo = L.wHi = real(1);
     if (kin && lo_in) {
         const int q = qlo + k * plane;
-        L.rLo = __ldg(reinterpret_cast<const uint2 *>(o.rec) + q);
+        L.rLo = __ldg(o.rec + q);
         L.uLo = __ldg(o.src + q);
         if (MODE == M_PAR_MONO || MODE == M_PAR_BI || MODE == M_IE_RHS) L.wLo = __ldg(o.w + q);
         if (MODE == M_PAR_BI || MODE == M_IE_RHS) L.veLo = __ldg(o.ve + q);
@@ -140,7 +142,7 @@ __device__ __forceinline__ void load_plane(const Op<real> &o, int k, bool lo_in,
     }
     if (kin && hi_in) {
         const int q = qhi + k * plane;
-        L.rHi = __ldg(reinterpret_cast<const uint2 *>(o.rec) + q);
+        L.rHi = __ldg(o.rec + q);
         L.uHi = __ldg(o.src + q);
         if (MODE == M_PAR_MONO || MODE == M_PAR_BI || MODE == M_IE_RHS) L.wHi = __ldg(o.w + q);
         if (MODE == M_PAR_BI || MODE == M_IE_RHS) L.veHi = __ldg(o.ve + q);
@@ -167,9 +169,8 @@ __device__ __forceinline__ void plane_step(const Inst<real> &I, const Op<real> &
     const bool dlo = rec_tissue(L.rLo), dhi = rec_tissue(L.rHi);   // in the records' domain
     const bool tlo = TT ? dlo && !rec_bath(L.rLo) : dlo;           // tissue
     const bool thi = TT ? dhi && !rec_bath(L.rHi) : dhi;
-    const float2 alo = lo_hi_f(L.rLo.x), blo = lo_hi_f(L.rLo.y), ahi = lo_hi_f(L.rHi.x), bhi = lo_hi_f(L.rHi.y);
-    const real flo0 = (real)alo.x, flo1 = (real)alo.y, flo2 = (real)blo.x;
-    const real fhi0 = (real)ahi.x, fhi1 = (real)ahi.y, fhi2 = (real)bhi.x;
+    const real flo0 = (real)L.rLo.x, flo1 = (real)L.rLo.y, flo2 = (real)L.rLo.z;
+    const real fhi0 = (real)L.rHi.x, fhi1 = (real)L.rHi.y, fhi2 = (real)L.rHi.z;
     real ulo, uhi;
     C.e0 = C.e1 = C.e2 = real(0);
     if (MODE == M_PAR_MONO || MODE == M_PAR_BI || MODE == M_IE_RHS) {
@@ -187,7 +188,7 @@ __device__ __forceinline__ void plane_step(const Inst<real> &I, const Op<real> &
     } else {
         ulo = dlo ? L.uLo : real(0);
         uhi = dhi ? L.uHi : real(0);
-        if (kJac<MODE>) { C.e0 = L.bLo; C.e1 = (real)blo.y; C.e2 = L.iLo; }
+        if (kJac<MODE>) { C.e0 = L.bLo; C.e1 = (real)L.rLo.w; C.e2 = L.iLo; }
         if (MODE == M_IE) { C.e0 = L.bLo; C.e1 = L.iLo; }
     }
     C.uLo = ulo;
@@ -396,7 +397,7 @@ struct Ring {
     static constexpr int D = sizeof(real) == 4 ? 4 : 2;   // divides the unroll of 4; static smem < 48 KB
     static constexpr int NX = 2;   // b and x_{k-1} (Chebyshev) of row lo (Jacobi sweep), f and 1/(1+aD) of
                                    // row lo (implicit sweep), or w of rows lo, hi (monodomain step)
-    uint2 rec[D][2][kThreads];   // fp16 records of rows lo / hi
+    float4 rec[D][2][kThreads];  // records of rows lo / hi
     real u[D][2][kThreads];
     real x[D][NX][kThreads];
 };
@@ -414,6 +415,19 @@ struct StencilSmem {
     typename std::conditional<kRinged<real, MODE>, Ring<real, MODE>, NoRing>::type ring;
     typename std::conditional<kTwoTerm<MODE>, TorsoSmem<real>, NoTorso>::type tor;
 };
+
+// Bytes of shared memory of a stencil CTA (dynamic: with the ring and fp32 records the
+// larger instances exceed the 48 KB of static shared memory; the host raises the limit).
+template <typename real, int MODE>
+constexpr size_t kSmemBytes = sizeof(StencilSmem<real, MODE>);
+
+// The dynamic shared memory of the launch, as an object of type T.
+template <typename T>
+__device__ __forceinline__ T &dyn_smem()
+{
+    extern __shared__ __align__(16) unsigned char ep_dyn_smem[];
+    return *reinterpret_cast<T *>(ep_dyn_smem);
+}
 
 template <int BYTES>
 __device__ __forceinline__ void cp_async_n(void *dst, const void *src)
@@ -435,25 +449,25 @@ __device__ __forceinline__ void ring_issue(const Op<real> &o, Ring<real, MODE> &
     const bool kin = (unsigned)k < (unsigned)o.nz;
     if (kin && lo_in) {
         const int q = qlo + k * plane;
-        cp_async_n<8>(&R.rec[slot][0][t], o.rec + q);
+        cp_async_n<16>(&R.rec[slot][0][t], o.rec + q);
         cp_async_n<sizeof(real)>(&R.u[slot][0][t], o.src + q);
         cp_async_n<sizeof(real)>(&R.x[slot][0][t], (MODE == M_PAR_MONO ? o.w : o.b) + q);
         if (MODE == M_IE) cp_async_n<sizeof(real)>(&R.x[slot][1][t], o.inv + q);
         // x_{k-1} sits where this thread will write x_{k+1} of this voxel, one plane later
         if (kCheb<MODE> && o.cheb) cp_async_n<sizeof(real)>(&R.x[slot][1][t], o.out + q);
     } else {
-        R.rec[slot][0][t] = make_uint2(0u, (unsigned)kNonTissue << 16);
+        R.rec[slot][0][t] = make_float4(0.f, 0.f, 0.f, kNonTissueW);
         R.u[slot][0][t] = real(0);
         R.x[slot][0][t] = MODE == M_PAR_MONO ? real(1) : real(0);
         if (MODE == M_IE || kCheb<MODE>) R.x[slot][1][t] = real(0);
     }
     if (kin && hi_in) {
         const int q = qhi + k * plane;
-        cp_async_n<8>(&R.rec[slot][1][t], o.rec + q);
+        cp_async_n<16>(&R.rec[slot][1][t], o.rec + q);
         cp_async_n<sizeof(real)>(&R.u[slot][1][t], o.src + q);
         if (MODE == M_PAR_MONO) cp_async_n<sizeof(real)>(&R.x[slot][Ring<real, MODE>::NX - 1][t], o.w + q);
     } else {
-        R.rec[slot][1][t] = make_uint2(0u, (unsigned)kNonTissue << 16);
+        R.rec[slot][1][t] = make_float4(0.f, 0.f, 0.f, kNonTissueW);
         R.u[slot][1][t] = real(0);
         if (MODE == M_PAR_MONO) R.x[slot][Ring<real, MODE>::NX - 1][t] = real(1);
     }
@@ -494,6 +508,50 @@ __device__ __forceinline__ void ring_plane(const Inst<real> &I, const Op<real> &
     cp_async_wait<D - 1>();
     ring_read<real, MODE>(R, slot, L, o.cheb != 0);
     plane_step<real, MODE>(I, o, g, k, k > kbeg, k > kbeg + 1, P, Cn, L, sF, sT, ts, check, acc);
+}
+
+// End of a sweep's work item: count its arrival; on a checking sweep the item
+// that arrives last sums the FP64 partial norms in a fixed order and decides
+// the stop (converged, diverged, non-finite) in the control block.
+template <typename real>
+__device__ __forceinline__ void sweep_finish(const Inst<real> &I, int sweep, int item, int nitems, bool check,
+                                             float acc, double *sred, int *sflag)
+{
+    Ctl *ctl = I.ctl;
+    if (!check) {   // count the arrival; nobody waits on it within this launch
+        if (threadIdx.x == 0) atomicAdd(&ctl->jarrive, 1ull);
+        return;
+    }
+    // residual norm of this sweep's input: per-thread FP32 partial over its few voxels,
+    // FP64 above; deterministic fixed-order reduction by the item that arrives last
+    const double tot = block_sum<kThreads>((double)acc, sred);
+    if (threadIdx.x == 0) {
+        I.partials[item] = tot;
+        __threadfence();
+        const unsigned long long last = (unsigned long long)(sweep + 1) * (unsigned long long)nitems - 1ull;
+        *sflag = atomicAdd(&ctl->jarrive, 1ull) == last;
+    }
+    __syncthreads();
+    if (*sflag) {
+        __threadfence();
+        double s = 0;
+        for (int i = threadIdx.x; i < nitems; i += kThreads) s += ((volatile double *)I.partials)[i];
+        s = block_sum<kThreads>(s, sred);
+        if (threadIdx.x == 0) {
+            const int j = sweep + 1;
+            ctl->sweep = j;
+            ctl->rnorm2 = s;
+            if (!(s == s) || isinf(s)) {
+                ctl->nonfinite = 1; ctl->done = 1; ctl->iters = j;
+            } else if (s <= ctl->thresh2) {
+                ctl->converged = 1; ctl->done = 1; ctl->iters = j;
+            } else if (s > I.div_factor * ctl->bnorm2) {
+                ctl->diverged = 1; ctl->noconv = 1; ctl->done = 1; ctl->iters = j;
+            }
+            __threadfence();
+        }
+        __syncthreads();
+    }
 }
 
 // One work item (segment) of one instance.  item / nitems: index of this item
@@ -638,43 +696,7 @@ __device__ __forceinline__ void stencil_item(const Inst<real> &I, int seg_index,
         }
     }
 
-    if (kSweep<MODE>) {
-        if (!check) {   // count the arrival; nobody waits on it within this launch
-            if (threadIdx.x == 0) atomicAdd(&ctl->jarrive, 1ull);
-            return;
-        }
-        // residual norm of this sweep's input: per-thread FP32 partial over its
-        // few voxels, FP64 above; deterministic fixed-order reduction by the
-        // item that arrives last
-        const double tot = block_sum<kThreads>((double)acc, sm.sred);
-        if (threadIdx.x == 0) {
-            I.partials[item] = tot;
-            __threadfence();
-            const unsigned long long last = (unsigned long long)(sweep + 1) * (unsigned long long)nitems - 1ull;
-            sm.sflag = atomicAdd(&ctl->jarrive, 1ull) == last;
-        }
-        __syncthreads();
-        if (sm.sflag) {
-            __threadfence();
-            double s = 0;
-            for (int i = threadIdx.x; i < nitems; i += kThreads) s += ((volatile double *)I.partials)[i];
-            s = block_sum<kThreads>(s, sm.sred);
-            if (threadIdx.x == 0) {
-                const int j = sweep + 1;
-                ctl->sweep = j;
-                ctl->rnorm2 = s;
-                if (!(s == s) || isinf(s)) {
-                    ctl->nonfinite = 1; ctl->done = 1; ctl->iters = j;
-                } else if (s <= ctl->thresh2) {
-                    ctl->converged = 1; ctl->done = 1; ctl->iters = j;
-                } else if (s > I.div_factor * ctl->bnorm2) {
-                    ctl->diverged = 1; ctl->noconv = 1; ctl->done = 1; ctl->iters = j;
-                }
-                __threadfence();
-            }
-            __syncthreads();
-        }
-    }
+    if (kSweep<MODE>) sweep_finish<real>(I, sweep, item, nitems, check, acc, sm.sred, &sm.sflag);
 }
 
 // Single instance: one CTA per segment.  The two-term modes keep both terms'
@@ -682,7 +704,7 @@ __device__ __forceinline__ void stencil_item(const Inst<real> &I, int seg_index,
 template <typename real, int MODE>
 __global__ void __launch_bounds__(kThreads, kTwoTerm<MODE> ? 2 : kMinBlocks) k_stencil(Inst<real> I, ApplyIO<real> io)
 {
-    __shared__ StencilSmem<real, MODE> sm;
+    StencilSmem<real, MODE> &sm = dyn_smem<StencilSmem<real, MODE>>();
     if (kSweep<MODE> && I.ctl->done) return;   // converged earlier: queued sweeps are no-ops
     const int nitems = I.nitems_all > 0 ? I.nitems_all : (int)gridDim.x;
     stencil_item<real, MODE>(I, blockIdx.x, I.item0 + (int)blockIdx.x, nitems, &io, sm);
@@ -709,7 +731,7 @@ template <typename real, int MODE>
 __global__ void __launch_bounds__(kThreads, kMinBlocks)
 k_stencil_batch(const Inst<real> *insts, const BItem *items)
 {
-    __shared__ StencilSmem<real, MODE> sm;
+    StencilSmem<real, MODE> &sm = dyn_smem<StencilSmem<real, MODE>>();
     __shared__ Inst<real> sI;
     const BItem it = items[blockIdx.x];
     if (kJac<MODE> && *(volatile int *)&insts[it.inst].ctl->done) return;
@@ -728,7 +750,7 @@ template <typename real, int MODE>
 __global__ void __launch_bounds__(kThreads, kMinBlocks)
 k_stencil_active(const Inst<real> *insts, const ActRec *act, int n)
 {
-    __shared__ StencilSmem<real, MODE> sm;
+    StencilSmem<real, MODE> &sm = dyn_smem<StencilSmem<real, MODE>>();
     __shared__ Inst<real> sI;
     __shared__ int sk;
     const int i = blockIdx.x;

@@ -38,7 +38,7 @@ def _pair(case, state_seed, precision):
 def test_implicit_monodomain_fp64_matches_oracle(shape):
     """Three implicit steps: same sweeps to the same stop rule, so the states
     agree to rounding and the sweep counts are equal."""
-    c = _ie_case(21, shape, W.MONO, dt=0.05, rel_tol=1e-10, check_every=3)
+    c = _ie_case(21, shape, W.MONO, dt=0.05, rel_tol=1e-10, check_every=3).fibres_as_float32()
     s, o = _pair(c, 21, ep.EP_FP64)
     total = 0
     for _ in range(3):
@@ -53,7 +53,7 @@ def test_implicit_monodomain_fp64_matches_oracle(shape):
 
 
 def test_implicit_bidomain_fp64_matches_oracle():
-    c = _ie_case(22, (13, 9, 8), W.BI, rel_tol=1e-11, check_every=5)
+    c = _ie_case(22, (13, 9, 8), W.BI, rel_tol=1e-11, check_every=5).fibres_as_float32()
     c.params.max_iter = 200000
     s, o = _pair(c, 22, ep.EP_FP64)
     for _ in range(2):
@@ -91,7 +91,7 @@ def test_implicit_fp32_small_shell_against_oracle(model):
 
 
 def test_implicit_solve_cap_is_reported():
-    c = _ie_case(23, (16, 12, 10), W.MONO, rel_tol=1e-14, check_every=2)
+    c = _ie_case(23, (16, 12, 10), W.MONO, rel_tol=1e-14, check_every=2).fibres_as_float32()
     c.params.max_iter = 3
     s, o = _pair(c, 23, ep.EP_FP64)
     stats = s.step(1, allow_noconv=True)

@@ -14,10 +14,16 @@ import workloads as W
 
 pytestmark = pytest.mark.gpu
 
-# FP32 stencil: terms are O(sigma/dx^2 |u|); 27-point sums in FP32 with fp16-exact
-# fibres give relative errors of a few 1e-7 of the largest term.
+# FP32 stencil: terms are O(sigma/dx^2 |u|); 27-point sums in FP32 give relative
+# errors of a few 1e-7 of the largest term.
 FP32_OP_RTOL = 2e-5
+# FP64 stencil on the very fibres the oracle uses (float32 values, the input type
+# of ep_set_fibres): rounding of the sums only.
 FP64_OP_RTOL = 1e-12
+# FP64 stencil on a caller's FP64 fibres, which the library receives as float32:
+# |f32(f) - f| <= 2^-24 |f| per component moves each tensor by at most
+# 2^-23 (sig_L - sig_T), a few 1e-7 of the largest term.
+FP64_CALLER_OP_RTOL = 2e-6
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -67,8 +73,14 @@ def _op_case(kind, seed=0):
 @pytest.mark.parametrize("kind", ["random", "ragged_small", "wide", "full", "isolated", "sheet", "column", "edges",
                                   "single_in_tile"])
 @pytest.mark.parametrize("precision", [ep.EP_FP32, ep.EP_FP64])
-def test_operator_matches_oracle(kind, precision):
+@pytest.mark.parametrize("fibres", ["caller", "float32"])
+def test_operator_matches_oracle(kind, precision, fibres):
+    """One operator application against the oracle's, element by element.
+    "caller": the oracle takes the FP64 fibres as generated, the library their
+    float32 values through ep_set_fibres; "float32": both take the float32 values."""
     c = _op_case(kind)
+    if fibres == "float32":
+        c = c.fibres_as_float32()
     g = oracle.Grid.from_case(c)
     s = _sim(c, precision=precision)
     rng = np.random.default_rng(1)
@@ -78,7 +90,8 @@ def test_operator_matches_oracle(kind, precision):
         ref = g.apply_L(sL, sT, np.where(t, u, 0.0))
         got = s.apply_operator(sL, sT, u)
         scale = max(np.abs(ref).max(), 1e-30)
-        tol = FP64_OP_RTOL if precision == ep.EP_FP64 else FP32_OP_RTOL
+        tol = FP32_OP_RTOL if precision == ep.EP_FP32 else (FP64_OP_RTOL if fibres == "float32"
+                                                              else FP64_CALLER_OP_RTOL)
         assert np.all(got[~t] == 0.0)
         np.testing.assert_allclose(got, ref, rtol=0, atol=tol * scale)
     s.close()
@@ -95,7 +108,7 @@ def _pair(case, state_seed, precision):
 
 @pytest.mark.parametrize("shape", [(8, 7, 6), (35, 10, 9)])
 def test_one_step_monodomain_fp64(shape):
-    c = W.random_case(2, *shape, model=W.MONO, dt=0.02)
+    c = W.random_case(2, *shape, model=W.MONO, dt=0.02).fibres_as_float32()
     s, o = _pair(c, 2, ep.EP_FP64)
     for _ in range(3):
         s.step(1)
@@ -107,13 +120,14 @@ def test_one_step_monodomain_fp64(shape):
 
 
 def test_one_step_bidomain_fp64_tight_solve():
-    c = W.random_case(3, 13, 9, 8, model=W.BI, rel_tol=1e-11, check_every=5)
+    c = W.random_case(3, 13, 9, 8, model=W.BI, rel_tol=1e-11, check_every=5).fibres_as_float32()
     c.params.max_iter = 200000
     s, o = _pair(c, 3, ep.EP_FP64)
     for _ in range(2):
         stats = s.step(1)
         assert o.step() == 0
         assert stats.converged == 1
+        assert stats.iters == o.last_iters   # the same iteration: exact diagonal, same stop rule
     st = o.state()
     np.testing.assert_allclose(s.read(ep.EP_V), st["v"], rtol=0, atol=1e-10)
     np.testing.assert_allclose(s.read(ep.EP_W), st["w"], rtol=0, atol=1e-13)

@@ -97,7 +97,7 @@ def test_binding_fails_loudly_without_library(tmp_path):
 
 def test_footprint_is_planned_on_the_host(lib):
     """ep_footprint needs no device: the layout plan is host work.  The peak
-    adds the set-up staging (fp32 fibres, mask bytes, raw fp16 records: 21
+    adds the set-up staging (fp32 fibres, mask bytes, raw fp32 records: 29
     bytes a voxel) to the resident bytes, and an FP64 handle holds its eight
     state and solve fields at 8 instead of 4 bytes a voxel."""
     import workloads as W
@@ -109,9 +109,9 @@ def test_footprint_is_planned_on_the_host(lib):
         s.close()
     n = c.n
     (r32, p32), (r64, p64) = got[ep.EP_FP32], got[ep.EP_FP64]
-    assert p32 - r32 == 21 * n and p64 - r64 == 21 * n
+    assert p32 - r32 == 29 * n and p64 - r64 == 29 * n
     assert r64 - r32 == 8 * 4 * n
-    assert r32 >= 40 * n + 4 * c.n_tissue
+    assert r32 >= 48 * n + 4 * c.n_tissue
     s = ep.Sim(5, 4, 3, 0.5, use_torch=False)
     with pytest.raises(ep.EPError) as e:
         s.footprint()
@@ -156,7 +156,7 @@ def test_footprint_counts_the_interval_estimate(lib):
 
 def test_torso_and_ecg_are_validated_and_planned_on_the_host(lib):
     """ep_set_torso / ep_set_ecg check their arguments without a device; a
-    torso adds the domain's records (8 bytes a voxel) and work items to the
+    torso adds the domain's records (16 bytes a voxel) and work items to the
     resident bytes and its staging (1 byte a voxel) to the peak; an ECG adds its
     record (3 doubles a sample)."""
     import workloads as W
@@ -166,8 +166,8 @@ def test_torso_and_ecg_are_validated_and_planned_on_the_host(lib):
     plain.set_ecg(None, 0)
     s = ep.sim_from_case(c, use_torch=False, ecg_capacity=100)
     (r0, p0), (r1, p1) = plain.footprint(), s.footprint()
-    assert p0 - r0 == 21 * c.n and p1 - r1 == 22 * c.n
-    assert r1 - r0 >= 8 * c.n + 3 * 8 * 100
+    assert p0 - r0 == 29 * c.n and p1 - r1 == 30 * c.n
+    assert r1 - r0 >= 16 * c.n + 3 * 8 * 100
     for bad in (0.0, -1.0, float("nan"), float("inf")):
         with pytest.raises(ep.EPError) as e:
             s.set_torso(c.torso, bad)

@@ -1,6 +1,9 @@
-"""ep_step_noalloc: the step variant for callers that cannot allocate device
-memory while they run (memory planned up front, real-time loops, fixed
-budgets).  Its scratch lives in one static device array inside the library.
+"""ep_step_noalloc: the step for callers that cannot allocate device memory
+while they advance the model -- code that plans all its device memory up
+front (a framework that forbids library allocations after initialisation), a
+real-time loop that must not block in an allocator, a service with a fixed
+memory budget.  Its scratch lives in one static device array inside the
+library.
 
 This file is named to be collected last, so a run that stops at the first
 failure has run every other test before it.  It must pass both on its own in
@@ -24,30 +27,54 @@ def _built():
     ep.load()
 
 
-def _pair(case, seed):
-    v, w, ve = W.random_state(seed, case)
-    a = ep.sim_from_case(case)
-    b = ep.sim_from_case(case)
-    for s in (a, b):
-        s.set_state(v, w, ve, 0)   # set-up (the allocating part) happens here
-    return a, b
+class CountingAllocator:
+    """torch's caching allocator behind the library's dev_alloc / dev_free
+    hooks, counting the calls."""
+
+    def __init__(self):
+        self.alloc, self.free = ep.torch_allocator()
+        self.n_alloc = self.n_free = 0
+
+    def pair(self):
+        def alloc(nbytes):
+            self.n_alloc += 1
+            return self.alloc(nbytes)
+
+        def free(ptr):
+            self.n_free += 1
+            self.free(ptr)
+
+        return alloc, free
 
 
 @pytest.mark.parametrize("model", [ep.EP_BI, ep.EP_MONO])
 def test_noalloc_step_matches_step_on_two_calls(model):
-    """Two consecutive calls of the no-allocation step give the same state as
-    two calls of ep_step, within the FP32 parity tolerance of the other tests
-    (the kernels and their order are the same, so they agree to the bit)."""
+    """Two consecutive calls of the no-allocation step give the state that two
+    calls of ep_step give, bit for bit (the same kernels in the same order;
+    ep_step only queues its sweeps through a CUDA graph), while the handle's
+    allocator hook is not called and the device's free memory does not move."""
+    import torch
     case = W.random_case(21, 37, 19, 15, model=model)   # random mask: several components
-    a, b = _pair(case, 21)
+    v, w, ve = W.random_state(21, case)
+    counter = CountingAllocator()
+    a = ep.sim_from_case(case, allocator=counter.pair())
+    b = ep.sim_from_case(case, allocator=counter.pair())
+    for s in (a, b):
+        s.set_state(v, w, ve, 0)   # set-up (the allocating part) happens here
     for _ in range(2):
         sa = a.step(1, allow_noconv=True)
+        torch.cuda.synchronize()
+        calls, free0 = counter.n_alloc, torch.cuda.mem_get_info()[0]
         sb = b.step_noalloc(1, allow_noconv=True)
-        assert sa.iters == sb.iters and sa.step == sb.step
+        torch.cuda.synchronize()
+        assert counter.n_alloc == calls, "the no-allocation step called the device allocator"
+        assert torch.cuda.mem_get_info()[0] == free0, "device free memory changed during the call"
+        assert sa.iters == sb.iters and sa.step == sb.step and sa.total_iters == sb.total_iters
         for f in FIELDS:
-            np.testing.assert_allclose(b.read(f), a.read(f), rtol=0, atol=5e-6)
+            np.testing.assert_array_equal(b.read(f), a.read(f))
     a.close()
     b.close()
+    assert counter.n_free == counter.n_alloc   # every block the handles took came back
 
 
 def test_noalloc_step_checks_setup_and_limits():

@@ -10,9 +10,12 @@ Conventions
 * Grid ``nx x ny x nz``; arrays have numpy shape ``(nz, ny, nx)`` so the flat
   C-order index is ``i + nx*(j + ny*k)`` (x fastest).
 * Voxel ``(i, j, k)`` has centre ``((i+1/2) dx, (j+1/2) dx, (k+1/2) dx)``.
-* ``mask`` is uint8 (1 = myocardium).  ``fib`` is float32 ``(nz, ny, nx, 3)``
-  whose components are exactly representable in IEEE half precision, so a
-  consumer that stores fibres as fp16 sees the identical field.
+* ``mask`` is uint8 (1 = myocardium).  ``fib`` is float64 ``(nz, ny, nx, 3)``,
+  unit or zero, as generated (no rounding to any storage precision): the FP64
+  oracle takes it as it is and the library takes its float32 values (the type
+  of ``ep_set_fibres``), so parity measures what the library does with a
+  caller's fibres.  :meth:`Case.fibres_as_float32` gives the variant whose
+  values both sides see exactly, for tests that pin FP64 arithmetic.
 * Units: mm, ms, mS/mm; ``v`` dimensionless (0 rest, 1 peak).
 
 Workload recipes (sizes and structure follow the thesis' experiments: the
@@ -89,7 +92,7 @@ class Case:
     nz: int
     dx: float
     mask: np.ndarray          # uint8 (nz, ny, nx)
-    fib: np.ndarray           # float32 (nz, ny, nx, 3), fp16-exact
+    fib: np.ndarray           # float64 (nz, ny, nx, 3), unit or zero
     params: Params
     stimuli: List[Stimulus]
     model: int = BI
@@ -107,16 +110,19 @@ class Case:
         return int(self.mask.sum())
 
     def fib_flat(self) -> np.ndarray:
-        """Fibres as a contiguous float32 array of length 3n, (fx, fy, fz) per voxel."""
+        """Fibres as a contiguous float32 array of length 3n, (fx, fy, fz) per
+        voxel: the input type of ``ep_set_fibres``."""
         return np.ascontiguousarray(self.fib.reshape(-1, 3), dtype=np.float32).reshape(-1)
+
+    def fibres_as_float32(self) -> "Case":
+        """A copy whose fibres are rounded to float32 (kept as float64), so the
+        oracle and the library see exactly the same values."""
+        c = dataclasses.replace(self)
+        c.fib = self.fib.astype(np.float32).astype(np.float64)
+        return c
 
     def mask_flat(self) -> np.ndarray:
         return np.ascontiguousarray(self.mask.reshape(-1), dtype=np.uint8)
-
-
-def _fp16_exact(f: np.ndarray) -> np.ndarray:
-    """Round fibre components to the nearest half-precision value (kept as float32)."""
-    return f.astype(np.float16).astype(np.float32)
 
 
 def _centres(n: Tuple[int, int, int], centre: Tuple[float, float, float]):
@@ -193,7 +199,7 @@ def config0() -> Case:
     f[..., 1] = np.sin(theta)[:, None, None]
     p = Params(dt=0.01, sig_iL=0.20, sig_iT=0.05, sig_eL=0.20, sig_eT=0.05, lam=1.0, K=1.0)
     return Case("config0_mono_fp64_slab32", n, n, n, 0.25,
-                np.ones((n, n, n), np.uint8), _fp16_exact(f), p,
+                np.ones((n, n, n), np.uint8), f, p,
                 [Stimulus((0, 0, 0), (4, 4, 4), 0.0, 1.0, 0.5)],
                 model=MONO, precision=FP64, steps=1000)
 
@@ -207,7 +213,6 @@ def slab(n: int = 512, model: int = MONO, unequal: bool = False) -> Case:
     k = np.arange(n, dtype=np.float64)
     theta = np.deg2rad(-60.0 + 120.0 * k / max(n - 1, 1))
     fz = np.stack([np.cos(theta), np.sin(theta), np.zeros(n)], axis=-1)   # (n, 3), per z plane
-    fz = _fp16_exact(fz).astype(np.float32)
     fib = np.broadcast_to(fz[:, None, None, :], (n, n, n, 3))
     p = Params(dt=0.05, sig_iL=0.20, sig_iT=0.05, sig_eL=0.20, sig_eT=0.10 if unequal else 0.05)
     return Case(f"slab{n}_{'bi' if model == BI else 'mono'}", n, n, n, 0.5, np.ones((n, n, n), np.uint8), fib, p,
@@ -227,7 +232,7 @@ def shell_case(n: int = 128, semi=(40.0, 40.0, 55.0), wall: float = 10.0,
     p = Params(dt=dt, sig_iL=sig[0], sig_iT=sig[1], sig_eL=sig[2], sig_eT=sig[3])
     mask = m.astype(np.uint8)
     stim = _apex_block(mask, c, c, stim_size)
-    return Case(name or f"shell{n}", n, n, n, 0.5, mask, _fp16_exact(f), p, [stim],
+    return Case(name or f"shell{n}", n, n, n, 0.5, mask, f, p, [stim],
                 model=BI, precision=FP32, steps=steps)
 
 
@@ -270,7 +275,7 @@ def config2(seed: int = 0, unequal: bool = False, n: int = 256) -> Case:
     mask = m.astype(np.uint8)
     stim = _apex_block(mask * lv.astype(np.uint8), c + lv_c[0], c + lv_c[1], max(2, int(round(6 * s))))
     return Case(f"config2_bi_biv{n}" + ("_unequal" if unequal else ""), n, n, n, 0.5, mask,
-                _fp16_exact(f), p, [stim], model=BI, precision=FP32, steps=20000)
+                f, p, [stim], model=BI, precision=FP32, steps=20000)
 
 
 def ecg_case(n: int = 256, sig_o: float = 1.0, seed: int = 0) -> Case:
@@ -345,7 +350,7 @@ def random_fibres(rng: np.random.Generator, shape, zero_frac: float = 0.05) -> n
     f = rng.standard_normal(tuple(shape) + (3,))
     f /= np.maximum(np.linalg.norm(f, axis=-1, keepdims=True), 1e-12)
     f[rng.uniform(size=shape) < zero_frac] = 0.0
-    return _fp16_exact(f)
+    return f
 
 
 def random_case(seed: int, nx: int, ny: int, nz: int, model: int = BI, precision: int = FP32,
@@ -397,7 +402,7 @@ def with_torso(case: Case, sig_o: float = 1.0, pad: int = 0, fill: Optional[floa
     them, for tests).  Electrodes RA, LA, LL at corners of the box."""
     nx, ny, nz = case.nx + 2 * pad, case.ny + 2 * pad, case.nz + 2 * pad
     mask = np.zeros((nz, ny, nx), np.uint8)
-    fib = np.zeros((nz, ny, nx, 3), np.float32)
+    fib = np.zeros((nz, ny, nx, 3), np.float64)
     sl = (slice(pad, pad + case.nz), slice(pad, pad + case.ny), slice(pad, pad + case.nx))
     mask[sl] = case.mask
     fib[sl] = case.fib
