@@ -31,12 +31,26 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-BYTES_PER_SWEEP_VOXEL = 19      # x 4 + b 4 + x' 4 + fibre 6 + mask 1 (algorithmic, per tissue voxel)
-BYTES_PER_CHEB_SWEEP_VOXEL = 23  # the same plus x_{k-1} 4 (the Chebyshev semi-iteration's second operand)
-BYTES_PER_MONO_VOXEL = 23       # fused monodomain step: v, w read 8 + written 8 + fibre 6 + mask 1
-BYTES_PER_IE_SWEEP_VOXEL = 23   # implicit sweep: x, f, 1/(1 + a D) read 12 + fibre 6 + mask 1 + x' written 4
+# Algorithmic bytes per tissue voxel of one launch of the dominant kernel, with
+# the fp32 record of 16 bytes (fibre 12 + the diagonal's 1/D 4; the mask is the
+# sign of its last lane):
+BYTES_PER_SWEEP_VOXEL = 28      # x 4 + b 4 + record 16 read, x' 4 written
+BYTES_PER_CHEB_SWEEP_VOXEL = 32  # the same plus x_{k-1} 4 (the Chebyshev semi-iteration's second operand)
+BYTES_PER_MONO_VOXEL = 32       # fused monodomain step: v, w read 8 + written 8 + record 16
+BYTES_PER_IE_SWEEP_VOXEL = 32   # implicit sweep: x, f, 1/(1 + a D) read 12 + record 16 + x' written 4
+FP16_LAYOUT_SWEEP_BYTES = 19    # a sweep's bytes with fp16 fibre records (6 + 1 mask): for comparison only
 REF_SAMPLE_SWEEPS = (8, 64)     # oracle sweeps timed per sample step (two caps -> per-sweep cost)
-DEFAULT_REF_SWEEPS_PER_STEP = 4000  # elliptic sweeps per step assumed by the reference arm when no GPU figure exists
+# Damped-Jacobi sweeps of each step from rest (steps 0, 1, 2, ...) of the 256^3
+# biventricular and the 128^3 shell workloads, as the library's solve to
+# rel_tol 1e-6 took them on GB300 (bench.py --warmup 0 --steps 30).  The
+# reference arm runs before the GPU arm, so it takes its sweeps per step from
+# here; the GPU arm reports its own.
+SWEEPS_FROM_REST = {
+    "config2": [21701, 15781, 13031, 11351, 10251, 9471, 8841, 8391, 8031, 7771, 7541, 7331, 7191, 7041, 6921,
+                6821, 6731, 6611, 6511, 6371, 4131, 4051, 4001, 3971, 3941, 3911, 3881, 3831, 3781, 3731],
+    "config1": [16651, 13081, 11171, 9921, 9021, 8391, 7891, 7491, 7171, 6921, 6731, 6541, 6411, 6261, 6151,
+                6041, 5951, 5851, 5761, 5661, 3551, 3501, 3461, 3451, 3441, 3431, 3411, 3381, 3351, 3321],
+}
 
 
 def _args():
@@ -69,6 +83,9 @@ def _args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--ref-sweeps-per-step", type=float, default=None)
+    ap.add_argument("--start-ms", type=float, default=0.0,
+                    help="start the window at this time of the beat instead of at rest: the state is made "
+                         "first on a separate handle with loosely converged solves, then timed as asked")
     return ap.parse_args()
 
 
@@ -269,35 +286,145 @@ def _oracle_case(a, case):
     return case
 
 
+def ref_sweeps_per_step(a, case):
+    """Elliptic (and implicit) sweeps per step of the GPU arm's window, for the
+    reference arm: --ref-sweeps-per-step if given, else the GB300 measurement of
+    the same window from rest (SWEEPS_FROM_REST), else None."""
+    if a.ref_sweeps_per_step:
+        return float(a.ref_sweeps_per_step), "--ref-sweeps-per-step"
+    if case.model == 0 and getattr(case.params, "diffusion", 0) == 0:
+        return 0.0, "monodomain with explicit diffusion: no solve"
+    table = SWEEPS_FROM_REST.get(a.workload)
+    if (table and a.solver == "jacobi" and a.omega is None and a.diffusion == "explicit" and a.start_ms == 0.0
+            and len(table) >= a.warmup + a.steps):
+        w = table[a.warmup:a.warmup + a.steps]
+        return float(np.mean(w)), (f"GB300 measurement of steps {a.warmup}..{a.warmup + a.steps - 1} from rest "
+                                   f"(damped Jacobi to rel_tol 1e-6)")
+    return None, "no GB300 measurement of this window"
+
+
 def run_reference(a):
+    """The oracle as the reference arm.  Each timed step is a bounded sample
+    that really runs: one oracle step of the workload with its Jacobi solve
+    capped at REF_SAMPLE_SWEEPS[0] and at REF_SAMPLE_SWEEPS[1] sweeps, which
+    gives the step's fixed cost and its cost per sweep; ms_per_step is the time
+    these samples took.  The rate of a full step (value) is then
+    extrapolated to the sweeps per step the GPU arm's window needs, and the
+    line says so (extrapolated: true)."""
     world, rank, local = _dist()
     if rank != 0:
         return
     case, desc = _workload(a.workload, a.model, a.slab_n, a.diffusion, a.solver, a.sig_o, a.omega)
-    M = case.n_tissue
-    k_ref = a.ref_sweeps_per_step or DEFAULT_REF_SWEEPS_PER_STEP
-    times = []
-    info = None
     oc = _oracle_case(a, case)
+    k_ref, k_src = ref_sweeps_per_step(a, case)
+    times, samples = [], []
+    info = None
     for i in range(a.warmup + a.steps):
-        info = oracle_sample(oc, k_ref)
+        t0 = time.perf_counter()
+        info = oracle_sample(oc, k_ref or 0.0)
+        dt = time.perf_counter() - t0
         if i >= a.warmup:
-            times.append(info["step_s"])
-    tot = sum(times)
-    value = oc.n_tissue * a.steps / tot   # tissue voxel-steps/s of the sampled case
+            times.append(dt)
+            samples.append(info)
+    sample_s = sum(times)
+    fixed = float(np.median([x["fixed_s"] for x in samples]))
+    per = float(np.median([x["per_sweep_s"] for x in samples]))
     what = f"the same construction at {oc.nx}^3" if oc is not case else "the workload"
-    sample = (f"per step: one oracle step of {what} with the Jacobi solve capped at "
-              f"{REF_SAMPLE_SWEEPS[0]} and {REF_SAMPLE_SWEEPS[1]} sweeps (fixed {info['fixed_s']:.2f} s, "
-              f"{info['per_sweep_s']:.3f} s/sweep), extrapolated to {k_ref:.0f} sweeps per step")
-    line = {"impl": "reference", "metric": "voxel-steps/sec", "value": value, "unit": "tissue voxel-steps/s",
-            "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1e3 * M / value,
+    sample = (f"each step: one oracle step of {what} with the elliptic solve capped at {REF_SAMPLE_SWEEPS[0]} and "
+              f"at {REF_SAMPLE_SWEEPS[1]} sweeps ({sample_s / a.steps:.2f} s of CPU work a step; fixed "
+              f"{fixed:.2f} s + {per:.3f} s a sweep)")
+    line = {"impl": "reference", "metric": "voxel-steps/sec", "unit": "tissue voxel-steps/s",
+            "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1e3 * sample_s / a.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": desc, "tissue_voxels": M},
-            "cpu_baseline": {"value": value, "unit": "tissue voxel-steps/s", "cores": info["cores"],
-                             "kind": "oracle", "sample": sample},
-            "e2e": {"value": value, "unit": "tissue voxel-steps/s", "h2d_bytes_per_step": 0,
-                    "d2h_bytes_per_step": 0}}
+            "config": {"workload": desc, "tissue_voxels": case.n_tissue}}
+    if k_ref is None:
+        line.update({"value": None, "extrapolated": None,
+                     "unavailable": f"{k_src}: a full oracle step of this window cannot be sized"})
+    else:
+        step_s = fixed + k_ref * per
+        value = oc.n_tissue / step_s
+        line.update({"value": value, "extrapolated": True,
+                     "extrapolation": {"sweeps_per_step": k_ref, "source": k_src, "fixed_s": fixed,
+                                       "per_sweep_s": per, "full_step_s": step_s,
+                                       "model": "full step = fixed + sweeps x per-sweep (checked against complete "
+                                                "oracle steps, see the design notes)"},
+                     "e2e": {"value": value, "unit": "tissue voxel-steps/s", "h2d_bytes_per_step": 0,
+                             "d2h_bytes_per_step": 0}})
+    line["cpu_baseline"] = {"value": line["value"], "unit": "tissue voxel-steps/s", "cores": info["cores"],
+                            "kind": "oracle", "sample": sample, "extrapolated": k_ref is not None and k_ref > 0}
     print(json.dumps(line), flush=True)
+
+
+def beat_state(ep, case, n_steps, stream):
+    """The state blob after n_steps from rest, made on a separate handle whose
+    damped-Jacobi solves stop at a loose relative residual (1e-3, at most 2000
+    sweeps), so a window can be timed mid-beat without the full solves on the
+    way there; the timed steps then solve to the workload's tolerance from it.
+    (Chebyshev solves are not used here: late in a beat they stall below their
+    relative tolerance and run to their cap.)"""
+    import dataclasses
+    c = dataclasses.replace(case, params=dataclasses.replace(case.params, rel_tol=1e-3, max_iter=2000))
+    h = ep.Sim(c.nx, c.ny, c.nz, c.dx, c.model, c.precision, use_torch=True, stream=stream.cuda_stream)
+    h.set_mask(c.mask_flat())
+    h.set_fibres(c.fib_flat())
+    h.set_params(c.params)
+    for st in c.stimuli:
+        h.add_stimulus(st.lo, st.hi, st.t_start, st.dur, st.amp)
+    done = 0
+    while done < n_steps:
+        k = min(200, n_steps - done)
+        st = h.step(k, allow_noconv=True)
+        done += k
+        print(f"beat_state: step {done} of {n_steps}, last solve {st.iters} sweeps", file=sys.stderr, flush=True)
+    blob = h.read_state()
+    h.close()
+    return blob
+
+
+def oracle_step_error(ep, sim, case, a):
+    """Error of the timed window's last state against the FP64 oracle, from
+    quantities the oracle computes in one pass at full size: (1) one more step
+    from the library's state, by the library and by the oracle (v and w of the
+    new step do not depend on its elliptic solve, which the oracle caps at one
+    sweep); (2) for the bidomain, the relative residual of the library's v_e
+    under the oracle's elliptic operator with b = -L_i v (zero mean per
+    component), beside the residual the library reported."""
+    import oracle
+    import workloads as W
+    if case.n > 256 ** 3:
+        return {"skipped": f"{case.nx}^3 grid: above the 256^3 the oracle step check runs on"}
+    t0 = time.perf_counter()
+    v, w, ve = sim.read(ep.EP_V), sim.read(ep.EP_W), sim.read(ep.EP_VE)
+    blob = sim.read_state()
+    st = sim.step(1, allow_noconv=True)
+    v1, w1 = sim.read(ep.EP_V), sim.read(ep.EP_W)
+    sim.write_state(blob)   # the window's state back for the end-to-end leg
+    p1 = W.Params(**{**case.params.__dict__, "max_iter": 1})
+    o = oracle.Sim(case, params=p1)
+    o.set_state(v, w, ve, int(st.step) - 1)
+    o.step()
+    ref = o.state()
+    o.close()
+    t = case.mask.reshape(-1) > 0
+    out = {"one_step_max_abs_dVm_mV": float(100.0 * np.abs(v1 - ref["v"])[t].max()),
+           "one_step_max_abs_dw": float(np.abs(w1 - ref["w"])[t].max()),
+           "step_checked": int(st.step)}
+    if case.model == 1 and case.torso is None:
+        g = oracle.Grid.from_case(case)
+        p = case.params
+        b = -g.apply_L(p.sig_iL, p.sig_iT, np.where(t, v, 0.0))
+        nc, comp = g.components()
+        for cc in range(nc):
+            sel = comp == cc
+            b[sel] -= b[sel].mean()
+        r = b - g.apply_L(p.sig_iL + p.sig_eL, p.sig_iT + p.sig_eT, np.where(t, ve, 0.0))
+        out["elliptic_relres_under_oracle"] = float(np.linalg.norm(r[t]) / np.linalg.norm(b[t]))
+        out["rel_tol"] = p.rel_tol
+    out["method"] = ("the window's last state read back; one step from it by the library and by the FP64 oracle "
+                     "(v, w compared on every tissue voxel); the library's v_e put through the oracle's "
+                     "elliptic operator")
+    out["check_s"] = time.perf_counter() - t0
+    return out
 
 
 def run_ours(a):
@@ -335,6 +462,10 @@ def run_ours(a):
         case.params.cheb_lmin, case.params.cheb_lmax = info.cheb_lmin, info.cheb_lmax
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
+    start_step = 0
+    if a.start_ms > 0.0:   # a mid-beat window: the state at start_ms from a Chebyshev-accelerated run
+        start_step = int(round(a.start_ms / case.params.dt))
+        sim.write_state(beat_state(ep, case, start_step, stream))
     for _ in range(a.warmup):
         sim.step(1, allow_noconv=True)
     torch.cuda.synchronize()
@@ -367,6 +498,11 @@ def run_ours(a):
     torch.cuda.synchronize()
     clk = clocks.stop()
     prof = sim.profile()
+    err = None
+    if rank == 0 and world == 1 and not a.no_cpu_baseline:
+        err = oracle_step_error(ep, sim, case, a)
+        if case.model == 1:
+            err["library_relres"] = float(st.rel_res)   # the last timed step's solve, as the library reported it
     total_s = sum(ms) / 1e3
     if dist is not None:
         total_s = max_over_ranks(total_s, dist)
@@ -386,7 +522,7 @@ def run_ours(a):
         # the fused reaction + diffusion launch is the step (plus a one-thread step-counter kernel)
         launch_s = prof.other_ms / 1e3 / max(prof.steps, 1)
         # v, w read and written at the state precision, fibre 6, mask 1
-        alg_bytes = (BYTES_PER_MONO_VOXEL if case.precision == 0 else 4 * 8 + 7) * M
+        alg_bytes = (BYTES_PER_MONO_VOXEL if case.precision == 0 else 4 * 8 + 16) * M
         kname = "k_stencil<%s,M_PAR_MONO> (fused reaction + diffusion)" % ("float" if case.precision == 0 else "double")
         share = prof.other_ms / 1e3 / total_s
     else:
@@ -409,9 +545,13 @@ def run_ours(a):
     tpv = _traffic_record(stem)
     roofline = {"bound": "hbm", "kernel": kname,
                 "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "algorithmic_bytes_per_voxel": alg_bytes / (n_dom if not mono else M),
                 "traffic": (tpv * (n_dom if not mono else M)) if tpv is not None else None,
                 "algorithmic_bytes_per_launch": alg_bytes, "avg_launch_us": launch_s * 1e6,
                 "kernel_share_of_step": share if world == 1 else None, "peak_source": peak_src}
+    if not mono and a.solver != "chebyshev" and not torso:
+        # the same launch time counted at the 19 bytes a voxel of fp16 fibre records
+        roofline["frac_at_fp16_record_bytes"] = FP16_LAYOUT_SWEEP_BYTES * n_dom / launch_s / 1e9 / peak
 
     # end to end through the C ABI with host buffers: the same steps as the timed
     # window, each step's state in from pinned host memory and its new state out
@@ -438,11 +578,11 @@ def run_ours(a):
 
     cpu = None
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
-        k = float(np.mean(iters)) + float(np.mean(ie_iters)) if iters else DEFAULT_REF_SWEEPS_PER_STEP
+        k = float(np.mean(iters)) + float(np.mean(ie_iters))
         oc = _oracle_case(a, case)
         info = oracle_sample(oc, k)
         cpu = {"value": oc.n_tissue / info["step_s"], "unit": "tissue voxel-steps/s", "cores": info["cores"],
-               "kind": "oracle",
+               "kind": "oracle", "extrapolated": k > 0, "measured_cpu_s": info["sample_s"],
                "sample": (f"one oracle step of {f'the same construction at {oc.nx}^3' if oc is not case else 'this workload'} with the Jacobi solve capped at {REF_SAMPLE_SWEEPS[0]} "
                           f"and {REF_SAMPLE_SWEEPS[1]} sweeps (fixed {info['fixed_s']:.2f} s + "
                           f"{info['per_sweep_s']:.3f} s/sweep, {info['sample_s']:.1f} s of CPU work), extrapolated "
@@ -455,13 +595,15 @@ def run_ours(a):
                 "dtype": "f32" if case.precision == 0 else "f64", "data": "synthetic",
                 "config": {"workload": desc, "grid": [case.nx, case.ny, case.nz], "tissue_voxels": M,
                            "dt_ms": case.params.dt, "rel_tol": case.params.rel_tol,
-                           "window": f"steps {a.warmup}..{a.warmup + a.steps - 1} from rest, stimulus at t=0",
+                           "window": (f"steps {start_step + a.warmup}..{start_step + a.warmup + a.steps - 1} "
+                                      f"(t = {(start_step + a.warmup) * case.params.dt:g} ms on) of a beat from "
+                                      f"rest, stimulus at t=0"),
                            "sweeps_per_step": iters, "step_status": statuses,
                            "implicit_sweeps_per_step": ie_iters if a.diffusion == "implicit" else None,
                            "l2": "flushed between timed steps (256 MB write)",
                            "parallelism": f"replicas x{world}",
                            "elliptic_voxels": n_dom, "ecg": ecg_trace},
-                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "error_vs_oracle": err,
                 "gpu_launches": int(prof.sweep_launches + prof.other_launches),
                 "clocks": clk}
         print(json.dumps(line), flush=True)

@@ -158,7 +158,7 @@ ep_status ep_set_mask(ep_sim *s, const uint8_t *mask, size_t n);
  * Eq. sigma1, so |f|^2 = (g sigma_L - sigma_T) / (sigma_L - sigma_T) gives
  * the longitudinal conductivity g sigma_L; such voxels may need a smaller
  * jacobi_omega than the default).  Components finite and at most 4 in
- * magnitude (EP_EINVAL).  Stored as IEEE half precision.  Optional (default
+ * magnitude (EP_EINVAL).  Stored as given (float32).  Optional (default
  * zero fibres). */
 ep_status ep_set_fibres(ep_sim *s, const float *f, size_t n3);
 

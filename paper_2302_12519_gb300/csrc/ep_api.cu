@@ -1,6 +1,6 @@
 // ep_api.cu -- C ABI of the GB300 voxel electrophysiology step (see include/ep.h).
 //
-// Host side: validation, set-up of the data layout (fp16 fibre records,
+// Host side: validation, set-up of the data layout (fp32 fibre records,
 // z-march segment list, component-sorted tissue index list), and the step
 // orchestration.  Every arithmetic step of the time step runs in the kernels
 // of ep_kernels.cuh.

@@ -105,6 +105,24 @@ def interval(g, sL, sT):
     return float(lam[nc]), hi
 
 
+def largest(g, sL, sT):
+    """Largest eigenvalue of D^-1 A by the Lanczos method (scipy eigsh) on the
+    oracle's operator, for domains too large to assemble."""
+    from scipy.sparse.linalg import LinearOperator, eigsh
+
+    idx, d, _ = _restricted(g, sL, sT)
+    s = 1.0 / np.sqrt(d)
+
+    def apply_b(y):
+        u = np.zeros(g.n)
+        u[idx] = s * y
+        return s * g.apply_L(sL, sT, u)[idx]
+
+    m = len(idx)
+    return float(eigsh(LinearOperator((m, m), matvec=apply_b, dtype=np.float64), k=1, which="LA", tol=1e-8,
+                       return_eigenvectors=False)[0])
+
+
 def chebyshev_params(g, sL, sT):
     """The interval the library's set-up would target, scaled as it scales its
     own estimate (smallest by 0.8, largest by 1.05), from the oracle's spectrum."""

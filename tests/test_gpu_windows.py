@@ -1,0 +1,63 @@
+"""Full-run parity windows of the 128^3 shell (config 1) and the 256^3
+biventricular heart (config 2): the library, in FP32, runs the bidomain step
+from the same propagating start (workloads.front_state) with the elliptic
+solve by the Chebyshev semi-iteration on the same fixed interval as the FP64
+oracle did when tests/golden/make_windows.py wrote the expected results
+(interval, sweep counts, activation times, v and v_e at the end of the
+window).  Gates: V_m within 0.5 mV and activation times within 1 % on every
+stored voxel, the same set of voxels activated; the measured errors are
+printed."""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import paper_2302_12519_gb300 as ep
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2302_12519_gb300 import build
+    build.build()
+    ep.load()
+
+
+@pytest.mark.parametrize("name", ["config1", "config2"])
+def test_window_matches_oracle(name):
+    d = np.load(os.path.join(GOLDEN, f"window_{name}.npz"))
+    c = W.config1() if name == "config1" else W.config2()
+    assert int(d["n_tissue"]) == c.n_tissue
+    p = c.params
+    p.solver, p.cheb_lmin, p.cheb_lmax = 1, float(d["lmin"]), float(d["lmax"])
+    s = ep.sim_from_case(c)
+    assert s.info().cheb_lmin == p.cheb_lmin and s.info().cheb_lmax == p.cheb_lmax
+    s.set_state(*W.front_state(c), 0)
+    sweeps = []
+    for _ in range(int(d["steps"])):
+        st = s.step(1)
+        assert st.converged == 1
+        sweeps.append(st.iters)
+    idx = d["idx"]
+    vm_g = s.read(ep.EP_VM_MV)[idx]
+    ta_g = s.read(ep.EP_TACT)[idx]
+    ve_g = s.read(ep.EP_VE_MV)[idx]
+    vm_o = oracle.vm_mV(d["v"].astype(np.float64))
+    ta_o = d["tact"]
+    dvm = float(np.abs(vm_g - vm_o).max())
+    dve = float(np.abs(ve_g - 100.0 * d["ve"].astype(np.float64)).max())
+    act = ta_o > 0
+    np.testing.assert_array_equal(ta_g > 0, act)
+    rel = np.abs(ta_g[act] - ta_o[act]) / ta_o[act]
+    print(f"{name}: {int(d['steps'])} steps, {int(act.sum())} voxels activated in the window; max |dVm| "
+          f"{dvm:.3e} mV, max rel d t_act {rel.max():.3e}, max |dVe| {dve:.3e} mV; sweeps per step GPU "
+          f"{sweeps[:3]}..{sweeps[-1]}, oracle {list(d['sweeps'][:3])}..{int(d['sweeps'][-1])}")
+    assert act.sum() > 1000
+    assert dvm <= 0.5, dvm
+    assert rel.max() <= 0.01, rel.max()
+    s.close()

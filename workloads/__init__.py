@@ -388,6 +388,22 @@ def random_state(seed: int, case: Case):
             np.where(d, ve, 0.0).reshape(-1))
 
 
+def front_state(case: Case, rise_vox: float = 10.0, width_vox: float = 1.5):
+    """A propagating start (v, w, ve) in float64: excited tissue below a
+    horizontal front ``rise_vox`` voxels above the case's lowest tissue voxel
+    (the apex of the shells), v = 1/2 (1 - tanh(d / width)) with d the height
+    above the front, w = 1 (recovered gates), ve = 0.  Closed form, no seed:
+    the full-run parity windows start here so that the front crosses many
+    voxels within a few oracle steps."""
+    nz, ny, nx = case.mask.shape
+    ks = np.nonzero(case.mask.reshape(nz, -1).any(axis=1))[0]
+    z0 = (float(ks[0]) if len(ks) else 0.0) + rise_vox
+    z = np.broadcast_to(np.arange(nz, dtype=np.float64)[:, None, None] + 0.5, (nz, ny, nx))
+    v = 0.5 * (1.0 - np.tanh((z - z0) / width_vox))
+    t = case.mask > 0
+    return (np.where(t, v, 0.0).reshape(-1), np.where(t, 1.0, 1.0).reshape(-1), np.zeros(case.n))
+
+
 def corner_electrodes(nx: int, ny: int, nz: int) -> List[Tuple[int, int, int]]:
     """RA, LA, LL at corners of the box: the arms at the top (high z) on either
     side in y, the leg at the bottom corner diametrically opposite RA."""
