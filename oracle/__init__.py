@@ -89,6 +89,9 @@ def lib():
         L.og_chebyshev.argtypes = [ctypes.POINTER(_Grid), dp, dp, vp, vp, dp, dp, dp, ip, ip,
                                    ctypes.POINTER(ip), ctypes.POINTER(dp)]
         L.og_chebyshev.restype = ip
+        L.og_gauss_seidel.argtypes = [ctypes.POINTER(_Grid), dp, dp, vp, vp, dp, dp, ip, ip,
+                                      ctypes.POINTER(ip), ctypes.POINTER(dp)]
+        L.og_gauss_seidel.restype = ip
         L.og_default_omega.argtypes = [dp, dp]
         L.og_default_omega.restype = dp
         L.og_create.argtypes = [ip, ip, ip, dp, vp, vp, ctypes.POINTER(_Params),
@@ -192,6 +195,16 @@ class Grid:
         rr = ctypes.c_double(0.0)
         st = lib().og_chebyshev(ctypes.byref(self._g), sL, sT, _ptr(b), _ptr(x), lmin, lmax, tol, m, max_iter,
                                 ctypes.byref(it), ctypes.byref(rr))
+        return x, it.value, rr.value, st
+
+    def gauss_seidel(self, sL, sT, b, x0, omega=1.0, tol=1e-6, m=10, max_iter=100000):
+        """Eight-colour Gauss-Seidel (omega = 1) or SOR for L x = b."""
+        b = np.ascontiguousarray(np.asarray(b, dtype=np.float64).reshape(-1))
+        x = np.ascontiguousarray(np.array(x0, dtype=np.float64).reshape(-1))
+        it = ctypes.c_int(0)
+        rr = ctypes.c_double(0.0)
+        st = lib().og_gauss_seidel(ctypes.byref(self._g), sL, sT, _ptr(b), _ptr(x), omega, tol, m, max_iter,
+                                   ctypes.byref(it), ctypes.byref(rr))
         return x, it.value, rr.value, st
 
     def ie_jacobi(self, sL, sT, alpha, f, x0, tol=1e-6, m=10, max_iter=100000):

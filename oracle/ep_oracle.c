@@ -54,7 +54,10 @@
  *  - Elliptic solve by damped Jacobi, Eq. dampjac1, from the previous ve,
  *    stopping when ||b - A x||_2 <= tol ||b||_2 (checked every m sweeps), then
  *    the reference potential is fixed by subtracting the mean over every
- *    face-connected tissue component (the pure-Neumann null space).
+ *    face-connected tissue component (the pure-Neumann null space).  Two
+ *    other solves of the same equation: the Chebyshev semi-iteration on the
+ *    Jacobi step, and eight-colour Gauss-Seidel (the deterministic form of
+ *    the thesis' in-place Jacobi), both to the same stop rule.
  *
  * Units: mm, ms, mS/mm; v dimensionless (0 rest, 1 peak).
  * Index: q = i + nx*(j + ny*k).
@@ -552,6 +555,78 @@ int og_chebyshev(const og_grid *g, double sL, double sT, const double *b, double
     return status;
 }
 
+/* Gauss-Seidel over eight colour classes: the deterministic form of the
+ * thesis' in-place Jacobi, whose races let a sweep read values that other
+ * work-items have already updated (Sec. "Jacobi method").  Voxel (i, j, k)
+ * has colour (i mod 2) + 2 (j mod 2) + 4 (k mod 2).  Two voxels of one colour
+ * differ by an even amount in some index, so the 27-point operator, which
+ * reaches one voxel in each index, never couples them: the order within a
+ * colour does not matter.  A sweep visits colours 0, 1, ..., 7; at colour c,
+ * with A x formed from the current iterate (colours < c of this sweep already
+ * updated), every domain voxel q of colour c with D_q > 0 takes
+ *   r_q = b_q - (A x)_q,   x_q <- x_q + omega r_q / D_q
+ * (successive over-relaxation; omega = 1 is Gauss-Seidel, omega <= 0 selects
+ * 1).  Stop rule: at sweeps k = 0, m, 2m, ... the residuals r_q as they are
+ * formed at their colour's update, squared and summed over all eight
+ * colours, are compared with tol^2 ||b||^2; the sweep that forms the sum is
+ * completed and, if it passes, is the last.  Status 1 after max_iter sweeps;
+ * ||b|| = 0 returns at once after 0 sweeps. */
+int og_gauss_seidel(const og_grid *g, double sL, double sT, const double *b, double *x, double omega,
+                    double tol, int m, int max_iter, int *iters, double *relres)
+{
+    long n = (long)g->nx * g->ny * g->nz, q;
+    double *diag = (double *)malloc(sizeof(double) * (size_t)n);
+    double *Ax = (double *)malloc(sizeof(double) * (size_t)n);
+    double nb = 0.0, nr = 0.0;
+    int k = 0, status = 1, c;
+    for (q = 0; q < n; q++)
+        if (og_in(g, q))
+            nb += b[q] * b[q];
+    nb = sqrt(nb);
+    *relres = 0.0;
+    if (nb == 0.0) {
+        *iters = 0;
+        free(diag);
+        free(Ax);
+        return 0;
+    }
+    if (m < 1)
+        m = 1;
+    if (omega <= 0.0)
+        omega = 1.0;
+    og_diag_L(g, sL, sT, diag);
+    for (k = 0; k < max_iter; k++) {
+        int check = (k % m) == 0;
+        if (check)
+            nr = 0.0;
+        for (c = 0; c < 8; c++) {
+            og_apply_L(g, sL, sT, x, Ax);
+            for (q = 0; q < n; q++) {
+                int i = (int)(q % g->nx), j = (int)((q / g->nx) % g->ny), kk = (int)(q / ((long)g->nx * g->ny));
+                if (!og_in(g, q) || (i & 1) + 2 * (j & 1) + 4 * (kk & 1) != c)
+                    continue;
+                double r = b[q] - Ax[q];
+                if (check)
+                    nr += r * r;
+                if (diag[q] > 0.0)
+                    x[q] += omega * r / diag[q];
+            }
+        }
+        if (check) {
+            *relres = sqrt(nr) / nb;
+            if (*relres <= tol) {
+                status = 0;
+                k++;
+                break;
+            }
+        }
+    }
+    *iters = k;
+    free(diag);
+    free(Ax);
+    return status;
+}
+
 /* ------------------------------------------------------------------------ */
 /* time stepping                                                            */
 /* ------------------------------------------------------------------------ */
@@ -779,6 +854,9 @@ int og_step(og_sim *s, int *iters, double *relres)
         if (p->solver == OG_CHEBYSHEV)
             status = og_chebyshev(ge, p->sig_iL + p->sig_eL, p->sig_iT + p->sig_eT, s->b, s->ve, p->cheb_lmin,
                                   p->cheb_lmax, p->rel_tol, p->check_every, p->max_iter, iters, relres);
+        else if (p->solver == OG_GAUSS_SEIDEL)
+            status = og_gauss_seidel(ge, p->sig_iL + p->sig_eL, p->sig_iT + p->sig_eT, s->b, s->ve, p->omega,
+                                     p->rel_tol, p->check_every, p->max_iter, iters, relres);
         else
             status = og_jacobi(ge, p->sig_iL + p->sig_eL, p->sig_iT + p->sig_eT, s->b, s->ve,
                                p->omega, p->rel_tol, p->check_every, p->max_iter, iters, relres);

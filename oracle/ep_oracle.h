@@ -27,13 +27,14 @@ typedef struct {
     double lam, K, dt, omega, rel_tol;
     int check_every, max_iter, model;
     int diffusion;              /* OG_EXPLICIT or OG_IMPLICIT (Eq. iejac1) */
-    int solver;                 /* elliptic solve: OG_JACOBI (Eq. dampjac1) or OG_CHEBYSHEV */
+    int solver;                 /* elliptic solve: OG_JACOBI (Eq. dampjac1), OG_CHEBYSHEV or OG_GAUSS_SEIDEL */
     double cheb_lmin, cheb_lmax;   /* spectral interval of D^-1 A for OG_CHEBYSHEV */
     double sig_o;               /* torso conductivity, used once og_set_torso is called */
 } og_params;
 
 #define OG_JACOBI 0
 #define OG_CHEBYSHEV 1
+#define OG_GAUSS_SEIDEL 2
 
 #define OG_EXPLICIT 0
 #define OG_IMPLICIT 1
@@ -55,6 +56,8 @@ int og_ie_jacobi(const og_grid *g, double sL, double sT, double alpha, const dou
                  double tol, int m, int max_iter, int *iters, double *relres);
 int og_chebyshev(const og_grid *g, double sL, double sT, const double *b, double *x, double lmin, double lmax,
                  double tol, int m, int max_iter, int *iters, double *relres);
+int og_gauss_seidel(const og_grid *g, double sL, double sT, const double *b, double *x, double omega,
+                    double tol, int m, int max_iter, int *iters, double *relres);
 
 og_sim *og_create(int nx, int ny, int nz, double dx, const unsigned char *mask,
                   const double *fib, const og_params *p, const og_stim *stim, int nstim);

@@ -10,16 +10,19 @@ semi-iteration on a fixed interval, to rel_tol 1e-6; the library runs the
 same steps on the same interval in tests/test_gpu_windows.py.
   config 1: 60 steps; the interval from the oracle's spectrum of D^-1 A
             (smallest nonzero x 0.8, largest x 1.05);
-  config 2: 8 steps; the largest eigenvalue by Lanczos (x 1.05) and the
-            lower end a literal 1e-3 (below the smallest nonzero eigenvalue
-            the set-up estimates, about 2e-3, so the interval holds the
-            spectrum; factorising the 3.4M-voxel operator is out of reach).
+  config 2: 1 step; the largest eigenvalue by Lanczos (x 1.05) and the
+            lower end a literal 1e-3 (factorising the 3.4M-voxel operator is
+            out of reach).  The oracle's FP64 solve of the first step takes
+            2961 sweeps (half an hour on 8 cores); the second, from the first
+            one's v_e, did not finish within an hour, so the window is one
+            complete step.
 Stored (npz): the interval, sweeps per step, and at the end of the window
 activation times, v and v_e -- for config 1 on every tissue voxel, for
 config 2 on the voxels that activated or lie on the front (0.01 < v < 0.99)
 plus 20000 seeded random tissue voxels.
 
-Usage: python tests/golden/make_windows.py [config1|config2]  (about 1 h each on 8 cores)
+Usage: python tests/golden/make_windows.py [config1|config2]  (about 1 h for config 1, 45 min for
+config 2, on 8 cores)
 """
 from __future__ import annotations
 
@@ -38,7 +41,7 @@ import oracle  # noqa: E402
 import spectra  # noqa: E402
 import workloads as W  # noqa: E402
 
-WINDOWS = {"config1": 60, "config2": 8}
+WINDOWS = {"config1": 60, "config2": 1}
 CONFIG2_LMIN = 1e-3
 
 
