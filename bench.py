@@ -36,6 +36,7 @@ sys.path.insert(0, ROOT)
 # sign of its last lane):
 BYTES_PER_SWEEP_VOXEL = 28      # x 4 + b 4 + record 16 read, x' 4 written
 BYTES_PER_CHEB_SWEEP_VOXEL = 32  # the same plus x_{k-1} 4 (the Chebyshev semi-iteration's second operand)
+BYTES_PER_GS_PASS_VOXEL = 21     # one colour pass: x 4 + record 16 of every voxel, b 4 read and x 4 written for 1/8
 BYTES_PER_MONO_VOXEL = 32       # fused monodomain step: v, w read 8 + written 8 + record 16
 BYTES_PER_IE_SWEEP_VOXEL = 32   # implicit sweep: x, f, 1/(1 + a D) read 12 + record 16 + x' written 4
 FP16_LAYOUT_SWEEP_BYTES = 19    # a sweep's bytes with fp16 fibre records (6 + 1 mask): for comparison only
@@ -64,9 +65,11 @@ def _args():
     ap.add_argument("--sdf-n", type=int, default=512, help="sdf: voxels per side of the schematic heart's box")
     ap.add_argument("--model", choices=["mono", "bi"], default="mono", help="slab: model")
     ap.add_argument("--slab-n", type=int, default=512, help="slab: voxels per side")
-    ap.add_argument("--solver", choices=["jacobi", "chebyshev"], default=None,
-                    help="elliptic solve: the paper's damped Jacobi, or Chebyshev-accelerated Jacobi "
-                         "(default: jacobi; chebyshev for ecg)")
+    ap.add_argument("--solver", choices=["jacobi", "chebyshev", "gs"], default=None,
+                    help="elliptic solve: the paper's damped Jacobi, Chebyshev-accelerated Jacobi, or eight-colour "
+                         "Gauss-Seidel (default: jacobi; chebyshev for ecg)")
+    ap.add_argument("--no-solver-legs", action="store_true",
+                    help="skip the bidomain default's extra windows with the Chebyshev and Gauss-Seidel solves")
     ap.add_argument("--sig-o", type=float, default=1.0, help="ecg: torso conductivity (mS/mm)")
     ap.add_argument("--omega", type=float, default=None,
                     help="Jacobi damping: > 0 that value, 0 the bound rule, < 0 estimated from the spectrum")
@@ -101,6 +104,9 @@ def _workload(name, model="mono", slab_n=512, diffusion="explicit", solver=None,
     if solver == "chebyshev":
         c.params.solver = 1
         desc += "; elliptic solve by Chebyshev-accelerated Jacobi (interval estimated at set-up)"
+    if solver == "gs":
+        c.params.solver = 2
+        desc += "; elliptic solve by eight-colour Gauss-Seidel"
     return c, desc
 
 
@@ -427,6 +433,59 @@ def oracle_step_error(ep, sim, case, a):
     return out
 
 
+def solver_legs(ep, case, a, blob0, stream, flush, end_state, peak):
+    """The timed window again from its start state with the elliptic solve by
+    the Chebyshev semi-iteration (correction form, interval estimated at
+    set-up) and by eight-colour Gauss-Seidel, every solve to the same rel_tol:
+    rate, sweeps, sweep launch time against the HBM peak, and the largest
+    difference of V_m and V_e from the damped-Jacobi window's end state."""
+    import dataclasses
+    import torch
+    out = {}
+    M = case.n_tissue
+    for name, solver in (("chebyshev", 1), ("gauss_seidel", 2)):
+        c = dataclasses.replace(case, params=dataclasses.replace(case.params, solver=solver))
+        h = ep.Sim(c.nx, c.ny, c.nz, c.dx, c.model, c.precision, use_torch=True, stream=stream.cuda_stream)
+        h.set_mask(c.mask_flat())
+        h.set_fibres(c.fib_flat())
+        h.set_params(c.params)
+        for st in c.stimuli:
+            h.add_stimulus(st.lo, st.hi, st.t_start, st.dur, st.amp)
+        h.write_state(blob0)
+        info = h.info()
+        h.profile_enable(True)
+        ms, iters, statuses = [], [], []
+        for _ in range(a.steps):
+            with torch.cuda.stream(stream):
+                flush.fill_(1.0)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            st = h.step(1, allow_noconv=True)
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+            iters.append(st.iters)
+            statuses.append(h.last_status)
+        prof = h.profile()
+        passes = 8 if solver == 2 else 1
+        launch_s = prof.sweep_ms / 1e3 / max(prof.sweeps * passes, 1)
+        per = BYTES_PER_CHEB_SWEEP_VOXEL if solver == 1 else BYTES_PER_GS_PASS_VOXEL
+        total_s = sum(ms) / 1e3
+        d = {"value": M * a.steps / total_s, "unit": "tissue voxel-steps/s", "ms_per_step": 1e3 * total_s / a.steps,
+             "sweeps_per_step": iters, "step_status": statuses,
+             "kernel": ("k_stencil<float,M_JAC_CHEB> (correction form)" if solver == 1 else
+                        "k_stencil<float,M_JAC_GS> (one colour pass; 8 a sweep)"),
+             "avg_launch_us": launch_s * 1e6, "algorithmic_bytes_per_voxel": per,
+             "hbm_frac": per * M / launch_s / 1e9 / peak if launch_s > 0 else None,
+             "max_abs_dVm_vs_jacobi_mV": float(np.abs(h.read(ep.EP_VM_MV) - end_state[0]).max()),
+             "max_abs_dVe_vs_jacobi_mV": float(np.abs(h.read(ep.EP_VE_MV) - end_state[1]).max())}
+        if solver == 1:
+            d["interval"] = [info.cheb_lmin, info.cheb_lmax]
+        out[name] = d
+        h.close()
+    return out
+
+
 def run_ours(a):
     import torch
     import paper_2302_12519_gb300 as ep
@@ -474,6 +533,7 @@ def run_ours(a):
     nb = sim.state_bytes()
     blobs = [torch.empty(nb, dtype=torch.uint8, pin_memory=True).numpy() for _ in range(2)]
     sim.read_state(blobs[0])
+    blob0 = blobs[0].copy()
     if dist is not None:
         dist.barrier()
     sim.profile_enable(True)
@@ -498,6 +558,7 @@ def run_ours(a):
     torch.cuda.synchronize()
     clk = clocks.stop()
     prof = sim.profile()
+    end_state = (sim.read(ep.EP_VM_MV), sim.read(ep.EP_VE_MV)) if not mono else None
     err = None
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
         err = oracle_step_error(ep, sim, case, a)
@@ -527,14 +588,17 @@ def run_ours(a):
         share = prof.other_ms / 1e3 / total_s
     else:
         sweep_s = prof.sweep_ms / 1e3
-        launch_s = sweep_s / max(prof.sweeps, 1)
-        per_voxel = BYTES_PER_CHEB_SWEEP_VOXEL if a.solver == "chebyshev" else BYTES_PER_SWEEP_VOXEL
+        launch_s = sweep_s / max(prof.sweeps * (8 if a.solver == "gs" else 1), 1)
+        per_voxel = (BYTES_PER_CHEB_SWEEP_VOXEL if a.solver == "chebyshev" else
+                     BYTES_PER_GS_PASS_VOXEL if a.solver == "gs" else BYTES_PER_SWEEP_VOXEL)
         alg_bytes = per_voxel * n_dom   # over tissue + torso when a torso is set
         kname = ("k_stencil<float,M_JAC(_CHEB)> over the torso items away from the tissue + "
                  "k_stencil<float,M_JAC_BATH(_CHEB)> over the rest (one elliptic sweep over tissue + torso)"
                  if torso else "k_stencil<float,M_JAC> (damped Jacobi sweep)")
         if a.solver == "chebyshev":
             kname += ", Chebyshev-accelerated"
+        if a.solver == "gs":
+            kname = "k_stencil<float,M_JAC_GS> (one colour pass of the eight-colour Gauss-Seidel sweep)"
         share = sweep_s / total_s
     achieved = alg_bytes / launch_s / 1e9 if launch_s > 0 else 0.0
     stem = (f"ie_sweep_slab{a.slab_n}_mono" if mono and implicit else
@@ -549,7 +613,7 @@ def run_ours(a):
                 "traffic": (tpv * (n_dom if not mono else M)) if tpv is not None else None,
                 "algorithmic_bytes_per_launch": alg_bytes, "avg_launch_us": launch_s * 1e6,
                 "kernel_share_of_step": share if world == 1 else None, "peak_source": peak_src}
-    if not mono and a.solver != "chebyshev" and not torso:
+    if not mono and a.solver == "jacobi" and not torso:
         # the same launch time counted at the 19 bytes a voxel of fp16 fibre records
         roofline["frac_at_fp16_record_bytes"] = FP16_LAYOUT_SWEEP_BYTES * n_dom / launch_s / 1e9 / peak
 
@@ -588,6 +652,11 @@ def run_ours(a):
                           f"{info['per_sweep_s']:.3f} s/sweep, {info['sample_s']:.1f} s of CPU work), extrapolated "
                           f"to the {k:.0f} sweeps per step of the timed GPU steps")}
 
+    legs = None
+    if (not mono and a.solver == "jacobi" and not torso and a.diffusion == "explicit" and world == 1
+            and not a.no_solver_legs):
+        legs = solver_legs(ep, case, a, blob0, stream, flush, end_state, peak)
+
     if rank == 0:
         line = {"metric": "voxel-steps/sec", "value": value, "unit": "tissue voxel-steps/s", "n_gpus": world,
                 "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1e3 * total_s / a.steps,
@@ -605,7 +674,7 @@ def run_ours(a):
                            "elliptic_voxels": n_dom, "ecg": ecg_trace},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "error_vs_oracle": err,
                 "gpu_launches": int(prof.sweep_launches + prof.other_launches),
-                "clocks": clk}
+                "clocks": clk, "other_solvers": legs}
         print(json.dumps(line), flush=True)
     sim.close()
     if dist is not None:

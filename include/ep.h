@@ -104,10 +104,19 @@ typedef struct {
                              (a = dt/K, ve of step n), solved by the undamped Jacobi step of
                              Eq. iejac1 from v* to rel_tol (Sec. "Implicit Euler", "Diffusion").
                              Implicit handles are stepped by ep_step only, not in a batch. */
-    int solver;           /* elliptic solve: EP_SOLVER_JACOBI, the damped Jacobi of Eq. dampjac1 (default),
-                             or EP_SOLVER_CHEBYSHEV, Golub and Varga's Chebyshev semi-iteration on
+    int solver;           /* elliptic solve: EP_SOLVER_JACOBI, the damped Jacobi of Eq. dampjac1 (default);
+                             EP_SOLVER_CHEBYSHEV, Golub and Varga's Chebyshev semi-iteration on
                              the Jacobi step (no counterpart in the paper, whose future work names
-                             faster solvers).  Same stop rule, FP64 norms and cap. */
+                             faster solvers; FP32 handles run it in correction form, restarted from
+                             e = 0 on A e = b - A x each time a cycle has cut ||r|| by 1e3, which
+                             keeps the FP32 rounding of x out of the iteration);
+                             EP_SOLVER_GAUSS_SEIDEL, Gauss-Seidel (SOR with omega = jacobi_omega when
+                             0 < jacobi_omega < 2, else omega = 1) over the eight colour classes
+                             (i, j, k mod 2): the deterministic form of the paper's in-place Jacobi,
+                             whose races read already-updated neighbours (Sec. "Jacobi method");
+                             a sweep is eight colour passes, in place, its residual the sum of each
+                             colour's residuals as its pass forms them.  Not with a torso, not in
+                             a batch.  Same stop rule, FP64 norms and cap (in sweeps). */
     double cheb_lmin, cheb_lmax;  /* EP_SOLVER_CHEBYSHEV: interval of the eigenvalues of D^-1 A that the
                              polynomial targets (A the elliptic operator, D its diagonal as stored);
                              both <= 0: estimated at set-up (Lanczos, 40 steps), read back with
@@ -118,6 +127,7 @@ typedef struct {
 #define EP_IMPLICIT 1
 #define EP_SOLVER_JACOBI 0
 #define EP_SOLVER_CHEBYSHEV 1
+#define EP_SOLVER_GAUSS_SEIDEL 2
 
 typedef struct {
     int iters;               /* Jacobi sweeps of the last elliptic solve (0 for monodomain) */

@@ -23,7 +23,7 @@ STATUS_NAMES = ["EP_OK", "EP_EINVAL", "EP_ENOMEM", "EP_ECUDA", "EP_ENOCONV", "EP
                 "EP_EBUSY", "EP_EREJECTED", "EP_ECANCELLED"]
 EP_MONO, EP_BI = 0, 1
 EP_EXPLICIT, EP_IMPLICIT = 0, 1
-EP_SOLVER_JACOBI, EP_SOLVER_CHEBYSHEV = 0, 1
+EP_SOLVER_JACOBI, EP_SOLVER_CHEBYSHEV, EP_SOLVER_GAUSS_SEIDEL = 0, 1, 2
 EP_FP32, EP_FP64 = 0, 1
 EP_VM_MV, EP_W, EP_VE_MV, EP_TACT, EP_V, EP_VE = range(6)
 

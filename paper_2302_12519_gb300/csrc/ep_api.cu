@@ -119,6 +119,7 @@ struct ep_sim {
     cudaGraphExec_t sweep_graph = nullptr;
     cudaGraphExec_t ie_graph = nullptr;   // implicit-diffusion sweeps
     void *ie_x = nullptr, *ie_inv = nullptr;
+    void *x2 = nullptr;          // second correction buffer of the FP32 Chebyshev solve
     long long ie_seen = 0;                // implicit sweeps counted by earlier calls
     long long step = 0;
     bool noalloc_call = false;   // inside ep_step_noalloc: scratch is the static array, no graph
@@ -191,7 +192,10 @@ bool params_ok(const ep_params &p, std::string &why)
     if (!std::isfinite(p.rel_tol) || p.rel_tol < 0.0) { why = "rel_tol must be >= 0"; return false; }
     if (p.check_every < 1 || p.max_iter < 1) { why = "check_every and max_iter must be >= 1"; return false; }
     if (p.diffusion != EP_EXPLICIT && p.diffusion != EP_IMPLICIT) { why = "diffusion must be EP_EXPLICIT or EP_IMPLICIT"; return false; }
-    if (p.solver != EP_SOLVER_JACOBI && p.solver != EP_SOLVER_CHEBYSHEV) { why = "solver must be EP_SOLVER_JACOBI or EP_SOLVER_CHEBYSHEV"; return false; }
+    if (p.solver != EP_SOLVER_JACOBI && p.solver != EP_SOLVER_CHEBYSHEV && p.solver != EP_SOLVER_GAUSS_SEIDEL) {
+        why = "solver must be EP_SOLVER_JACOBI, EP_SOLVER_CHEBYSHEV or EP_SOLVER_GAUSS_SEIDEL";
+        return false;
+    }
     if (p.solver == EP_SOLVER_CHEBYSHEV && !(p.cheb_lmin <= 0.0 && p.cheb_lmax <= 0.0) &&
         !(std::isfinite(p.cheb_lmin) && std::isfinite(p.cheb_lmax) && p.cheb_lmin > 0.0 && p.cheb_lmin < p.cheb_lmax)) {
         why = "Chebyshev interval must satisfy 0 < cheb_lmin < cheb_lmax (both <= 0: estimated)";
@@ -286,14 +290,36 @@ size_t abytes(size_t b) { return b ? b : 16; }   // dalloc's size of a request
 constexpr int kLanczosSteps = 40;
 constexpr int kLanczosScalars = 2 + 2 * kLanczosSteps;   // alpha, beta of the current step; alpha_j, beta_{j+1}
 
+// The set-up estimates the spectrum of D^-1 A for the Chebyshev solver and for the
+// damped Jacobi's estimated damping.
+bool needs_spectrum(const ep_sim *s)
+{
+    return s->p.solver == EP_SOLVER_CHEBYSHEV || (s->p.solver == EP_SOLVER_JACOBI && s->p.jacobi_omega < 0.0);
+}
+
+// Residual partial sums per stencil work item: one, or one per colour pass of the
+// eight-colour sweep.
+long long partial_slots(const ep_sim *s)
+{
+    const long long per = s->have_params && s->p.solver == EP_SOLVER_GAUSS_SEIDEL ? 8 : 1;
+    return std::max<long long>(per * s->max_items, s->nchunk);
+}
+
 // Set-up scratch of the Chebyshev interval estimate (0 when the interval is
 // given or the solver is damped Jacobi): the Lanczos scalars and two partial
 // sums per reduction chunk.
 size_t lanczos_bytes(const ep_sim *s)
 {
     if (!s->have_params || s->d.model != EP_BI || s->p.cheb_lmin > 0.0) return 0;
-    if (s->p.solver != EP_SOLVER_CHEBYSHEV && !(s->p.jacobi_omega < 0.0)) return 0;   // no spectrum needed
+    if (!needs_spectrum(s)) return 0;
     return sizeof(double) * ((size_t)kLanczosScalars + 2 * (size_t)s->nchunk);
+}
+
+// FP32 bidomain handles with the Chebyshev solver run it in correction form, which
+// needs a third iterate buffer.
+bool cheb_eform(const ep_sim *s, size_t rb)
+{
+    return rb == sizeof(float) && s->have_params && s->d.model == EP_BI && s->p.solver == EP_SOLVER_CHEBYSHEV;
 }
 
 void footprint(const ep_sim *s, size_t rb, size_t *resident, size_t *peak)
@@ -304,8 +330,9 @@ void footprint(const ep_sim *s, size_t rb, size_t *resident, size_t *peak)
     r += abytes(sizeof(Seg) * (size_t)s->max_items) + abytes(sizeof(int) * P.order.size());
     r += abytes(sizeof(Chunk) * P.chunks.size()) + abytes(sizeof(int) * P.comp_chunk0.size());
     r += abytes(sizeof(long long) * P.comp_count.size()) + abytes(sizeof(double) * (size_t)s->ncomp);
-    r += abytes(sizeof(double) * (size_t)std::max<long long>(s->max_items, s->nchunk)) + abytes(sizeof(Ctl));
+    r += abytes(sizeof(double) * (size_t)partial_slots(s)) + abytes(sizeof(Ctl));
     if (s->have_params && s->p.diffusion == EP_IMPLICIT) r += 2 * abytes(rb * n);   // second iterate, 1/(1 + a D)
+    if (cheb_eform(s, rb)) r += abytes(rb * n);
     const bool torso = !s->torso.empty();
     if (torso) r += abytes(sizeof(float4) * n) + abytes(sizeof(Seg) * (size_t)s->max_items);   // domain records, items
     if (s->ecg_q[0] >= 0) r += abytes(sizeof(double) * 3 * (size_t)s->ecg_cap);
@@ -560,12 +587,17 @@ ep_status setup_typed(ep_sim *s)
     s->comp_chunk0 = (int *)dalloc(s, sizeof(int) * comp_chunk0.size());
     s->comp_count = (long long *)dalloc(s, sizeof(long long) * comp_count.size());
     s->means = (double *)dalloc(s, sizeof(double) * nc);
-    s->partials = (double *)dalloc(s, sizeof(double) * std::max<long long>(s->max_items, s->nchunk));
+    s->partials = (double *)dalloc(s, sizeof(double) * (size_t)partial_slots(s));
     s->ctl = (Ctl *)dalloc(s, sizeof(Ctl));
     if (ie) {
         s->ie_x = dalloc(s, rb * n);
         s->ie_inv = dalloc(s, rb * n);
         if (!s->ie_x || !s->ie_inv) return fail(s, EP_ENOMEM, "device allocation failed");
+    }
+    s->x2 = nullptr;
+    if (cheb_eform(s, rb)) {
+        s->x2 = dalloc(s, rb * n);
+        if (!s->x2) return fail(s, EP_ENOMEM, "device allocation failed");
     }
     s->rec_e = s->rec;
     s->segs_e = s->segs;
@@ -625,7 +657,7 @@ ep_status setup_typed(ep_sim *s)
         CK(cudaGetLastError());
     }
     // the spectrum of D^-1 A: for the Chebyshev solver, and for damped Jacobi with estimated damping
-    if ((s->p.solver == EP_SOLVER_CHEBYSHEV || s->p.jacobi_omega < 0.0) && s->d.model == EP_BI) {
+    if (needs_spectrum(s) && s->d.model == EP_BI) {
         if (s->p.cheb_lmin > 0.0) {
             s->cheb_lmin = s->p.cheb_lmin;
             s->cheb_lmax = s->p.cheb_lmax;
@@ -646,6 +678,7 @@ ep_status setup_typed(ep_sim *s)
         k_fill<real><<<grid_for(n, 256), 256, 0, st>>>((real *)s->x[i], n, real(0));
     }
     k_fill<real><<<grid_for(n, 256), 256, 0, st>>>((real *)s->b, n, real(0));
+    if (s->x2) k_fill<real><<<grid_for(n, 256), 256, 0, st>>>((real *)s->x2, n, real(0));
     k_fill<real><<<grid_for(n, 256), 256, 0, st>>>((real *)s->tact, n, real(-1));
     CK(cudaGetLastError());
     CK(cudaMemsetAsync(s->ctl, 0, sizeof(Ctl), st));
@@ -726,6 +759,7 @@ Inst<real> make_inst(const ep_sim *s)
     I.pad2 = 0;
     I.ie_x = (real *)s->ie_x;
     I.ie_inv = (const real *)s->ie_inv;
+    I.x2 = (real *)s->x2;
     const double C = 1.0 / (8.0 * s->d.dx_mm * s->d.dx_mm);
     const double sLie = s->p.sig_iL + s->p.sig_eL, sTie = s->p.sig_iT + s->p.sig_eT;
     const double fac = s->d.model == EP_MONO ? s->p.lambda / (1.0 + s->p.lambda) : 1.0;
@@ -737,10 +771,13 @@ Inst<real> make_inst(const ep_sim *s)
     I.coef_par = (real)(s->p.dt_ms / s->p.K * fac);
     I.coef_jac = (real)(s->omega / C);
     I.alpha_ie = (real)(s->p.dt_ms / s->p.K * fac);
-    I.solver = s->p.solver == EP_SOLVER_CHEBYSHEV && s->cheb_lmax > 0.0 ? 1 : 0;
+    I.solver = s->p.solver == EP_SOLVER_CHEBYSHEV && s->cheb_lmax > 0.0 ? 1
+               : s->p.solver == EP_SOLVER_GAUSS_SEIDEL && s->d.model == EP_BI ? 2 : 0;
     I.pad3 = 0;
     I.cheb_tau_c = real(0);
     I.cheb_rho = I.cheb_theta = 0.0;
+    I.cheb_eform = I.solver && s->x2 ? 1 : 0;
+    I.pad5 = 0;
     if (I.solver) {
         const double lo = s->cheb_lmin, hi = s->cheb_lmax;
         const double rho = (hi - lo) / (hi + lo);
@@ -825,17 +862,18 @@ ep_status build_sweep_graph(ep_sim *s, const Sweep &sweep, cudaGraphExec_t *out)
 
 // Queues the sweeps of one solve in graph chunks with one chunk of look-ahead:
 // the host reads the control block one chunk behind, so the GPU never waits
-// for it.  At most max_iter sweeps do work; launch max_iter + 1 marks a capped
-// solve done.  Returns the launches queued in *queued_out.
+// for it.  At most max_iter sweeps (per_sweep launches each) do work; the
+// launch after them marks a capped solve done.  Returns the launches queued in
+// *queued_out.
 template <typename Sweep>
-ep_status run_sweeps(ep_sim *s, const Sweep &sweep, cudaGraphExec_t *graph, long long *queued_out)
+ep_status run_sweeps(ep_sim *s, const Sweep &sweep, cudaGraphExec_t *graph, long long *queued_out, int per_sweep = 1)
 {
     cudaStream_t st = s->stream;
     if (!s->noalloc_call) {
         ep_status gs = build_sweep_graph(s, sweep, graph);
         if (gs != EP_OK) return gs;
     }
-    const long long limit = (long long)s->p.max_iter + 1;
+    const long long limit = (long long)per_sweep * s->p.max_iter + 1;
     long long queued = 0;
     for (int c = 0;; ++c) {
         if (!s->noalloc_call && queued + kSweepChunk <= limit) {
@@ -905,7 +943,7 @@ cudaError_t allow_stencil_active(std::integer_sequence<int, MODES...>)
 ep_status configure_kernels(ep_sim *s)
 {
     using Modes = std::integer_sequence<int, M_APPLY, M_RHS, M_PAR_MONO, M_PAR_BI, M_JAC, M_IE_RHS, M_IE, M_JAC_BATH,
-                                        M_APPLY_BATH, M_JAC_CHEB, M_JAC_BATH_CHEB>;
+                                        M_APPLY_BATH, M_JAC_CHEB, M_JAC_BATH_CHEB, M_JAC_GS>;
     cudaError_t e = allow_stencil<float>(Modes{});
     if (e == cudaSuccess) e = allow_stencil<double>(Modes{});
     if (e == cudaSuccess)
@@ -945,6 +983,10 @@ ep_status ensure_ready(ep_sim *s)
     }
     const double sL = s->p.sig_iL + s->p.sig_eL, sT = s->p.sig_iT + s->p.sig_eT;
     s->omega = s->p.jacobi_omega > 0.0 ? s->p.jacobi_omega : std::min(1.0, 1.8 * (sL + 2.0 * sT) / (8.0 * sL));
+    if (s->p.solver == EP_SOLVER_GAUSS_SEIDEL) {   // SOR factor: given, else Gauss-Seidel
+        if (!s->torso.empty()) return fail(s, EP_EINVAL, "the Gauss-Seidel solve does not take a torso");
+        s->omega = s->p.jacobi_omega > 0.0 ? s->p.jacobi_omega : 1.0;
+    }
     ep_status cs = configure_kernels(s);
     if (cs != EP_OK) return cs;
     ep_status st = s->d.precision == EP_FP64 ? setup_typed<double>(s) : setup_typed<float>(s);
@@ -982,7 +1024,9 @@ ep_status solve_elliptic(ep_sim *s, const Inst<real> &I, int &iters, double &rel
     long long queued = 0;
     ep_status rs = EP_OK;
     const bool cheb = I.solver == 1;   // the sweep instance matches the handle's solver
-    if (s->torso.empty()) {
+    if (I.solver == 2) {   // eight colour passes a sweep
+        rs = run_sweeps(s, OneSweep<real, M_JAC_GS>{I}, &s->sweep_graph, &queued, 8);
+    } else if (s->torso.empty()) {
         rs = cheb ? run_sweeps(s, OneSweep<real, M_JAC_CHEB>{I}, &s->sweep_graph, &queued)
                   : run_sweeps(s, OneSweep<real, M_JAC>{I}, &s->sweep_graph, &queued);
     } else {   // tissue + torso: the domain's items and records, split by distance from the tissue
@@ -1637,9 +1681,10 @@ ep_status ep_step_noalloc(ep_sim *s, int n_steps, ep_step_stats *stats)
                                   "ep_set_state or ep_get_info once first): set-up allocates device memory");
     if (s->ecg_q[0] >= 0 && s->ecg_n + n_steps > s->ecg_cap)
         return fail(s, EP_EBUSY, "the ECG record would overflow: read it with ep_read_ecg first");
-    if (std::max(stencil_blocks(s), s->nseg_e) > kNoAllocMaxPartials || s->nchunk > kNoAllocMaxPartials)
-        return fail(s, EP_EINVAL, "grid too large for ep_step_noalloc: more than 32768 stencil work items or "
-                                  "reduction chunks (use ep_step)");
+    const long long passes = s->p.solver == EP_SOLVER_GAUSS_SEIDEL ? 8 : 1;   // partial sums per work item
+    if (passes * std::max(stencil_blocks(s), s->nseg_e) > kNoAllocMaxPartials || s->nchunk > kNoAllocMaxPartials)
+        return fail(s, EP_EINVAL, "grid too large for ep_step_noalloc: more than 32768 stencil work items "
+                                  "(4096 with the Gauss-Seidel solve) or reduction chunks (use ep_step)");
     if (s->ncomp > kNoAllocMaxComponents)
         return fail(s, EP_EINVAL, "mask has more than 4096 tissue components: too many for ep_step_noalloc "
                                   "(use ep_step)");
@@ -2076,6 +2121,8 @@ ep_status ep_batch_add(ep_batch *b, ep_sim *s, int *slot)
         return bfail(b, EP_EINVAL, "implicit-diffusion handles are stepped by ep_step only");
     if (!s->torso.empty() || s->ecg_q[0] >= 0)
         return bfail(b, EP_EINVAL, "torso and ECG handles are stepped by ep_step only");
+    if (s->have_params && s->p.solver == EP_SOLVER_GAUSS_SEIDEL)
+        return bfail(b, EP_EINVAL, "Gauss-Seidel handles are stepped by ep_step only");
     if (b->model >= 0 && s->d.model != b->model)
         return bfail(b, EP_EINVAL, "batched members must share the model (monodomain or bidomain)");
     for (ep_sim *t : b->slot)
@@ -2210,6 +2257,7 @@ ep_status ep_batch_autotune(ep_batch *b, int trial_sweeps)
             for (int r = 0; r < b->ninst; ++r) {
                 Ctl c = ctl0[r];
                 c.done = 0; c.sweep = 0; c.arrive = 0; c.jarrive = 0; c.thresh2 = -1.0; c.bnorm2 = 1e300;
+                c.cycle0 = 0; c.r0n2 = 0.0;
                 CKB(cudaMemcpyAsync(b->slot[b->order[r]]->ctl, &c, sizeof(Ctl), cudaMemcpyHostToDevice, s0));
             }
             // one sweep of every group in turn, each group swept trial_sweeps times

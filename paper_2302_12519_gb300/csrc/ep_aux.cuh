@@ -171,19 +171,38 @@ struct RedSmem {
 
 enum RedField { RED_B = 0, RED_X_FINAL = 1 };
 
-// means[c] = mean over component c of b, or of the final iterate of the solve
-// (x1 when the solve took an odd number of sweeps).
+// Final iterate of an elliptic solve of `iters` sweeps at voxel q: x1 after an
+// odd number of sweeps, else x0; in the Chebyshev correction form x0 + e, e the
+// last correction (x1 after an odd number of sweeps, else x2; none after 0);
+// x0 for the eight-colour sweep, which works in place.
+template <typename real>
+__device__ __forceinline__ double final_iterate(const Inst<real> &I, int iters, int q)
+{
+    if (I.solver == 2) return (double)I.x0[q];
+    if (I.cheb_eform) {
+        double x = (double)I.x0[q];
+        if (iters > 0) x += (double)((iters & 1) ? I.x1[q] : I.x2[q]);
+        return x;
+    }
+    return (double)((iters & 1) ? I.x1[q] : I.x0[q]);
+}
+
+// means[c] = mean over component c of b, or of the final iterate of the solve.
 template <typename real>
 __device__ __forceinline__ void comp_mean_item(const Inst<real> &I, int field, int item, int nitems, RedSmem &sm)
 {
     Ctl *ctl = I.ctl;
-    const real *x = field == RED_B ? I.b : ((ctl->iters & 1) ? I.x1 : I.x0);
+    const int iters = ctl->iters;
     const Chunk ch = I.chunks[item];
     const bool rhs_torso = field == RED_B && I.torso;   // b is 0 on the torso (stale values there are skipped)
     double s = 0.0;
     for (int i = ch.start + threadIdx.x; i < ch.end; i += kRedThreads) {
         const int q = I.idx[i];
-        if (!rhs_torso || rec_tissue(I.rec[q])) s += (double)x[q];
+        if (field == RED_B) {
+            if (!rhs_torso || rec_tissue(I.rec[q])) s += (double)I.b[q];
+        } else {
+            s += final_iterate(I, iters, q);
+        }
     }
     s = block_sum<kRedThreads>(s, sm.sred);
     if (threadIdx.x == 0) I.partials[item] = s;
@@ -230,6 +249,8 @@ __device__ __forceinline__ void comp_subtract_item(const Inst<real> &I, int item
         ctl->sweep = 0;
         ctl->jarrive = 0;
         ctl->iters = 0;
+        ctl->cycle0 = 0;
+        ctl->r0n2 = 0.0;
         ctl->converged = (t == 0.0);
         ctl->diverged = 0;
         ctl->rnorm2 = 0.0;
@@ -292,6 +313,8 @@ __global__ void __launch_bounds__(kRedThreads) k_ie_start(Inst<real> I)
         ctl->sweep = 0;
         ctl->jarrive = 0;
         ctl->iters = 0;
+        ctl->cycle0 = 0;
+        ctl->r0n2 = 0.0;
         ctl->converged = (t == 0.0);
         ctl->diverged = 0;
         ctl->rnorm2 = 0.0;
@@ -484,12 +507,12 @@ __global__ void k_ecg_record(const real *ve, int q0, int q1, int q2, double *rec
 template <typename real>
 __device__ __forceinline__ void project_item(const Inst<real> &I, int item)
 {
-    const real *src = (I.ctl->iters & 1) ? I.x1 : I.x0;
+    const int iters = I.ctl->iters;
     const Chunk ch = I.chunks[item];
     const double m = I.means[ch.comp];
     for (int i = ch.start + threadIdx.x; i < ch.end; i += kRedThreads) {
         const int q = I.idx[i];
-        I.x0[q] = (real)((double)src[q] - m);
+        I.x0[q] = (real)(final_iterate(I, iters, q) - m);
     }
 }
 

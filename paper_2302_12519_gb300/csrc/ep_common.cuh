@@ -36,15 +36,19 @@ constexpr int kChunk = 2048;                // tissue voxels per reduction chunk
 // voxels, sig_o I per torso voxel of the vertex block).
 // M_JAC_CHEB, M_JAC_BATH_CHEB: the same sweeps accelerated by the Chebyshev
 // semi-iteration (separate instances, so the plain sweeps carry none of it).
+// M_JAC_GS: one colour pass of the eight-colour Gauss-Seidel / SOR sweep, in
+// place on x0 (a sweep is eight launches, colours 0..7).
 enum Mode { M_APPLY = 0, M_RHS = 1, M_PAR_MONO = 2, M_PAR_BI = 3, M_JAC = 4, M_IE_RHS = 5, M_IE = 6, M_JAC_BATH = 7,
-            M_APPLY_BATH = 8, M_JAC_CHEB = 9, M_JAC_BATH_CHEB = 10 };
+            M_APPLY_BATH = 8, M_JAC_CHEB = 9, M_JAC_BATH_CHEB = 10, M_JAC_GS = 11 };
 enum Diffusion { DIFF_EXPLICIT = 0, DIFF_IMPLICIT = 1 };
 
 // Modes that run a solve sweep (Jacobi of the elliptic or the implicit parabolic system).
 template <int MODE>
 constexpr bool kCheb = MODE == M_JAC_CHEB || MODE == M_JAC_BATH_CHEB;
 template <int MODE>
-constexpr bool kJac = MODE == M_JAC || MODE == M_JAC_BATH || kCheb<MODE>;
+constexpr bool kGS = MODE == M_JAC_GS;
+template <int MODE>
+constexpr bool kJac = MODE == M_JAC || MODE == M_JAC_BATH || kCheb<MODE> || kGS<MODE>;
 template <int MODE>
 constexpr bool kTwoTerm = MODE == M_JAC_BATH || MODE == M_APPLY_BATH || MODE == M_JAC_BATH_CHEB;
 template <int MODE>
@@ -88,6 +92,10 @@ struct Ctl {
     // jarrive / nitems = j; sweeps that do not check the residual only add to it
     unsigned long long jarrive;
     long long ie_total;   // sweeps of the implicit parabolic solves, summed over steps
+    // Chebyshev solve in correction form: the sweep that starts the current cycle, and
+    // ||r||^2 at that cycle's start
+    int cycle0, pad_c;
+    double r0n2;
 };
 
 struct Chunk {
@@ -129,7 +137,8 @@ struct Inst {
     const real *ie_inv;
     real alpha_ie;
     // Chebyshev semi-iteration of the elliptic solve (solver == 1): tau / C for the
-    // basic step, rho and theta = acosh(1 / rho) for the weights
+    // basic step, rho and theta = acosh(1 / rho) for the weights; solver == 2 is the
+    // eight-colour Gauss-Seidel / SOR solve (coef_jac = omega / C)
     int solver, pad3;
     real cheb_tau_c;
     double cheb_rho, cheb_theta;
@@ -142,7 +151,16 @@ struct Inst {
     // single-term kernel): this launch's first item among the sweep's items, and their count
     // (0: the launch is the whole sweep)
     int item0, nitems_all;
+    // Chebyshev solve in correction form (FP32 handles): the iterate is x0 + e, e in x1 / x2
+    // (sweep j >= 1 reads e_j from x1 when j is odd, else from x2), b holds the residual of x0
+    // at the cycle's start; a cycle restarts from e = 0 once it has cut ||r|| by kRestart
+    real *x2;
+    int cheb_eform, pad5;
 };
+
+// A correction-form Chebyshev cycle restarts when ||r||^2 has fallen below this
+// fraction of its value at the cycle's start (a factor 1e3 in the norm).
+constexpr double kRestart2 = 1e-6;
 
 // Weight of sweep k of the Chebyshev semi-iteration: w = 1 for k = 0, else
 // w_{k+1} = 2 T_k(1/rho) / (rho T_{k+1}(1/rho)) in the overflow-free form

@@ -82,7 +82,14 @@ struct Op {
     int nz;
     int cheb;          // Jacobi sweep accelerated by the Chebyshev semi-iteration
     real cheb_w;       // its weight for this sweep
+    // correction form, bits: kRestart = first sweep of a cycle (e starts from 0: the output
+    // is tau D^-1 r, and r becomes the cycle's right-hand side, stored over b); kFold = add
+    // the iterate read (the old cycle's e) into x0; kPrev0 = the cycle's previous iterate is 0
+    int cform;
+    int colour;        // eight-colour sweep: the colour this launch updates
 };
+
+constexpr int kRestart = 1, kFold = 2, kPrev0 = 4;
 
 // Loads of one plane for a lane's two voxel rows (lo = y0 + w - 1, hi = y0 + w).
 template <typename real, int MODE>
@@ -326,7 +333,10 @@ __device__ __forceinline__ void plane_step(const Inst<real> &I, const Op<real> &
             so_sum = P.dLoL * qxm - dR * qxp + P.dYm * qym - P.dHi * qyp + P.dzm * qzm - C.dLo * qzp;
             own = P.dLo;
         }
-        if (g.out_lane && own != real(0)) {
+        bool mine = true;
+        if constexpr (kGS<MODE>)   // this launch's colour only: (x & 1) + 2 (y & 1) + 4 (z & 1)
+            mine = ((g.x & 1) | ((g.ylo & 1) << 1) | (((k - 1) & 1) << 2)) == o.colour;
+        if (g.out_lane && own != real(0) && mine) {
             real s = P.tLoL * phxm - tR * phxp + P.tYm * phym - P.tHi * phyp + P.tzm * phzm - C.tLo * phzp;
             if constexpr (TT) s = P.tLo * s + so_sum;   // the tissue term acts on tissue voxels only
             const real Lu = o.C * s;
@@ -337,12 +347,18 @@ __device__ __forceinline__ void plane_step(const Inst<real> &I, const Op<real> &
                 o.out[q] = -Lu;
             } else if (kJac<MODE>) {
                 const real r = P.e0 - Lu;
-                const real basic = P.uLo + o.coef * P.e1 * r;
-                if (kCheb<MODE> && o.cheb) {   // x_{k+1} = w (basic - x_{k-1}) + x_{k-1}; x_{k-1} came through the ring
-                    const real prev = P.e2;
-                    o.out[q] = o.cheb_w * (basic - prev) + prev;
+                if (kCheb<MODE> && (o.cform & kRestart)) {   // correction form, first sweep of a cycle
+                    if (o.cform & kFold) I.x0[q] += P.uLo;
+                    I.b[q] = r;
+                    o.out[q] = o.coef * P.e1 * r;
                 } else {
-                    o.out[q] = basic;
+                    const real basic = P.uLo + o.coef * P.e1 * r;
+                    if (kCheb<MODE> && o.cheb) {   // x_{k+1} = w (basic - x_{k-1}) + x_{k-1}; x_{k-1} came through the ring
+                        const real prev = (o.cform & kPrev0) ? real(0) : P.e2;
+                        o.out[q] = o.cheb_w * (basic - prev) + prev;
+                    } else {
+                        o.out[q] = basic;
+                    }
                 }
                 if (check) acc += (float)r * (float)r;
             } else if (MODE == M_IE) {   // r = f - (I + a L) x;  x+ = x + r / (1 + a D)  (Eq. iejac1)
@@ -513,9 +529,13 @@ __device__ __forceinline__ void ring_plane(const Inst<real> &I, const Op<real> &
 // End of a sweep's work item: count its arrival; on a checking sweep the item
 // that arrives last sums the FP64 partial norms in a fixed order and decides
 // the stop (converged, diverged, non-finite) in the control block.
+// (unit: the launch's index in the solve's launches, a sweep or, for the
+// eight-colour sweep, a colour pass; parts: launches whose partial sums make up
+// one sweep's residual, 1 or 8, and part this launch's place among them.)
 template <typename real>
-__device__ __forceinline__ void sweep_finish(const Inst<real> &I, int sweep, int item, int nitems, bool check,
-                                             float acc, double *sred, int *sflag)
+__device__ __forceinline__ void sweep_finish(const Inst<real> &I, int sweep, int unit, int part, int parts,
+                                             int item, int nitems, bool check, bool eform, float acc, double *sred,
+                                             int *sflag)
 {
     Ctl *ctl = I.ctl;
     if (!check) {   // count the arrival; nobody waits on it within this launch
@@ -524,18 +544,19 @@ __device__ __forceinline__ void sweep_finish(const Inst<real> &I, int sweep, int
     }
     // residual norm of this sweep's input: per-thread FP32 partial over its few voxels,
     // FP64 above; deterministic fixed-order reduction by the item that arrives last
+    // (of the sweep's last launch)
     const double tot = block_sum<kThreads>((double)acc, sred);
     if (threadIdx.x == 0) {
-        I.partials[item] = tot;
+        I.partials[part * nitems + item] = tot;
         __threadfence();
-        const unsigned long long last = (unsigned long long)(sweep + 1) * (unsigned long long)nitems - 1ull;
-        *sflag = atomicAdd(&ctl->jarrive, 1ull) == last;
+        const unsigned long long last = (unsigned long long)(unit + 1) * (unsigned long long)nitems - 1ull;
+        *sflag = atomicAdd(&ctl->jarrive, 1ull) == last && part == parts - 1;
     }
     __syncthreads();
     if (*sflag) {
         __threadfence();
         double s = 0;
-        for (int i = threadIdx.x; i < nitems; i += kThreads) s += ((volatile double *)I.partials)[i];
+        for (int i = threadIdx.x; i < parts * nitems; i += kThreads) s += ((volatile double *)I.partials)[i];
         s = block_sum<kThreads>(s, sred);
         if (threadIdx.x == 0) {
             const int j = sweep + 1;
@@ -547,6 +568,13 @@ __device__ __forceinline__ void sweep_finish(const Inst<real> &I, int sweep, int
                 ctl->converged = 1; ctl->done = 1; ctl->iters = j;
             } else if (s > I.div_factor * ctl->bnorm2) {
                 ctl->diverged = 1; ctl->noconv = 1; ctl->done = 1; ctl->iters = j;
+            } else if (eform) {   // correction form: sweep 0 starts the first cycle; a cycle that
+                if (sweep == 0) {  // has cut ||r|| by 1e3 restarts at the next sweep
+                    ctl->r0n2 = s;
+                } else if (s <= kRestart2 * ctl->r0n2) {
+                    ctl->cycle0 = j;
+                    ctl->r0n2 = s;
+                }
             }
             __threadfence();
         }
@@ -575,15 +603,22 @@ __device__ __forceinline__ void stencil_item(const Inst<real> &I, int seg_index,
     o.out = o.wout = o.tact = o.out2 = nullptr;
     o.cheb = 0;
     o.cheb_w = real(1);
+    o.cform = 0;
+    o.colour = 0;
     o.so = I.sig_o;
     o.tn = 0.0;
     o.dt_d = I.dt_d;
-    int sweep = 0;
+    int sweep = 0, unit = 0;
     bool check = false;
     const long long step = (MODE == M_APPLY || MODE == M_APPLY_BATH) ? 0 : ctl->step;
     const int cur = (int)(step & 1);
     if (kSweep<MODE>) {
-        sweep = (int)(*(volatile unsigned long long *)&ctl->jarrive / (unsigned long long)nitems);
+        unit = (int)(*(volatile unsigned long long *)&ctl->jarrive / (unsigned long long)nitems);
+        sweep = unit;
+        if (kGS<MODE>) {   // eight launches a sweep: colour pass unit & 7 of sweep unit >> 3
+            sweep = unit >> 3;
+            o.colour = unit & 7;
+        }
         if (sweep >= I.max_iter) {   // sweep cap reached: the solve ends with the last iterate
             if (threadIdx.x == 0) {
                 ctl->noconv = 1;
@@ -593,14 +628,29 @@ __device__ __forceinline__ void stencil_item(const Inst<real> &I, int seg_index,
             }
             return;
         }
-        if (kJac<MODE>) {
+        if (kGS<MODE>) {   // in place: a colour's voxels are coupled to none of their own colour
+            o.src = I.x0;
+            o.out = I.x0;
+            o.sT = I.sTie; o.dS = I.dSie; o.coef = I.coef_jac;
+        } else if (kJac<MODE>) {
             o.src = (sweep & 1) ? I.x1 : I.x0;
             o.out = (sweep & 1) ? I.x0 : I.x1;
             o.sT = I.sTie; o.dS = I.dSie; o.coef = I.coef_jac;
             if (kCheb<MODE>) {   // the launch matches the descriptor's solver (host)
                 o.coef = I.cheb_tau_c;
-                if (sweep > 0) {   // sweep 0 is the basic step itself
-                    if (threadIdx.x == 0) sm.cheb_w = cheb_weight(sweep, I.cheb_rho, I.cheb_theta);
+                int kc = sweep;   // index of the sweep in the semi-iteration
+                if (I.cheb_eform) {
+                    // correction form: the iterate is x0 + e; sweep 0 reads x0 itself (e_0 = 0 and
+                    // b - A x0 is the first cycle's right-hand side), later sweeps read e
+                    kc = sweep - *(volatile int *)&ctl->cycle0;
+                    if (sweep > 0) {
+                        o.src = (sweep & 1) ? I.x1 : I.x2;
+                        o.out = (sweep & 1) ? I.x2 : I.x1;
+                    }
+                    o.cform = (kc == 0 ? kRestart : 0) | (kc == 0 && sweep > 0 ? kFold : 0) | (kc == 1 ? kPrev0 : 0);
+                }
+                if (kc > 0) {   // the first sweep of a cycle is the basic step itself
+                    if (threadIdx.x == 0) sm.cheb_w = cheb_weight(kc, I.cheb_rho, I.cheb_theta);
                     __syncthreads();
                     o.cheb = 1;
                     o.cheb_w = (real)sm.cheb_w;
@@ -696,7 +746,11 @@ __device__ __forceinline__ void stencil_item(const Inst<real> &I, int seg_index,
         }
     }
 
-    if (kSweep<MODE>) sweep_finish<real>(I, sweep, item, nitems, check, acc, sm.sred, &sm.sflag);
+    if (kGS<MODE>)
+        sweep_finish<real>(I, sweep, unit, o.colour, 8, item, nitems, check, false, acc, sm.sred, &sm.sflag);
+    else if (kSweep<MODE>)
+        sweep_finish<real>(I, sweep, sweep, 0, 1, item, nitems, check, kCheb<MODE> && I.cheb_eform, acc, sm.sred,
+                           &sm.sflag);
 }
 
 // Single instance: one CTA per segment.  The two-term modes keep both terms'

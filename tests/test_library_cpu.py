@@ -134,24 +134,37 @@ def test_footprint_is_planned_on_the_host(lib):
 def test_footprint_counts_the_interval_estimate(lib):
     """A Chebyshev bidomain handle without a given interval estimates it at
     set-up: the peak adds the Lanczos scalars (82 doubles) and two partial sums
-    per reduction chunk; with the interval given, or for damped Jacobi, nothing."""
+    per reduction chunk; with the interval given, or for damped Jacobi, nothing.
+    An FP32 Chebyshev handle keeps a third iterate (the correction form, 4 bytes
+    a voxel); the eight-colour Gauss-Seidel handle keeps eight residual partial
+    sums per work item and estimates nothing."""
     import workloads as W
     c = W.random_case(4, 17, 12, 10, model=W.BI)
     peaks = {}
-    for key, solver, lmin, lmax in (("jac", 0, 0.0, 0.0), ("est", 1, 0.0, 0.0), ("given", 1, 0.01, 4.0)):
+    for key, solver, lmin, lmax in (("jac", 0, 0.0, 0.0), ("est", 1, 0.0, 0.0), ("given", 1, 0.01, 4.0),
+                                    ("gs", 2, 0.0, 0.0)):
         c.params.solver, c.params.cheb_lmin, c.params.cheb_lmax = solver, lmin, lmax
         s = ep.sim_from_case(c, use_torch=False)
         peaks[key] = s.footprint()
         s.close()
-    (rj, pj), (re_, pe), (rg, pg) = peaks["jac"], peaks["est"], peaks["given"]
-    assert rj == re_ == rg and pj == pg
-    extra = pe - pj
+    (rj, pj), (re_, pe), (rg, pg), (rs, ps) = peaks["jac"], peaks["est"], peaks["given"], peaks["gs"]
+    assert re_ == rg == rj + 4 * c.n and pg - rg == pj - rj
+    extra = (pe - re_) - (pj - rj)
     assert extra >= 8 * 82 + 16 and (extra - 8 * 82) % 16 == 0
+    assert rs >= rj and ps - rs == pj - rj   # (this mask has more reduction chunks than 8 x items)
     # damped Jacobi with estimated damping runs the same estimate
     c.params.solver, c.params.cheb_lmin, c.params.cheb_lmax, c.params.omega = 0, 0.0, 0.0, -1.0
     s = ep.sim_from_case(c, use_torch=False)
-    assert s.footprint() == (re_, pe)
+    assert s.footprint() == (rj, pj + extra)
     s.close()
+    # an FP64 Chebyshev handle runs the plain semi-iteration: no third iterate
+    c.params.solver, c.params.omega = 1, 0.0
+    s64 = ep.sim_from_case(c, use_torch=False, precision=ep.EP_FP64)
+    c.params.solver = 0
+    j64 = ep.sim_from_case(c, use_torch=False, precision=ep.EP_FP64)
+    assert s64.footprint()[0] == j64.footprint()[0]
+    s64.close()
+    j64.close()
 
 
 def test_torso_and_ecg_are_validated_and_planned_on_the_host(lib):

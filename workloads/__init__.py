@@ -78,7 +78,8 @@ class Params:
     check_every: int = 10     # residual check interval (sweeps)
     max_iter: int = 100000    # sweep cap per solve
     diffusion: int = 0        # 0 explicit Euler, 1 implicit Euler (Eq. iejac1)
-    solver: int = 0           # elliptic solve: 0 damped Jacobi (Eq. dampjac1), 1 Chebyshev-accelerated Jacobi
+    solver: int = 0           # elliptic solve: 0 damped Jacobi (Eq. dampjac1), 1 Chebyshev-accelerated Jacobi,
+                              # 2 eight-colour Gauss-Seidel / SOR (omega > 0 the SOR factor, else 1)
     cheb_lmin: float = 0.0    # spectral interval of D^-1 A for the Chebyshev solver (<= 0: estimated)
     cheb_lmax: float = 0.0
     sig_o: float = 0.0        # isotropic torso conductivity (mS/mm), used when the case has a torso
