@@ -476,6 +476,8 @@ def solver_legs(ep, case, a, blob0, stream, flush, end_state, peak):
              "kernel": ("k_stencil<float,M_JAC_CHEB> (correction form)" if solver == 1 else
                         "k_stencil<float,M_JAC_GS> (one colour pass; 8 a sweep)"),
              "avg_launch_us": launch_s * 1e6, "algorithmic_bytes_per_voxel": per,
+             "traffic_bytes_per_voxel": _traffic_record(("chebyshev_sweep_" if solver == 1 else "gauss_seidel_pass_")
+                                                        + a.workload),
              "hbm_frac": per * M / launch_s / 1e9 / peak if launch_s > 0 else None,
              "max_abs_dVm_vs_jacobi_mV": float(np.abs(h.read(ep.EP_VM_MV) - end_state[0]).max()),
              "max_abs_dVe_vs_jacobi_mV": float(np.abs(h.read(ep.EP_VE_MV) - end_state[1]).max())}
@@ -603,7 +605,9 @@ def run_ours(a):
     achieved = alg_bytes / launch_s / 1e9 if launch_s > 0 else 0.0
     stem = (f"ie_sweep_slab{a.slab_n}_mono" if mono and implicit else
             f"fused_step_slab{a.slab_n}_mono" if mono else
-            f"jacobi_sweep_slab{a.slab_n}_bi" if a.workload == "slab" else f"jacobi_sweep_{a.workload}")
+            f"jacobi_sweep_slab{a.slab_n}_bi" if a.workload == "slab" else
+            f"chebyshev_sweep_{a.workload}" if a.solver == "chebyshev" else
+            f"gauss_seidel_pass_{a.workload}" if a.solver == "gs" else f"jacobi_sweep_{a.workload}")
     if torso:
         stem = f"elliptic_sweep_{a.workload}"
     tpv = _traffic_record(stem)

@@ -287,7 +287,10 @@ size_t abytes(size_t b) { return b ? b : 16; }   // dalloc's size of a request
 // Device bytes of a handle after set-up (resident) and during it (peak, which
 // adds the staging buffers of fibres, mask and raw records).  Matches the
 // allocations of setup_typed exactly.
-constexpr int kLanczosSteps = 40;
+#ifndef EP_LANCZOS_STEPS
+#define EP_LANCZOS_STEPS 40
+#endif
+constexpr int kLanczosSteps = EP_LANCZOS_STEPS;
 constexpr int kLanczosScalars = 2 + 2 * kLanczosSteps;   // alpha, beta of the current step; alpha_j, beta_{j+1}
 
 // The set-up estimates the spectrum of D^-1 A for the Chebyshev solver and for the
