@@ -755,11 +755,23 @@ __device__ __forceinline__ void stencil_item(const Inst<real> &I, int seg_index,
 
 // Single instance: one CTA per segment.  The two-term modes keep both terms'
 // vertex state and run two CTAs an SM.
+// Whether the solve of `ctl` is finished, read once for the whole CTA: a capped
+// solve sets its flag while other CTAs of the same launch may be starting, and
+// threads of one CTA that read it at different moments would part ways (in the
+// batched kernels some of them would then miss their share of the descriptor
+// copy).  Ends with a barrier.
+__device__ __forceinline__ bool cta_done(const Ctl *ctl, int *sflag)
+{
+    if (threadIdx.x == 0) *sflag = *(const volatile int *)&ctl->done;
+    __syncthreads();
+    return *sflag != 0;
+}
+
 template <typename real, int MODE>
 __global__ void __launch_bounds__(kThreads, kTwoTerm<MODE> ? 2 : kMinBlocks) k_stencil(Inst<real> I, ApplyIO<real> io)
 {
     StencilSmem<real, MODE> &sm = dyn_smem<StencilSmem<real, MODE>>();
-    if (kSweep<MODE> && I.ctl->done) return;   // converged earlier: queued sweeps are no-ops
+    if (kSweep<MODE> && cta_done(I.ctl, &sm.sflag)) return;   // converged earlier: queued sweeps are no-ops
     const int nitems = I.nitems_all > 0 ? I.nitems_all : (int)gridDim.x;
     stencil_item<real, MODE>(I, blockIdx.x, I.item0 + (int)blockIdx.x, nitems, &io, sm);
 }
@@ -788,7 +800,7 @@ k_stencil_batch(const Inst<real> *insts, const BItem *items)
     StencilSmem<real, MODE> &sm = dyn_smem<StencilSmem<real, MODE>>();
     __shared__ Inst<real> sI;
     const BItem it = items[blockIdx.x];
-    if (kJac<MODE> && *(volatile int *)&insts[it.inst].ctl->done) return;
+    if (kJac<MODE> && cta_done(insts[it.inst].ctl, &sm.sflag)) return;
     const Inst<real> &I = stage_inst(insts + it.inst, sI);
     stencil_item<real, MODE>(I, it.item, it.item, it.nitems, nullptr, sm);
 }
@@ -817,7 +829,7 @@ k_stencil_active(const Inst<real> *insts, const ActRec *act, int n)
     __syncthreads();
     if (sk < 0) return;
     const ActRec r = act[sk];
-    if (kJac<MODE> && *(volatile int *)&r.ctl->done) return;   // converged at a check in this loop pass
+    if (kJac<MODE> && cta_done(r.ctl, &sm.sflag)) return;   // converged at a check in this loop pass
     const Inst<real> &I = stage_inst(insts + r.inst, sI);
     const int item = i - r.cum;
     stencil_item<real, MODE>(I, item, item, I.nseg, nullptr, sm);

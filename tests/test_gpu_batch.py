@@ -145,3 +145,37 @@ def test_mixed_solvers_same_alone_and_in_the_mix():
         for f in FIELDS:
             np.testing.assert_array_equal(s_mix.read(f), s_alone.read(f))
     b.close()
+
+
+@pytest.mark.parametrize("solver", [0, 1])
+def test_capped_solves_same_alone_and_in_the_mix(solver):
+    """Every solve hits its sweep cap (max_iter 7, rel_tol 0): the cap is met
+    at the start of a launch, while other work items of the same member may be
+    starting, so the finished flag must be read once per CTA (packed members
+    copy their descriptor with the whole CTA).  Ten members (eight packed, two
+    solo), twelve steps in one graph launch: every member equals its
+    standalone run bit for bit, and every step reports the cap."""
+    rng = np.random.default_rng(11)
+    cases = [W.random_case(90 + i, 17 + 3 * i, 13 + i, 9 + (i % 4), model=W.BI) for i in range(8)]
+    cases += [W.sampled_shell(rng, n, 10, f"cap{n}") for n in (176, 184)]
+    for c in cases:
+        c.model = W.BI
+        c.params.solver, c.params.max_iter, c.params.rel_tol, c.params.check_every = solver, 7, 0.0, 3
+    alone = _handles(cases, seed0=700)
+    for s in alone:
+        st = s.step(12, allow_noconv=True)
+        assert st.converged == 0 and st.iters == 7
+    mixed = _handles(cases, seed0=700)
+    b = ep.Batch(len(cases))
+    slots = [b.add(s) for s in mixed]
+    assert 1 <= b.info().solo_members < len(cases)
+    with pytest.raises(ep.EPError) as e:   # the cap reached: EP_ENOCONV unless allowed
+        b.step(1)
+    assert e.value.status == ep.EP_ENOCONV
+    b.step(11, allow_noconv=True)
+    for s_alone, s_mix, slot in zip(alone, mixed, slots):
+        st = b.slot_stats(slot)
+        assert st.step == 15 and st.iters == 7 and st.converged == 0
+        for f in FIELDS:
+            np.testing.assert_array_equal(s_mix.read(f), s_alone.read(f))
+    b.close()
