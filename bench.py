@@ -488,6 +488,26 @@ def solver_legs(ep, case, a, blob0, stream, flush, end_state, peak):
     return out
 
 
+def oracle_error_sample(ep, pairs, a):
+    """oracle_step_error over a sample of (handle, case) members of a batch
+    or a serving run: the largest one-step V_m and w errors and the largest
+    elliptic residual under the oracle, with the members checked."""
+    outs = [oracle_step_error(ep, h, c, a) for h, c in pairs]
+    outs = [o for o in outs if "skipped" not in o]
+    if not outs:
+        return None
+    res = {"members_checked": len(outs),
+           "one_step_max_abs_dVm_mV": max(o["one_step_max_abs_dVm_mV"] for o in outs),
+           "one_step_max_abs_dw": max(o["one_step_max_abs_dw"] for o in outs),
+           "check_s": sum(o["check_s"] for o in outs),
+           "method": outs[0]["method"]}
+    rr = [o["elliptic_relres_under_oracle"] for o in outs if "elliptic_relres_under_oracle" in o]
+    if rr:
+        res["max_elliptic_relres_under_oracle"] = max(rr)
+        res["rel_tol"] = outs[0]["rel_tol"]
+    return res
+
+
 def run_ours(a):
     import torch
     import paper_2302_12519_gb300 as ep
@@ -735,6 +755,8 @@ def run_batched(a):
     batch_s = e0.elapsed_time(e1) / 1e3
     vm_b = [h.read(ep.EP_VM_MV) for h in hb]
     b.close()
+    # every eighth member's end state against the FP64 oracle (one step, the elliptic residual)
+    err = None if a.no_cpu_baseline else oracle_error_sample(ep, list(zip(hb, cases))[::8], a)
     for h in hb:
         h.close()
     # plain: the same instances one after another
@@ -766,7 +788,7 @@ def run_batched(a):
                        "l2": "inputs larger than L2 (all instances' state)"},
             "plain_sequential": {"value": plain, "unit": "tissue voxel-steps/s", "ms_per_step": 1e3 * plain_s / a.steps},
             "speedup_vs_plain": value / plain,
-            "max_abs_dVm_batched_vs_alone_mV": dv}
+            "max_abs_dVm_batched_vs_alone_mV": dv, "error_vs_oracle": err}
     print(json.dumps(line), flush=True)
 
 
@@ -915,7 +937,7 @@ def run_served(a):
 
     loads = [float(x) for x in a.loads.split(",") if x.strip()]
     budget = int(a.hbm_budget_gb * (1 << 30))
-    runs, dv = [], 0.0
+    runs, dv, err = [], 0.0, None
     for load in loads:
         lam = load * mu
         arr = np.asarray(unit_arrivals) / lam
@@ -932,6 +954,8 @@ def run_served(a):
         got = {r.id: (r, h) for r, h in srv.collect_n(len(ids), timeout_s=3600)}
         st = srv.stats()
         lat, t_end, bad = [], 0.0, 0
+        if load == max(loads) and not a.no_cpu_baseline:   # a sample of the served results against the oracle
+            err = oracle_error_sample(ep, [(got[rid][1], cases[q]) for q, rid in enumerate(ids)][::4], a)
         for q, rid in enumerate(ids):
             r, h = got[rid]
             if r.status not in (ep.EP_OK, ep.EP_ENOCONV) or r.steps_done != S:
@@ -963,7 +987,7 @@ def run_served(a):
                                  "service_s": svc, "rate_req_per_s": mu},
             "speedup_vs_plain": top["value"] / plain_value,
             "loads": runs,
-            "max_abs_dVm_served_vs_alone_mV": dv}
+            "max_abs_dVm_served_vs_alone_mV": dv, "error_vs_oracle": err}
     print(json.dumps(line), flush=True)
 
 

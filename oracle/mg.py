@@ -5,8 +5,12 @@ product).
 
 The thesis solves the elliptic equation (Eq. bidomain1, second line) by
 Jacobi iteration (Eq. dampjac1) and names multigrid as future work for the
-solver (chapter "Review & Outlook").  This is that future work written out
-plainly, as the CUDA path implements it:
+solver (chapter "Review & Outlook").  This is a study of that future work,
+written out plainly; no CUDA path implements it (the operator's near-null
+hourglass modes defeat constant aggregates).  Pinned by
+tests/test_oracle_mg_pins.py: the probing assembly against an independent
+assembly, the Galerkin levels, the symmetry of the V-cycle, the solve against
+a dense least-squares solution.
 
 * A = the elliptic operator L_{i+e} of the oracle (og_apply_L) on its domain
   (tissue, plus the torso if the grid has one), assembled exactly into a
