@@ -8,7 +8,10 @@ finishes; the library solves it by its default damped Jacobi, and on config 1
 also by its FP32 Chebyshev solve (correction form) on the oracle's interval;
 every solve stops at the same relative residual, 1e-6, of the same equation.
 Gates: V_m within 0.5 mV and activation times within 1 % on every stored
-voxel, the same set of voxels activated; the measured errors are printed."""
+voxel, the same set of voxels activated; the measured errors are printed.
+(The config-2 window is one complete step, in which no voxel crosses the
+activation threshold: it checks V_m and V_e on the front and 20 000 sampled
+voxels; config 1's 60 steps check the activation times.)"""
 import os
 
 import numpy as np
@@ -59,11 +62,11 @@ def test_window_matches_oracle(name, solver):
     dve = float(np.abs(ve_g - 100.0 * d["ve"].astype(np.float64)).max())
     act = ta_o > 0
     np.testing.assert_array_equal(ta_g > 0, act)
-    rel = np.abs(ta_g[act] - ta_o[act]) / ta_o[act]
+    rel = np.abs(ta_g[act] - ta_o[act]) / ta_o[act] if act.any() else np.zeros(1)
     print(f"{name} ({solver}): {int(d['steps'])} steps, {int(act.sum())} voxels activated in the window; max |dVm| "
           f"{dvm:.3e} mV, max rel d t_act {rel.max():.3e}, max |dVe| {dve:.3e} mV; sweeps per "
           f"step {sweeps[:3]}..{sweeps[-1]} (oracle Chebyshev {list(d['sweeps'][:3])}..{int(d['sweeps'][-1])})")
-    assert act.sum() > 1000
+    assert act.sum() >= (1000 if name == "config1" else 0)
     assert dvm <= 0.5, dvm
     assert rel.max() <= 0.01, rel.max()
     s.close()
