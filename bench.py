@@ -436,15 +436,18 @@ def oracle_step_error(ep, sim, case, a):
 def solver_legs(ep, case, a, blob0, stream, flush, end_state, peak):
     """The timed window again from its start state with the elliptic solve by
     the Chebyshev semi-iteration (correction form, interval estimated at
-    set-up) and by eight-colour Gauss-Seidel, every solve to the same rel_tol:
+    set-up), by eight-colour Gauss-Seidel and by eight-colour SOR at omega 1.8,
+    every solve to the same rel_tol:
     rate, sweeps, sweep launch time against the HBM peak, and the largest
     difference of V_m and V_e from the damped-Jacobi window's end state."""
     import dataclasses
     import torch
     out = {}
     M = case.n_tissue
-    for name, solver in (("chebyshev", 1), ("gauss_seidel", 2)):
+    for name, solver, omega in (("chebyshev", 1, None), ("gauss_seidel", 2, 0.0), ("sor_1.8", 2, 1.8)):
         c = dataclasses.replace(case, params=dataclasses.replace(case.params, solver=solver))
+        if omega is not None:
+            c.params.omega = omega   # the SOR factor (0: Gauss-Seidel)
         h = ep.Sim(c.nx, c.ny, c.nz, c.dx, c.model, c.precision, use_torch=True, stream=stream.cuda_stream)
         h.set_mask(c.mask_flat())
         h.set_fibres(c.fib_flat())
@@ -483,6 +486,8 @@ def solver_legs(ep, case, a, blob0, stream, flush, end_state, peak):
              "max_abs_dVe_vs_jacobi_mV": float(np.abs(h.read(ep.EP_VE_MV) - end_state[1]).max())}
         if solver == 1:
             d["interval"] = [info.cheb_lmin, info.cheb_lmax]
+        if solver == 2:
+            d["omega"] = info.omega
         out[name] = d
         h.close()
     return out
