@@ -70,6 +70,9 @@ def _args():
                          "Gauss-Seidel (default: jacobi; chebyshev for ecg)")
     ap.add_argument("--no-solver-legs", action="store_true",
                     help="skip the bidomain default's extra windows with the Chebyshev and Gauss-Seidel solves")
+    ap.add_argument("--mid-beat-ms", type=float, default=60.0,
+                    help="the bidomain default also times the damped-Jacobi step at this time of the beat "
+                         "(state made by the Chebyshev solve to the same tolerance; 0: off)")
     ap.add_argument("--sig-o", type=float, default=1.0, help="ecg: torso conductivity (mS/mm)")
     ap.add_argument("--omega", type=float, default=None,
                     help="Jacobi damping: > 0 that value, 0 the bound rule, < 0 estimated from the spectrum")
@@ -513,6 +516,65 @@ def oracle_error_sample(ep, pairs, a):
     return res
 
 
+def mid_beat_window(ep, case, a, stream, flush):
+    """The damped-Jacobi step timed mid-beat: the state at --mid-beat-ms from
+    rest is made on a separate handle with the Chebyshev solve (correction
+    form) to the workload's tolerance, then a damped-Jacobi handle takes W
+    untimed and K timed steps from it."""
+    import dataclasses
+    import torch
+    n = int(round(a.mid_beat_ms / case.params.dt))
+    t0 = time.perf_counter()
+    c = dataclasses.replace(case, params=dataclasses.replace(case.params, solver=1))
+    h = ep.Sim(c.nx, c.ny, c.nz, c.dx, c.model, c.precision, use_torch=True, stream=stream.cuda_stream)
+    h.set_mask(c.mask_flat())
+    h.set_fibres(c.fib_flat())
+    h.set_params(c.params)
+    for st in c.stimuli:
+        h.add_stimulus(st.lo, st.hi, st.t_start, st.dur, st.amp)
+    prep_sweeps, prep_conv = 0, True
+    done = 0
+    while done < n:
+        k = min(200, n - done)
+        st = h.step(k, allow_noconv=True)
+        prep_sweeps += st.total_iters
+        prep_conv = prep_conv and h.last_status == 0
+        done += k
+    blob = h.read_state()
+    activated = int((h.read(ep.EP_TACT) > 0).sum())
+    h.close()
+    prep_s = time.perf_counter() - t0
+    j = ep.Sim(case.nx, case.ny, case.nz, case.dx, case.model, case.precision, use_torch=True,
+               stream=stream.cuda_stream)
+    j.set_mask(case.mask_flat())
+    j.set_fibres(case.fib_flat())
+    j.set_params(case.params)
+    for st in case.stimuli:
+        j.add_stimulus(st.lo, st.hi, st.t_start, st.dur, st.amp)
+    j.write_state(blob)
+    for _ in range(a.warmup):
+        j.step(1, allow_noconv=True)
+    ms, iters, statuses = [], [], []
+    for _ in range(a.steps):
+        with torch.cuda.stream(stream):
+            flush.fill_(1.0)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        st = j.step(1, allow_noconv=True)
+        e1.record(stream)
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+        iters.append(st.iters)
+        statuses.append(j.last_status)
+    j.close()
+    total_s = sum(ms) / 1e3
+    return {"t_ms": a.mid_beat_ms, "window": f"steps {n + a.warmup}..{n + a.warmup + a.steps - 1}",
+            "value": case.n_tissue * a.steps / total_s, "unit": "tissue voxel-steps/s",
+            "ms_per_step": 1e3 * total_s / a.steps, "sweeps_per_step": iters, "step_status": statuses,
+            "tissue_voxels_activated": activated, "state_made_by": "Chebyshev solve (correction form) to rel_tol",
+            "state_steps_all_converged": prep_conv, "prep_s": prep_s}
+
+
 def run_ours(a):
     import torch
     import paper_2302_12519_gb300 as ep
@@ -685,6 +747,10 @@ def run_ours(a):
     if (not mono and a.solver == "jacobi" and not torso and a.diffusion == "explicit" and world == 1
             and not a.no_solver_legs):
         legs = solver_legs(ep, case, a, blob0, stream, flush, end_state, peak)
+    mid = None
+    if (not mono and a.solver == "jacobi" and not torso and a.diffusion == "explicit" and world == 1
+            and a.mid_beat_ms > 0.0 and a.start_ms == 0.0):
+        mid = mid_beat_window(ep, case, a, stream, flush)
 
     if rank == 0:
         line = {"metric": "voxel-steps/sec", "value": value, "unit": "tissue voxel-steps/s", "n_gpus": world,
@@ -703,7 +769,7 @@ def run_ours(a):
                            "elliptic_voxels": n_dom, "ecg": ecg_trace},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "error_vs_oracle": err,
                 "gpu_launches": int(prof.sweep_launches + prof.other_launches),
-                "clocks": clk, "other_solvers": legs}
+                "clocks": clk, "other_solvers": legs, "mid_beat": mid}
         print(json.dumps(line), flush=True)
     sim.close()
     if dist is not None:
