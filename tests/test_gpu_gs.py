@@ -123,3 +123,23 @@ def test_gauss_seidel_refused_with_torso_and_in_a_batch():
     with pytest.raises(ep.EPError):
         t.step(1)
     t.close()
+
+
+def test_gauss_seidel_with_implicit_diffusion_fp64_matches_oracle():
+    """The implicit-Euler parabolic step (Eq. iejac1) with the elliptic solve by
+    Gauss-Seidel: sweep for sweep equal to the oracle's, in FP64."""
+    c = W.random_case(55, 31, 12, 9, model=W.BI, rel_tol=1e-10, check_every=4).fibres_as_float32()
+    c.params.solver, c.params.diffusion, c.params.max_iter = 2, 1, 100000
+    s = ep.sim_from_case(c, precision=ep.EP_FP64)
+    o = oracle.Sim(c)
+    v, w, ve = W.random_state(55, c)
+    s.set_state(v, w, ve, 0)
+    o.set_state(v, w, ve, 0)
+    for _ in range(2):
+        stats = s.step(1)
+        assert o.step() == 0 and stats.converged == 1 and stats.iters == o.last_iters, (stats.iters, o.last_iters)
+    st = o.state()
+    np.testing.assert_allclose(s.read(ep.EP_V), st["v"], rtol=0, atol=1e-9)
+    np.testing.assert_allclose(s.read(ep.EP_VE), st["ve"], rtol=0, atol=1e-7 * max(1.0, np.abs(st["ve"]).max()))
+    s.close()
+    o.close()

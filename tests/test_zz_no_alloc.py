@@ -47,14 +47,17 @@ class CountingAllocator:
         return alloc, free
 
 
-@pytest.mark.parametrize("model", [ep.EP_BI, ep.EP_MONO])
-def test_noalloc_step_matches_step_on_two_calls(model):
+@pytest.mark.parametrize("model,solver", [(ep.EP_BI, 0), (ep.EP_MONO, 0), (ep.EP_BI, 1), (ep.EP_BI, 2)])
+def test_noalloc_step_matches_step_on_two_calls(model, solver):
     """Two consecutive calls of the no-allocation step give the state that two
     calls of ep_step give, bit for bit (the same kernels in the same order;
     ep_step only queues its sweeps through a CUDA graph), while the handle's
-    allocator hook is not called and the device's free memory does not move."""
+    allocator hook is not called and the device's free memory does not move;
+    for the damped-Jacobi, Chebyshev (FP32 correction form, interval estimated
+    at set-up) and eight-colour Gauss-Seidel solves."""
     import torch
     case = W.random_case(21, 37, 19, 15, model=model)   # random mask: several components
+    case.params.solver = solver
     v, w, ve = W.random_state(21, case)
     counter = CountingAllocator()
     a = ep.sim_from_case(case, allocator=counter.pair())
