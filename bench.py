@@ -47,10 +47,10 @@ REF_SAMPLE_SWEEPS = (8, 64)     # oracle sweeps timed per sample step (two caps 
 # reference arm runs before the GPU arm, so it takes its sweeps per step from
 # here; the GPU arm reports its own.
 SWEEPS_FROM_REST = {
-    "config2": [21701, 15781, 13031, 11351, 10251, 9471, 8841, 8391, 8031, 7771, 7541, 7331, 7191, 7041, 6921,
-                6821, 6731, 6611, 6511, 6371, 4131, 4051, 4001, 3971, 3941, 3911, 3881, 3831, 3781, 3731],
-    "config1": [16651, 13081, 11171, 9921, 9021, 8391, 7891, 7491, 7171, 6921, 6731, 6541, 6411, 6261, 6151,
-                6041, 5951, 5851, 5761, 5661, 3551, 3501, 3461, 3451, 3441, 3431, 3411, 3381, 3351, 3321],
+    "config2": [21631, 15711, 12951, 11301, 10201, 9401, 8811, 8361, 8001, 7721, 7491, 7301, 7141, 7011, 6891,
+                6781, 6671, 6571, 6461, 6331, 4101, 4021, 3981, 3951, 3921, 3881, 3851, 3811, 3761, 3711],
+    "config1": [16631, 13051, 11131, 9881, 9011, 8351, 7861, 7461, 7151, 6901, 6691, 6511, 6371, 6241, 6121,
+                6021, 5921, 5831, 5721, 5621, 3541, 3471, 3451, 3431, 3421, 3411, 3391, 3361, 3341, 3301],
 }
 
 

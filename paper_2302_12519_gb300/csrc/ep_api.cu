@@ -119,7 +119,7 @@ struct ep_sim {
     cudaGraphExec_t sweep_graph = nullptr;
     cudaGraphExec_t ie_graph = nullptr;   // implicit-diffusion sweeps
     void *ie_x = nullptr, *ie_inv = nullptr;
-    void *x2 = nullptr;          // second correction buffer of the FP32 Chebyshev solve
+    void *x2 = nullptr;          // second correction buffer of the FP32 elliptic solve (correction form)
     long long ie_seen = 0;                // implicit sweeps counted by earlier calls
     long long step = 0;
     bool noalloc_call = false;   // inside ep_step_noalloc: scratch is the static array, no graph
@@ -318,11 +318,12 @@ size_t lanczos_bytes(const ep_sim *s)
     return sizeof(double) * ((size_t)kLanczosScalars + 2 * (size_t)s->nchunk);
 }
 
-// FP32 bidomain handles with the Chebyshev solver run it in correction form, which
+// FP32 bidomain handles run the damped-Jacobi and Chebyshev solves in correction
+// form (the FP32 rounding of the full iterate would floor the residual), which
 // needs a third iterate buffer.
-bool cheb_eform(const ep_sim *s, size_t rb)
+bool solve_eform(const ep_sim *s, size_t rb)
 {
-    return rb == sizeof(float) && s->have_params && s->d.model == EP_BI && s->p.solver == EP_SOLVER_CHEBYSHEV;
+    return rb == sizeof(float) && s->have_params && s->d.model == EP_BI && s->p.solver != EP_SOLVER_GAUSS_SEIDEL;
 }
 
 void footprint(const ep_sim *s, size_t rb, size_t *resident, size_t *peak)
@@ -335,7 +336,7 @@ void footprint(const ep_sim *s, size_t rb, size_t *resident, size_t *peak)
     r += abytes(sizeof(long long) * P.comp_count.size()) + abytes(sizeof(double) * (size_t)s->ncomp);
     r += abytes(sizeof(double) * (size_t)partial_slots(s)) + abytes(sizeof(Ctl));
     if (s->have_params && s->p.diffusion == EP_IMPLICIT) r += 2 * abytes(rb * n);   // second iterate, 1/(1 + a D)
-    if (cheb_eform(s, rb)) r += abytes(rb * n);
+    if (solve_eform(s, rb)) r += abytes(rb * n);
     const bool torso = !s->torso.empty();
     if (torso) r += abytes(sizeof(float4) * n) + abytes(sizeof(Seg) * (size_t)s->max_items);   // domain records, items
     if (s->ecg_q[0] >= 0) r += abytes(sizeof(double) * 3 * (size_t)s->ecg_cap);
@@ -598,7 +599,7 @@ ep_status setup_typed(ep_sim *s)
         if (!s->ie_x || !s->ie_inv) return fail(s, EP_ENOMEM, "device allocation failed");
     }
     s->x2 = nullptr;
-    if (cheb_eform(s, rb)) {
+    if (solve_eform(s, rb)) {
         s->x2 = dalloc(s, rb * n);
         if (!s->x2) return fail(s, EP_ENOMEM, "device allocation failed");
     }
@@ -779,7 +780,7 @@ Inst<real> make_inst(const ep_sim *s)
     I.pad3 = 0;
     I.cheb_tau_c = real(0);
     I.cheb_rho = I.cheb_theta = 0.0;
-    I.cheb_eform = I.solver && s->x2 ? 1 : 0;
+    I.eform = I.solver != 2 && s->x2 ? 1 : 0;
     I.pad5 = 0;
     if (I.solver) {
         const double lo = s->cheb_lmin, hi = s->cheb_lmax;

@@ -172,14 +172,14 @@ struct RedSmem {
 enum RedField { RED_B = 0, RED_X_FINAL = 1 };
 
 // Final iterate of an elliptic solve of `iters` sweeps at voxel q: x1 after an
-// odd number of sweeps, else x0; in the Chebyshev correction form x0 + e, e the
-// last correction (x1 after an odd number of sweeps, else x2; none after 0);
-// x0 for the eight-colour sweep, which works in place.
+// odd number of sweeps, else x0; in the correction form x0 + e, e the last
+// correction (x1 after an odd number of sweeps, else x2; none after 0); x0 for
+// the eight-colour sweep, which works in place.
 template <typename real>
 __device__ __forceinline__ double final_iterate(const Inst<real> &I, int iters, int q)
 {
     if (I.solver == 2) return (double)I.x0[q];
-    if (I.cheb_eform) {
+    if (I.eform) {
         double x = (double)I.x0[q];
         if (iters > 0) x += (double)((iters & 1) ? I.x1[q] : I.x2[q]);
         return x;

@@ -151,15 +151,16 @@ struct Inst {
     // single-term kernel): this launch's first item among the sweep's items, and their count
     // (0: the launch is the whole sweep)
     int item0, nitems_all;
-    // Chebyshev solve in correction form (FP32 handles): the iterate is x0 + e, e in x1 / x2
-    // (sweep j >= 1 reads e_j from x1 when j is odd, else from x2), b holds the residual of x0
-    // at the cycle's start; a cycle restarts from e = 0 once it has cut ||r|| by kRestart
+    // elliptic solve in correction form (FP32 handles, damped Jacobi and Chebyshev): the iterate
+    // is x0 + e, e in x1 / x2 (sweep j >= 1 reads e_j from x1 when j is odd, else from x2), b holds
+    // the residual of x0 at the cycle's start; a cycle restarts from e = 0 once it has cut ||r||
+    // by a factor 1e3 (kRestart2)
     real *x2;
-    int cheb_eform, pad5;
+    int eform, pad5;
 };
 
-// A correction-form Chebyshev cycle restarts when ||r||^2 has fallen below this
-// fraction of its value at the cycle's start (a factor 1e3 in the norm).
+// A correction-form cycle restarts when ||r||^2 has fallen below this fraction of
+// its value at the cycle's start (a factor 1e3 in the norm).
 constexpr double kRestart2 = 1e-6;
 
 // Weight of sweep k of the Chebyshev semi-iteration: w = 1 for k = 0, else

@@ -347,7 +347,7 @@ __device__ __forceinline__ void plane_step(const Inst<real> &I, const Op<real> &
                 o.out[q] = -Lu;
             } else if (kJac<MODE>) {
                 const real r = P.e0 - Lu;
-                if (kCheb<MODE> && (o.cform & kRestart)) {   // correction form, first sweep of a cycle
+                if (o.cform & kRestart) {   // correction form, first sweep of a cycle
                     if (o.cform & kFold) I.x0[q] += P.uLo;
                     I.b[q] = r;
                     o.out[q] = o.coef * P.e1 * r;
@@ -636,19 +636,19 @@ __device__ __forceinline__ void stencil_item(const Inst<real> &I, int seg_index,
             o.src = (sweep & 1) ? I.x1 : I.x0;
             o.out = (sweep & 1) ? I.x0 : I.x1;
             o.sT = I.sTie; o.dS = I.dSie; o.coef = I.coef_jac;
+            int kc = sweep;   // index of the sweep in its cycle (the semi-iteration's index)
+            if (I.eform) {
+                // correction form: the iterate is x0 + e; sweep 0 reads x0 itself (e_0 = 0 and
+                // b - A x0 is the first cycle's right-hand side), later sweeps read e
+                kc = sweep - *(volatile int *)&ctl->cycle0;
+                if (sweep > 0) {
+                    o.src = (sweep & 1) ? I.x1 : I.x2;
+                    o.out = (sweep & 1) ? I.x2 : I.x1;
+                }
+                o.cform = (kc == 0 ? kRestart : 0) | (kc == 0 && sweep > 0 ? kFold : 0) | (kc == 1 ? kPrev0 : 0);
+            }
             if (kCheb<MODE>) {   // the launch matches the descriptor's solver (host)
                 o.coef = I.cheb_tau_c;
-                int kc = sweep;   // index of the sweep in the semi-iteration
-                if (I.cheb_eform) {
-                    // correction form: the iterate is x0 + e; sweep 0 reads x0 itself (e_0 = 0 and
-                    // b - A x0 is the first cycle's right-hand side), later sweeps read e
-                    kc = sweep - *(volatile int *)&ctl->cycle0;
-                    if (sweep > 0) {
-                        o.src = (sweep & 1) ? I.x1 : I.x2;
-                        o.out = (sweep & 1) ? I.x2 : I.x1;
-                    }
-                    o.cform = (kc == 0 ? kRestart : 0) | (kc == 0 && sweep > 0 ? kFold : 0) | (kc == 1 ? kPrev0 : 0);
-                }
                 if (kc > 0) {   // the first sweep of a cycle is the basic step itself
                     if (threadIdx.x == 0) sm.cheb_w = cheb_weight(kc, I.cheb_rho, I.cheb_theta);
                     __syncthreads();
@@ -749,7 +749,7 @@ __device__ __forceinline__ void stencil_item(const Inst<real> &I, int seg_index,
     if (kGS<MODE>)
         sweep_finish<real>(I, sweep, unit, o.colour, 8, item, nitems, check, false, acc, sm.sred, &sm.sflag);
     else if (kSweep<MODE>)
-        sweep_finish<real>(I, sweep, sweep, 0, 1, item, nitems, check, kCheb<MODE> && I.cheb_eform, acc, sm.sred,
+        sweep_finish<real>(I, sweep, sweep, 0, 1, item, nitems, check, kJac<MODE> && I.eform, acc, sm.sred,
                            &sm.sflag);
 }
 

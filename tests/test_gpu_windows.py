@@ -2,13 +2,13 @@
 biventricular heart (config 2): the library, in FP32, runs the bidomain step
 from the propagating start of the FP64 oracle's run (workloads.front_state)
 over the same steps, and its activation times, V_m and V_e are compared with
-the ones tests/golden/make_windows.py stored from the oracle.  Both sides
-solve the elliptic equation by the Chebyshev semi-iteration on the oracle's
-interval (the library's FP32 solve in its correction form), every solve to the
-same relative residual, 1e-6, of the same equation.  (Damped Jacobi from v_e = 0
-under the front's right-hand side does not reach 1e-6 within 3 million sweeps
-on either grid, in FP32; it is checked at full size per kernel launch and on
-the bench's window.)
+the ones tests/golden/make_windows.py stored from the oracle.  The oracle
+solved the elliptic equation by the Chebyshev semi-iteration so that it
+finishes; the library solves it by its damped Jacobi and by the Chebyshev
+semi-iteration on the oracle's interval, both in their FP32 correction form
+(the plain FP32 Jacobi iterate floors at a relative residual of 1.56e-6 on the
+128^3 window's first step); every solve stops at the same relative residual,
+1e-6, of the same equation.
 Gates: V_m within 0.5 mV and activation times within 1 % on every stored
 voxel, the same set of voxels activated; the measured errors are printed.
 (The config-2 window is one complete step, in which no voxel crosses the
@@ -35,15 +35,19 @@ def _built():
     ep.load()
 
 
-@pytest.mark.parametrize("name", ["config1", "config2"])
-def test_window_matches_oracle(name):
-    solver = "chebyshev"
+@pytest.mark.parametrize("name,solver", [("config1", "jacobi"), ("config1", "chebyshev"), ("config2", "jacobi"),
+                                         ("config2", "chebyshev")])
+def test_window_matches_oracle(name, solver):
     d = np.load(os.path.join(GOLDEN, f"window_{name}.npz"))
     c = W.config1() if name == "config1" else W.config2()
     assert int(d["n_tissue"]) == c.n_tissue
-    # the oracle's interval, given to the library as a literal
-    c.params.solver, c.params.cheb_lmin, c.params.cheb_lmax = 1, float(d["lmin"]), float(d["lmax"])
-    c.params.max_iter = 20_000
+    if solver == "chebyshev":   # the oracle's interval, given to the library as a literal
+        c.params.solver, c.params.cheb_lmin, c.params.cheb_lmax = 1, float(d["lmin"]), float(d["lmax"])
+        c.params.max_iter = 20_000
+    else:
+        # the first solve starts from v_e = 0 under a right-hand side spread over the whole heart:
+        # damped Jacobi needs far more sweeps there than from rest (FP64: 48 001 on config 1)
+        c.params.max_iter = 3_000_000
     s = ep.sim_from_case(c)
     s.set_state(*W.front_state(c), 0)
     sweeps = []
