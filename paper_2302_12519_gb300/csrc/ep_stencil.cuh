@@ -83,8 +83,9 @@ struct Op {
     int cheb;          // Jacobi sweep accelerated by the Chebyshev semi-iteration
     real cheb_w;       // its weight for this sweep
     // correction form, bits: kRestart = first sweep of a cycle (e starts from 0: the output
-    // is tau D^-1 r, and r becomes the cycle's right-hand side, stored over b); kFold = add
+    // is coef D^-1 r, and r becomes the cycle's right-hand side, stored over b); kFold = add
     // the iterate read (the old cycle's e) into x0; kPrev0 = the cycle's previous iterate is 0
+    // (Chebyshev)
     int cform;
     int colour;        // eight-colour sweep: the colour this launch updates
 };
@@ -753,8 +754,6 @@ __device__ __forceinline__ void stencil_item(const Inst<real> &I, int seg_index,
                            &sm.sflag);
 }
 
-// Single instance: one CTA per segment.  The two-term modes keep both terms'
-// vertex state and run two CTAs an SM.
 // Whether the solve of `ctl` is finished, read once for the whole CTA: a capped
 // solve sets its flag while other CTAs of the same launch may be starting, and
 // threads of one CTA that read it at different moments would part ways (in the
@@ -767,6 +766,8 @@ __device__ __forceinline__ bool cta_done(const Ctl *ctl, int *sflag)
     return *sflag != 0;
 }
 
+// Single instance: one CTA per segment.  The two-term modes keep both terms'
+// vertex state and run two CTAs an SM.
 template <typename real, int MODE>
 __global__ void __launch_bounds__(kThreads, kTwoTerm<MODE> ? 2 : kMinBlocks) k_stencil(Inst<real> I, ApplyIO<real> io)
 {
