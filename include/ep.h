@@ -107,9 +107,14 @@ typedef struct {
     int solver;           /* elliptic solve: EP_SOLVER_JACOBI, the damped Jacobi of Eq. dampjac1 (default);
                              EP_SOLVER_CHEBYSHEV, Golub and Varga's Chebyshev semi-iteration on
                              the Jacobi step (no counterpart in the paper, whose future work names
-                             faster solvers; FP32 handles run it in correction form, restarted from
-                             e = 0 on A e = b - A x each time a cycle has cut ||r|| by 1e3, which
-                             keeps the FP32 rounding of x out of the iteration);
+                             faster solvers).  FP32 bidomain handles run both in correction form:
+                             the iterate is x0 + e, e iterated on A e = b - A x0 from e = 0 and
+                             folded into x0 each time a cycle has cut ||r|| by 1e3 (the Chebyshev
+                             polynomial restarts there), which keeps the FP32 rounding of the full
+                             iterate out of the iteration; the stop rule applies to the residual of
+                             x0 + e, and v_e is its FP32 rounding.  It costs a third iterate buffer
+                             (4 bytes a voxel; ep_footprint counts it).  FP64 handles run the plain
+                             iterations;
                              EP_SOLVER_GAUSS_SEIDEL, Gauss-Seidel (SOR with omega = jacobi_omega when
                              0 < jacobi_omega < 2, else omega = 1) over the eight colour classes
                              (i, j, k mod 2): the deterministic form of the paper's in-place Jacobi,
