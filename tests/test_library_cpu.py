@@ -74,6 +74,19 @@ def test_setters_validate_before_any_device_work(lib):
     p.check_every = 0
     with pytest.raises(ep.EPError):
         s.set_params(p)
+    for solver, ok in ((0, True), (1, True), (2, True), (3, False), (-1, False)):   # the three elliptic solves
+        p = W.Params()
+        p.solver = solver
+        if ok:
+            s.set_params(p)
+        else:
+            with pytest.raises(ep.EPError) as e:
+                s.set_params(p)
+            assert e.value.status == ep.EP_EINVAL and "solver" in str(e.value)
+    p = W.Params()
+    p.solver, p.omega = 2, 2.0   # the SOR factor must stay below 2
+    with pytest.raises(ep.EPError):
+        s.set_params(p)
     for _ in range(8):
         s.add_stimulus((0, 0, 0), (1, 1, 1), 0.0, 1.0, 0.5)
     with pytest.raises(ep.EPError):
@@ -154,6 +167,15 @@ def test_footprint_counts_the_interval_estimate(lib):
     extra = (pe - re_) - (pj - rj)
     assert extra >= 8 * 82 + 16 and (extra - 8 * 82) % 16 == 0
     assert rs >= rj - 4 * c.n and ps - rs == pj - rj   # (this mask has more reduction chunks than 8 x items)
+    # on one connected block the eight partial sums per item outgrow the reduction chunks
+    blk = W.random_case(4, 40, 30, 20, model=W.BI, mask=np.ones((20, 30, 40), np.uint8))
+    res = {}
+    for solver in (0, 2):
+        blk.params.solver = solver
+        h = ep.sim_from_case(blk, use_torch=False)
+        res[solver] = h.footprint()[0]
+        h.close()
+    assert res[2] - (res[0] - 4 * blk.n) > 0
     # damped Jacobi with estimated damping runs the same estimate
     c.params.solver, c.params.cheb_lmin, c.params.cheb_lmax, c.params.omega = 0, 0.0, 0.0, -1.0
     s = ep.sim_from_case(c, use_torch=False)
