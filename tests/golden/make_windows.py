@@ -6,8 +6,9 @@ oracle's operator (``tests/spectra.py``).
 
 Each window starts from ``workloads.front_state`` (a front ten voxels above
 the apex) and runs the bidomain step with the elliptic solve by the Chebyshev
-semi-iteration on a fixed interval, to rel_tol 1e-6; the library runs the
-same steps on the same interval in tests/test_gpu_windows.py.
+semi-iteration on a fixed interval, to rel_tol 1e-6; tests/test_gpu_windows.py
+runs the same steps on the library with its damped Jacobi and with the
+Chebyshev semi-iteration on the same interval, to the same tolerance.
   config 1: 60 steps; the interval from the oracle's spectrum of D^-1 A
             (smallest nonzero x 0.8, largest x 1.05);
   config 2: 1 step; the largest eigenvalue by Lanczos (x 1.05) and the
