@@ -314,3 +314,35 @@ def test_config2_fullsize_kernels():
     stats, rr = _fullsize_checks(c, 12)
     assert stats.iters > 0
     assert abs(rr - stats.rel_res) <= 0.05 * stats.rel_res + 1e-5, (rr, stats.rel_res)
+
+
+@pytest.mark.parametrize("solver", [0, 1])
+def test_fp32_correction_form_on_several_components_against_oracle(solver):
+    """FP32 damped Jacobi and Chebyshev (correction form, R22) on a random mask
+    with several face-connected components, each solve from v_e = 0 (a cold
+    start: cycles restart along the way): every step converges, and V_m and
+    V_e agree with the FP64 oracle (V_e to 0.05 mV: both solves stop at the
+    same relative residual, 1e-6, not at the same iterate)."""
+    import spectra
+    c = W.random_case(57, 33, 21, 14, model=W.BI, fill=0.5)
+    c.params.max_iter = 400000
+    g = oracle.Grid.elliptic_from_case(c)
+    assert g.components()[0] > 1
+    if solver == 1:   # an interval from the oracle's operator: Lanczos top, a literal bottom below the spectrum's
+        p = c.params
+        hi = spectra.largest(g, p.sig_iL + p.sig_eL, p.sig_iT + p.sig_eT)
+        c.params.solver, c.params.cheb_lmin, c.params.cheb_lmax = 1, 1e-4, 1.05 * hi
+    s = ep.sim_from_case(c)
+    o = oracle.Sim(c)
+    v, w, _ = W.random_state(57, c)
+    ve = np.zeros(c.n)
+    s.set_state(v, w, ve, 0)
+    o.set_state(v, w, ve, 0)
+    for _ in range(3):
+        assert s.step(1).converged == 1
+        assert o.step() == 0
+    st = o.state()
+    assert np.abs(s.read(ep.EP_VM_MV) - oracle.vm_mV(st["v"])).max() <= 0.5
+    assert np.abs(s.read(ep.EP_VE_MV) - 100.0 * st["ve"]).max() <= 0.05
+    s.close()
+    o.close()
