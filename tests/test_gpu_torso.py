@@ -285,3 +285,23 @@ def test_far_items_single_term_sweep_matches_oracle():
     st = o.state()
     np.testing.assert_allclose(s.read(ep.EP_V), st["v"], rtol=0, atol=1e-10)
     np.testing.assert_allclose(s.read(ep.EP_VE), st["ve"], rtol=0, atol=1e-7)
+
+
+def test_torso_fp32_jacobi_correction_form_against_oracle():
+    """The FP32 damped Jacobi in correction form over tissue + torso (the
+    single-term and two-term launches of one sweep both fold and restart):
+    every step converges, and V_m and V_e agree with the FP64 oracle within the
+    full-run gates (0.5 mV; both solves stop at rel_tol 1e-5)."""
+    c = _heart_in_box(steps=2)
+    c.params.solver, c.params.rel_tol, c.params.max_iter = 0, 1e-5, 400000
+    s = ep.sim_from_case(c)
+    o = oracle.Sim(c)
+    for _ in range(c.steps):
+        assert s.step(1).converged == 1
+        assert o.step() == 0
+    st = o.state()
+    assert np.abs(s.read(ep.EP_VM_MV) - oracle.vm_mV(st["v"])).max() <= 0.5
+    dve = np.abs(s.read(ep.EP_VE_MV) - 100.0 * st["ve"]).max()
+    assert dve <= 0.5, dve
+    s.close()
+    o.close()
